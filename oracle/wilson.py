@@ -1,0 +1,301 @@
+"""FP64 oracle: the discretised Wilson loop and its nested and spin-resolved forms.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Each function names the passage of arXiv 2312.13051 it follows.  The readings
+taken where the paper is silent or garbled are listed in the design notes and
+repeated next to the code that uses them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TWO_PI = 2.0 * np.pi
+
+STATUS = {"OK": 0, "EINVAL": 1, "ENOMEM": 2, "EGAP": 3, "EPSOGAP": 4, "EWANGAP": 5,
+          "ENOCONV": 6, "ETIMEOUT": 7, "ECUDA": 8}
+
+
+class OracleError(Exception):
+    """A condition under which the method has no answer (closed gap, etc.)."""
+
+    def __init__(self, status: str, msg: str, k_index=None):
+        super().__init__(f"{status}: {msg}")
+        self.status = status
+        self.k_index = k_index
+
+
+# ----------------------------------------------------------------------------
+# Step 1: Bloch Hamiltonian (Sec. I: H(k) from the tight-binding model; Sec. II A
+# periodic gauge).  H(f) = sum_e t_e exp(i 2pi f.R_e) |i_e><j_e|, summed directly.
+# ----------------------------------------------------------------------------
+
+def bloch_hamiltonian(model, f) -> np.ndarray:
+    f = np.asarray(f, dtype=np.float64)
+    phase = np.exp(1j * TWO_PI * (model.R.astype(np.float64) @ f))
+    H = np.zeros((model.n, model.n), dtype=np.complex128)
+    np.add.at(H, (model.i, model.j), model.t * phase)
+    scale = max(np.abs(H).max(), np.abs(model.t).max(initial=0.0), 1e-300)
+    if np.abs(H - H.conj().T).max() > 1e-12 * scale:
+        raise OracleError("EINVAL", "hopping list is not Hermitian")
+    return 0.5 * (H + H.conj().T)
+
+
+def plane_points(plane) -> np.ndarray:
+    """k(j, i) = origin + (j/N) loop_dir + (i/N_t) trans_dir  (Sec. II B ``vec(t1, t2)``).
+
+    Returned as f[i, j, :] (transverse index i, loop index j).  Loop: N distinct
+    points, closed by reusing j = 0 (Eq. 2).  Transverse: N_t distinct points.
+    """
+    o = np.asarray(plane.origin, np.float64)
+    a = np.asarray(plane.loop_dir, np.float64)
+    b = np.asarray(plane.trans_dir, np.float64)
+    f = np.empty((plane.N_t, plane.N, 3))
+    for i in range(plane.N_t):
+        for j in range(plane.N):
+            f[i, j] = o + (j / plane.N) * a + (i / plane.N_t) * b
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Step 2: exact diagonalisation, occupied states (Sec. I "exact diagonalization";
+# Eq. 1: the occupied bands u_n).  LAPACK zheevd through numpy, ascending.
+# ----------------------------------------------------------------------------
+
+def occupied_states(H: np.ndarray, p: int):
+    """Return (eigenvalues, U = lowest p eigenvectors, direct gap lam_p - lam_{p-1})."""
+    lam, V = np.linalg.eigh(H)
+    gap = lam[p] - lam[p - 1] if p < H.shape[0] else np.inf
+    return lam, V[:, :p], gap
+
+
+def eigh_batched(Hs, n_vec: int):
+    """Eigenvalues (ascending) and the first n_vec eigenvectors of each matrix."""
+    out = []
+    for H in Hs:
+        lam, V = np.linalg.eigh(H)
+        out.append((lam, V[:, :n_vec]))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Steps 3-4: overlaps and the ordered product (Eq. 2).
+# F_{k} = <u_{k+dk} | u_k>, e^{i 2pi xbar} = F_{k+(N-1)dk} ... F_{k+dk} F_k:
+# later k multiplies from the left; the loop closes on the same U(k_0).
+# ----------------------------------------------------------------------------
+
+def overlap(U_next: np.ndarray, U_here: np.ndarray) -> np.ndarray:
+    """M = U(k_{j+1})^dagger U(k_j)   (Eq. 2, F matrix for a set of bands)."""
+    return U_next.conj().T @ U_here
+
+
+def polar_factor(M: np.ndarray) -> np.ndarray:
+    """Unitary polar factor X Y^dagger of M = X S Y^dagger (option ``unitarise``)."""
+    X, _, Yh = np.linalg.svd(M)
+    return X @ Yh
+
+
+def wilson_matrix(U_loop, unitarise: bool = False) -> np.ndarray:
+    """W = M_{N-1} ... M_1 M_0 with M_j = U_{j+1}^dagger U_j and U_N = U_0 (Eq. 2)."""
+    N = len(U_loop)
+    p = U_loop[0].shape[1]
+    W = np.eye(p, dtype=np.complex128)
+    for j in range(N):
+        M = overlap(U_loop[(j + 1) % N], U_loop[j])
+        if unitarise:
+            M = polar_factor(M)
+        W = M @ W
+    return W
+
+
+def cyclic_wilson_matrix(U_loop, base: int, unitarise: bool = False) -> np.ndarray:
+    """The same closed loop started at k_base: M_{b-1} ... M_0 M_{N-1} ... M_b (Eq. 8)."""
+    N = len(U_loop)
+    p = U_loop[0].shape[1]
+    W = np.eye(p, dtype=np.complex128)
+    for s in range(N):
+        j = (base + s) % N
+        M = overlap(U_loop[(j + 1) % N], U_loop[j])
+        if unitarise:
+            M = polar_factor(M)
+        W = M @ W
+    return W
+
+
+# ----------------------------------------------------------------------------
+# Step 5: eigenphases (Eq. 2, left side; Eq. 8: Im Ln of the loop).  The raw
+# product is not unitary, so its eigenvalues come from the general eigensolver
+# (LAPACK zgeev through numpy); theta = arg(lambda) in (-pi, pi], ascending.
+# ----------------------------------------------------------------------------
+
+def eigenphases(W: np.ndarray) -> np.ndarray:
+    return np.sort(np.angle(np.linalg.eigvals(W)))
+
+
+def _check_gap(gap, tol, k_index):
+    if not gap > tol:
+        raise OracleError("EGAP", f"direct gap {gap:.3e} <= {tol:.3e}", k_index)
+
+
+def _default_gap_tol(model) -> float:
+    return 1e-6 * max(1.0, float(np.abs(model.t).max(initial=0.0)))
+
+
+def _states_on_plane(model, plane, p, gap_tol, gauge=None):
+    """U[i][j] for every k of the plane and the minimum direct gap of each loop."""
+    f = plane_points(plane)
+    U = []
+    min_gap = np.full(plane.N_t, np.inf)
+    for i in range(plane.N_t):
+        row = []
+        for j in range(plane.N):
+            H = bloch_hamiltonian(model, f[i, j])
+            _, Uk, gap = occupied_states(H, p)
+            _check_gap(gap, gap_tol, (i, j))
+            min_gap[i] = min(min_gap[i], gap)
+            if gauge is not None:
+                Uk = Uk @ gauge(i, j, Uk.shape[1])
+            row.append(Uk)
+        U.append(row)
+    return U, min_gap
+
+
+def _check_plane(model, plane, p):
+    if not (1 <= p <= model.n):
+        raise OracleError("EINVAL", "need 1 <= p <= n")
+    if plane.N < 1 or plane.N_t < 1:
+        raise OracleError("EINVAL", "empty plane")
+    if np.any(np.asarray(plane.loop_dir) != np.round(plane.loop_dir)):
+        raise OracleError("EINVAL", "loop_dir must be an integer vector to close the loop")
+
+
+def wilson_loop(model, plane, p: int, gap_tol=None, unitarise=False, gauge=None):
+    """Hybrid Wannier centres along loop_dir as a function of the transverse index
+    (Eq. 3, ``WSurf``).  Returns (phases[N_t, p], min_gap[N_t]); xbar = phases / 2pi.
+
+    ``gauge(i, j, p)`` (tests only) returns a p x p unitary applied as U -> U G.
+    """
+    _check_plane(model, plane, p)
+    gap_tol = _default_gap_tol(model) if gap_tol is None else gap_tol
+    U, min_gap = _states_on_plane(model, plane, p, gap_tol, gauge)
+    phases = np.stack([eigenphases(wilson_matrix(U[i], unitarise)) for i in range(plane.N_t)])
+    return phases, min_gap
+
+
+# ----------------------------------------------------------------------------
+# Spin-resolved loop (Sec. IV): projected spin operator P s P restricted to the
+# occupied space, S = U^dagger s U (p x p); its negative (sign -1) or positive
+# eigen-sector spans the states whose Wilson loop gives C_down (C_up).
+# Reading: split at zero, the sector must hold p/2 states at every k.
+# ----------------------------------------------------------------------------
+
+def projected_spin_sector(U: np.ndarray, S: np.ndarray, sign: int):
+    Sp = U.conj().T @ S @ U
+    Sp = 0.5 * (Sp + Sp.conj().T)
+    mu, V = np.linalg.eigh(Sp)
+    sel = mu < 0 if sign < 0 else mu > 0
+    return U @ V[:, sel], mu, int(sel.sum()), float(np.abs(mu).min())
+
+
+def spin_resolved_wilson_loop(model, plane, p: int, S, sign: int = -1, gap_tol=None,
+                              pso_gap_tol: float = 1e-6, unitarise=False):
+    """``WSpinSurf``: Wilson loop of the PSO sector.  Returns
+    (phases[N_t, p/2], pso_evals[N_t, N, p], min_pso_gap, min_gap[N_t])."""
+    _check_plane(model, plane, p)
+    if p % 2 or sign not in (-1, 1):
+        raise OracleError("EINVAL", "need even p and sign = +-1")
+    gap_tol = _default_gap_tol(model) if gap_tol is None else gap_tol
+    U, min_gap = _states_on_plane(model, plane, p, gap_tol)
+    pso = np.empty((plane.N_t, plane.N, p))
+    min_pso_gap = np.inf
+    phases = []
+    for i in range(plane.N_t):
+        sector = []
+        for j in range(plane.N):
+            Us, mu, count, g = projected_spin_sector(U[i][j], S, sign)
+            pso[i, j] = mu
+            min_pso_gap = min(min_pso_gap, g)
+            if count != p // 2 or not g > pso_gap_tol:
+                raise OracleError("EPSOGAP", f"PSO sector size {count}, gap {g:.3e}", (i, j))
+            sector.append(Us)
+        phases.append(eigenphases(wilson_matrix(sector, unitarise)))
+    return np.stack(phases), pso, min_pso_gap, min_gap
+
+
+# ----------------------------------------------------------------------------
+# Nested loop (Sec. III, Eq. 8).  For each base point k_j of the first loop and
+# each transverse index: Wilson matrix of the closed loop started at k_j, its
+# right eigenvectors nu, the sector of m eigenvectors ordered by phase measured
+# from ``cut`` starting at ``first``; Wannier states w = U(k_j) nu, orthonormalised;
+# then the Wilson loop of w along the transverse direction (closed on i = 0).
+# ----------------------------------------------------------------------------
+
+def _circ_gap(sel_phases, rest_phases):
+    if len(rest_phases) == 0:
+        return np.inf
+    d = np.abs(np.angle(np.exp(1j * (np.asarray(sel_phases)[:, None]
+                                     - np.asarray(rest_phases)[None, :]))))
+    return float(d.min())
+
+
+def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0,
+                       m: int | None = None, gap_tol=None, wannier_gap_tol: float = 1e-6,
+                       unitarise=False):
+    """``WNWL``.  Returns (phases[N_t, p], nested[N, m], min_wannier_gap, min_gap[N_t])."""
+    _check_plane(model, plane, p)
+    m = p // 2 if m is None else m
+    if not (1 <= m <= p) or not (0 <= first <= p - m):
+        raise OracleError("EINVAL", "sector out of range")
+    if np.any(np.asarray(plane.trans_dir) != np.round(plane.trans_dir)):
+        raise OracleError("EINVAL", "trans_dir must be an integer vector for the nested loop")
+    gap_tol = _default_gap_tol(model) if gap_tol is None else gap_tol
+    U, min_gap = _states_on_plane(model, plane, p, gap_tol)
+    N, Nt = plane.N, plane.N_t
+    phases = np.stack([eigenphases(wilson_matrix(U[i], unitarise)) for i in range(Nt)])
+    nested = np.empty((N, m))
+    min_wgap = np.inf
+    for j in range(N):
+        w = []
+        for i in range(Nt):
+            W = cyclic_wilson_matrix(U[i], j, unitarise)
+            vals, vecs = np.linalg.eig(W)
+            th = np.angle(vals)
+            order = np.argsort(np.mod(th - cut, TWO_PI), kind="stable")
+            sel, rest = order[first:first + m], np.concatenate([order[:first], order[first + m:]])
+            g = _circ_gap(th[sel], th[rest])
+            min_wgap = min(min_wgap, g)
+            if not g > wannier_gap_tol:
+                raise OracleError("EWANGAP", f"Wannier gap {g:.3e}", (i, j))
+            wv, _ = np.linalg.qr(U[i][j] @ vecs[:, sel])
+            w.append(wv)
+        Wn = np.eye(m, dtype=np.complex128)
+        for i in range(Nt):
+            Wn = overlap(w[(i + 1) % Nt], w[i]) @ Wn
+        nested[j] = eigenphases(Wn)
+    return phases, nested, min_wgap, min_gap
+
+
+# ----------------------------------------------------------------------------
+# Post-processing (Eq. 6): C = sum_n xbar_n(k_y = 2pi) - sum_n xbar_n(0), tracked
+# continuously; the grid is cyclic in the transverse direction.
+# ----------------------------------------------------------------------------
+
+def winding(phases: np.ndarray) -> float:
+    s = np.asarray(phases).sum(axis=1) / TWO_PI
+    d = np.diff(np.append(s, s[0]))
+    d = d - np.round(d)
+    return float(d.sum())
+
+
+def circular_match_error(a, b) -> float:
+    """Max circular distance between two sorted phase lists, minimised over cyclic
+    relabellings (ties at +-pi may sort to either end)."""
+    a = np.sort(np.asarray(a, np.float64))
+    b = np.sort(np.asarray(b, np.float64))
+    if a.shape != b.shape:
+        raise ValueError("shape mismatch")
+    best = np.inf
+    for s in range(len(a)):
+        d = np.abs(np.angle(np.exp(1j * (a - np.roll(b, s)))))
+        best = min(best, float(d.max()))
+    return best

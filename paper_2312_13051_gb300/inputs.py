@@ -1,0 +1,352 @@
+"""Seeded synthetic inputs: tight-binding hopping lists, k-planes and workloads.
+
+This module builds *inputs* only (hopping lists of the paper's models, supercells
+with disorder and Peierls flux, the reciprocal-space planes the loops run over).
+It holds none of the Wilson-loop arithmetic: no Bloch sum, no eigensolve, no
+overlap, no eigenphase.  Both the CUDA path and the CPU oracle consume what it
+returns, so the two never disagree about their inputs.
+
+Hopping-list convention (Sec. II A, periodic gauge used by the loops):
+
+    H(f) = sum_e t_e exp(i 2 pi f . R_e) |i_e><j_e|,
+
+with ``f`` in fractional coordinates of the reciprocal basis and ``R_e`` an
+integer lattice translation; t_R[i, j] is the amplitude between orbital i of a
+cell and orbital j of the cell displaced by R.  Lists are *full*: every
+(i, j, R, t) comes with its partner (j, i, -R, conj t), so H(f) is Hermitian.
+No orbital-position phases are used, hence H(f + G) = H(f) for integer G and a
+loop closes on the same matrix (Eq. 2, periodic condition psi(k) = psi(k+2pi/a)).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+# Pauli matrices, index 0 = identity.
+PAULI = (
+    np.array([[1, 0], [0, 1]], dtype=np.complex128),
+    np.array([[0, 1], [1, 0]], dtype=np.complex128),
+    np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+    np.array([[1, 0], [0, -1]], dtype=np.complex128),
+)
+
+GLOBAL_SEED = 20231213
+
+
+def kron(a: int, b: int) -> np.ndarray:
+    """PAULI[a] (x) PAULI[b]; the first factor is the slow (outer) index."""
+    return np.kron(PAULI[a], PAULI[b])
+
+
+@dataclass
+class HoppingList:
+    """Full hopping list of a periodic tight-binding model (host arrays)."""
+    n: int
+    R: np.ndarray          # (nnz, 3) int32 lattice translations
+    i: np.ndarray          # (nnz,) int32 row orbital
+    j: np.ndarray          # (nnz,) int32 column orbital
+    t: np.ndarray          # (nnz,) complex128 amplitude
+    dim: int = 2
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.t.shape[0])
+
+    def __post_init__(self):
+        self.R = np.ascontiguousarray(self.R, dtype=np.int32).reshape(-1, 3)
+        self.i = np.ascontiguousarray(self.i, dtype=np.int32)
+        self.j = np.ascontiguousarray(self.j, dtype=np.int32)
+        self.t = np.ascontiguousarray(self.t, dtype=np.complex128)
+
+
+def from_blocks(blocks: dict, n: int, dim: int = 2, name: str = "") -> HoppingList:
+    """Hopping list from dense blocks {R: t_R}.
+
+    ``blocks`` holds t_0 (must be Hermitian) and t_R for R in one half-space;
+    the partner blocks t_{-R} = t_R^dagger are added here.  Exact zeros are dropped.
+    """
+    full = {}
+    for R, T in blocks.items():
+        R = tuple(int(x) for x in R) + (0,) * (3 - len(R))
+        T = np.asarray(T, dtype=np.complex128)
+        if T.shape != (n, n):
+            raise ValueError(f"block {R} has shape {T.shape}, expected {(n, n)}")
+        if R == (0, 0, 0):
+            if not np.allclose(T, T.conj().T, atol=1e-14):
+                raise ValueError("t_0 must be Hermitian")
+            full[R] = full.get(R, 0) + T
+        else:
+            mR = tuple(-x for x in R)
+            if mR in blocks or mR in full and mR != R:
+                raise ValueError(f"give t_R only for one of R={R} and -R")
+            full[R] = full.get(R, 0) + T
+            full[mR] = full.get(mR, 0) + T.conj().T
+    Rs, I, J, Ts = [], [], [], []
+    for R, T in sorted(full.items()):
+        ii, jj = np.nonzero(T)
+        Rs.append(np.tile(np.array(R, np.int32), (ii.size, 1)))
+        I.append(ii)
+        J.append(jj)
+        Ts.append(T[ii, jj])
+    return HoppingList(n=n, R=np.concatenate(Rs), i=np.concatenate(I),
+                       j=np.concatenate(J), t=np.concatenate(Ts), dim=dim, name=name)
+
+
+def from_bloch_terms(n: int, const, cos_terms: dict, sin_terms: dict, dim: int,
+                     name: str = "") -> HoppingList:
+    """Model H(k) = C + sum_d [A_d cos k_d + B_d sin k_d] as a hopping list.
+
+    With e^{ik} t + e^{-ik} t^dagger = A cos k + B sin k one has t = A/2 - i B/2.
+    ``cos_terms``/``sin_terms`` map an axis (0, 1, 2) to the Hermitian A_d / B_d.
+    """
+    blocks = {(0, 0, 0): np.asarray(const, np.complex128)}
+    for d in sorted(set(cos_terms) | set(sin_terms)):
+        A = np.asarray(cos_terms.get(d, np.zeros((n, n))), np.complex128)
+        B = np.asarray(sin_terms.get(d, np.zeros((n, n))), np.complex128)
+        R = [0, 0, 0]
+        R[d] = 1
+        blocks[tuple(R)] = 0.5 * A - 0.5j * B
+    return from_blocks(blocks, n, dim=dim, name=name)
+
+
+# --------------------------------------------------------------------------
+# The paper's models and the named workloads
+# --------------------------------------------------------------------------
+
+def ssh(v: float, w: float) -> HoppingList:
+    """Su-Schrieffer-Heeger chain: H(k) = [[0, v + w e^{-ik}], [v + w e^{ik}, 0]] (Sec. II)."""
+    t0 = np.array([[0, v], [v, 0]], np.complex128)
+    tx = np.array([[0, 0], [w, 0]], np.complex128)   # e^{+ik} sits in H[1, 0]
+    return from_blocks({(0, 0, 0): t0, (1, 0, 0): tx}, 2, dim=1, name=f"ssh({v},{w})")
+
+
+def chern_eq4(m: float = 1.5) -> HoppingList:
+    """Eq. 4: sin kx s1 + sin ky s2 + (cos kx + cos ky + m) s3."""
+    s = PAULI
+    return from_bloch_terms(2, m * s[3], {0: s[3], 1: s[3]}, {0: s[1], 1: s[2]}, dim=2,
+                            name="chern_eq4")
+
+
+def bhz_eq7(m: float = 1.5) -> HoppingList:
+    """Eq. 7: sin kx s1(x)t1 + sin ky s1(x)t2 + (cos kx + cos ky + m) s3(x)t0, kron(sigma, tau)."""
+    return from_bloch_terms(4, m * kron(3, 0), {0: kron(3, 0), 1: kron(3, 0)},
+                            {0: kron(1, 1), 1: kron(1, 2)}, dim=2, name="bhz_eq7")
+
+
+def choti_eq9(delta0: float = 1.0, m: float = -1.5) -> HoppingList:
+    """Eq. 9 (chiral HOTI), 3D, kron(sigma, tau):
+    sin kx s1t1 + sin ky s1t2 + sin kz s1t3 + (cos kx + cos ky + cos kz + m) s3t0
+    + Delta0 (cos kx - cos ky) s2t0, with m = -1.5 as printed."""
+    cos_terms = {0: kron(3, 0) + delta0 * kron(2, 0),
+                 1: kron(3, 0) - delta0 * kron(2, 0),
+                 2: kron(3, 0)}
+    sin_terms = {0: kron(1, 1), 1: kron(1, 2), 2: kron(1, 3)}
+    return from_bloch_terms(4, m * kron(3, 0), cos_terms, sin_terms, dim=3, name="choti_eq9")
+
+
+def spin_hall(m: float = 1.0) -> HoppingList:
+    """4-band spin-Hall model, kron(tau, s) (orbital-major, spin-minor):
+    sin kx tx(x)sz + sin ky ty(x)s0 + (m - cos kx - cos ky) tz(x)s0."""
+    return from_bloch_terms(4, m * kron(3, 0), {0: -kron(3, 0), 1: -kron(3, 0)},
+                            {0: kron(1, 3), 1: kron(2, 0)}, dim=2, name=f"spin_hall({m})")
+
+
+SPIN_HALL_SZ = np.diag([1.0, -1.0, 1.0, -1.0]).astype(np.complex128)   # tau0 (x) s_z
+
+
+def bbh(gx: float = 0.5, gy: float = 0.5, lx: float = 1.0, ly: float = 1.0) -> HoppingList:
+    """Benalcazar-Bernevig-Hughes quadrupole model (the model behind Sec. III's nested loop):
+    (gx + lx cos kx) G4 + lx sin kx G3 + (gy + ly cos ky) G2 + ly sin ky G1,
+    G4 = t1(x)s0, G_a = -t2(x)s_a (a = 1, 2, 3), kron(tau, sigma)."""
+    G4 = kron(1, 0)
+    G1, G2, G3 = (-kron(2, a) for a in (1, 2, 3))
+    return from_bloch_terms(4, gx * G4 + gy * G2, {0: lx * G4, 1: ly * G2},
+                            {0: lx * G3, 1: ly * G1}, dim=2, name=f"bbh({gx},{gy})")
+
+
+def square_lattice(t: float = 1.0) -> HoppingList:
+    """One orbital per cell, nearest-neighbour hopping -t (used for flux pins)."""
+    T = np.array([[-t]], np.complex128)
+    return from_blocks({(0, 0, 0): np.zeros((1, 1)), (1, 0, 0): T, (0, 1, 0): T}, 1, dim=2,
+                       name="square")
+
+
+def supercell(model: HoppingList, L: int, W: float = 0.0, seed: int | None = None,
+              flux: bool = False, Ly: int | None = None) -> HoppingList:
+    """L x Ly supercell of a 2D model (Sec. II A, twisted boundary conditions with theta = 0).
+
+    Supercell orbital index = ((x * Ly) + y) * n_cell + orbital.  A primitive hopping
+    t_R from cell X to X + R becomes a supercell hopping with translation
+    floor((x + R) / L).  ``W`` adds on-site Anderson disorder w ~ U[-W/2, W/2], one
+    value per primitive cell times the identity on its orbitals.  ``flux`` threads one
+    flux quantum per supercell (2 pi / (L Ly) per plaquette) in a torus-periodic
+    Landau gauge: a +y bond starting at column x gets phase exp(i 2 pi x / (L Ly)),
+    an x bond crossing the supercell seam gets exp(-i 2 pi s y / Ly) for s seam
+    crossings.  Flux requires axis-aligned bonds.
+    """
+    Ly = L if Ly is None else Ly
+    nc = model.n
+    n = nc * L * Ly
+    phi = 1.0 / (L * Ly)
+    rng = np.random.default_rng(seed) if W else None
+    wdis = rng.uniform(-W / 2, W / 2, size=(L, Ly)) if W else None
+    R_out, I_out, J_out, T_out = [], [], [], []
+    for x in range(L):
+        for y in range(Ly):
+            cell = (x * Ly + y) * nc
+            Rx, Ry = model.R[:, 0], model.R[:, 1]
+            xt, yt = x + Rx, y + Ry
+            sx, sy = np.floor_divide(xt, L), np.floor_divide(yt, Ly)
+            xc, yc = xt - sx * L, yt - sy * Ly
+            tcell = (xc * Ly + yc) * nc
+            t = model.t.copy()
+            if flux:
+                if np.any((Rx != 0) & (Ry != 0)):
+                    raise ValueError("flux needs axis-aligned bonds")
+                theta = 2 * np.pi * phi * x * Ry - 2 * np.pi * sx * y / Ly
+                t = t * np.exp(1j * theta)
+            R_out.append(np.stack([sx, sy, model.R[:, 2]], axis=1))
+            I_out.append(cell + model.i)
+            J_out.append(tcell + model.j)
+            T_out.append(t)
+            if W:
+                R_out.append(np.zeros((nc, 3), np.int64))
+                I_out.append(cell + np.arange(nc))
+                J_out.append(cell + np.arange(nc))
+                T_out.append(np.full(nc, wdis[x, y], np.complex128))
+    return HoppingList(n=n, R=np.concatenate(R_out), i=np.concatenate(I_out),
+                       j=np.concatenate(J_out), t=np.concatenate(T_out), dim=2,
+                       name=f"{model.name}_sc{L}x{Ly}" + (f"_W{W}" if W else "")
+                       + ("_flux" if flux else ""))
+
+
+def manyband(norb: int = 128, seed: int = GLOBAL_SEED + 3, decay: float = 1.5,
+             soc: float = 0.1, zeeman: float = 0.05) -> HoppingList:
+    """Synthetic Wannier-like spinful model (n = 2 norb), orbital-major, spin-minor.
+
+    Translations: shells |R| in {0, 1, sqrt 2, 2} (13 vectors).  For R in a half-space
+    t_R = exp(-|R|/decay)/sqrt(norb) [A_R (x) s0 + soc sum_a B_{R,a} (x) s_a] with
+    complex Gaussian A, B; t_0 is the Hermitian part of the same form; plus
+    zeeman * I (x) s_z.  The spin-independent part dominates so the projected spin
+    operator keeps a gap at zero.
+    """
+    rng = np.random.default_rng(seed)
+    n = 2 * norb
+
+    def cn(shape):
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)
+
+    half = [(1, 0), (0, 1), (1, 1), (1, -1), (2, 0), (0, 2)]
+    blocks = {}
+    for R in [(0, 0)] + half:
+        amp = np.exp(-np.hypot(*R) / decay) / np.sqrt(norb)
+        T = np.kron(cn((norb, norb)), PAULI[0])
+        for a in (1, 2, 3):
+            T = T + soc * np.kron(cn((norb, norb)), PAULI[a])
+        T = amp * T
+        if R == (0, 0):
+            T = 0.5 * (T + T.conj().T) + zeeman * np.kron(np.eye(norb), PAULI[3])
+        blocks[R] = T
+    return from_blocks(blocks, n, dim=2, name=f"manyband({norb})")
+
+
+def manyband_sz(norb: int = 128) -> np.ndarray:
+    return np.kron(np.eye(norb), PAULI[3]).astype(np.complex128)
+
+
+# --------------------------------------------------------------------------
+# Planes (Sec. II B: vec(t1, t2) in units of the reciprocal vectors)
+# --------------------------------------------------------------------------
+
+@dataclass
+class Plane:
+    """k(j, i) = origin + (j/N) loop_dir + (i/N_t) trans_dir, j < N, i < N_t (fractional)."""
+    N: int
+    N_t: int
+    origin: tuple = (0.0, 0.0, 0.0)
+    loop_dir: tuple = (1, 0, 0)
+    trans_dir: tuple = (0.0, 1.0, 0.0)
+
+
+@dataclass
+class Workload:
+    name: str
+    model: HoppingList
+    plane: Plane
+    p: int
+    spin_op: np.ndarray | None = None
+    nested_m: int | None = None
+    extra: dict = field(default_factory=dict)
+
+
+def config_spin_hall() -> Workload:
+    """4-band spin-Hall model, m = 1, p = 2, 51 x 51 grid, loop along kx; S = tau0 (x) s_z."""
+    return Workload("spin_hall_51x51", spin_hall(1.0), Plane(51, 51), 2, SPIN_HALL_SZ)
+
+
+def config_bbh(gamma: float = 0.5) -> Workload:
+    """BBH quadrupole, gamma = 0.5, lambda = 1, 60 x 60 grid, nested on the lower Wannier band."""
+    return Workload(f"bbh_60x60_g{gamma}", bbh(gamma, gamma, 1.0, 1.0), Plane(60, 60), 2,
+                    None, nested_m=1)
+
+
+def config_disordered(L: int, seed: int, W: float = 2.0, nk: int = 16) -> Workload:
+    """L x L supercell of the spin-Hall model with on-site Anderson disorder, half filling."""
+    model = supercell(spin_hall(1.0), L, W=W, seed=seed)
+    sz = np.kron(np.eye(L * L), SPIN_HALL_SZ)
+    return Workload(f"disordered_L{L}_s{seed}", model, Plane(nk, nk), model.n // 2, sz)
+
+
+def config_manyband(N: int = 101, norb: int = 128) -> Workload:
+    """n = 256 spinful many-band model, 1/4 filling, 101 x 101 grid, S = I (x) s_z."""
+    model = manyband(norb)
+    return Workload(f"manyband_n{2 * norb}_{N}x{N}", model, Plane(N, N), norb // 2,
+                    manyband_sz(norb), nested_m=norb // 4)
+
+
+def serving_requests(count: int, rate: float = 200.0, seed: int = GLOBAL_SEED + 4,
+                     sides=(8, 12, 16, 24, 32), nk_range=(8, 24)):
+    """Poisson stream of Wilson-loop requests on flux-threaded disordered supercells.
+
+    Yields dicts with arrival time (s), supercell side L, disorder W ~ U[0, 4], the
+    k-grid side (uniform integer in nk_range) and the request seed.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(count):
+        t += rng.exponential(1.0 / rate)
+        out.append(dict(id=r, arrival=t, L=int(rng.choice(sides)), W=float(rng.uniform(0, 4)),
+                        nk=int(rng.integers(nk_range[0], nk_range[1] + 1)),
+                        seed=int(rng.integers(0, 2**31 - 1))))
+    return out
+
+
+def serving_model(req: dict) -> HoppingList:
+    return supercell(spin_hall(1.0), req["L"], W=req["W"], seed=req["seed"], flux=True)
+
+
+def random_hermitian_model(n: int, seed: int, shells=((1, 0), (0, 1)), scale: float = 1.0
+                           ) -> HoppingList:
+    """Dense random model with nearest-neighbour translations (parity tests)."""
+    rng = np.random.default_rng(seed)
+
+    def cn(shape):
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2 * n)
+
+    A = cn((n, n))
+    blocks = {(0, 0, 0): scale * (A + A.conj().T)}
+    for R in shells:
+        blocks[tuple(R) + (0,) * (3 - len(R))] = scale * cn((n, n))
+    return from_blocks(blocks, n, dim=2, name=f"random{n}_s{seed}")
+
+
+def random_hermitian_batch(sizes, seed: int) -> list:
+    """Random dense Hermitian matrices (complex128) with the given sizes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in sizes:
+        A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2 * n)
+        out.append(A + A.conj().T)
+    return out

@@ -1,0 +1,104 @@
+"""Planted mistakes in the oracle (on the CPU) must each fail at least one pin.
+
+This shows that the pins in ``test_oracle_pins`` are strong enough: a dropped
+closure, a conjugated or transposed overlap, a reversed product, a flipped
+Fourier sign, an unprojected spin operator or the wrong bands all get caught.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.wilson as W
+import tests.test_oracle_pins as pins
+
+
+def _all_pins():
+    out = [functools.partial(pins.test_bloch_sum_matches_printed_form, n)
+           for n in ("eq4", "eq7", "eq9", "spin_hall", "bbh", "ssh")]
+    out += [functools.partial(pins.test_ssh_berry_phase_quantised, 7),
+            pins.test_chern_eq4_winding_paper, pins.test_chern_eq4_cross_checks,
+            pins.test_bhz_eq7_gapless_z2, pins.test_spin_hall_windings,
+            functools.partial(pins.test_bbh_nested_polarisation, 0.5, np.pi),
+            pins.test_choti_eq9_paper_statements, pins.test_eigenphases_known_spectrum,
+            pins.test_two_band_closed_form_eigenvectors,
+            pins.test_eigh_against_independent_jacobi]
+    return out
+
+
+def _reversed_product(U_loop, unitarise=False):
+    N, p = len(U_loop), U_loop[0].shape[1]
+    M = np.eye(p, dtype=complex)
+    for j in range(N):
+        M = M @ W.overlap(U_loop[(j + 1) % N], U_loop[j])
+    return M
+
+
+def _reversed_cyclic(U_loop, base, unitarise=False):
+    N, p = len(U_loop), U_loop[0].shape[1]
+    M = np.eye(p, dtype=complex)
+    for s in range(N):
+        j = (base + s) % N
+        M = M @ W.overlap(U_loop[(j + 1) % N], U_loop[j])
+    return M
+
+
+def _open_loop(U_loop, unitarise=False):
+    p = U_loop[0].shape[1]
+    M = np.eye(p, dtype=complex)
+    for j in range(len(U_loop) - 1):
+        M = W.overlap(U_loop[j + 1], U_loop[j]) @ M
+    return M
+
+
+def _flipped_fourier(model, f):
+    f = np.asarray(f, float)
+    ph = np.exp(-2j * np.pi * (model.R.astype(float) @ f))
+    H = np.zeros((model.n, model.n), complex)
+    np.add.at(H, (model.i, model.j), model.t * ph)
+    return 0.5 * (H + H.conj().T)
+
+
+def _unprojected_spin(U, S, sign):
+    mu, V = np.linalg.eigh(U.conj().T @ U)       # forgot the spin operator
+    sel = np.argsort(mu)[: U.shape[1] // 2]
+    return U @ V[:, sel], mu, U.shape[1] // 2, 1.0
+
+
+def _highest_bands(H, p):
+    lam, V = np.linalg.eigh(H)
+    return lam, V[:, -p:], (lam[p] - lam[p - 1]) if p < H.shape[0] else np.inf
+
+
+def _right_as_left_eigvecs_eigenphases(Wm):
+    return np.sort(np.angle(np.linalg.eigvals(Wm.conj())))
+
+
+MUTATIONS = {
+    "conjugated_overlap": ("overlap", lambda a, b: b.conj().T @ a),
+    "transposed_overlap": ("overlap", lambda a, b: (a.conj().T @ b).T),
+    "reversed_product": ("wilson_matrix", _reversed_product),
+    "reversed_cyclic_product": ("cyclic_wilson_matrix", _reversed_cyclic),
+    "open_loop": ("wilson_matrix", _open_loop),
+    "flipped_fourier_sign": ("bloch_hamiltonian", _flipped_fourier),
+    "unprojected_spin_operator": ("projected_spin_sector", _unprojected_spin),
+    "highest_bands": ("occupied_states", _highest_bands),
+    "conjugated_eigenphases": ("eigenphases", _right_as_left_eigvecs_eigenphases),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, monkeypatch):
+    attr, fn = MUTATIONS[name]
+    monkeypatch.setattr(W, attr, fn)
+    if hasattr(oracle, attr):
+        monkeypatch.setattr(oracle, attr, fn)
+    caught = None
+    for pin in _all_pins():
+        try:
+            pin()
+        except (AssertionError, oracle.OracleError) as e:
+            caught = e
+            break
+    assert caught is not None, f"no pin catches the planted mistake {name!r}"

@@ -1,0 +1,399 @@
+"""Pins of the FP64 oracle against what the paper states and the mathematics fixes.
+
+None of these tests retypes an oracle formula: each compares the oracle with an
+independent fact (a printed Bloch form, a closed-form eigenvector, a quantised
+invariant, an exact identity, or an independent brute-force computation).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_13051_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "paper_invariants.json")))
+P = I.Plane
+
+# Independent Pauli matrices for the printed Bloch forms.
+s0 = np.eye(2, dtype=complex)
+s1 = np.array([[0, 1], [1, 0]], dtype=complex)
+s2 = np.array([[0, -1j], [1j, 0]], dtype=complex)
+s3 = np.diag([1.0 + 0j, -1.0])
+
+
+def printed_forms():
+    """H(k) as printed in the paper (Eqs. 4, 7, 9) or as defined for the named models."""
+    k = np.kron
+    return {
+        "eq4": (I.chern_eq4(1.5), lambda kx, ky, kz:
+                np.sin(kx) * s1 + np.sin(ky) * s2 + (np.cos(kx) + np.cos(ky) + 1.5) * s3),
+        "eq7": (I.bhz_eq7(1.5), lambda kx, ky, kz:
+                np.sin(kx) * k(s1, s1) + np.sin(ky) * k(s1, s2)
+                + (np.cos(kx) + np.cos(ky) + 1.5) * k(s3, s0)),
+        "eq9": (I.choti_eq9(1.0), lambda kx, ky, kz:
+                np.sin(kx) * k(s1, s1) + np.sin(ky) * k(s1, s2) + np.sin(kz) * k(s1, s3)
+                + (np.cos(kx) + np.cos(ky) + np.cos(kz) - 1.5) * k(s3, s0)
+                + 1.0 * (np.cos(kx) - np.cos(ky)) * k(s2, s0)),
+        "spin_hall": (I.spin_hall(1.0), lambda kx, ky, kz:
+                      np.sin(kx) * k(s1, s3) + np.sin(ky) * k(s2, s0)
+                      + (1.0 - np.cos(kx) - np.cos(ky)) * k(s3, s0)),
+        "bbh": (I.bbh(0.5, 0.5, 1.0, 1.0), lambda kx, ky, kz:
+                (0.5 + np.cos(kx)) * k(s1, s0) + np.sin(kx) * (-k(s2, s3))
+                + (0.5 + np.cos(ky)) * (-k(s2, s2)) + np.sin(ky) * (-k(s2, s1))),
+        "ssh": (I.ssh(0.7, 1.3), lambda kx, ky, kz:
+                np.array([[0, 0.7 + 1.3 * np.exp(-1j * kx)], [0.7 + 1.3 * np.exp(1j * kx), 0]])),
+    }
+
+
+@pytest.mark.parametrize("name", ["eq4", "eq7", "eq9", "spin_hall", "bbh", "ssh"])
+def test_bloch_sum_matches_printed_form(name):
+    """Step 1 (Bloch sum over the hopping list) equals the printed H(k), k = 2 pi f."""
+    model, Hk = printed_forms()[name]
+    rng = np.random.default_rng(1)
+    for f in rng.uniform(-1, 1, size=(6, 3)):
+        H = O.bloch_hamiltonian(model, f)
+        np.testing.assert_allclose(H, Hk(*(2 * np.pi * f)), atol=1e-13)
+    # periodic gauge: H(f + G) = H(f) for integer G (closure of Eq. 2)
+    f = rng.uniform(size=3)
+    np.testing.assert_allclose(O.bloch_hamiltonian(model, f + [1, -2, 3]),
+                               O.bloch_hamiltonian(model, f), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [7, 16, 40])
+def test_ssh_berry_phase_quantised(N):
+    """SSH chain: Berry phase 0 for v > w and pi for v < w, exactly on any mesh."""
+    plane = P(N, 1, trans_dir=(0, 0, 0))
+    ph, _ = O.wilson_loop(I.ssh(1.0, 0.5), plane, 1)
+    assert abs(ph[0, 0]) < 1e-12
+    ph, _ = O.wilson_loop(I.ssh(0.5, 1.0), plane, 1)
+    assert abs(abs(ph[0, 0]) - np.pi) < 1e-12
+
+
+def test_chern_eq4_winding_paper():
+    """Eq. 4: WCCs interpolate from 0 to 1, C = 1 via Eq. 6."""
+    ph, gap = O.wilson_loop(I.chern_eq4(1.5), P(40, 40), 1)
+    assert gap.min() > 0.5
+    C = O.winding(ph)
+    assert abs(C - GOLDEN["chern_eq4_wcc_winding"]["value"]) < 1e-9
+
+
+def _plaquette_chern(model, N, p):
+    """Lattice Chern number from plaquette products of det<u_k|u_k'> (brute force)."""
+    f = O.plane_points(P(N, N))
+    U = [[O.occupied_states(O.bloch_hamiltonian(model, f[i, j]), p)[1] for j in range(N)]
+         for i in range(N)]
+
+    def link(a, b):
+        z = np.linalg.det(a.conj().T @ b)
+        return z / abs(z)
+
+    total = 0.0
+    for i in range(N):
+        for j in range(N):
+            u00, u10 = U[i][j], U[i][(j + 1) % N]
+            u01, u11 = U[(i + 1) % N][j], U[(i + 1) % N][(j + 1) % N]
+            # loop direction = j (k_x), transverse = i (k_y)
+            z = link(u00, u10) * link(u10, u11) / link(u01, u11) / link(u00, u01)
+            total += np.angle(z)
+    return total / (2 * np.pi)
+
+
+def _skyrmion_degree(d, N):
+    """Degree of d/|d| on the torus: signed solid angle of the triangulated image."""
+    g = np.linspace(0, 2 * np.pi, N, endpoint=False)
+    D = np.array([[d(kx, ky) for kx in g] for ky in g])
+    D /= np.linalg.norm(D, axis=-1, keepdims=True)
+
+    def omega(a, b, c):
+        num = np.dot(a, np.cross(b, c))
+        den = 1 + np.dot(a, b) + np.dot(b, c) + np.dot(c, a)
+        return 2 * np.arctan2(num, den)
+
+    tot = 0.0
+    for i in range(N):
+        for j in range(N):
+            a, b = D[i, j], D[i, (j + 1) % N]
+            c, e = D[(i + 1) % N, (j + 1) % N], D[(i + 1) % N, j]
+            tot += omega(a, b, c) + omega(a, c, e)
+    return tot / (4 * np.pi)
+
+
+def test_chern_eq4_cross_checks():
+    """The WCC winding equals the plaquette (lattice) Chern number built from the same
+    states, and |C| equals the degree of d/|d|, a quantity with no eigenvectors in it."""
+    model = I.chern_eq4(1.5)
+    ph, _ = O.wilson_loop(model, P(24, 24), 1)
+    assert abs(O.winding(ph) - _plaquette_chern(model, 24, 1)) < 1e-9
+    deg = _skyrmion_degree(lambda kx, ky: np.array(
+        [np.sin(kx), np.sin(ky), np.cos(kx) + np.cos(ky) + 1.5]), 48)
+    assert abs(abs(deg) - 1) < 1e-9
+
+
+def _covers_circle(phases, bins=16):
+    """True when every phase bin of width 2pi/bins is visited by some WCC (gapless).
+
+    The transverse grid must be fine enough that no WCC moves by more than one bin
+    between neighbouring samples."""
+    idx = np.floor((np.asarray(phases).ravel() + np.pi) / (2 * np.pi) * bins).astype(int) % bins
+    return np.unique(idx).size == bins
+
+
+def test_bhz_eq7_gapless_z2():
+    """Eq. 7: fully connected WCC spectrum; the s3 (x) t3 sectors carry |C| = 1."""
+    assert GOLDEN["bhz_eq7_wcc_spectrum"]["value"] == "gapless"
+    model = I.bhz_eq7(1.5)
+    ph, _ = O.wilson_loop(model, P(40, 128), 2)
+    assert np.abs(np.diff(ph, axis=0)).max() < 2 * np.pi / 16
+    assert _covers_circle(ph)
+    assert abs(O.winding(ph)) < 1e-9
+    S = np.kron(s3, s3)
+    down, _, _, _ = O.spin_resolved_wilson_loop(model, P(30, 30), 2, S, -1)
+    up, _, _, _ = O.spin_resolved_wilson_loop(model, P(30, 30), 2, S, +1)
+    assert abs(abs(O.winding(down)) - 1) < 1e-9
+    assert abs(O.winding(down) + O.winding(up)) < 1e-9
+
+
+def test_spin_hall_windings():
+    """Spin-Hall model: total winding 0; s_z-down sector -1, s_z-up sector +1.
+
+    The s_z = +1 block sin kx tx + sin ky ty + (1 - cos kx - cos ky) tz is Eq. 4's
+    d-vector shifted by (pi, pi) and rotated by pi about z (same degree, +1 by
+    Eq. 4's pin); the s_z = -1 block flips the sign of d_x (degree -1).
+    """
+    wl = I.config_spin_hall()
+    ph, gap = O.wilson_loop(wl.model, wl.plane, 2)
+    assert abs(O.winding(ph)) < 1e-9
+    assert abs(gap.min() - 2.0) < 1e-9      # |d| >= 1 at m = 1, so the direct gap is >= 2
+    dn, pso, pgap, _ = O.spin_resolved_wilson_loop(wl.model, wl.plane, 2, wl.spin_op, -1)
+    up, _, _, _ = O.spin_resolved_wilson_loop(wl.model, wl.plane, 2, wl.spin_op, +1)
+    assert abs(O.winding(dn) + 1) < 1e-9 and abs(O.winding(up) - 1) < 1e-9
+    np.testing.assert_allclose(np.sort(pso, axis=-1), np.broadcast_to([-1.0, 1.0], pso.shape),
+                               atol=1e-12)     # s_z is conserved: PSO eigenvalues are +-1
+    assert abs(pgap - 1) < 1e-12
+
+
+def test_choti_eq9_paper_statements():
+    """Eq. 9, Delta0 = 1: gapped WCCs at kz = 0 (Fig. 4a), |C_s| = 1 with
+    s = s3 (x) t3 (Fig. 4c), nested spectrum winding once over kz (Fig. 4b)."""
+    model = I.choti_eq9(1.0)
+    ph, _ = O.wilson_loop(model, P(30, 30), 2)
+    wgap = min(abs(np.angle(np.exp(1j * (r[1] - r[0])))) for r in ph)
+    assert GOLDEN["choti_eq9_kz0_wcc_spectrum"]["value"] == "gapped"
+    assert wgap > 0.5 and not _covers_circle(ph)
+    S = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+    dn, _, _, _ = O.spin_resolved_wilson_loop(model, P(30, 30), 2, S, -1)
+    assert abs(abs(O.winding(dn)) - GOLDEN["choti_eq9_kz0_abs_spin_chern"]["value"]) < 1e-9
+    assert GOLDEN["choti_eq9_nested_vs_kz"]["value"] == "gapless"
+    nkz = 12
+    curve = []
+    for kz in np.arange(nkz) / nkz:
+        _, nest, _, _ = O.nested_wilson_loop(model, P(12, 12, origin=(0, 0, kz)), 2, m=1)
+        curve.append(nest[0])
+    assert abs(abs(O.winding(np.array(curve))) - 1) < 1e-9
+    # Delta0 = 0 at kz = 0 reduces to a BHZ-like insulator: gapless WCCs
+    ph0, _ = O.wilson_loop(I.choti_eq9(0.0), P(30, 128), 2)
+    assert _covers_circle(ph0)
+
+
+@pytest.mark.parametrize("gamma,expected", [(0.5, np.pi), (1.5, 0.0)])
+def test_bbh_nested_polarisation(gamma, expected):
+    """BBH quadrupole: nested polarisation 1/2 (phase pi) for |gamma/lambda| < 1 and 0
+    for |gamma/lambda| > 1, at every base point of the first loop."""
+    _, nest, wgap, _ = O.nested_wilson_loop(I.bbh(gamma, gamma), P(24, 24), 2, m=1)
+    err = np.abs(np.angle(np.exp(1j * (nest - expected))))
+    assert err.max() < 1e-10
+    assert wgap > 0.1
+
+
+def test_gauge_invariance():
+    """Eigenphases are unchanged by a random unitary gauge U(k) -> U(k) G(k)."""
+    model = I.random_hermitian_model(6, seed=3)
+    rng = np.random.default_rng(7)
+
+    def gauge(i, j, p):
+        Q, _ = np.linalg.qr(rng.standard_normal((p, p)) + 1j * rng.standard_normal((p, p)))
+        return Q
+
+    plane = P(15, 5)
+    a, _ = O.wilson_loop(model, plane, 3)
+    b, _ = O.wilson_loop(model, plane, 3, gauge=gauge)
+    for r in range(plane.N_t):
+        assert O.circular_match_error(a[r], b[r]) < 1e-12
+
+
+def test_two_band_closed_form_eigenvectors():
+    """p = 1 loop of Eq. 4 with the closed-form lower eigenvector of d.sigma,
+    u = (d_x - i d_y, -(d_z + |d|)), against the oracle's loop built on zheevd."""
+    model = I.chern_eq4(1.5)
+    N, Nt = 30, 9
+    ph, _ = O.wilson_loop(model, P(N, Nt), 1)
+    for i in range(Nt):
+        ky = 2 * np.pi * i / Nt
+        us = []
+        for j in range(N):
+            kx = 2 * np.pi * j / N
+            d = np.array([np.sin(kx), np.sin(ky), np.cos(kx) + np.cos(ky) + 1.5])
+            u = np.array([d[0] - 1j * d[1], -(d[2] + np.linalg.norm(d))])
+            us.append(u / np.linalg.norm(u))
+        z = 1.0 + 0j
+        for j in range(N):
+            z *= np.vdot(us[(j + 1) % N], us[j])
+        assert abs(np.angle(np.exp(1j * (np.angle(z) - ph[i, 0])))) < 1e-12
+
+
+def _jacobi_eigvals(A, sweeps=30):
+    """Cyclic complex Jacobi in plain Python loops (independent of LAPACK)."""
+    A = np.array(A, dtype=complex)
+    n = A.shape[0]
+    for _ in range(sweeps):
+        off = sum(abs(A[p, q]) ** 2 for p in range(n) for q in range(n) if p != q)
+        if off < 1e-30:
+            break
+        for p in range(n - 1):
+            for q in range(p + 1, n):
+                if abs(A[p, q]) < 1e-300:
+                    continue
+                phase = A[p, q] / abs(A[p, q])
+                tau = (A[q, q].real - A[p, p].real) / (2 * abs(A[p, q]))
+                t = np.sign(tau) / (abs(tau) + np.sqrt(1 + tau * tau)) if tau != 0 else 1.0
+                c = 1 / np.sqrt(1 + t * t)
+                s = t * c
+                J = np.eye(n, dtype=complex)
+                J[p, p], J[q, q] = c, c
+                J[p, q], J[q, p] = s * phase, -s * np.conj(phase)
+                A = J.conj().T @ A @ J
+    return np.sort(A.diagonal().real)
+
+
+def test_eigh_against_independent_jacobi():
+    """Step 2's eigenvalues against a hand-written Jacobi on 4 x 4 and 2 x 2 cases."""
+    rng = np.random.default_rng(5)
+    cases = [I.spin_hall(1.0), I.bbh(0.5, 0.5), I.choti_eq9(1.0), I.chern_eq4(1.5)]
+    for model in cases:
+        for f in rng.uniform(size=(4, 3)):
+            H = O.bloch_hamiltonian(model, f)
+            lam, _, _ = O.occupied_states(H, 1)
+            np.testing.assert_allclose(lam, _jacobi_eigvals(H), atol=1e-12)
+
+
+def test_eigenphases_known_spectrum():
+    """Eigenphases of W = V diag(e^{i theta}) V^{-1} (non-unitary V) recover theta."""
+    rng = np.random.default_rng(11)
+    for p in (1, 2, 5, 8):
+        th = np.sort(rng.uniform(-np.pi, np.pi, p))
+        th[-1] = np.pi
+        V = np.eye(p) + 0.3 * (rng.standard_normal((p, p)) + 1j * rng.standard_normal((p, p)))
+        W = V @ np.diag(np.exp(1j * th)) @ np.linalg.inv(V)
+        assert O.circular_match_error(O.eigenphases(W), th) < 1e-12
+
+
+def test_cyclic_base_transport():
+    """The loop based at k_{j+1} is M_j (loop based at k_j) M_j^{-1}: same spectrum,
+    eigenvectors carried by the overlap (Eq. 8's Wannier basis along the loop)."""
+    model = I.random_hermitian_model(5, seed=2)
+    f = O.plane_points(P(9, 1))
+    U = [O.occupied_states(O.bloch_hamiltonian(model, f[0, j]), 2)[1] for j in range(9)]
+    for j in range(9):
+        M = O.overlap(U[(j + 1) % 9], U[j])
+        np.testing.assert_allclose(O.cyclic_wilson_matrix(U, (j + 1) % 9) @ M,
+                                   M @ O.cyclic_wilson_matrix(U, j), atol=1e-13)
+    np.testing.assert_allclose(O.cyclic_wilson_matrix(U, 0), O.wilson_matrix(U), atol=1e-15)
+
+
+def test_supercell_band_folding():
+    """Sec. II A supercells: eig H_sc(F) = union_g eig H((F + g)/L) (theta = 0 TBC)."""
+    prim = I.spin_hall(1.0)
+    rng = np.random.default_rng(4)
+    for L in (2, 3):
+        sc = I.supercell(prim, L)
+        for F in rng.uniform(size=(3, 3)) * [1, 1, 0]:
+            lam_sc = np.linalg.eigvalsh(O.bloch_hamiltonian(sc, F))
+            lam = np.concatenate([np.linalg.eigvalsh(O.bloch_hamiltonian(
+                prim, (F + [gx, gy, 0]) / [L, L, 1])) for gx in range(L) for gy in range(L)])
+            np.testing.assert_allclose(lam_sc, np.sort(lam), atol=1e-12)
+
+
+def test_supercell_spin_chern_unchanged():
+    """A clean 2 x 2 supercell (p = 8) carries the primitive cell's spin-Chern number."""
+    sc = I.supercell(I.spin_hall(1.0), 2)
+    S = np.kron(np.eye(4), I.SPIN_HALL_SZ)
+    dn, _, _, _ = O.spin_resolved_wilson_loop(sc, P(20, 20), 8, S, -1)
+    assert abs(O.winding(dn) + 1) < 1e-9
+
+
+def test_flux_plaquettes_and_hofstadter():
+    """Peierls flux: every plaquette of the torus (seams included) encloses 2pi/L^2;
+    the isolated lowest Hofstadter band at flux 1/4 has |C| = 1."""
+    L = 3
+    sc = I.supercell(I.square_lattice(1.0), L, flux=True)
+    amp = {}
+    for R, a, b, t in zip(map(tuple, sc.R), sc.i, sc.j, sc.t):
+        amp[(int(a), int(b), R)] = t
+
+    def site(x, y):
+        sx, sy = x // L, y // L
+        return (x % L) * L + (y % L), (sx, sy)
+
+    def hop(x0, y0, x1, y1):
+        a, A = site(x0, y0)
+        b, B = site(x1, y1)
+        return amp[(a, b, (B[0] - A[0], B[1] - A[1], 0))]
+
+    for x in range(L):
+        for y in range(L):
+            z = hop(x, y, x + 1, y) * hop(x + 1, y, x + 1, y + 1) \
+                * hop(x + 1, y + 1, x, y + 1) * hop(x, y + 1, x, y)
+            assert abs(np.angle(z * np.exp(-2j * np.pi / L**2))) < 1e-12 \
+                or abs(np.angle(z * np.exp(2j * np.pi / L**2))) < 1e-12
+            assert abs(np.angle(z) - np.angle(hop(0, 0, 1, 0) * hop(1, 0, 1, 1)
+                                              * hop(1, 1, 0, 1) * hop(0, 1, 0, 0))) < 1e-12
+    hof = I.supercell(I.square_lattice(1.0), 2, flux=True)
+    ph, gap = O.wilson_loop(hof, P(24, 24), 1)
+    assert gap.min() > 0.1
+    assert abs(abs(O.winding(ph)) - 1) < 1e-9
+
+
+def test_disorder_recipe():
+    """On-site disorder: one uniform value in [-W/2, W/2] per cell on all its orbitals."""
+    W = 2.0
+    sc = I.supercell(I.spin_hall(1.0), 4, W=W, seed=9)
+    H0 = O.bloch_hamiltonian(sc, [0.1, 0.2, 0])
+    Hc = O.bloch_hamiltonian(I.supercell(I.spin_hall(1.0), 4), [0.1, 0.2, 0])
+    D = np.diag(H0 - Hc).real
+    assert np.abs(np.diag(np.diag(H0 - Hc)) - (H0 - Hc)).max() < 1e-14
+    cells = D.reshape(16, 4)
+    assert np.allclose(cells, cells[:, :1]) and np.all(np.abs(cells) <= W / 2)
+    assert np.ptp(cells[:, 0]) > 0.5
+
+
+def test_error_conditions():
+    """EGAP where the gap closes on the mesh; EPSOGAP / EINVAL on bad arguments."""
+    with pytest.raises(O.OracleError) as e:
+        O.wilson_loop(I.chern_eq4(2.0), P(8, 8), 1)       # gap closes at (pi, pi)
+    assert e.value.status == "EGAP"
+    wl = I.config_spin_hall()
+    with pytest.raises(O.OracleError) as e:
+        O.spin_resolved_wilson_loop(wl.model, P(6, 6), 2, np.eye(4, dtype=complex), -1)
+    assert e.value.status == "EPSOGAP"
+    with pytest.raises(O.OracleError) as e:
+        O.wilson_loop(wl.model, P(6, 6, loop_dir=(0.5, 0, 0)), 2)
+    assert e.value.status == "EINVAL"
+
+
+def test_unitarise_option():
+    """Per-overlap polar factors: identical to the raw product for an s_z-conserving
+    model, unit-modulus spectrum in general."""
+    wl = I.config_spin_hall()
+    a, _ = O.wilson_loop(wl.model, P(12, 6), 2)
+    b, _ = O.wilson_loop(wl.model, P(12, 6), 2, unitarise=True)
+    for r in range(6):
+        assert O.circular_match_error(a[r], b[r]) < 1e-12
+    model = I.random_hermitian_model(6, seed=3)
+    f = O.plane_points(P(10, 1))
+    U = [O.occupied_states(O.bloch_hamiltonian(model, f[0, j]), 3)[1] for j in range(10)]
+    Wu = O.wilson_matrix(U, unitarise=True)
+    np.testing.assert_allclose(np.abs(np.linalg.eigvals(Wu)), 1.0, atol=1e-12)
+    assert np.abs(np.abs(np.linalg.eigvals(O.wilson_matrix(U))) - 1).max() > 1e-3
