@@ -1,0 +1,191 @@
+/*
+ * berrywl.h -- C ABI of the GB300 (sm_103a) Wilson-loop library.
+ *
+ * The library computes Wannier-centre charges by discretised, path-ordered Wilson
+ * loops (arXiv 2312.13051, Sec. II A, Eq. 2), hybrid Wannier centres over a plane
+ * (Sec. II B, Eq. 3), the nested Wilson loop on a Wannier-band subspace (Sec. III,
+ * Eq. 8) and the spin-resolved Wilson loop of a projected-spin-operator sector
+ * (Sec. IV), for tight-binding models given as hopping lists.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers are bw_c128 {re, im} (FP64), or {float re, im} where stated.
+ *  - Matrices are row-major.  An eigenvector block U (n x p) stores U[r*p + c]
+ *    (row r = orbital, column c = band), like numpy's V[:, :p].
+ *  - The model (hopping list) and the spin operator are HOST arrays, read during
+ *    the call and not retained: the library turns them into its own device plan.
+ *    Every other array argument is a DEVICE pointer owned by the caller.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  The return value reports argument errors and launch failures only.
+ *    Numerical conditions found on the device (closed gap, PSO gap, Wannier gap,
+ *    no convergence) go to a sticky per-context status word; read it with
+ *    bw_get_status(), which synchronises the stream.
+ *  - Scratch memory comes from a per-context device arena bounded by the context's
+ *    memory budget (BW_ENOMEM beyond it).  One context must not be used from two
+ *    host threads at once; calls on different streams are ordered by the context.
+ *  - Calls may be captured into a CUDA graph once the same call has run uncaptured on
+ *    the context (so that its arena and staging buffer are large enough).  A replay
+ *    re-reads the hopping list from the context's pinned staging buffer, so no other
+ *    call may be issued on that context while its graphs are being replayed.
+ *  - There is no CPU fallback: every numerical step runs in the library's CUDA
+ *    kernels.  Without a usable CUDA device bw_create() fails with BW_ECUDA.
+ */
+#ifndef BERRYWL_H
+#define BERRYWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bw_ctx bw_ctx;
+
+typedef enum {
+  BW_OK = 0,
+  BW_EINVAL = 1,    /* bad argument, non-Hermitian list, unsupported size          */
+  BW_ENOMEM = 2,    /* scratch would exceed the context's memory budget            */
+  BW_EGAP = 3,      /* direct gap lam_p - lam_{p-1} <= gap_tol at some k           */
+  BW_EPSOGAP = 4,   /* PSO sector size != p/2, or min |PSO eigenvalue| <= tol      */
+  BW_EWANGAP = 5,   /* Wannier (phase) gap around the nested sector <= tol         */
+  BW_ENOCONV = 6,   /* an iterative eigensolver hit its iteration cap              */
+  BW_ETIMEOUT = 7,  /* a bounded device-side wait gave up                          */
+  BW_ECUDA = 8      /* CUDA runtime error                                          */
+} bw_status;
+
+typedef enum {
+  BW_FP64 = 0,      /* every step in FP64                                          */
+  BW_MIXED = 1      /* eigensolve in FP32, occupied block refined in FP64          */
+} bw_precision;
+
+typedef struct { double re, im; } bw_c128;
+
+/* Tight-binding model, full hopping list (HOST arrays):
+ *   H(f) = sum_e t[e] exp(i 2 pi f . R[e]) |i[e]><j[e]|
+ * f in fractional reciprocal coordinates, R[e] integer translations (nnz x 3).
+ * Every (i, j, R, t) must come with (j, i, -R, conj t); the list is checked and
+ * rejected with BW_EINVAL when H(f) would not be Hermitian.  No orbital-position
+ * phases are applied, so H(f + G) = H(f) for integer G (Sec. II A, periodic
+ * condition psi(k) = psi(k + 2 pi / a)). */
+typedef struct {
+  int32_t n;              /* orbitals per (super)cell, >= 1                        */
+  int64_t nnz;            /* entries in the list, >= 0                              */
+  const int32_t* R;       /* nnz x 3                                                */
+  const int32_t* i;       /* nnz, 0 <= i < n                                        */
+  const int32_t* j;       /* nnz, 0 <= j < n                                        */
+  const bw_c128* t;       /* nnz                                                    */
+} bw_model;
+
+/* Plane of k-points (Sec. II B, vec(t1, t2) in units of the reciprocal vectors):
+ *   f(j, i) = origin + (j / N) loop_dir + (i / N_t) trans_dir,  j < N, i < N_t.
+ * loop_dir is an integer vector so each loop closes on the k-point it started from
+ * (Eq. 2); the loop reuses the eigenvectors of j = 0 at j = N.  For the nested loop
+ * trans_dir must be an integer vector as well (closure along the second direction).
+ * k-point index k = i * N + j. */
+typedef struct {
+  double origin[3];
+  int32_t loop_dir[3];
+  double trans_dir[3];
+  int32_t N;              /* points per loop, >= 1                                  */
+  int32_t N_t;            /* transverse points, >= 1                                */
+} bw_plane;
+
+/* Options.  A negative tolerance selects the default. */
+typedef struct {
+  double gap_tol;         /* direct gap; default 1e-6 * max(1, max|t|)              */
+  double pso_gap_tol;     /* min |PSO eigenvalue|; default 1e-6                     */
+  double wannier_gap_tol; /* phase gap around the nested sector; default 1e-6 rad   */
+  int32_t unitarise;      /* 1: replace each overlap by its unitary polar factor    */
+  int32_t max_sweeps;     /* Jacobi sweep cap; 0 = default (30)                     */
+} bw_opts;
+
+/* Context: binds device `device`, allocates nothing yet.  mem_budget_bytes bounds
+ * the scratch arena (0 = 90% of the device's free memory at creation). */
+bw_status bw_create(bw_ctx** out, int device, size_t mem_budget_bytes);
+void bw_destroy(bw_ctx* ctx);
+
+/* Message of the last failure on this context (argument error or device status,
+ * with the failing k index).  Valid until the next call on the context. */
+const char* bw_last_error(const bw_ctx* ctx);
+
+/* Synchronises `stream`, returns and clears the sticky device status of the calls
+ * issued so far (BW_OK, BW_EGAP, BW_EPSOGAP, BW_EWANGAP or BW_ENOCONV).  When
+ * k_index is non-NULL it receives the first failing k-point index (or -1). */
+bw_status bw_get_status(bw_ctx* ctx, void* stream, int64_t* k_index);
+
+/* Per-kernel timing.  With profiling enabled, CUDA events are recorded around every
+ * kernel launch of each call (as external events under stream capture, so replays of
+ * a captured graph are timed as well).  No paper counterpart: measurement only. */
+bw_status bw_set_profiling(bw_ctx* ctx, int enable);
+
+/* Waits for the last timing event of the most recent profiled call (or replay) and
+ * writes up to `max` kernel names (32 bytes each, NUL-terminated; may be NULL) and
+ * durations in milliseconds (may be NULL).  Returns the count, -1 on error. */
+int bw_profile_read(bw_ctx* ctx, int max, char* names, double* ms);
+
+/* Step 1, Bloch Hamiltonian (Sec. I: H(k) from the hopping list).
+ * f: DEVICE, K x 3 doubles.  H_out: DEVICE, K x n x n complex, complex128
+ * (complex64 = 0) or complex64 pairs of floats (complex64 = 1). */
+bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64_t K,
+                      int complex64, void* H_out, void* stream);
+
+/* Step 2, exact diagonalisation (Sec. I), batched with uneven sizes.
+ * H: DEVICE, matrices packed back to back (matrix b holds n_per[b]^2 complex128,
+ * row-major, Hermitian; only its lower triangle is read for n > 32 ... the full
+ * matrix for n <= 32).  n_per: HOST, batch sizes.  evals: DEVICE, sum(n_per)
+ * doubles, ascending per matrix.  evecs: DEVICE, sum(n_per[b] * n_vec) complex128,
+ * matrix b's lowest n_vec eigenvectors as an n x n_vec row-major block (NULL: values
+ * only).  BW_MIXED: FP32 solve, lowest n_vec block refined in FP64 (needs
+ * n_vec < n and a gap above it).  1 <= n <= 1024, 0 <= n_vec <= n. */
+bw_status bw_eigh_batched(bw_ctx* ctx, const void* H, const int32_t* n_per, int64_t batch,
+                          int32_t n_vec, bw_precision prec, double* evals, void* evecs,
+                          void* stream);
+
+/* Hybrid Wannier centres (Sec. II B, Eq. 3, BerryEasy's WSurf): for each transverse
+ * index i the Wilson loop along loop_dir of the lowest p bands,
+ *   W_i = M_{N-1} ... M_1 M_0,   M_j = U(k_{j+1})^dagger U(k_j),  U(k_N) = U(k_0)
+ * (Eq. 2, later k multiplied from the left), and its eigenphases theta in (-pi, pi].
+ * phases: DEVICE, N_t x p doubles, ascending per row (xbar = theta / 2pi).
+ * min_gap: DEVICE, N_t doubles, min over the loop of lam_p - lam_{p-1} (may be NULL).
+ * 1 <= p <= n. */
+bw_status bw_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
+                         int32_t p, bw_precision prec, const bw_opts* opts,
+                         double* phases, double* min_gap, void* stream);
+
+/* Nested Wilson loop (Sec. III, Eq. 8, BerryEasy's WNWL).  For each base point
+ * k_j of the first loop: the right eigenvectors nu of the loop started at k_j,
+ * ordered by phase measured from `cut` (mod 2pi, ascending); the sector
+ * [first, first + m) spans the Wannier states w = U(k_j) nu (orthonormalised);
+ * their Wilson loop along trans_dir (closed on i = 0) gives the nested phases.
+ * phases: DEVICE, N_t x p (first loop, as bw_wilson_loop).  nested: DEVICE, N x m,
+ * ascending per base point.  min_wannier_gap: DEVICE, N_t doubles: circular phase
+ * distance between the sector and the other phases (may be NULL).  min_gap as in
+ * bw_wilson_loop (may be NULL).  1 <= m, 0 <= first, first + m <= p. */
+bw_status bw_nested_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
+                                int32_t p, double cut, int32_t first, int32_t m,
+                                bw_precision prec, const bw_opts* opts, double* phases,
+                                double* nested, double* min_wannier_gap, double* min_gap,
+                                void* stream);
+
+/* Spin-resolved Wilson loop (Sec. IV, BerryEasy's WSpinSurf / spin_spectrum).
+ * At each k the projected spin operator restricted to the occupied space,
+ * S_occ = U^dagger s U (p x p), is diagonalised; its eigenvectors with eigenvalue
+ * of sign `sign` (-1: C_down, +1: C_up) form the sector U_s = U V_s, which must
+ * hold p/2 states at every k with min |eigenvalue| > pso_gap_tol (else
+ * BW_EPSOGAP).  The Wilson loop of U_s as in bw_wilson_loop.
+ * spin_op: HOST, n x n complex128 Hermitian (e.g. diag(1,-1,-1,1) = s3 (x) t3).
+ * phases: DEVICE, N_t x p/2.  pso_evals: DEVICE, K x p ascending (may be NULL).
+ * min_pso_gap, min_gap: DEVICE, N_t doubles each (may be NULL).  p even. */
+bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
+                                       const bw_plane* plane, int32_t p,
+                                       const bw_c128* spin_op, int32_t sign,
+                                       bw_precision prec, const bw_opts* opts,
+                                       double* phases, double* pso_evals,
+                                       double* min_pso_gap, double* min_gap, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BERRYWL_H */

@@ -1,0 +1,311 @@
+"""ctypes binding of ``libberrywl.so`` (argument marshalling only).
+
+Each function here has the name of its C entry point without the ``bw_`` prefix
+and does nothing but check types, allocate the output tensors on the device and
+pass pointers, sizes and the current CUDA stream through.  Every numerical step
+runs in the library's kernels; without the library or a CUDA device the calls
+raise instead of computing anything on the host.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libberrywl.so")
+
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP", "ENOCONV", "ETIMEOUT",
+                "ECUDA"]
+PRECISION = {"fp64": 0, "mixed": 1}
+
+
+class BWError(RuntimeError):
+    def __init__(self, code: int, msg: str, k_index: int = -1):
+        name = STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else str(code)
+        super().__init__(f"{name}: {msg}")
+        self.code = code
+        self.status = name
+        self.k_index = k_index
+
+
+class bw_model(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("R", C.c_void_p), ("i", C.c_void_p),
+                ("j", C.c_void_p), ("t", C.c_void_p)]
+
+
+class bw_plane(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("loop_dir", C.c_int32 * 3),
+                ("trans_dir", C.c_double * 3), ("N", C.c_int32), ("N_t", C.c_int32)]
+
+
+class bw_opts(C.Structure):
+    _fields_ = [("gap_tol", C.c_double), ("pso_gap_tol", C.c_double),
+                ("wannier_gap_tol", C.c_double), ("unitarise", C.c_int32),
+                ("max_sweeps", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Loads the library (raises when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2312_13051_gb300.build.build() first")
+        lib = C.CDLL(path)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "bw_create": (i32, [C.POINTER(vp), C.c_int, C.c_size_t]),
+            "bw_destroy": (None, [vp]),
+            "bw_last_error": (C.c_char_p, [vp]),
+            "bw_get_status": (i32, [vp, vp, C.POINTER(i64)]),
+            "bw_set_profiling": (i32, [vp, C.c_int]),
+            "bw_profile_read": (C.c_int, [vp, C.c_int, C.c_char_p, C.POINTER(dbl)]),
+            "bw_build_hk": (i32, [vp, C.POINTER(bw_model), vp, i64, C.c_int, vp, vp]),
+            "bw_eigh_batched": (i32, [vp, vp, vp, i64, i32, i32, vp, vp, vp]),
+            "bw_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
+                                     C.POINTER(bw_opts), vp, vp, vp]),
+            "bw_nested_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32,
+                                            dbl, i32, i32, i32, C.POINTER(bw_opts), vp, vp, vp,
+                                            vp, vp]),
+            "bw_spin_resolved_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane),
+                                                   i32, vp, i32, i32, C.POINTER(bw_opts), vp,
+                                                   vp, vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
+            "bw_profile_read", "bw_build_hk",
+            "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
+            "bw_spin_resolved_wilson_loop"]
+
+
+class Context:
+    """Owns one ``bw_ctx`` (device scratch arena, status word, staging buffer)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.bw_create(C.byref(h), device, mem_budget_bytes)
+        if rc != 0:
+            raise BWError(rc, f"bw_create(device={device}) failed")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self.lib.bw_last_error(self.h).decode()
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise BWError(rc, self.error())
+
+    def set_profiling(self, enable: bool = True) -> None:
+        self.check(self.lib.bw_set_profiling(self.h, int(enable)))
+
+    def profile_read(self, max_kernels: int = 8):
+        """[(kernel name, ms)] of the most recent profiled call or graph replay."""
+        names = C.create_string_buffer(32 * max_kernels)
+        ms = (C.c_double * max_kernels)()
+        n = self.lib.bw_profile_read(self.h, max_kernels, names, ms)
+        if n < 0:
+            raise BWError(8, "bw_profile_read failed")
+        return [(names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), ms[i]) for i in range(n)]
+
+    def status(self, stream=None) -> None:
+        """Synchronises the stream and raises on a device-side numerical status."""
+        k = C.c_int64(-1)
+        rc = self.lib.bw_get_status(self.h, _stream_ptr(stream), C.byref(k))
+        if rc != 0:
+            raise BWError(rc, self.error(), int(k.value))
+
+
+_contexts: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class _HostModel:
+    """Keeps the contiguous host arrays of a hopping list alive during a call."""
+
+    def __init__(self, model):
+        self.R = np.ascontiguousarray(model.R, dtype=np.int32).reshape(-1, 3)
+        self.i = np.ascontiguousarray(model.i, dtype=np.int32)
+        self.j = np.ascontiguousarray(model.j, dtype=np.int32)
+        self.t = np.ascontiguousarray(model.t, dtype=np.complex128)
+        self.s = bw_model(int(model.n), int(self.t.shape[0]), self.R.ctypes.data,
+                          self.i.ctypes.data, self.j.ctypes.data, self.t.ctypes.data)
+
+
+def _plane(plane) -> bw_plane:
+    loop = [int(round(x)) for x in plane.loop_dir]
+    if any(abs(float(x) - round(float(x))) > 0 for x in plane.loop_dir):
+        raise BWError(1, "loop_dir must be an integer vector")
+    return bw_plane((C.c_double * 3)(*map(float, plane.origin)), (C.c_int32 * 3)(*loop),
+                    (C.c_double * 3)(*map(float, plane.trans_dir)), int(plane.N), int(plane.N_t))
+
+
+def _opts(gap_tol=-1.0, pso_gap_tol=-1.0, wannier_gap_tol=-1.0, unitarise=False, max_sweeps=0):
+    return bw_opts(float(gap_tol), float(pso_gap_tol), float(wannier_gap_tol), int(unitarise),
+                   int(max_sweeps))
+
+
+def _empty(shape, dtype, device):
+    import torch
+    return torch.empty(shape, dtype=dtype, device=device)
+
+
+def _cuda_device(ctx: Context):
+    import torch
+    return torch.device("cuda", ctx.device)
+
+
+def build_hk(model, f, complex64: bool = False, ctx: Context | None = None, check=True):
+    """H(f) for each row of the device tensor ``f`` (K x 3 float64); returns K x n x n."""
+    import torch
+    ctx = ctx or context()
+    if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.dim() == 2
+            and f.shape[1] == 3):
+        raise BWError(1, "f must be a contiguous CUDA float64 tensor of shape (K, 3)")
+    hm = _HostModel(model)
+    K = f.shape[0]
+    H = _empty((K, model.n, model.n), torch.complex64 if complex64 else torch.complex128, f.device)
+    ctx.check(ctx.lib.bw_build_hk(ctx.h, C.byref(hm.s), _ptr(f), K, int(complex64), _ptr(H),
+                                  _stream_ptr()))
+    if check:
+        ctx.status()
+    return H
+
+
+def eigh_batched(H, n_per, n_vec: int, precision: str = "fp64", ctx: Context | None = None,
+                 check=True):
+    """Batched Hermitian eigensolver.  ``H``: packed complex128 CUDA tensor holding the
+    matrices back to back; ``n_per``: their sizes.  Returns (evals, evecs) packed."""
+    import torch
+    ctx = ctx or context()
+    n_per = np.ascontiguousarray(n_per, dtype=np.int32)
+    if not (H.is_cuda and H.dtype == torch.complex128 and H.is_contiguous()):
+        raise BWError(1, "H must be a contiguous CUDA complex128 tensor")
+    if H.numel() != int(np.sum(n_per.astype(np.int64) ** 2)):
+        raise BWError(1, "H size does not match n_per")
+    ev = _empty((int(n_per.sum()),), torch.float64, H.device)
+    vec = _empty((int(n_per.astype(np.int64).sum() * n_vec),), torch.complex128, H.device)
+    ctx.check(ctx.lib.bw_eigh_batched(ctx.h, _ptr(H), n_per.ctypes.data, len(n_per), int(n_vec),
+                                      PRECISION[precision], _ptr(ev),
+                                      _ptr(vec) if n_vec > 0 else C.c_void_p(0), _stream_ptr()))
+    if check:
+        ctx.status()
+    return ev, vec
+
+
+def wilson_loop(model, plane, p: int, precision: str = "fp64", ctx: Context | None = None,
+                check=True, out=None, **opts):
+    """Hybrid Wannier centres: (phases[N_t, p], min_gap[N_t]) as CUDA float64 tensors."""
+    import torch
+    ctx = ctx or context()
+    dev = _cuda_device(ctx)
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    if out is None:
+        out = (_empty((plane.N_t, p), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+    ph, gap = out
+    ctx.check(ctx.lib.bw_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
+                                     PRECISION[precision], C.byref(o), _ptr(ph), _ptr(gap),
+                                     _stream_ptr()))
+    if check:
+        ctx.status()
+    return ph, gap
+
+
+def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0,
+                       m: int | None = None, precision: str = "fp64",
+                       ctx: Context | None = None, check=True, out=None, **opts):
+    """Nested loop: (phases[N_t, p], nested[N, m], min_wannier_gap[N_t], min_gap[N_t])."""
+    import torch
+    ctx = ctx or context()
+    dev = _cuda_device(ctx)
+    m = p // 2 if m is None else int(m)
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    if out is None:
+        out = (_empty((plane.N_t, p), torch.float64, dev), _empty((plane.N, m), torch.float64, dev),
+               _empty((plane.N_t,), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+    ph, nest, wg, gap = out
+    ctx.check(ctx.lib.bw_nested_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
+                                            float(cut), int(first), int(m), PRECISION[precision],
+                                            C.byref(o), _ptr(ph), _ptr(nest), _ptr(wg), _ptr(gap),
+                                            _stream_ptr()))
+    if check:
+        ctx.status()
+    return ph, nest, wg, gap
+
+
+def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
+                              precision: str = "fp64", ctx: Context | None = None, check=True,
+                              want_pso=True, out=None, **opts):
+    """Spin-resolved loop: (phases[N_t, p/2], pso_evals[N_t, N, p] or None,
+    min_pso_gap[N_t], min_gap[N_t])."""
+    import torch
+    ctx = ctx or context()
+    dev = _cuda_device(ctx)
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    S = np.ascontiguousarray(spin_op, dtype=np.complex128)
+    if S.shape != (model.n, model.n):
+        raise BWError(1, f"spin operator must be {model.n} x {model.n}")
+    if out is None:
+        out = (_empty((plane.N_t, p // 2), torch.float64, dev),
+               _empty((plane.N_t, plane.N, p), torch.float64, dev) if want_pso else None,
+               _empty((plane.N_t,), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+    ph, pso, pg, gap = out
+    ctx.check(ctx.lib.bw_spin_resolved_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
+                                                   S.ctypes.data, int(sign), PRECISION[precision],
+                                                   C.byref(o), _ptr(ph), _ptr(pso), _ptr(pg),
+                                                   _ptr(gap), _stream_ptr()))
+    if check:
+        ctx.status()
+    return ph, pso, pg, gap

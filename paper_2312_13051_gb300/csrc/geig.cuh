@@ -1,0 +1,281 @@
+// Block-wide eigensolver for a general complex matrix in shared memory (FP64).
+//
+// The Wilson matrix of Eq. 2 is a product of raw overlaps and is not unitary, so
+// its eigenvalues need a general (non-Hermitian) solver: Householder reduction to
+// upper Hessenberg form, then single-shift implicit QR sweeps with Givens
+// rotations, Wilkinson shifts and deflation on small subdiagonals.  With vectors
+// requested the rotations are applied to whole rows/columns, leaving the Schur
+// form T = Z^dagger W Z; right eigenvectors are x = Z y with T y = lambda y solved
+// by back substitution.
+#pragma once
+
+#include "common.cuh"
+
+namespace bw {
+
+struct GeigShared {
+  z64 c0;        // Givens: G = [[c, s], [-conj(s), c]], c real (stored in c0.re)
+  z64 s;
+  z64 mu;
+  int l, hi, active, fail, k;
+  double scale;
+};
+
+__device__ __forceinline__ double zabs(z64 a) { return hypot(a.re, a.im); }
+
+// Givens G with G [x; y] = [r; 0], c real >= 0.
+__device__ __forceinline__ void givens(z64 x, z64 y, double& c, z64& s) {
+  const double ax = zabs(x), ay = zabs(y);
+  if (ay == 0.0) {
+    c = 1.0;
+    s = z64(0.0, 0.0);
+    return;
+  }
+  if (ax == 0.0) {
+    c = 0.0;
+    s = z64(y.re / ay, -y.im / ay);  // conj(y)/|y|
+    return;
+  }
+  const double r = hypot(ax, ay);
+  c = ax / r;
+  const z64 ux(x.re / ax, x.im / ax);
+  s = (1.0 / r) * (ux * conj(y));
+}
+
+// Eigen-decomposition of H (p x p, leading dimension ld), destroyed on output.
+// lam[p] receives the eigenvalues.  With want_vec, Z (p x p) receives the right
+// eigenvectors as unit-norm columns; vec scratch needs p z64.  Returns 0, or -1
+// when the QR iteration cap (40 p sweeps) is reached.
+__device__ int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64* vec,
+                    GeigShared* sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double eps = 2.220446049250313e-16;
+  if (want_vec)
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      Z[r * ld + c] = z64(double(r == c), 0.0);
+    }
+  __syncthreads();
+  // --- Householder reduction to Hessenberg form
+  for (int c = 0; c + 2 < p; ++c) {
+    if (tid == 0) {
+      double nrm2 = 0.0;
+      for (int r = c + 1; r < p; ++r) nrm2 += abs2(H[r * ld + c]);
+      double tail = nrm2 - abs2(H[(c + 1) * ld + c]);
+      sh->active = (tail > 0.0);
+      if (sh->active) {
+        const z64 x0 = H[(c + 1) * ld + c];
+        const double nx = sqrt(nrm2), ax0 = zabs(x0);
+        const z64 ph = ax0 > 0.0 ? z64(x0.re / ax0, x0.im / ax0) : z64(1.0, 0.0);
+        const z64 alpha = -nx * ph;
+        for (int r = c + 1; r < p; ++r) vec[r] = H[r * ld + c];
+        vec[c + 1] = vec[c + 1] - alpha;
+        double nv = 0.0;
+        for (int r = c + 1; r < p; ++r) nv += abs2(vec[r]);
+        nv = 1.0 / sqrt(nv);
+        for (int r = c + 1; r < p; ++r) vec[r] = nv * vec[r];
+        sh->mu = alpha;
+      }
+    }
+    __syncthreads();
+    if (!sh->active) continue;
+    // left: H <- (I - 2 v v^dagger) H on rows c+1.., columns c..
+    for (int col = c + tid; col < p; col += nt) {
+      z64 w(0.0, 0.0);
+      for (int r = c + 1; r < p; ++r) cfma_conj(w, vec[r], H[r * ld + col]);
+      for (int r = c + 1; r < p; ++r) H[r * ld + col] = H[r * ld + col] - 2.0 * (vec[r] * w);
+    }
+    __syncthreads();
+    // right: H <- H (I - 2 v v^dagger) on columns c+1..; Z likewise
+    for (int row = tid; row < p; row += nt) {
+      z64 w(0.0, 0.0);
+      for (int k = c + 1; k < p; ++k) cfma(w, H[row * ld + k], vec[k]);
+      for (int k = c + 1; k < p; ++k) H[row * ld + k] = H[row * ld + k] - 2.0 * (w * conj(vec[k]));
+      if (want_vec) {
+        z64 wz(0.0, 0.0);
+        for (int k = c + 1; k < p; ++k) cfma(wz, Z[row * ld + k], vec[k]);
+        for (int k = c + 1; k < p; ++k)
+          Z[row * ld + k] = Z[row * ld + k] - 2.0 * (wz * conj(vec[k]));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      H[(c + 1) * ld + c] = sh->mu;
+      for (int r = c + 2; r < p; ++r) H[r * ld + c] = z64(0.0, 0.0);
+    }
+    __syncthreads();
+  }
+  // --- shifted QR on the Hessenberg matrix
+  if (tid == 0) {
+    sh->hi = p - 1;
+    sh->fail = 0;
+  }
+  __syncthreads();
+  int iter = 0, total = 0;
+  const int cap = 40 * p + 40;
+  while (true) {
+    if (tid == 0) {
+      int hi = sh->hi;
+      sh->active = 0;
+      while (hi >= 0) {
+        if (hi == 0) {
+          lam[0] = H[0];
+          hi = -1;
+          break;
+        }
+        int l = hi;
+        while (l > 0) {
+          const double sub = zabs(H[l * ld + l - 1]);
+          const double dia = zabs(H[l * ld + l]) + zabs(H[(l - 1) * ld + l - 1]);
+          if (sub <= eps * dia || sub < 1e-300) {
+            H[l * ld + l - 1] = z64(0.0, 0.0);
+            break;
+          }
+          --l;
+        }
+        if (l == hi) {
+          lam[hi] = H[hi * ld + hi];
+          --hi;
+          iter = 0;
+          continue;
+        }
+        // shift from the trailing 2x2 of the active window
+        z64 mu;
+        const z64 a = H[(hi - 1) * ld + hi - 1], b = H[(hi - 1) * ld + hi];
+        const z64 c = H[hi * ld + hi - 1], d = H[hi * ld + hi];
+        if (iter > 0 && iter % 12 == 0) {
+          const double ex = zabs(H[hi * ld + hi - 1]) + (hi >= 2 ? zabs(H[(hi - 1) * ld + hi - 2]) : 0.0);
+          mu = d + z64(0.75 * ex, 0.0);
+        } else {
+          // eigenvalue of [[a,b],[c,d]] closest to d
+          const z64 half = 0.5 * (a - d);
+          const z64 disc = half * half + b * c;
+          // complex sqrt
+          const double r = zabs(disc);
+          double sr = sqrt(0.5 * (r + fabs(disc.re)));
+          z64 sq;
+          if (sr == 0.0) {
+            sq = z64(0.0, 0.0);
+          } else if (disc.re >= 0.0) {
+            sq = z64(sr, disc.im / (2.0 * sr));
+          } else {
+            sq = z64(fabs(disc.im) / (2.0 * sr), disc.im >= 0.0 ? sr : -sr);
+          }
+          // mu = d + half -/+ sq, choose closer to d
+          const z64 m1 = d + half - sq, m2 = d + half + sq;
+          mu = (abs2(m1 - d) <= abs2(m2 - d)) ? m1 : m2;
+        }
+        sh->mu = mu;
+        sh->l = l;
+        sh->active = 1;
+        break;
+      }
+      sh->hi = hi;
+      ++iter;
+      ++total;
+      if (total > cap) {
+        sh->fail = 1;
+        sh->active = 0;
+        sh->hi = -1;
+      }
+    }
+    __syncthreads();
+    if (!sh->active) break;
+    const int l = sh->l, hi = sh->hi;
+    const int col_end = want_vec ? p - 1 : hi;
+    const int row_beg = want_vec ? 0 : l;
+    for (int k = l; k < hi; ++k) {
+      if (tid == 0) {
+        z64 x, y;
+        if (k == l) {
+          x = H[l * ld + l] - sh->mu;
+          y = H[(l + 1) * ld + l];
+        } else {
+          x = H[k * ld + k - 1];
+          y = H[(k + 1) * ld + k - 1];
+        }
+        double c;
+        z64 s;
+        givens(x, y, c, s);
+        sh->c0 = z64(c, 0.0);
+        sh->s = s;
+      }
+      __syncthreads();
+      const double c = sh->c0.re;
+      const z64 s = sh->s;
+      // rows k, k+1: [rk; rk1] <- G [rk; rk1]
+      const int cb = (k > l) ? k - 1 : l;
+      for (int col = cb + tid; col <= col_end; col += nt) {
+        const z64 x = H[k * ld + col], y = H[(k + 1) * ld + col];
+        H[k * ld + col] = c * x + s * y;
+        H[(k + 1) * ld + col] = c * y - conj(s) * x;
+      }
+      __syncthreads();
+      if (tid == 0 && k > l) H[(k + 1) * ld + k - 1] = z64(0.0, 0.0);
+      // columns k, k+1: H <- H G^dagger ; Z <- Z G^dagger
+      const int re = min(k + 2, hi);
+      for (int row = row_beg + tid; row <= re; row += nt) {
+        const z64 x = H[row * ld + k], y = H[row * ld + k + 1];
+        H[row * ld + k] = c * x + y * conj(s);
+        H[row * ld + k + 1] = c * y - x * s;
+      }
+      if (want_vec)
+        for (int row = tid; row < p; row += nt) {
+          const z64 x = Z[row * ld + k], y = Z[row * ld + k + 1];
+          Z[row * ld + k] = c * x + y * conj(s);
+          Z[row * ld + k + 1] = c * y - x * s;
+        }
+      __syncthreads();
+    }
+  }
+  const int fail = sh->fail;
+  __syncthreads();
+  if (fail) return -1;
+  if (!want_vec) return 0;
+  // --- right eigenvectors of the triangular T by back substitution; column k of
+  // the result replaces column k of Z (T stays in H's upper triangle).
+  double tn = 0.0;
+  for (int e = tid; e < p * p; e += nt) {
+    const int r = e / p, c = e - r * p;
+    if (c >= r) tn = fmax(tn, zabs(H[r * ld + c]));
+  }
+  __shared__ double tmax[32];
+  tn = -block_min(-tn, tmax);
+  const double small = fmax(eps * tn, 1e-300);
+  // Decreasing k: column k of X = Z[:, 0..k] y_k only uses columns <= k of the
+  // original Z, which are untouched when columns are replaced from the right.
+  for (int k = p - 1; k >= 0; --k) {
+    if (tid == 0) {
+      const z64 lk = H[k * ld + k];
+      for (int r = k + 1; r < p; ++r) vec[r] = z64(0.0, 0.0);
+      vec[k] = z64(1.0, 0.0);
+      for (int r = k - 1; r >= 0; --r) {
+        z64 acc(0.0, 0.0);
+        for (int c = r + 1; c <= k; ++c) cfma(acc, H[r * ld + c], vec[c]);
+        z64 den = H[r * ld + r] - lk;
+        if (zabs(den) < small) den = z64(small, 0.0);
+        const double dd = abs2(den);
+        vec[r] = z64(-(acc.re * den.re + acc.im * den.im) / dd,
+                     -(acc.im * den.re - acc.re * den.im) / dd);
+      }
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    z64 xr[4];
+    int cnt = 0;
+    for (int row = tid; row < p; row += nt, ++cnt) {
+      z64 acc(0.0, 0.0);
+      for (int c = 0; c <= k; ++c) cfma(acc, Z[row * ld + c], vec[c]);
+      if (cnt < 4) xr[cnt] = acc;
+      nrm += abs2(acc);
+    }
+    nrm = block_sum(nrm, tmax);
+    const double inv = 1.0 / sqrt(nrm);
+    cnt = 0;
+    for (int row = tid; row < p; row += nt, ++cnt) Z[row * ld + k] = inv * xr[cnt];
+    __syncthreads();
+  }
+  return 0;
+}
+
+}  // namespace bw

@@ -1,0 +1,101 @@
+// Internal launch interface between the host runtime and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace bw {
+
+// Largest n handled by the shared-memory Jacobi path.
+constexpr int SMALL_N_MAX = 32;
+// Largest p handled by the shared-memory loop kernels (Wilson matrix p x p).
+constexpr int LOOP_P_MAX = 64;
+// Distinct translations whose phases are cached in shared memory per k-point.
+constexpr int PHASE_CACHE = 256;
+
+struct StatesArgs {
+  DevModel model;
+  DevPlane plane;       // used when f == nullptr
+  const double* f;      // optional explicit k-points (K x 3)
+  long long K;
+  int p;                // occupied bands
+  int mixed;            // 0: FP64 Jacobi, 1: FP32 Jacobi + FP64 refinement
+  int max_sweeps;
+  double gap_tol;
+  // projected spin operator (optional)
+  DevOp op;             // op.nnz == 0: no spin split
+  int sign;
+  double pso_gap_tol;
+  // outputs
+  z64* U;               // K x n x p_out
+  double* gap;          // K
+  double* pso_evals;    // K x p (optional)
+  double* pso_gap;      // K (optional)
+  DevStatus* status;
+};
+
+struct EighArgs {
+  const z64* H;               // packed
+  const long long* h_off;     // batch: offset of matrix b in z64 units
+  const int* n_per;           // batch
+  const long long* e_off;     // batch: offset into evals (doubles)
+  const long long* v_off;     // batch: offset into evecs (z64)
+  long long batch;
+  int n_vec;
+  int mixed;
+  int max_sweeps;
+  double* evals;
+  z64* evecs;
+  DevStatus* status;
+};
+
+struct BuildArgs {
+  DevModel model;
+  const double* f;  // K x 3
+  long long K;
+  int complex64;
+  void* H;
+};
+
+struct LoopArgs {
+  const z64* U;          // K x n x p
+  z64* M;                // K x p x p (overlap scratch)
+  int n, p, N, N_t;
+  int unitarise;
+  int max_sweeps;
+  const double* gap;     // K (optional)
+  const double* pso_gap; // K (optional)
+  double* phases;        // N_t x p
+  double* min_gap;       // N_t (optional)
+  double* min_pso_gap;   // N_t (optional)
+  // nested
+  int nested;
+  double cut;
+  int first, m;
+  double wannier_gap_tol;
+  z64* w;                // N x N_t x n x m
+  double* min_wannier_gap;  // N_t (optional)
+  double* nested_out;    // N x m
+  DevStatus* status;
+};
+
+// Raises a kernel's dynamic shared-memory limit only when a launch needs more than
+// any earlier one (so repeated and captured launches make no attribute call).
+template <typename Kern>
+inline cudaError_t set_smem_once(Kern kernel, size_t bytes, size_t& cached) {
+  if (bytes <= cached) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) cached = bytes;
+  return e;
+}
+
+cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
+cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);
+cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s);
+cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s);
+
+}  // namespace bw

@@ -1,0 +1,384 @@
+// Loop kernels: overlaps, ordered products and eigenphases (Eq. 2), and the nested
+// loop over Wannier states (Eq. 8).
+//
+//  - k_overlaps: M_j = U(k_{j+1})^dagger U(k_j) for every k-point of the plane, the
+//                loop closing on j = 0 (optionally replaced by its unitary polar
+//                factor).
+//  - k_loops:    one CTA per transverse index: W = M_{N-1} ... M_0 (later k on the
+//                left), general complex eigenvalues, theta = arg(lambda) ascending.
+//                For the nested loop also the right eigenvectors nu of the chosen
+//                sector, carried along the loop by nu_{j+1} = M_j nu_j (the loop
+//                based at k_{j+1} is M_j W_j M_j^{-1}), orthonormalised, and the
+//                Wannier states w = U(k_j) nu_j.
+//  - k_nested:   one CTA per base point: product of w(i+1)^dagger w(i) along the
+//                transverse direction (closed on i = 0) and its eigenphases.
+#include <float.h>
+
+#include "geig.cuh"
+#include "jacobi.cuh"
+#include "launch.h"
+
+namespace bw {
+
+__device__ __forceinline__ double phase_of(z64 z) { return atan2(z.im, z.re); }
+
+// Ranks th[0..p) ascending (stable) into ord.
+__device__ void rank_sort(const double* th, int p, int* ord) {
+  for (int a = threadIdx.x; a < p; a += blockDim.x) {
+    int rank = 0;
+    const double x = th[a];
+    for (int b = 0; b < p; ++b) rank += (th[b] < x) || (th[b] == x && b < a);
+    ord[rank] = a;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Overlaps
+// ---------------------------------------------------------------------------
+__global__ void k_overlaps(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
+  const long long K = (long long)N * a.N_t;
+  z64* Ms = reinterpret_cast<z64*>(smem);            // p x p
+  z64* P = Ms + p * p;                               // p x p
+  z64* Vp = P + p * p;                               // p x p
+  z64* Tp = Vp + p * p;                              // p x p
+  JacRot<double>* rot = reinterpret_cast<JacRot<double>*>(Tp + p * p);
+  double* red = reinterpret_cast<double*>(rot + (p / 2 + 2));
+  for (long long k = blockIdx.x; k < K; k += gridDim.x) {
+    const int i = int(k / N), j = int(k - (long long)i * N);
+    const long long kn = (long long)i * N + (j + 1 == N ? 0 : j + 1);
+    const z64* Uh = a.U + k * (long long)n * p;
+    const z64* Un = a.U + kn * (long long)n * p;
+    z64* M = a.M + k * (long long)p * p;
+    if (!a.unitarise) {
+      for (int e = tid; e < p * p; e += nt) {
+        const int r = e / p, c = e - r * p;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < n; ++q) cfma_conj(acc, Un[q * p + r], Uh[q * p + c]);
+        M[e] = acc;
+      }
+      continue;
+    }
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < n; ++q) cfma_conj(acc, Un[q * p + r], Uh[q * p + c]);
+      Ms[e] = acc;
+    }
+    __syncthreads();
+    // polar factor: M (M^dagger M)^{-1/2} = M V diag(1/sigma) V^dagger
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) cfma_conj(acc, Ms[q * p + r], Ms[q * p + c]);
+      P[e] = (r == c) ? z64(acc.re, 0.0) : acc;
+    }
+    __syncthreads();
+    const int sw = jacobi_eigh<double>(P, Vp, p, p, a.max_sweeps, rot, red);
+    if (sw < 0 && tid == 0) report(a.status, ST_ENOCONV, k, 0.0);
+    // P <- V diag(1/sigma) V^dagger (sigma^2 on P's diagonal)
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) {
+        const double s2 = P[q * p + q].re;
+        const double w = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+        const z64 v = Vp[r * p + q] * conj(Vp[c * p + q]);
+        acc = acc + w * v;
+      }
+      Tp[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) cfma(acc, Ms[r * p + q], Tp[q * p + c]);
+      M[e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-loop product, eigenphases and (nested) Wannier states
+// ---------------------------------------------------------------------------
+struct LoopSmem {
+  size_t X, Y, G, lam, vec, th, key, ord, sh, red, total;
+};
+
+__host__ __device__ inline LoopSmem loop_layout(int p, int m) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  LoopSmem L;
+  size_t o = 0;
+  L.X = o; o = al(o + size_t(p) * p * sizeof(z64));
+  L.Y = o; o = al(o + size_t(p) * p * sizeof(z64));
+  L.G = o; o = al(o + size_t(m) * m * sizeof(z64));
+  L.lam = o; o = al(o + size_t(p) * sizeof(z64));
+  L.vec = o; o = al(o + size_t(p) * sizeof(z64));
+  L.th = o; o = al(o + size_t(p) * sizeof(double));
+  L.key = o; o = al(o + size_t(p) * sizeof(double));
+  L.ord = o; o = al(o + size_t(p) * sizeof(int));
+  L.sh = o; o = al(o + sizeof(GeigShared));
+  L.red = o; o = al(o + 64 * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+// One Cholesky-QR pass on nu (p x m) with Gram scratch G (m x m).
+__device__ void cholqr_small(z64* nu, z64* G, int p, int m, int* flag) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int a = e / m, b = e - a * m;
+    z64 acc(0.0, 0.0);
+    for (int r = 0; r < p; ++r) cfma_conj(acc, nu[r * m + a], nu[r * m + b]);
+    G[e] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    for (int j = 0; j < m && ok; ++j) {
+      double d = G[j * m + j].re;
+      for (int k = 0; k < j; ++k) d -= abs2(G[j * m + k]);
+      if (!(d > 0.0)) { ok = 0; break; }
+      d = sqrt(d);
+      G[j * m + j] = z64(d, 0.0);
+      for (int i = j + 1; i < m; ++i) {
+        z64 s = G[i * m + j];
+        for (int k = 0; k < j; ++k) s = s - G[i * m + k] * conj(G[j * m + k]);
+        G[i * m + j] = (1.0 / d) * s;
+      }
+    }
+    *flag = ok;
+  }
+  __syncthreads();
+  if (!*flag) return;
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    z64* q = nu + r * m;
+    for (int j = 0; j < m; ++j) {
+      z64 y = conj(q[j]);
+      for (int k = 0; k < j; ++k) y = y - G[j * m + k] * conj(q[k]);
+      q[j] = conj((1.0 / G[j * m + j].re) * y);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_loops(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
+  const int m = a.nested ? a.m : 1;
+  const LoopSmem L = loop_layout(p, m);
+  z64* X = reinterpret_cast<z64*>(smem + L.X);
+  z64* Y = reinterpret_cast<z64*>(smem + L.Y);
+  z64* G = reinterpret_cast<z64*>(smem + L.G);
+  z64* lam = reinterpret_cast<z64*>(smem + L.lam);
+  z64* vec = reinterpret_cast<z64*>(smem + L.vec);
+  double* th = reinterpret_cast<double*>(smem + L.th);
+  double* key = reinterpret_cast<double*>(smem + L.key);
+  int* ord = reinterpret_cast<int*>(smem + L.ord);
+  GeigShared* sh = reinterpret_cast<GeigShared*>(smem + L.sh);
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  int* flag = reinterpret_cast<int*>(red + 40);
+
+  for (int i = blockIdx.x; i < a.N_t; i += gridDim.x) {
+    const long long k0 = (long long)i * N;
+    // minimum gaps along the loop
+    if (a.min_gap || a.min_pso_gap) {
+      double g = INFINITY, gp = INFINITY;
+      for (int j = tid; j < N; j += nt) {
+        if (a.gap) g = fmin(g, a.gap[k0 + j]);
+        if (a.pso_gap) gp = fmin(gp, a.pso_gap[k0 + j]);
+      }
+      g = block_min(g, red);
+      gp = block_min(gp, red);
+      if (tid == 0) {
+        if (a.min_gap) a.min_gap[i] = g;
+        if (a.min_pso_gap) a.min_pso_gap[i] = gp;
+      }
+    }
+    // W = M_{N-1} ... M_0
+    z64* W = X;
+    z64* T = Y;
+    for (int e = tid; e < p * p; e += nt) {
+      const int r = e / p, c = e - r * p;
+      W[e] = z64(double(r == c), 0.0);
+    }
+    __syncthreads();
+    for (int j = 0; j < N; ++j) {
+      const z64* M = a.M + (k0 + j) * (long long)p * p;
+      for (int e = tid; e < p * p; e += nt) {
+        const int r = e / p, c = e - r * p;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < p; ++q) cfma(acc, M[r * p + q], W[q * p + c]);
+        T[e] = acc;
+      }
+      __syncthreads();
+      z64* t = W; W = T; T = t;
+    }
+    // eigen-decomposition (vectors for the nested loop); Z goes to T
+    const int rc = geig(W, T, p, p, a.nested != 0, lam, vec, sh);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+    for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
+    __syncthreads();
+    rank_sort(th, p, ord);
+    for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
+    if (!a.nested) {
+      __syncthreads();
+      continue;
+    }
+    // sector: phases measured from `cut`, ascending (stable in eigenvalue index)
+    const double two_pi = 6.283185307179586;
+    for (int c = tid; c < p; c += nt) {
+      double x = fmod(th[c] - a.cut, two_pi);
+      if (x < 0.0) x += two_pi;
+      if (x >= two_pi) x = 0.0;
+      key[c] = x;
+    }
+    __syncthreads();
+    rank_sort(key, p, ord);
+    // Wannier gap: circular distance between sector and rest
+    double wg = INFINITY;
+    for (int e = tid; e < p * p; e += nt) {
+      const int s = e / p, r = e - s * p;
+      const bool in_s = s >= a.first && s < a.first + m;
+      const bool in_r = !(r >= a.first && r < a.first + m);
+      if (in_s && in_r) {
+        double d = fabs(th[ord[s]] - th[ord[r]]);
+        d = fmod(d, two_pi);
+        d = fmin(d, two_pi - d);
+        wg = fmin(wg, d);
+      }
+    }
+    wg = block_min(wg, red);
+    if (tid == 0) {
+      if (a.min_wannier_gap) a.min_wannier_gap[i] = wg;
+      if (!(wg > a.wannier_gap_tol)) report(a.status, ST_EWANGAP, k0, wg);
+    }
+    // nu_0 = Z[:, sector] -> X (W no longer needed), transport with Y as scratch
+    z64* nu = (W == X) ? X : Y;
+    z64* Zm = (W == X) ? Y : X;
+    for (int e = tid; e < p * m; e += nt) {
+      const int r = e / m, c = e - r * m;
+      nu[e] = Zm[r * p + ord[a.first + c]];
+    }
+    __syncthreads();
+    z64* nx = Zm;  // scratch for nu_{j+1}
+    for (int j = 0; j < N; ++j) {
+      cholqr_small(nu, G, p, m, flag);
+      cholqr_small(nu, G, p, m, flag);
+      const z64* Uk = a.U + (k0 + j) * (long long)n * p;
+      z64* w = a.w + ((long long)j * a.N_t + i) * (long long)n * m;
+      for (int e = tid; e < n * m; e += nt) {
+        const int r = e / m, c = e - r * m;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < p; ++q) cfma(acc, Uk[r * p + q], nu[q * m + c]);
+        w[e] = acc;
+      }
+      const z64* M = a.M + (k0 + j) * (long long)p * p;
+      for (int e = tid; e < p * m; e += nt) {
+        const int r = e / m, c = e - r * m;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < p; ++q) cfma(acc, M[r * p + q], nu[q * m + c]);
+        nx[e] = acc;
+      }
+      __syncthreads();
+      z64* t = nu; nu = nx; nx = t;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Nested loop per base point
+// ---------------------------------------------------------------------------
+__global__ void k_nested(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, m = a.m, Nt = a.N_t, tid = threadIdx.x, nt = blockDim.x;
+  const LoopSmem L = loop_layout(m, 1);
+  z64* W = reinterpret_cast<z64*>(smem + L.X);
+  z64* T = reinterpret_cast<z64*>(smem + L.Y);
+  z64* lam = reinterpret_cast<z64*>(smem + L.lam);
+  z64* vec = reinterpret_cast<z64*>(smem + L.vec);
+  double* th = reinterpret_cast<double*>(smem + L.th);
+  int* ord = reinterpret_cast<int*>(smem + L.ord);
+  GeigShared* sh = reinterpret_cast<GeigShared*>(smem + L.sh);
+  z64* Mt = reinterpret_cast<z64*>(smem + L.total);  // m x m after the layout
+  for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = e / m, c = e - r * m;
+      W[e] = z64(double(r == c), 0.0);
+    }
+    __syncthreads();
+    const z64* wj = a.w + (long long)j * Nt * n * m;
+    for (int i = 0; i < Nt; ++i) {
+      const z64* wa = wj + (long long)i * n * m;
+      const z64* wb = wj + (long long)(i + 1 == Nt ? 0 : i + 1) * n * m;
+      for (int e = tid; e < m * m; e += nt) {
+        const int r = e / m, c = e - r * m;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q * m + r], wa[q * m + c]);
+        Mt[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {
+        const int r = e / m, c = e - r * m;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < m; ++q) cfma(acc, Mt[r * m + q], W[q * m + c]);
+        T[e] = acc;
+      }
+      __syncthreads();
+      z64* t = W; W = T; T = t;
+    }
+    const int rc = geig(W, T, m, m, false, lam, vec, sh);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, j, 0.0);
+    for (int c = tid; c < m; c += nt) th[c] = phase_of(lam[c]);
+    __syncthreads();
+    rank_sort(th, m, ord);
+    for (int c = tid; c < m; c += nt) a.nested_out[(long long)j * m + c] = th[ord[c]];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int loop_threads(int p) { return p <= 4 ? 32 : (p <= 16 ? 64 : 128); }
+
+cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
+  const long long K = (long long)a.N * a.N_t;
+  if (K <= 0) return cudaSuccess;
+  const size_t sm = a.unitarise ? (4 * size_t(a.p) * a.p * sizeof(z64) +
+                                   (a.p / 2 + 2) * sizeof(JacRot<double>) + 64 * sizeof(double))
+                                : 0;
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_overlaps, sm, cached);
+  if (e != cudaSuccess) return e;
+  const long long cap = 152LL * 32;
+  const int grid = int(K < cap ? K : cap);
+  k_overlaps<<<grid, loop_threads(a.p), sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
+  if (a.N_t <= 0) return cudaSuccess;
+  const LoopSmem L = loop_layout(a.p, a.nested ? a.m : 1);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_loops, L.total, cached);
+  if (e != cudaSuccess) return e;
+  k_loops<<<a.N_t, loop_threads(a.p), L.total, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  const LoopSmem L = loop_layout(a.m, 1);
+  const size_t sm = L.total + size_t(a.m) * a.m * sizeof(z64);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_nested, sm, cached);
+  if (e != cudaSuccess) return e;
+  k_nested<<<a.N, loop_threads(a.m), sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bw

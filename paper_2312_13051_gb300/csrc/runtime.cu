@@ -1,0 +1,707 @@
+// Host runtime of the C ABI: context, scratch arena, hopping-list plans, entry points.
+//
+// A hopping list arrives as host arrays and is turned into a device plan: the
+// distinct translations R (their phases are evaluated once per k-point), and the
+// distinct (row, col) entries of H, each owning the hoppings that sum into it.
+// The plan groups duplicate (i, j, R) hoppings, and rejects lists for which
+// H(f) would not be Hermitian (every (i, j, R) must match (j, i, -R) conjugated).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/berrywl.h"
+#include "launch.h"
+
+using bw::z64;
+
+struct bw_ctx {
+  int device = 0;
+  size_t budget = 0;
+  char* arena = nullptr;
+  size_t arena_cap = 0;
+  size_t arena_off = 0;
+  bw::DevStatus* status = nullptr;
+  char* staging = nullptr;
+  size_t staging_cap = 0;
+  cudaEvent_t upload_ev = nullptr;
+  bool upload_pending = false;
+  cudaEvent_t done_ev = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool have_last = false;
+  std::string err;
+  // per-kernel timing (bw_set_profiling)
+  bool prof = false;
+  int prof_n = 0;
+  const char* prof_names[8] = {};
+  cudaEvent_t prof_ev[9] = {};
+};
+
+namespace {
+
+bw_status fail(bw_ctx* c, bw_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+bw_status cuda_fail(bw_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, BW_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define BW_CUDA(call, where)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Host blob whose segments are copied to the device in one transfer.
+struct Blob {
+  std::vector<char> data;
+  size_t add(const void* src, size_t bytes) {
+    const size_t off = al256(data.size());
+    data.resize(off + std::max<size_t>(bytes, 1));
+    if (bytes) std::memcpy(data.data() + off, src, bytes);
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
+};
+
+struct HostPlan {
+  int n = 0, n_R = 0, n_ent = 0;
+  std::vector<int> Rv, ent_row, ent_col, ent_start, hop_r;
+  std::vector<z64> hop_t;
+  double tmax = 0.0;
+  size_t o_Rv, o_row, o_col, o_start, o_r, o_t;
+};
+
+bw_status make_plan(bw_ctx* ctx, const bw_model* m, HostPlan& P) {
+  if (!m) return fail(ctx, BW_EINVAL, "model is NULL");
+  if (m->n < 1) return fail(ctx, BW_EINVAL, "model.n = %d < 1", m->n);
+  if (m->nnz < 0 || m->nnz > (int64_t(1) << 31) - 2)
+    return fail(ctx, BW_EINVAL, "model.nnz = %lld out of range", (long long)m->nnz);
+  const int64_t nnz = m->nnz;
+  if (nnz > 0 && (!m->R || !m->i || !m->j || !m->t))
+    return fail(ctx, BW_EINVAL, "model arrays are NULL");
+  const int n = m->n;
+  P.n = n;
+  for (int64_t e = 0; e < nnz; ++e) {
+    if (m->i[e] < 0 || m->i[e] >= n || m->j[e] < 0 || m->j[e] >= n)
+      return fail(ctx, BW_EINVAL, "hopping %lld has orbital index out of [0, %d)", (long long)e, n);
+    if (!std::isfinite(m->t[e].re) || !std::isfinite(m->t[e].im))
+      return fail(ctx, BW_EINVAL, "hopping %lld has a non-finite amplitude", (long long)e);
+    P.tmax = std::max(P.tmax, std::hypot(m->t[e].re, m->t[e].im));
+  }
+  // distinct translations
+  std::vector<std::array<int, 3>> Rs(nnz);
+  for (int64_t e = 0; e < nnz; ++e) Rs[e] = {m->R[3 * e], m->R[3 * e + 1], m->R[3 * e + 2]};
+  std::vector<std::array<int, 3>> U(Rs);
+  std::sort(U.begin(), U.end());
+  U.erase(std::unique(U.begin(), U.end()), U.end());
+  P.n_R = int(U.size());
+  P.Rv.resize(3 * U.size());
+  for (size_t r = 0; r < U.size(); ++r)
+    for (int d = 0; d < 3; ++d) P.Rv[3 * r + d] = U[r][d];
+  auto rid = [&](const std::array<int, 3>& R) -> int {
+    auto it = std::lower_bound(U.begin(), U.end(), R);
+    return (it != U.end() && *it == R) ? int(it - U.begin()) : -1;
+  };
+  std::vector<int> hr(nnz);
+  for (int64_t e = 0; e < nnz; ++e) hr[e] = rid(Rs[e]);
+  // group hoppings by (i, j, r), summing duplicates, in a deterministic order
+  std::vector<int64_t> idx(nnz);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    if (m->i[a] != m->i[b]) return m->i[a] < m->i[b];
+    if (m->j[a] != m->j[b]) return m->j[a] < m->j[b];
+    if (hr[a] != hr[b]) return hr[a] < hr[b];
+    return a < b;
+  });
+  struct Grp { int i, j, r; z64 t; };
+  std::vector<Grp> g;
+  for (int64_t q = 0; q < nnz; ++q) {
+    const int64_t e = idx[q];
+    const z64 t(m->t[e].re, m->t[e].im);
+    if (!g.empty() && g.back().i == m->i[e] && g.back().j == m->j[e] && g.back().r == hr[e])
+      g.back().t = g.back().t + t;
+    else
+      g.push_back({m->i[e], m->j[e], hr[e], t});
+  }
+  // Hermiticity: t(i, j, R) = conj t(j, i, -R)
+  const double tol = 1e-12 * std::max(1.0, P.tmax);
+  auto find = [&](int i, int j, int r) -> const Grp* {
+    auto it = std::lower_bound(g.begin(), g.end(), Grp{i, j, r, z64(0, 0)}, [](const Grp& a, const Grp& b) {
+      if (a.i != b.i) return a.i < b.i;
+      if (a.j != b.j) return a.j < b.j;
+      return a.r < b.r;
+    });
+    return (it != g.end() && it->i == i && it->j == j && it->r == r) ? &*it : nullptr;
+  };
+  for (const Grp& x : g) {
+    const std::array<int, 3>& R = U[x.r];
+    const int rn = rid({-R[0], -R[1], -R[2]});
+    const Grp* y = rn >= 0 ? find(x.j, x.i, rn) : nullptr;
+    const z64 yt = y ? y->t : z64(0.0, 0.0);
+    if (std::hypot(x.t.re - yt.re, x.t.im + yt.im) > tol)
+      return fail(ctx, BW_EINVAL,
+                  "hopping list is not Hermitian: (i=%d, j=%d, R=(%d,%d,%d)) has no conjugate partner",
+                  x.i, x.j, R[0], R[1], R[2]);
+  }
+  // entries
+  for (size_t q = 0; q < g.size(); ++q) {
+    if (q == 0 || g[q].i != g[q - 1].i || g[q].j != g[q - 1].j) {
+      P.ent_row.push_back(g[q].i);
+      P.ent_col.push_back(g[q].j);
+      P.ent_start.push_back(int(q));
+    }
+    P.hop_r.push_back(g[q].r);
+    P.hop_t.push_back(g[q].t);
+  }
+  P.ent_start.push_back(int(g.size()));
+  P.n_ent = int(P.ent_row.size());
+  return BW_OK;
+}
+
+void plan_to_blob(HostPlan& P, Blob& b) {
+  P.o_Rv = b.add(P.Rv);
+  P.o_row = b.add(P.ent_row);
+  P.o_col = b.add(P.ent_col);
+  P.o_start = b.add(P.ent_start);
+  P.o_r = b.add(P.hop_r);
+  P.o_t = b.add(P.hop_t);
+}
+
+bw::DevModel dev_model(const HostPlan& P, const char* base) {
+  bw::DevModel d;
+  d.n = P.n;
+  d.n_R = P.n_R;
+  d.n_ent = P.n_ent;
+  d.Rv = reinterpret_cast<const int*>(base + P.o_Rv);
+  d.ent_row = reinterpret_cast<const int*>(base + P.o_row);
+  d.ent_col = reinterpret_cast<const int*>(base + P.o_col);
+  d.ent_start = reinterpret_cast<const int*>(base + P.o_start);
+  d.hop_r = reinterpret_cast<const int*>(base + P.o_r);
+  d.hop_t = reinterpret_cast<const z64*>(base + P.o_t);
+  return d;
+}
+
+struct HostOp {
+  std::vector<int> row, col;
+  std::vector<z64> val;
+  size_t o_row, o_col, o_val;
+};
+
+bw_status make_op(bw_ctx* ctx, const bw_c128* S, int n, HostOp& op) {
+  if (!S) return fail(ctx, BW_EINVAL, "spin operator is NULL");
+  double smax = 0.0;
+  for (int64_t e = 0; e < int64_t(n) * n; ++e) smax = std::max(smax, std::hypot(S[e].re, S[e].im));
+  const double tol = 1e-12 * std::max(1.0, smax);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const bw_c128 a = S[int64_t(r) * n + c], b = S[int64_t(c) * n + r];
+      if (!std::isfinite(a.re) || !std::isfinite(a.im))
+        return fail(ctx, BW_EINVAL, "spin operator has a non-finite entry");
+      if (std::hypot(a.re - b.re, a.im + b.im) > tol)
+        return fail(ctx, BW_EINVAL, "spin operator is not Hermitian at (%d, %d)", r, c);
+      if (a.re != 0.0 || a.im != 0.0) {
+        op.row.push_back(r);
+        op.col.push_back(c);
+        op.val.push_back(z64(a.re, a.im));
+      }
+    }
+  if (op.val.empty()) return fail(ctx, BW_EINVAL, "spin operator is zero");
+  return BW_OK;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st == cudaStreamCaptureStatusActive;
+}
+
+// Orders this call after the previous one when the stream changes.  Under stream
+// capture nothing is waited on or recorded: the caller orders the captured graph.
+void begin_call(bw_ctx* ctx, cudaStream_t s) {
+  cudaSetDevice(ctx->device);
+  if (!capturing(s) && ctx->have_last && ctx->last_stream != s)
+    cudaStreamWaitEvent(s, ctx->done_ev, 0);
+  ctx->arena_off = 0;
+  ctx->prof_n = 0;
+}
+
+void end_call(bw_ctx* ctx, cudaStream_t s) {
+  if (capturing(s)) return;
+  cudaEventRecord(ctx->done_ev, s);
+  ctx->last_stream = s;
+  ctx->have_last = true;
+}
+
+// Timing marks around kernel launches (recorded as external events under capture,
+// so that replays of a captured graph can be timed too).
+void prof_mark(bw_ctx* ctx, cudaStream_t s, const char* name) {
+  if (!ctx->prof || ctx->prof_n >= 8) return;
+  const int i = ctx->prof_n;
+  if (!ctx->prof_ev[0])
+    for (auto& e : ctx->prof_ev) cudaEventCreate(&e);
+  ctx->prof_names[i] = name;
+  cudaEventRecordWithFlags(ctx->prof_ev[i + 1], s, capturing(s) ? cudaEventRecordExternal : 0);
+  ctx->prof_n = i + 1;
+}
+
+// Records the start mark before the first kernel of a call.
+void prof_start(bw_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prof) return;
+  if (!ctx->prof_ev[0])
+    for (auto& e : ctx->prof_ev) cudaEventCreate(&e);
+  cudaEventRecordWithFlags(ctx->prof_ev[0], s, capturing(s) ? cudaEventRecordExternal : 0);
+}
+
+// Makes sure the arena holds `bytes`; growing it waits for outstanding work.
+bw_status reserve(bw_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes > ctx->budget)
+    return fail(ctx, BW_ENOMEM, "call needs %zu bytes of scratch, budget is %zu", bytes, ctx->budget);
+  if (bytes <= ctx->arena_cap) return BW_OK;
+  if (capturing(s))
+    return fail(ctx, BW_EINVAL, "scratch arena must grow during stream capture: run the call once "
+                "uncaptured first");
+  BW_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (ctx->have_last) BW_CUDA(cudaStreamSynchronize(ctx->last_stream), "cudaStreamSynchronize");
+  if (ctx->arena) cudaFree(ctx->arena);
+  ctx->arena = nullptr;
+  ctx->arena_cap = 0;
+  size_t cap = std::min(ctx->budget, std::max(bytes + bytes / 4, size_t(64) << 20));
+  cudaError_t e = cudaMalloc(&ctx->arena, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", cap, cudaGetErrorString(e));
+  }
+  ctx->arena_cap = cap;
+  return BW_OK;
+}
+
+char* carve(bw_ctx* ctx, size_t bytes) {
+  const size_t off = al256(ctx->arena_off);
+  ctx->arena_off = off + al256(std::max<size_t>(bytes, 1));
+  return ctx->arena + off;
+}
+
+// Copies the blob to `dst` on stream s through the pinned staging buffer.
+bw_status upload(bw_ctx* ctx, const Blob& b, char* dst, cudaStream_t s) {
+  const size_t bytes = b.data.size();
+  if (!bytes) return BW_OK;
+  const bool cap = capturing(s);
+  if (ctx->upload_pending && !cap) {
+    BW_CUDA(cudaEventSynchronize(ctx->upload_ev), "cudaEventSynchronize");
+    ctx->upload_pending = false;
+  }
+  if (bytes > ctx->staging_cap) {
+    if (cap)
+      return fail(ctx, BW_EINVAL, "staging buffer must grow during stream capture: run the call "
+                  "once uncaptured first");
+    if (ctx->staging) cudaFreeHost(ctx->staging);
+    ctx->staging = nullptr;
+    ctx->staging_cap = 0;
+    const size_t cap = std::max(bytes, size_t(1) << 20);
+    BW_CUDA(cudaMallocHost(&ctx->staging, cap), "cudaMallocHost");
+    ctx->staging_cap = cap;
+  }
+  std::memcpy(ctx->staging, b.data.data(), bytes);
+  BW_CUDA(cudaMemcpyAsync(dst, ctx->staging, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+  if (!cap) {
+    BW_CUDA(cudaEventRecord(ctx->upload_ev, s), "cudaEventRecord");
+    ctx->upload_pending = true;
+  }
+  return BW_OK;
+}
+
+struct Opts {
+  double gap_tol, pso_gap_tol, wannier_gap_tol;
+  int unitarise, max_sweeps;
+};
+
+Opts resolve_opts(const bw_opts* o, double tmax) {
+  Opts r;
+  r.gap_tol = (o && o->gap_tol >= 0.0) ? o->gap_tol : 1e-6 * std::max(1.0, tmax);
+  r.pso_gap_tol = (o && o->pso_gap_tol >= 0.0) ? o->pso_gap_tol : 1e-6;
+  r.wannier_gap_tol = (o && o->wannier_gap_tol >= 0.0) ? o->wannier_gap_tol : 1e-6;
+  r.unitarise = o ? o->unitarise : 0;
+  r.max_sweeps = (o && o->max_sweeps > 0) ? o->max_sweeps : 30;
+  return r;
+}
+
+bw_status check_plane(bw_ctx* ctx, const bw_plane* pl, bool nested) {
+  if (!pl) return fail(ctx, BW_EINVAL, "plane is NULL");
+  if (pl->N < 1 || pl->N_t < 1) return fail(ctx, BW_EINVAL, "plane needs N >= 1 and N_t >= 1");
+  if (int64_t(pl->N) * pl->N_t > (int64_t(1) << 31))
+    return fail(ctx, BW_EINVAL, "plane has too many k-points");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(pl->origin[d]) || !std::isfinite(pl->trans_dir[d]))
+      return fail(ctx, BW_EINVAL, "plane has non-finite coordinates");
+  if (nested)
+    for (int d = 0; d < 3; ++d)
+      if (pl->trans_dir[d] != std::round(pl->trans_dir[d]))
+        return fail(ctx, BW_EINVAL, "nested loop needs an integer trans_dir to close");
+  return BW_OK;
+}
+
+bw::DevPlane dev_plane(const bw_plane* pl) {
+  bw::DevPlane d;
+  for (int k = 0; k < 3; ++k) {
+    d.origin[k] = pl->origin[k];
+    d.loop_dir[k] = double(pl->loop_dir[k]);
+    d.trans_dir[k] = pl->trans_dir[k];
+  }
+  d.N = pl->N;
+  d.N_t = pl->N_t;
+  return d;
+}
+
+// Shared driver of the three loop entry points.
+enum class LoopKind { Plain, Nested, Spin };
+
+bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_plane* plane,
+                   int p, bw_precision prec, const bw_opts* opts, const bw_c128* spin_op,
+                   int sign, double cut, int first, int m, double* phases, double* min_gap,
+                   double* nested_out, double* min_wgap, double* pso_evals, double* min_pso_gap,
+                   cudaStream_t s) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  bw_status st = check_plane(ctx, plane, kind == LoopKind::Nested);
+  if (st) return st;
+  if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
+  if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
+  HostPlan P;
+  if ((st = make_plan(ctx, model, P))) return st;
+  const int n = P.n;
+  if (p < 1 || p > n) return fail(ctx, BW_EINVAL, "need 1 <= p <= n (p = %d, n = %d)", p, n);
+  if (n > bw::SMALL_N_MAX)
+    return fail(ctx, BW_EINVAL, "n = %d exceeds the largest supported size %d", n, bw::SMALL_N_MAX);
+  int p_eff = p;
+  HostOp op;
+  if (kind == LoopKind::Spin) {
+    if (p % 2) return fail(ctx, BW_EINVAL, "spin-resolved loop needs an even p (p = %d)", p);
+    if (sign != -1 && sign != 1) return fail(ctx, BW_EINVAL, "sign must be -1 or +1");
+    if ((st = make_op(ctx, spin_op, n, op))) return st;
+    p_eff = p / 2;
+  }
+  if (kind == LoopKind::Nested) {
+    if (!nested_out) return fail(ctx, BW_EINVAL, "nested output is NULL");
+    if (m < 1 || first < 0 || first + m > p)
+      return fail(ctx, BW_EINVAL, "nested sector [first, first+m) = [%d, %d) outside [0, %d)", first,
+                  first + m, p);
+    if (!std::isfinite(cut)) return fail(ctx, BW_EINVAL, "cut is not finite");
+  }
+  if (p_eff > bw::LOOP_P_MAX) return fail(ctx, BW_EINVAL, "p = %d exceeds %d", p_eff, bw::LOOP_P_MAX);
+  const Opts o = resolve_opts(opts, P.tmax);
+  if (o.unitarise && p_eff > 32) return fail(ctx, BW_EINVAL, "unitarise supports p <= 32");
+  const long long K = (long long)plane->N * plane->N_t;
+  Blob blob;
+  plan_to_blob(P, blob);
+  if (kind == LoopKind::Spin) {
+    op.o_row = blob.add(op.row);
+    op.o_col = blob.add(op.col);
+    op.o_val = blob.add(op.val);
+  }
+  const size_t bU = al256(size_t(K) * n * p_eff * sizeof(z64));
+  const size_t bGap = al256(size_t(K) * sizeof(double));
+  const size_t bM = al256(size_t(K) * p_eff * p_eff * sizeof(z64));
+  const size_t bW = kind == LoopKind::Nested ? al256(size_t(K) * n * m * sizeof(z64)) : 0;
+  const size_t bPso = kind == LoopKind::Spin ? al256(size_t(K) * sizeof(double)) : 0;
+  const size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bPso + 4096;
+  begin_call(ctx, s);
+  if ((st = reserve(ctx, total, s))) return st;
+  char* dblob = carve(ctx, blob.data.size());
+  z64* U = reinterpret_cast<z64*>(carve(ctx, bU));
+  double* gap = reinterpret_cast<double*>(carve(ctx, bGap));
+  z64* M = reinterpret_cast<z64*>(carve(ctx, bM));
+  z64* w = bW ? reinterpret_cast<z64*>(carve(ctx, bW)) : nullptr;
+  double* psog = bPso ? reinterpret_cast<double*>(carve(ctx, bPso)) : nullptr;
+  if ((st = upload(ctx, blob, dblob, s))) return st;
+
+  bw::StatesArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.model = dev_model(P, dblob);
+  sa.plane = dev_plane(plane);
+  sa.f = nullptr;
+  sa.K = K;
+  sa.p = p;
+  sa.mixed = prec == BW_MIXED;
+  sa.max_sweeps = o.max_sweeps;
+  sa.gap_tol = o.gap_tol;
+  sa.op.nnz = 0;
+  if (kind == LoopKind::Spin) {
+    sa.op.nnz = int(op.val.size());
+    sa.op.row = reinterpret_cast<const int*>(dblob + op.o_row);
+    sa.op.col = reinterpret_cast<const int*>(dblob + op.o_col);
+    sa.op.val = reinterpret_cast<const z64*>(dblob + op.o_val);
+    sa.sign = sign;
+    sa.pso_gap_tol = o.pso_gap_tol;
+    sa.pso_evals = pso_evals;
+    sa.pso_gap = psog;
+  }
+  sa.U = U;
+  sa.gap = gap;
+  sa.status = ctx->status;
+  prof_start(ctx, s);
+  BW_CUDA(bw::launch_states_small(sa, p_eff, s), "states kernel");
+  prof_mark(ctx, s, "states");
+
+  bw::LoopArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.U = U;
+  la.M = M;
+  la.n = n;
+  la.p = p_eff;
+  la.N = plane->N;
+  la.N_t = plane->N_t;
+  la.unitarise = o.unitarise;
+  la.max_sweeps = o.max_sweeps;
+  la.gap = gap;
+  la.pso_gap = psog;
+  la.phases = phases;
+  la.min_gap = min_gap;
+  la.min_pso_gap = min_pso_gap;
+  la.status = ctx->status;
+  if (kind == LoopKind::Nested) {
+    la.nested = 1;
+    la.cut = cut;
+    la.first = first;
+    la.m = m;
+    la.wannier_gap_tol = o.wannier_gap_tol;
+    la.w = w;
+    la.min_wannier_gap = min_wgap;
+    la.nested_out = nested_out;
+  }
+  BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
+  prof_mark(ctx, s, "overlaps");
+  BW_CUDA(bw::launch_loops(la, s), "loop kernel");
+  prof_mark(ctx, s, "loops");
+  if (kind == LoopKind::Nested) {
+    BW_CUDA(bw::launch_nested(la, s), "nested kernel");
+    prof_mark(ctx, s, "nested");
+  }
+  end_call(ctx, s);
+  return BW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bw_status bw_create(bw_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return BW_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return BW_ECUDA;
+  }
+  if (device < 0 || device >= count) return BW_EINVAL;
+  bw_ctx* ctx = new bw_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(bw::DevStatus));
+  if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(bw::DevStatus));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->upload_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
+  size_t fr = 0, tot = 0;
+  if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
+  if (e != cudaSuccess) {
+    bw_destroy(ctx);
+    return BW_ECUDA;
+  }
+  ctx->budget = mem_budget_bytes ? mem_budget_bytes : size_t(0.9 * double(fr));
+  *out = ctx;
+  return BW_OK;
+}
+
+void bw_destroy(bw_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->status) cudaFree(ctx->status);
+  if (ctx->staging) cudaFreeHost(ctx->staging);
+  if (ctx->upload_ev) cudaEventDestroy(ctx->upload_ev);
+  if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+  for (auto& e : ctx->prof_ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* bw_last_error(const bw_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+bw_status bw_set_profiling(bw_ctx* ctx, int enable) {
+  if (!ctx) return BW_EINVAL;
+  ctx->prof = enable != 0;
+  return BW_OK;
+}
+
+int bw_profile_read(bw_ctx* ctx, int max, char* names, double* ms) {
+  if (!ctx || max < 0) return -1;
+  const int n = std::min(ctx->prof_n, max);
+  if (n <= 0) return 0;
+  if (cudaEventSynchronize(ctx->prof_ev[ctx->prof_n]) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    if (ms) ms[i] = double(t);
+    if (names) {
+      std::strncpy(names + 32 * i, ctx->prof_names[i], 31);
+      names[32 * i + 31] = 0;
+    }
+  }
+  return n;
+}
+
+bw_status bw_get_status(bw_ctx* ctx, void* stream, int64_t* k_index) {
+  if (!ctx) return BW_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BW_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  bw::DevStatus h;
+  BW_CUDA(cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost), "cudaMemcpy status");
+  if (k_index) *k_index = h.code ? h.k_index : -1;
+  if (h.code) {
+    static const char* names[] = {"OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP",
+                                  "ENOCONV", "ETIMEOUT", "ECUDA"};
+    const char* nm = (h.code >= 0 && h.code <= 8) ? names[h.code] : "?";
+    fail(ctx, bw_status(h.code), "device status %s at k index %lld (value %.6e)", nm, h.k_index, h.value);
+    BW_CUDA(cudaMemset(ctx->status, 0, sizeof(bw::DevStatus)), "cudaMemset status");
+  }
+  return bw_status(h.code);
+}
+
+bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64_t K,
+                      int complex64, void* H_out, void* stream) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  if (K < 0) return fail(ctx, BW_EINVAL, "K < 0");
+  if (K > 0 && (!f || !H_out)) return fail(ctx, BW_EINVAL, "f or H_out is NULL");
+  HostPlan P;
+  bw_status st = make_plan(ctx, model, P);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Blob blob;
+  plan_to_blob(P, blob);
+  begin_call(ctx, s);
+  if ((st = reserve(ctx, al256(blob.data.size()) + 4096, s))) return st;
+  char* dblob = carve(ctx, blob.data.size());
+  if ((st = upload(ctx, blob, dblob, s))) return st;
+  bw::BuildArgs a;
+  a.model = dev_model(P, dblob);
+  a.f = f;
+  a.K = K;
+  a.complex64 = complex64 ? 1 : 0;
+  a.H = H_out;
+  prof_start(ctx, s);
+  BW_CUDA(bw::launch_build_hk(a, s), "build kernel");
+  prof_mark(ctx, s, "build_hk");
+  end_call(ctx, s);
+  return BW_OK;
+}
+
+bw_status bw_eigh_batched(bw_ctx* ctx, const void* H, const int32_t* n_per, int64_t batch,
+                          int32_t n_vec, bw_precision prec, double* evals, void* evecs,
+                          void* stream) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  if (batch < 0) return fail(ctx, BW_EINVAL, "batch < 0");
+  if (batch == 0) return BW_OK;
+  if (!H || !n_per || !evals) return fail(ctx, BW_EINVAL, "H, n_per or evals is NULL");
+  if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision");
+  if (n_vec < 0) return fail(ctx, BW_EINVAL, "n_vec < 0");
+  int n_max = 0;
+  std::vector<long long> ho(batch), eo(batch), vo(batch);
+  long long h = 0, ev = 0, vv = 0;
+  for (int64_t b = 0; b < batch; ++b) {
+    const int n = n_per[b];
+    if (n < 1 || n > bw::SMALL_N_MAX)
+      return fail(ctx, BW_EINVAL, "matrix %lld has n = %d outside [1, %d]", (long long)b, n, bw::SMALL_N_MAX);
+    if (n_vec > n) return fail(ctx, BW_EINVAL, "n_vec = %d exceeds n = %d of matrix %lld", n_vec, n, (long long)b);
+    n_max = std::max(n_max, n);
+    ho[b] = h;
+    eo[b] = ev;
+    vo[b] = vv;
+    h += (long long)n * n;
+    ev += n;
+    vv += (long long)n * n_vec;
+  }
+  std::vector<int> np(n_per, n_per + batch);
+  Blob blob;
+  const size_t o_h = blob.add(ho), o_e = blob.add(eo), o_v = blob.add(vo), o_n = blob.add(np);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  begin_call(ctx, s);
+  bw_status st;
+  if ((st = reserve(ctx, al256(blob.data.size()) + 4096, s))) return st;
+  char* d = carve(ctx, blob.data.size());
+  if ((st = upload(ctx, blob, d, s))) return st;
+  bw::EighArgs a;
+  a.H = static_cast<const z64*>(H);
+  a.h_off = reinterpret_cast<const long long*>(d + o_h);
+  a.e_off = reinterpret_cast<const long long*>(d + o_e);
+  a.v_off = reinterpret_cast<const long long*>(d + o_v);
+  a.n_per = reinterpret_cast<const int*>(d + o_n);
+  a.batch = batch;
+  a.n_vec = n_vec;
+  a.mixed = prec == BW_MIXED;
+  a.max_sweeps = 30;
+  a.evals = evals;
+  a.evecs = static_cast<z64*>(evecs);
+  a.status = ctx->status;
+  prof_start(ctx, s);
+  BW_CUDA(bw::launch_eigh_small(a, n_max, s), "eigh kernel");
+  prof_mark(ctx, s, "eigh");
+  end_call(ctx, s);
+  return BW_OK;
+}
+
+bw_status bw_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane, int32_t p,
+                         bw_precision prec, const bw_opts* opts, double* phases, double* min_gap,
+                         void* stream) {
+  return run_loop(ctx, LoopKind::Plain, model, plane, p, prec, opts, nullptr, 0, 0.0, 0, 0, phases,
+                  min_gap, nullptr, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+bw_status bw_nested_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
+                                int32_t p, double cut, int32_t first, int32_t m,
+                                bw_precision prec, const bw_opts* opts, double* phases,
+                                double* nested, double* min_wannier_gap, double* min_gap,
+                                void* stream) {
+  return run_loop(ctx, LoopKind::Nested, model, plane, p, prec, opts, nullptr, 0, cut, first, m,
+                  phases, min_gap, nested, min_wannier_gap, nullptr, nullptr,
+                  static_cast<cudaStream_t>(stream));
+}
+
+bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
+                                       int32_t p, const bw_c128* spin_op, int32_t sign,
+                                       bw_precision prec, const bw_opts* opts, double* phases,
+                                       double* pso_evals, double* min_pso_gap, double* min_gap,
+                                       void* stream) {
+  return run_loop(ctx, LoopKind::Spin, model, plane, p, prec, opts, spin_op, sign, 0.0, 0, 0,
+                  phases, min_gap, nullptr, nullptr, pso_evals, min_pso_gap,
+                  static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

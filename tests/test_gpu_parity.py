@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances: eigenphases within 1e-10 rad in FP64 and 1e-6 rad in mixed precision
+(compared as sorted lists on the circle); Hamiltonians within 1e-13 relative;
+eigenvalues within 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_13051_gb300 import inputs as I
+from tests.gpu_common import circ_err_rows, ctx, lib  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+P = I.Plane
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---------------------------------------------------------------- build_hk
+@pytest.mark.parametrize("complex64", [False, True])
+def test_build_hk_parity(lib, ctx, complex64):
+    torch = _torch()
+    rng = np.random.default_rng(0)
+    models = [I.random_hermitian_model(7, 1, shells=((1, 0), (0, 1), (1, 1), (2, -1))),
+              I.choti_eq9(1.0), I.supercell(I.spin_hall(1.0), 3, W=2.0, seed=5),
+              I.supercell(I.spin_hall(1.0), 2, flux=True), I.manyband(20)]
+    for model in models:
+        f = rng.uniform(-2, 2, size=(37, 3))
+        H = lib.build_hk(model, torch.tensor(f, device="cuda"), complex64=complex64, ctx=ctx)
+        H = H.cpu().numpy()
+        for k in range(f.shape[0]):
+            ref = oracle.bloch_hamiltonian(model, f[k])
+            scale = max(1.0, np.abs(ref).max())
+            tol = 2e-7 if complex64 else 1e-13
+            assert np.abs(H[k] - ref).max() <= tol * scale, model.name
+
+
+# ---------------------------------------------------------------- eigh_batched
+def _pack(mats):
+    return np.concatenate([m.ravel() for m in mats])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_eigh_batched_ragged(lib, ctx, precision):
+    torch = _torch()
+    # mixed precision refines the lowest n_vec block and needs n_vec < n
+    sizes = ([1, 2, 3, 4, 5, 7, 8, 13, 16, 17, 31, 32, 4, 2] if precision == "fp64"
+             else [4, 5, 7, 8, 13, 16, 17, 31, 32, 4, 6])
+    mats = I.random_hermitian_batch(sizes, seed=3)
+    n_vec = 1 if precision == "fp64" else 3
+    H = torch.tensor(_pack(mats), device="cuda")
+    ev, vec = lib.eigh_batched(H, sizes, n_vec, precision=precision, ctx=ctx)
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy()
+    eo = vo = 0
+    for A, n in zip(mats, sizes):
+        ref = np.linalg.eigvalsh(A)
+        got = ev[eo:eo + n]
+        scale = max(1.0, np.abs(ref).max())
+        tol_v = 1e-12 if precision == "fp64" else 2e-5
+        assert np.abs(got - ref).max() <= tol_v * scale
+        assert np.abs(got[:n_vec] - ref[:n_vec]).max(initial=0) <= 1e-12 * scale
+        V = vec[vo:vo + n * n_vec].reshape(n, n_vec)
+        if n_vec:
+            res = A @ V - V * got[:n_vec]
+            assert np.abs(res).max() <= 1e-11 * scale
+            assert np.abs(V.conj().T @ V - np.eye(n_vec)).max() <= 1e-12
+        eo += n
+        vo += n * n_vec
+
+
+def test_eigh_degenerate_spectrum(lib, ctx):
+    """Exactly doubly degenerate spectra (Kramers-like pairs): the span of each pair."""
+    torch = _torch()
+    rng = np.random.default_rng(8)
+    mats = []
+    for n2 in (2, 4, 8, 16):
+        A = I.random_hermitian_batch([n2], seed=n2)[0]
+        Q, _ = np.linalg.qr(rng.standard_normal((2 * n2, 2 * n2)) + 1j * rng.standard_normal((2 * n2, 2 * n2)))
+        mats.append(Q @ np.kron(A, np.eye(2)) @ Q.conj().T)
+    sizes = [m.shape[0] for m in mats]
+    H = torch.tensor(_pack(mats), device="cuda")
+    ev, vec = lib.eigh_batched(H, sizes, 2, ctx=ctx)
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy()
+    eo = vo = 0
+    for A, n in zip(mats, sizes):
+        lam, W = np.linalg.eigh(A)
+        assert np.abs(ev[eo:eo + n] - lam).max() < 1e-12 * max(1, np.abs(lam).max())
+        V = vec[vo:vo + 2 * n].reshape(n, 2)
+        Pg, Pr = V @ V.conj().T, W[:, :2] @ W[:, :2].conj().T
+        assert np.abs(Pg - Pr).max() < 1e-10
+        eo += n
+        vo += 2 * n
+
+
+# ---------------------------------------------------------------- Wilson loops
+CASES = {
+    "spin_hall_51": (lambda: I.spin_hall(1.0), P(51, 51), 2),
+    "chern_eq4": (lambda: I.chern_eq4(1.5), P(30, 13), 1),
+    "ssh_pi": (lambda: I.ssh(0.5, 1.0), P(7, 1, trans_dir=(0, 0, 0)), 1),
+    "random6_p3": (lambda: I.random_hermitian_model(6, 2), P(17, 5), 3),
+    "random13_p5": (lambda: I.random_hermitian_model(13, 4, shells=((1, 0), (0, 1), (1, 1))),
+                    P(11, 3, origin=(0.1, 0.2, 0.3), trans_dir=(0.5, 1, 0)), 5),
+    "choti_kz": (lambda: I.choti_eq9(1.0), P(20, 9, origin=(0, 0, 0.3)), 2),
+    "supercell_L2": (lambda: I.supercell(I.spin_hall(1.0), 2, W=1.0, seed=1), P(9, 6), 8),
+    "one_point_loop": (lambda: I.random_hermitian_model(4, 9), P(1, 3), 2),
+    "all_bands": (lambda: I.random_hermitian_model(5, 6), P(8, 2), 5),
+    "single_band_model": (lambda: I.square_lattice(1.0), P(6, 4), 1),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_wilson_loop_parity(lib, ctx, case, precision):
+    mk, plane, p = CASES[case]
+    model = mk()
+    ref, rgap = oracle.wilson_loop(model, plane, p)
+    ph, gap = lib.wilson_loop(model, plane, p, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    g = gap.cpu().numpy()
+    fin = np.isfinite(rgap)
+    assert np.all(np.isfinite(g) == fin)
+    assert np.abs(g[fin] - rgap[fin]).max(initial=0) <= 1e-9 * max(1, np.abs(rgap[fin]).max(initial=1))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_unitarised_loop_parity(lib, ctx, precision):
+    model = I.random_hermitian_model(8, 12)
+    plane = P(13, 4)
+    ref, _ = oracle.wilson_loop(model, plane, 3, unitarise=True)
+    ph, _ = lib.wilson_loop(model, plane, 3, precision=precision, ctx=ctx, unitarise=True)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+
+
+# ---------------------------------------------------------------- nested
+NESTED = {
+    "bbh_24": (lambda: I.bbh(0.5, 0.5), P(24, 24), 2, 1),
+    "bbh_trivial": (lambda: I.bbh(1.5, 1.5), P(12, 10), 2, 1),
+    "choti_kz": (lambda: I.choti_eq9(1.0), P(12, 12, origin=(0, 0, 0.25)), 2, 1),
+    "random8_p4_m2": (lambda: I.random_hermitian_model(8, 21), P(9, 7), 4, 2),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(NESTED))
+def test_nested_parity(lib, ctx, case, precision):
+    mk, plane, p, m = NESTED[case]
+    model = mk()
+    try:
+        ref_ph, ref_n, ref_wg, _ = oracle.nested_wilson_loop(model, plane, p, m=m)
+    except oracle.OracleError as e:
+        pytest.skip(f"oracle: {e}")
+    ph, nest, wg, _ = lib.nested_wilson_loop(model, plane, p, m=m, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= TOL[precision]
+    assert circ_err_rows(nest.cpu().numpy(), ref_n) <= TOL[precision]
+    assert abs(wg.cpu().numpy().min() - ref_wg) <= 10 * TOL[precision]
+
+
+def test_bbh_config_full_size(lib, ctx):
+    """The 60 x 60 BBH workload the benchmark times: FP64 and mixed against the oracle."""
+    wl = I.config_bbh()
+    ref_ph, ref_n, _, _ = oracle.nested_wilson_loop(wl.model, wl.plane, wl.p, m=1)
+    for prec in ("fp64", "mixed"):
+        ph, nest, _, _ = lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=1, precision=prec,
+                                                ctx=ctx)
+        assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= TOL[prec]
+        assert circ_err_rows(nest.cpu().numpy(), ref_n) <= TOL[prec]
+        assert np.all(np.abs(np.abs(nest.cpu().numpy()) - np.pi) < 1e-9)
+
+
+# ---------------------------------------------------------------- spin-resolved
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_spin_resolved_parity(lib, ctx, sign, precision):
+    wl = I.config_spin_hall()
+    ref, rpso, rpg, _ = oracle.spin_resolved_wilson_loop(wl.model, wl.plane, 2, wl.spin_op, sign)
+    ph, pso, pg, _ = lib.spin_resolved_wilson_loop(wl.model, wl.plane, 2, wl.spin_op, sign,
+                                                   precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    assert np.abs(pso.cpu().numpy() - rpso).max() <= 1e-10
+    assert abs(pg.cpu().numpy().min() - rpg) <= 1e-10
+    assert abs(oracle.winding(ph.cpu().numpy()) - sign) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spin_resolved_choti_and_random(lib, ctx, precision):
+    model = I.choti_eq9(1.0)
+    S = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+    plane = P(20, 20)
+    ref, rpso, _, _ = oracle.spin_resolved_wilson_loop(model, plane, 2, S, -1)
+    ph, pso, _, _ = lib.spin_resolved_wilson_loop(model, plane, 2, S, -1, precision=precision,
+                                                  ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    assert np.abs(pso.cpu().numpy() - rpso).max() <= 1e-9
+    # a 2 x 2 disordered supercell, p = 8 -> sector of 4
+    sc = I.supercell(I.spin_hall(1.0), 2, W=1.5, seed=3)
+    S = np.kron(np.eye(4), I.SPIN_HALL_SZ)
+    plane = P(8, 6)
+    ref, _, _, _ = oracle.spin_resolved_wilson_loop(sc, plane, 8, S, -1)
+    ph, _, _, _ = lib.spin_resolved_wilson_loop(sc, plane, 8, S, -1, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+
+
+# ---------------------------------------------------------------- statuses and errors
+def test_device_status_gap(lib, ctx):
+    with pytest.raises(lib.BWError) as e:
+        lib.wilson_loop(I.chern_eq4(2.0), P(8, 8), 1, ctx=ctx)
+    assert e.value.status == "EGAP"
+    # the status is cleared after being read
+    ph, _ = lib.wilson_loop(I.chern_eq4(1.5), P(8, 8), 1, ctx=ctx)
+
+
+def test_device_status_pso_and_wannier(lib, ctx):
+    wl = I.config_spin_hall()
+    with pytest.raises(lib.BWError) as e:
+        lib.spin_resolved_wilson_loop(wl.model, P(6, 6), 2, np.eye(4, dtype=complex), -1, ctx=ctx)
+    assert e.value.status == "EPSOGAP"
+    with pytest.raises(lib.BWError) as e:      # Kramers-degenerate WCCs at ky = 0
+        lib.nested_wilson_loop(wl.model, P(8, 8), 2, m=1, ctx=ctx)
+    assert e.value.status == "EWANGAP"
+
+
+def test_argument_errors(lib, ctx):
+    wl = I.config_spin_hall()
+    bad = I.HoppingList(n=2, R=np.zeros((1, 3)), i=[0], j=[1], t=[1.0 + 0j])   # no partner
+    for call in (lambda: lib.wilson_loop(bad, P(4, 4), 1, ctx=ctx),
+                 lambda: lib.wilson_loop(wl.model, P(4, 4), 5, ctx=ctx),
+                 lambda: lib.wilson_loop(wl.model, P(0, 4), 1, ctx=ctx),
+                 lambda: lib.spin_resolved_wilson_loop(wl.model, P(4, 4), 1, wl.spin_op, -1, ctx=ctx),
+                 lambda: lib.spin_resolved_wilson_loop(wl.model, P(4, 4), 2, wl.spin_op, 0, ctx=ctx),
+                 lambda: lib.nested_wilson_loop(wl.model, P(4, 4, trans_dir=(0, 0.5, 0)), 2, m=1, ctx=ctx),
+                 lambda: lib.nested_wilson_loop(wl.model, P(4, 4), 2, first=1, m=2, ctx=ctx)):
+        with pytest.raises(lib.BWError) as e:
+            call()
+        assert e.value.status == "EINVAL"
+
+
+def test_two_streams_same_context(lib, ctx):
+    """Calls on different streams through one context are ordered by the context."""
+    torch = _torch()
+    wl = I.config_bbh()
+    ref, _ = lib.wilson_loop(wl.model, wl.plane, 2, ctx=ctx)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for s in (s1, s2, s1):
+        with torch.cuda.stream(s):
+            outs.append(lib.wilson_loop(wl.model, wl.plane, 2, ctx=ctx, check=False))
+    torch.cuda.synchronize()
+    ctx.status()
+    for ph, _ in outs:
+        assert torch.equal(ph, ref)
