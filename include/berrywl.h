@@ -184,6 +184,31 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
                                        double* phases, double* pso_evals,
                                        double* min_pso_gap, double* min_gap, void* stream);
 
+/* Allocation-free Wilson loop (no counterpart in the paper: it serves callers).
+ * Some callers cannot let a library allocate device memory: programs that give all
+ * device memory to their own pool under a hard cap, plugins running inside another
+ * program's CUDA context, or latency-critical loops where cudaMalloc / cudaFree
+ * would block on or synchronise the device.  This entry point computes exactly
+ * what bw_wilson_loop computes (same arguments and outputs, no context) without
+ * allocating: all scratch lives in one fixed 8 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ * The problem must fit in it: 16 K n p + 16 K p^2 + 8 K bytes (K = N * N_t) plus
+ * the hopping-list plan; larger problems return BW_ENOMEM with a message, before
+ * anything runs.  n <= 32 and p <= 64 as for bw_wilson_loop.
+ *  - Runs on the current CUDA device.  The first call on a device looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call before
+ *    any stream capture on that device.
+ *  - Every call uses the same array and finds the previous call's data in it; the
+ *    call clears its status word itself.  Calls whose work overlaps on the GPU
+ *    (other host threads, other streams) race on the array: serialise them.
+ *  - The call synchronises `stream` before returning and returns the device
+ *    status of its own work (BW_EGAP etc.) as well as argument errors.
+ *  - err (may be NULL) receives a NUL-terminated message of at most err_len bytes.
+ * phases, min_gap: DEVICE, caller-owned, as for bw_wilson_loop. */
+bw_status bw_wilson_loop_noalloc(const bw_model* model, const bw_plane* plane, int32_t p,
+                                 bw_precision prec, const bw_opts* opts, double* phases,
+                                 double* min_gap, void* stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

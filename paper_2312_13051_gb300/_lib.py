@@ -78,6 +78,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_spin_resolved_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane),
                                                    i32, vp, i32, i32, C.POINTER(bw_opts), vp,
                                                    vp, vp, vp, vp]),
+            "bw_wilson_loop_noalloc": (i32, [C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
+                                             C.POINTER(bw_opts), vp, vp, vp, C.c_char_p,
+                                             C.c_size_t]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -91,7 +94,7 @@ def exported_symbols():
     return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
             "bw_profile_read", "bw_build_hk",
             "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
-            "bw_spin_resolved_wilson_loop"]
+            "bw_spin_resolved_wilson_loop", "bw_wilson_loop_noalloc"]
 
 
 class Context:
@@ -309,3 +312,25 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     if check:
         ctx.status()
     return ph, pso, pg, gap
+
+
+def wilson_loop_noalloc(model, plane, p: int, precision: str = "fp64", out=None, **opts):
+    """``bw_wilson_loop_noalloc``: the same result as :func:`wilson_loop` computed without
+    any device allocation by the library (its scratch is a fixed array inside it).
+    ``out`` = (phases[N_t, p], min_gap[N_t]) caller-owned CUDA float64 tensors; when
+    omitted they are allocated here, by the caller side, before the call."""
+    import torch
+    lib = load()
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    if out is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = (_empty((plane.N_t, p), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+    ph, gap = out
+    err = C.create_string_buffer(512)
+    rc = lib.bw_wilson_loop_noalloc(C.byref(hm.s), C.byref(pl), int(p), PRECISION[precision],
+                                    C.byref(o), _ptr(ph), _ptr(gap), _stream_ptr(), err, 512)
+    if rc != 0:
+        raise BWError(rc, err.value.decode())
+    return ph, gap

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -705,3 +706,149 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model, const
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free Wilson loop.
+//
+// Some callers cannot let a library allocate device memory: a host program that
+// hands all device memory to its own pool under a hard cap, a plugin that runs
+// inside another program's CUDA context, or a latency-critical loop where
+// cudaMalloc / cudaFree would block on (or implicitly synchronise) the device.
+// For them bw_wilson_loop_noalloc runs the same kernels as bw_wilson_loop with
+// all of its scratch (the hopping-list plan, the occupied states, the overlaps,
+// the gaps and the status word) in one fixed file-scope device array.  The array
+// is part of the library image: every device that loads the library holds it
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of the fixed array on the current device.  The host-side name
+// g_noalloc_scratch is only a stand-in for the symbol and must never reach a
+// kernel; the address comes from cudaGetSymbolAddress, once per device, with that
+// device current.
+bw_status noalloc_base(bw_ctx* ctx, char** out) {
+  int dev = -1;
+  BW_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(ctx, BW_EINVAL, "device %d outside the %d devices the fixed scratch supports", dev,
+                kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    BW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+    g_noalloc_base[dev] = static_cast<char*>(p);
+  }
+  *out = g_noalloc_base[dev];
+  return BW_OK;
+}
+
+bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane, int p,
+                      bw_precision prec, const bw_opts* opts, double* phases, double* min_gap,
+                      cudaStream_t s) {
+  bw_status st = check_plane(ctx, plane, false);
+  if (st) return st;
+  if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
+  if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
+  HostPlan P;
+  if ((st = make_plan(ctx, model, P))) return st;
+  const int n = P.n;
+  if (p < 1 || p > n) return fail(ctx, BW_EINVAL, "need 1 <= p <= n (p = %d, n = %d)", p, n);
+  if (n > bw::SMALL_N_MAX)
+    return fail(ctx, BW_EINVAL, "n = %d exceeds the largest supported size %d", n, bw::SMALL_N_MAX);
+  if (p > bw::LOOP_P_MAX) return fail(ctx, BW_EINVAL, "p = %d exceeds %d", p, bw::LOOP_P_MAX);
+  const Opts o = resolve_opts(opts, P.tmax);
+  if (o.unitarise && p > 32) return fail(ctx, BW_EINVAL, "unitarise supports p <= 32");
+  const long long K = (long long)plane->N * plane->N_t;
+  Blob blob;
+  plan_to_blob(P, blob);
+  const size_t bStat = al256(sizeof(bw::DevStatus));
+  const size_t bBlob = al256(blob.data.size());
+  const size_t bU = al256(size_t(K) * n * p * sizeof(z64));
+  const size_t bGap = al256(size_t(K) * sizeof(double));
+  const size_t bM = al256(size_t(K) * p * p * sizeof(z64));
+  const size_t total = bStat + bBlob + bU + bGap + bM;
+  if (total > kNoAllocScratchBytes)
+    return fail(ctx, BW_ENOMEM,
+                "this problem needs %zu bytes of scratch; the fixed scratch of "
+                "bw_wilson_loop_noalloc holds %zu bytes (K * n * p * 16 + K * p * p * 16 + "
+                "K * 8 + the hopping-list plan must fit)",
+                total, kNoAllocScratchBytes);
+  char* base = nullptr;
+  if ((st = noalloc_base(ctx, &base))) return st;
+  bw::DevStatus* status = reinterpret_cast<bw::DevStatus*>(base);
+  char* dblob = base + bStat;
+  z64* U = reinterpret_cast<z64*>(dblob + bBlob);
+  double* gap = reinterpret_cast<double*>(reinterpret_cast<char*>(U) + bU);
+  z64* M = reinterpret_cast<z64*>(reinterpret_cast<char*>(gap) + bGap);
+  // The array keeps the previous call's contents: the status word must start at zero.
+  BW_CUDA(cudaMemsetAsync(status, 0, sizeof(bw::DevStatus), s), "cudaMemsetAsync");
+  BW_CUDA(cudaMemcpyAsync(dblob, blob.data.data(), blob.data.size(), cudaMemcpyHostToDevice, s),
+          "cudaMemcpyAsync");
+
+  bw::StatesArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.model = dev_model(P, dblob);
+  sa.plane = dev_plane(plane);
+  sa.K = K;
+  sa.p = p;
+  sa.mixed = prec == BW_MIXED;
+  sa.max_sweeps = o.max_sweeps;
+  sa.gap_tol = o.gap_tol;
+  sa.U = U;
+  sa.gap = gap;
+  sa.status = status;
+  BW_CUDA(bw::launch_states_small(sa, p, s), "states kernel");
+  bw::LoopArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.U = U;
+  la.M = M;
+  la.n = n;
+  la.p = p;
+  la.N = plane->N;
+  la.N_t = plane->N_t;
+  la.unitarise = o.unitarise;
+  la.max_sweeps = o.max_sweeps;
+  la.gap = gap;
+  la.phases = phases;
+  la.min_gap = min_gap;
+  la.status = status;
+  BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
+  BW_CUDA(bw::launch_loops(la, s), "loop kernel");
+  // Wait for the kernels (and for the copy out of the caller's host list), then
+  // report the device status of this call.
+  BW_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  bw::DevStatus h;
+  BW_CUDA(cudaMemcpy(&h, status, sizeof(h), cudaMemcpyDeviceToHost), "cudaMemcpy status");
+  if (h.code) {
+    static const char* names[] = {"OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP",
+                                  "ENOCONV", "ETIMEOUT", "ECUDA"};
+    const char* nm = (h.code >= 0 && h.code <= 8) ? names[h.code] : "?";
+    return fail(ctx, bw_status(h.code), "device status %s at k index %lld (value %.6e)", nm,
+                h.k_index, h.value);
+  }
+  return BW_OK;
+}
+
+}  // namespace
+
+extern "C" bw_status bw_wilson_loop_noalloc(const bw_model* model, const bw_plane* plane,
+                                            int32_t p, bw_precision prec, const bw_opts* opts,
+                                            double* phases, double* min_gap, void* stream,
+                                            char* err, size_t err_len) {
+  bw_ctx tmp;  // host-side message holder only; no device resources
+  const bw_status st = noalloc_run(&tmp, model, plane, p, prec, opts, phases, min_gap,
+                                   static_cast<cudaStream_t>(stream));
+  if (err && err_len) {
+    std::strncpy(err, tmp.err.c_str(), err_len - 1);
+    err[err_len - 1] = 0;
+  }
+  return st;
+}
