@@ -341,6 +341,237 @@ __global__ void k_nested(LoopArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Small-p loop kernels: all overlaps of a loop in shared memory at once and a
+// log-depth prefix product instead of a chain of dependent global loads.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_P_MAX = 4;
+constexpr size_t SCAN_SMEM_MAX = 96 * 1024;
+
+// In-place inclusive prefix product over L matrices of size q x q, later index on the
+// left: on return S[j] = A_j A_{j-1} ... A_0.  T is scratch of the same size.
+// Returns the buffer holding the result (S or T).
+__device__ z64* prefix_products(z64* S, z64* T, int L, int q) {
+  const int qq = q * q;
+  for (int d = 1; d < L; d <<= 1) {
+    for (int e = threadIdx.x; e < L * qq; e += blockDim.x) {
+      const int j = e / qq, rc = e - j * qq, r = rc / q, c = rc - r * q;
+      if (j < d) {
+        T[e] = S[e];
+      } else {
+        const z64* A = S + j * qq;
+        const z64* B = S + (j - d) * qq;
+        z64 acc(0.0, 0.0);
+        for (int k = 0; k < q; ++k) cfma(acc, A[r * q + k], B[k * q + c]);
+        T[e] = acc;
+      }
+    }
+    __syncthreads();
+    z64* t = S; S = T; T = t;
+  }
+  return S;
+}
+
+struct ScanSmem {
+  size_t S, T, Nu, X, Y, lam, vec, th, key, ord, sh, red, total;
+};
+
+__host__ __device__ inline ScanSmem scan_layout(int L, int q, int n_nu) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  ScanSmem Z;
+  size_t o = 0;
+  Z.S = o; o = al(o + size_t(L) * q * q * sizeof(z64));
+  Z.T = o; o = al(o + size_t(L) * q * q * sizeof(z64));
+  Z.Nu = o; o = al(o + size_t(n_nu) * sizeof(z64));
+  Z.X = o; o = al(o + size_t(q) * q * sizeof(z64));
+  Z.Y = o; o = al(o + size_t(q) * q * sizeof(z64));
+  Z.lam = o; o = al(o + size_t(q) * sizeof(z64));
+  Z.vec = o; o = al(o + size_t(q) * sizeof(z64));
+  Z.th = o; o = al(o + size_t(q) * sizeof(double));
+  Z.key = o; o = al(o + size_t(q) * sizeof(double));
+  Z.ord = o; o = al(o + size_t(q) * sizeof(int));
+  Z.sh = o; o = al(o + sizeof(GeigShared));
+  Z.red = o; o = al(o + 64 * sizeof(double));
+  Z.total = o;
+  return Z;
+}
+
+// Orders the eigenphases th[0..p) by their distance from `cut` (mod 2pi, stable),
+// writes the Wannier gap of the sector [first, first+m) for loop i and reports a
+// closed gap.  ord receives the ordering.  Every thread must call it.
+__device__ void nested_sector(const LoopArgs& a, const double* th, int p, int m, double* key,
+                              int* ord, double* red, int i, long long k0) {
+  const double two_pi = 6.283185307179586;
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    double x = fmod(th[c] - a.cut, two_pi);
+    if (x < 0.0) x += two_pi;
+    if (x >= two_pi) x = 0.0;
+    key[c] = x;
+  }
+  __syncthreads();
+  rank_sort(key, p, ord);
+  double wg = INFINITY;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int s = e / p, r = e - s * p;
+    const bool in_s = s >= a.first && s < a.first + m;
+    const bool in_r = !(r >= a.first && r < a.first + m);
+    if (in_s && in_r) {
+      double d = fmod(fabs(th[ord[s]] - th[ord[r]]), two_pi);
+      wg = fmin(wg, fmin(d, two_pi - d));
+    }
+  }
+  wg = block_min(wg, red);
+  if (threadIdx.x == 0) {
+    if (a.min_wannier_gap) a.min_wannier_gap[i] = wg;
+    if (!(wg > a.wannier_gap_tol)) report(a.status, ST_EWANGAP, k0, wg);
+  }
+}
+
+__global__ void k_loops_scan(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
+  const int m = a.nested ? a.m : 1;
+  const ScanSmem Z = scan_layout(N, p, a.nested ? N * p * m : 1);
+  z64* S = reinterpret_cast<z64*>(smem + Z.S);
+  z64* T = reinterpret_cast<z64*>(smem + Z.T);
+  z64* Nu = reinterpret_cast<z64*>(smem + Z.Nu);
+  z64* X = reinterpret_cast<z64*>(smem + Z.X);
+  z64* Y = reinterpret_cast<z64*>(smem + Z.Y);
+  z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
+  z64* vec = reinterpret_cast<z64*>(smem + Z.vec);
+  double* th = reinterpret_cast<double*>(smem + Z.th);
+  double* key = reinterpret_cast<double*>(smem + Z.key);
+  int* ord = reinterpret_cast<int*>(smem + Z.ord);
+  GeigShared* sh = reinterpret_cast<GeigShared*>(smem + Z.sh);
+  double* red = reinterpret_cast<double*>(smem + Z.red);
+  const int pp = p * p;
+  for (int i = blockIdx.x; i < a.N_t; i += gridDim.x) {
+    const long long k0 = (long long)i * N;
+    if (a.min_gap || a.min_pso_gap) {
+      double g = INFINITY, gp = INFINITY;
+      for (int j = tid; j < N; j += nt) {
+        if (a.gap) g = fmin(g, a.gap[k0 + j]);
+        if (a.pso_gap) gp = fmin(gp, a.pso_gap[k0 + j]);
+      }
+      g = block_min(g, red);
+      gp = block_min(gp, red);
+      if (tid == 0) {
+        if (a.min_gap) a.min_gap[i] = g;
+        if (a.min_pso_gap) a.min_pso_gap[i] = gp;
+      }
+    }
+    const z64* Mg = a.M + k0 * pp;
+    for (int e = tid; e < N * pp; e += nt) S[e] = Mg[e];
+    __syncthreads();
+    // P[j] = M_j ... M_0; the loop matrix is P[N-1]
+    z64* Pf = prefix_products(S, T, N, p);
+    for (int e = tid; e < pp; e += nt) X[e] = Pf[(N - 1) * pp + e];
+    __syncthreads();
+    const int rc = geig(X, Y, p, p, a.nested != 0, lam, vec, sh);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+    for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
+    __syncthreads();
+    rank_sort(th, p, ord);
+    for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
+    __syncthreads();
+    if (!a.nested) continue;
+    nested_sector(a, th, p, m, key, ord, red, i, k0);
+    // nu_j = P[j-1] nu_0 (nu_0 = Y[:, sector]), one thread per base point j:
+    // normalise the columns, then modified Gram-Schmidt (m <= SCAN_P_MAX)
+    for (int j = tid; j < N; j += nt) {
+      z64* nu = Nu + (size_t)j * p * m;
+      for (int r = 0; r < p; ++r)
+        for (int c = 0; c < m; ++c) {
+          const int col = ord[a.first + c];
+          z64 acc(0.0, 0.0);
+          if (j == 0) {
+            acc = Y[r * p + col];
+          } else {
+            const z64* P = Pf + (size_t)(j - 1) * pp;
+            for (int q = 0; q < p; ++q) cfma(acc, P[r * p + q], Y[q * p + col]);
+          }
+          nu[r * m + c] = acc;
+        }
+      for (int c = 0; c < m; ++c) {
+        for (int c2 = 0; c2 < c; ++c2) {
+          z64 d(0.0, 0.0);
+          for (int r = 0; r < p; ++r) cfma_conj(d, nu[r * m + c2], nu[r * m + c]);
+          for (int r = 0; r < p; ++r) nu[r * m + c] = nu[r * m + c] - nu[r * m + c2] * d;
+        }
+        double s = 0.0;
+        for (int r = 0; r < p; ++r) s += abs2(nu[r * m + c]);
+        s = 1.0 / sqrt(s);
+        for (int r = 0; r < p; ++r) nu[r * m + c] = s * nu[r * m + c];
+      }
+    }
+    __syncthreads();
+    // Wannier states w(j, i) = U(k_j) nu_j
+    for (int e = tid; e < N * n * m; e += nt) {
+      const int j = e / (n * m), rc2 = e - j * n * m, r = rc2 / m, c = rc2 - r * m;
+      const z64* Uk = a.U + (k0 + j) * (long long)n * p;
+      const z64* nu = Nu + (size_t)j * p * m;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) cfma(acc, Uk[r * p + q], nu[q * m + c]);
+      a.w[((long long)j * a.N_t + i) * n * m + rc2] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Nested loop for small m: one CTA per base point, all Wannier states of the base
+// point in shared memory, overlaps in parallel, product by prefix scan.
+__global__ void k_nested_scan(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, m = a.m, Nt = a.N_t, tid = threadIdx.x, nt = blockDim.x;
+  const ScanSmem Z = scan_layout(Nt, m, Nt * n * m);
+  z64* S = reinterpret_cast<z64*>(smem + Z.S);
+  z64* T = reinterpret_cast<z64*>(smem + Z.T);
+  z64* Wn = reinterpret_cast<z64*>(smem + Z.Nu);
+  z64* X = reinterpret_cast<z64*>(smem + Z.X);
+  z64* Y = reinterpret_cast<z64*>(smem + Z.Y);
+  z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
+  z64* vec = reinterpret_cast<z64*>(smem + Z.vec);
+  double* th = reinterpret_cast<double*>(smem + Z.th);
+  int* ord = reinterpret_cast<int*>(smem + Z.ord);
+  GeigShared* sh = reinterpret_cast<GeigShared*>(smem + Z.sh);
+  const int mm2 = m * m, nm = n * m;
+  for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
+    const z64* wj = a.w + (long long)j * Nt * nm;
+    for (int e = tid; e < Nt * nm; e += nt) Wn[e] = wj[e];
+    __syncthreads();
+    // A_i = w(i+1)^dagger w(i), closed on i = 0
+    for (int e = tid; e < Nt * mm2; e += nt) {
+      const int i = e / mm2, rc = e - i * mm2, r = rc / m, c = rc - r * m;
+      const z64* wa = Wn + (size_t)i * nm;
+      const z64* wb = Wn + (size_t)(i + 1 == Nt ? 0 : i + 1) * nm;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q * m + r], wa[q * m + c]);
+      S[e] = acc;
+    }
+    __syncthreads();
+    z64* Pf = prefix_products(S, T, Nt, m);
+    for (int e = tid; e < mm2; e += nt) X[e] = Pf[(Nt - 1) * mm2 + e];
+    __syncthreads();
+    const int rc = geig(X, Y, m, m, false, lam, vec, sh);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, j, 0.0);
+    for (int c = tid; c < m; c += nt) th[c] = phase_of(lam[c]);
+    __syncthreads();
+    rank_sort(th, m, ord);
+    for (int c = tid; c < m; c += nt) a.nested_out[(long long)j * m + c] = th[ord[c]];
+    __syncthreads();
+  }
+}
+
+static bool scan_loops_fit(const LoopArgs& a) {
+  if (a.p > SCAN_P_MAX) return false;
+  const int m = a.nested ? a.m : 1;
+  return scan_layout(a.N, a.p, a.nested ? a.N * a.p * m : 1).total <= SCAN_SMEM_MAX;
+}
+
+static bool scan_nested_fit(const LoopArgs& a) {
+  return a.m <= SCAN_P_MAX && scan_layout(a.N_t, a.m, a.N_t * a.n * a.m).total <= SCAN_SMEM_MAX;
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static int loop_threads(int p) { return p <= 4 ? 32 : (p <= 16 ? 64 : 128); }
@@ -362,6 +593,14 @@ cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
 
 cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
   if (a.N_t <= 0) return cudaSuccess;
+  if (scan_loops_fit(a)) {
+    const ScanSmem Z = scan_layout(a.N, a.p, a.nested ? a.N * a.p * a.m : 1);
+    static size_t cached_scan = 0;
+    cudaError_t e = set_smem_once(k_loops_scan, Z.total, cached_scan);
+    if (e != cudaSuccess) return e;
+    k_loops_scan<<<a.N_t, 128, Z.total, s>>>(a);
+    return cudaGetLastError();
+  }
   const LoopSmem L = loop_layout(a.p, a.nested ? a.m : 1);
   static size_t cached = 0;
   cudaError_t e = set_smem_once(k_loops, L.total, cached);
@@ -372,6 +611,14 @@ cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
 
 cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
+  if (scan_nested_fit(a)) {
+    const ScanSmem Z = scan_layout(a.N_t, a.m, a.N_t * a.n * a.m);
+    static size_t cached_scan = 0;
+    cudaError_t e = set_smem_once(k_nested_scan, Z.total, cached_scan);
+    if (e != cudaSuccess) return e;
+    k_nested_scan<<<a.N, 128, Z.total, s>>>(a);
+    return cudaGetLastError();
+  }
   const LoopSmem L = loop_layout(a.m, 1);
   const size_t sm = L.total + size_t(a.m) * a.m * sizeof(z64);
   static size_t cached = 0;

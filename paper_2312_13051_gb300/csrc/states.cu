@@ -188,77 +188,75 @@ __device__ bool ritz(const z64* H, z64* Q, z64* HQ, z64* C, z64* G, z64* Zg, dou
 
 // Mixed precision: refine the lowest-p invariant subspace of the FP64 matrix H
 // starting from an FP32 eigenbasis V (columns ordered by ord, eigenvalues lam).
-// Newton correction in the FP32 eigenbasis of the complement:
-//   Q <- Q + V_u C,  C[a][i] = (V_u^dagger R)[a][i] / (rho_i - lam_{p+a}),
-// with the FP64 residual R = H Q - Q diag(rho) of the Rayleigh-Ritz basis.
-// Returns the direct gap lam_p - lam_{p-1} (lam_p from the FP64 Rayleigh quotient of
-// the (p+1)-th FP32 vector) and sets *ok = 0 when the residual did not converge.
+// One Newton correction in the FP32 eigenbasis of the complement,
+//   Q <- Q + V_u C,  C[a][i] = (V_u^dagger R)[a][i] / (G_ii - lam_{p+a}),
+// with the FP64 residual R = H Q - Q G, G = Q^dagger H Q (its off-diagonal part is
+// of the order of the FP32 error and enters the correction at second order), then
+// Cholesky-QR.  The FP32 start is accurate to eps32 ||H|| / gap, the corrected
+// subspace to about (eps32 ||H|| / gap)^2.  Returns the direct gap from FP64
+// Rayleigh quotients of the p-th and (p+1)-th FP32 vectors; *ok = 0 when a
+// Cholesky factorisation broke down.
 __device__ double refine_mixed(const z64* H, const c32* V, const int* ord, const double* lam,
                                int n, int p, z64* Q, z64* HQ, z64* C, z64* G, z64* Zg,
                                double* rho, int* ord2, JacRot<double>* rot, double* red,
                                int max_sweeps, int* ok, int* flag) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  double hmax = 0.0;
-  for (int e = tid; e < n * n; e += nt) hmax = fmax(hmax, sqrt(abs2(H[e])));
-  hmax = -block_min(-hmax, red);
-  const double tol = 32.0 * n * DBL_EPSILON * fmax(hmax, 1e-300);
-  const int MAX_IT = 5;
-  *ok = 0;
-  for (int it = 0; it < MAX_IT; ++it) {
-    cholqr(Q, G, n, p, flag);
-    cholqr(Q, G, n, p, flag);
-    ritz(H, Q, HQ, C, G, Zg, rho, ord2, n, p, rot, red, max_sweeps);
-    double rmax = 0.0;
+  (void)Zg; (void)rho; (void)ord2; (void)rot; (void)max_sweeps;
+  *ok = cholqr(Q, G, n, p, flag) ? 1 : 0;
+  if (p < n) {
+    mm(H, Q, HQ, n, n, p);
+    // diagonal of G = Q^dagger H Q, then R = H Q - Q G (full G)
+    for (int e = tid; e < p * p; e += nt) {
+      const int a = e / p, b = e - a * p;
+      z64 acc(0.0, 0.0);
+      for (int r = 0; r < n; ++r) cfma_conj(acc, Q[r * p + a], HQ[r * p + b]);
+      G[e] = acc;
+    }
+    __syncthreads();
     for (int e = tid; e < n * p; e += nt) {
       const int r = e / p, c = e - r * p;
-      const z64 R = HQ[e] - rho[c] * Q[e];
-      HQ[e] = R;
-      rmax = fmax(rmax, sqrt(abs2(R)));
-      (void)r;
+      z64 acc = HQ[e];
+      for (int q = 0; q < p; ++q) acc = acc - Q[r * p + q] * G[q * p + c];
+      C[e] = acc;  // residual, kept in C
     }
-    rmax = -block_min(-rmax, red);
-    if (rmax <= tol) {
-      *ok = 1;
-      break;
-    }
-    if (it == MAX_IT - 1 || n == p) {
-      *ok = (n == p);
-      break;
-    }
-    // C = V_u^dagger R / (rho_i - lam_a)
+    __syncthreads();
     const int nu = n - p;
     for (int e = tid; e < nu * p; e += nt) {
       const int a = e / p, i = e - a * p;
       const int col = ord[p + a];
       z64 acc(0.0, 0.0);
-      for (int r = 0; r < n; ++r) cfma_conj(acc, ccast<double>(V[r * n + col]), HQ[r * p + i]);
-      const double den = rho[i] - lam[col];
-      C[e] = (1.0 / den) * acc;
+      for (int r = 0; r < n; ++r) cfma_conj(acc, ccast<double>(V[r * n + col]), C[r * p + i]);
+      HQ[e] = (1.0 / (G[i * p + i].re - lam[col])) * acc;  // correction coefficients
     }
     __syncthreads();
     for (int e = tid; e < n * p; e += nt) {
       const int r = e / p, i = e - r * p;
       z64 acc = Q[e];
-      for (int a = 0; a < nu; ++a) cfma(acc, ccast<double>(V[r * n + ord[p + a]]), C[a * p + i]);
+      for (int a = 0; a < nu; ++a) cfma(acc, ccast<double>(V[r * n + ord[p + a]]), HQ[a * p + i]);
       Q[e] = acc;
     }
     __syncthreads();
+    if (!cholqr(Q, G, n, p, flag)) *ok = 0;
   }
-  // gap: Rayleigh quotient of the (p+1)-th FP32 vector in FP64
+  // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p
   double gap = INFINITY;
   if (p < n) {
-    const int col = ord[p];
-    double num = 0.0, den = 0.0;
-    for (int r = tid; r < n; r += nt) {
-      z64 hv(0.0, 0.0);
-      for (int c = 0; c < n; ++c) cfma(hv, H[r * n + c], ccast<double>(V[c * n + col]));
-      const z64 v = ccast<double>(V[r * n + col]);
-      num += v.re * hv.re + v.im * hv.im;
-      den += abs2(v);
+    double rq[2];
+    for (int s = 0; s < 2; ++s) {
+      const int col = ord[p - 1 + s];
+      double num = 0.0, den = 0.0;
+      for (int r = tid; r < n; r += nt) {
+        z64 hv(0.0, 0.0);
+        for (int c = 0; c < n; ++c) cfma(hv, H[r * n + c], ccast<double>(V[c * n + col]));
+        const z64 v = ccast<double>(V[r * n + col]);
+        num += v.re * hv.re + v.im * hv.im;
+        den += abs2(v);
+      }
+      num = block_sum(num, red);
+      den = block_sum(den, red);
+      rq[s] = num / den;
     }
-    num = block_sum(num, red);
-    den = block_sum(den, red);
-    gap = num / den - rho[p - 1];
+    gap = rq[1] - rq[0];
   }
   return gap;
 }
@@ -458,6 +456,8 @@ __global__ void k_eigh_small(EighArgs a) {
       __syncthreads();
       refine_mixed(H64, reinterpret_cast<const c32*>(V), ord, lam, n, p, Q, HQ, C, G, Zg, rho,
                    ord2, rot64, red, a.max_sweeps, &ok, flag);
+      // individual eigenpairs: Rayleigh-Ritz on the refined subspace
+      if (!ritz(H64, Q, HQ, C, G, Zg, rho, ord2, n, p, rot64, red, a.max_sweeps)) ok = 0;
     }
     double* ev = a.evals + a.e_off[b];
     for (int c = tid; c < n; c += nt) ev[c] = (mixed && c < p) ? rho[c] : lam[ord[c]];
