@@ -14,6 +14,8 @@ constexpr int SMALL_N_MAX = 32;
 constexpr int LOOP_P_MAX = 64;
 // Distinct translations whose phases are cached in shared memory per k-point.
 constexpr int PHASE_CACHE = 256;
+// Distinct translations the one-thread-per-k-point path keeps per thread.
+constexpr int TINY_R_MAX = 16;
 
 struct StatesArgs {
   DevModel model;
@@ -93,6 +95,7 @@ inline cudaError_t set_smem_once(Kern kernel, size_t bytes, size_t& cached) {
 
 cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);
+cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, bool* handled);
 cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s);
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s);
 cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s);

@@ -502,6 +502,9 @@ static cudaError_t states_impl(const StatesArgs& a, int p_out, cudaStream_t s) {
 
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s) {
   if (a.K <= 0) return cudaSuccess;
+  bool handled = false;
+  const cudaError_t e = launch_states_tiny(a, p_out, s, &handled);
+  if (handled || e != cudaSuccess) return e;
   return a.mixed ? states_impl<float>(a, p_out, s) : states_impl<double>(a, p_out, s);
 }
 
