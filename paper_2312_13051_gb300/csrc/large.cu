@@ -1,0 +1,615 @@
+// Occupied states for large n (supercells, many-band models): Bloch Hamiltonian,
+// Householder tridiagonalisation, bisection, inverse iteration, back-transform,
+// and for the mixed path an FP64 Newton correction of the occupied block
+// (Sec. I "exact diagonalization" at many k-points; Eq. 1 occupied bands).
+//
+// Each stage is its own kernel over a wave of W k-points, one CTA (or one thread
+// per eigenpair) per k-point, with the wave's scratch in the context arena:
+//   A[kw]   n x n complex, reduced in place; the unit Householder vectors u_c are
+//           kept below the subdiagonal (column c, rows c+1..n-1)
+//   dg, od  diagonal and |off-diagonal| of the real tridiagonal T' = D^dag T D
+//   Dp      the unit phases D (x = Q D z maps eigenvectors z of T' to those of H)
+//   lam, Z  eigenvalues (ascending) and eigenvectors of T' (Z[kw][col][row])
+// T is the working precision of the reduction (double: FP64 path, float: mixed).
+#include <float.h>
+
+#include "jacobi.cuh"
+#include "launch.h"
+
+namespace bw {
+
+template <typename T>
+__device__ __forceinline__ T lg_eps();
+template <>
+__device__ __forceinline__ double lg_eps<double>() { return 2.220446049250313e-16; }
+template <>
+__device__ __forceinline__ float lg_eps<float>() { return 1.1920929e-7f; }
+
+// Warp-wide sum of a complex value.
+template <typename T>
+__device__ __forceinline__ cx<T> warp_csum(cx<T> v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+  }
+  return v;
+}
+
+
+__device__ __forceinline__ void lg_kpoint(const LargeArgs& a, long long k, double f[3]) {
+  if (a.f) {
+    f[0] = a.f[3 * k]; f[1] = a.f[3 * k + 1]; f[2] = a.f[3 * k + 2];
+  } else {
+    const int i = int(k / a.plane.N), j = int(k - (long long)i * a.plane.N);
+    plane_f(a.plane, i, j, f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: Bloch Hamiltonian of the wave's k-points (full Hermitian matrix).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lg_build(LargeArgs a) {
+  __shared__ __align__(16) unsigned char phs_raw[PHASE_CACHE * sizeof(z64)];
+  z64* phs = reinterpret_cast<z64*>(phs_raw);
+  const DevModel& md = a.model;
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  const int nRs = min(md.n_R, PHASE_CACHE);
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    const long long k = a.k0 + kw;
+    double f[3];
+    lg_kpoint(a, k, f);
+    for (int r = tid; r < nRs; r += nt) phs[r] = bloch_phase(f, md.Rv + 3 * r);
+    cx<T>* A = reinterpret_cast<cx<T>*>(a.A) + kw * (long long)n * n;
+    for (long long e = tid; e < (long long)n * n; e += nt) A[e] = cx<T>(T(0), T(0));
+    __syncthreads();
+    for (int e = tid; e < md.n_ent; e += nt) {
+      z64 acc(0.0, 0.0);
+      for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h) {
+        const int r = md.hop_r[h];
+        cfma(acc, md.hop_t[h], r < nRs ? phs[r] : bloch_phase(f, md.Rv + 3 * r));
+      }
+      A[(long long)md.ent_row[e] * n + md.ent_col[e]] = ccast<T>(acc);
+      if (a.Hent) a.Hent[kw * (long long)md.n_ent + e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: Householder reduction to tridiagonal form, one CTA per k-point.
+// For column c, x = A[c+1:, c]; P = I - 2 u u^dagger with u ~ x - alpha e_1,
+// alpha = -e^{i arg x_0} |x|, maps x to alpha e_1.  With p = A22 u, K = u^dag p
+// and w = p - K u, the trailing block becomes A22 - 2 (u w^dag + w u^dag).
+// The complex subdiagonal alpha_c is made real by D: D_0 = 1,
+// D_{c+1} = D_c alpha_c / |alpha_c|, off-diagonal |alpha_c|.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lg_tridiag(LargeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  cx<T>* u = reinterpret_cast<cx<T>*>(smem);          // n
+  cx<T>* w = u + n;                                   // n
+  cx<T>* al = w + n;                                  // n   complex subdiagonal
+  double* red = reinterpret_cast<double*>(al + n);    // 64
+  __shared__ double s_nrm2, s_x0re, s_x0im;
+  __shared__ int s_skip;
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    cx<T>* A = reinterpret_cast<cx<T>*>(a.A) + kw * (long long)n * n;
+    T* dg = reinterpret_cast<T*>(a.dg) + kw * n;
+    T* od = reinterpret_cast<T*>(a.od) + kw * n;
+    cx<T>* Dp = reinterpret_cast<cx<T>*>(a.Dp) + kw * n;
+    for (int c = 0; c + 2 < n; ++c) {
+      const int m = n - c - 1;  // length of x
+      double s = 0.0;
+      for (int r = tid; r < m; r += nt) {
+        const cx<T> x = A[(long long)(c + 1 + r) * n + c];
+        u[r] = x;
+        s += double(abs2(x));
+      }
+      s = block_sum(s, red);
+      if (tid == 0) {
+        s_nrm2 = s;
+        s_x0re = double(u[0].re);
+        s_x0im = double(u[0].im);
+        s_skip = !(s - (s_x0re * s_x0re + s_x0im * s_x0im) > 0.0);
+      }
+      __syncthreads();
+      const double nx = sqrt(s_nrm2), ax0 = hypot(s_x0re, s_x0im);
+      if (s_skip) {  // already tridiagonal in this column: no reflection
+        for (int r = tid; r < m; r += nt) A[(long long)(c + 1 + r) * n + c] = cx<T>(T(0), T(0));
+        if (tid == 0) {
+          al[c] = cx<T>(T(s_x0re), T(s_x0im));
+          dg[c] = A[(long long)c * n + c].re;
+        }
+        __syncthreads();
+        continue;
+      }
+      const double phr = ax0 > 0.0 ? s_x0re / ax0 : 1.0, phi = ax0 > 0.0 ? s_x0im / ax0 : 0.0;
+      // v = x - alpha e1 with alpha = -ph |x|: v_0 = ph (|x0| + |x|); |v|^2 = (|x0|+|x|)^2 + tail
+      const double tail = s_nrm2 - ax0 * ax0;
+      const double v0m = ax0 + nx;
+      const T inv = T(1.0 / sqrt(v0m * v0m + tail));
+      __syncthreads();
+      for (int r = tid; r < m; r += nt) {
+        cx<T> v = u[r];
+        if (r == 0) v = cx<T>(T(phr * v0m), T(phi * v0m));
+        u[r] = inv * v;
+      }
+      __syncthreads();
+      // p = A22 u: one warp per row, lanes along the row
+      for (int r = warp; r < m; r += nwarp) {
+        const cx<T>* row = A + (long long)(c + 1 + r) * n + (c + 1);
+        cx<T> acc(T(0), T(0));
+        for (int q = lane; q < m; q += 32) cfma(acc, row[q], u[q]);
+        acc = warp_csum(acc);
+        if (lane == 0) w[r] = acc;
+      }
+      __syncthreads();
+      double kr = 0.0;
+      for (int r = tid; r < m; r += nt) kr += double(u[r].re * w[r].re + u[r].im * w[r].im);
+      kr = block_sum(kr, red);
+      for (int r = tid; r < m; r += nt) w[r] = w[r] - T(kr) * u[r];
+      __syncthreads();
+      // A22 <- A22 - 2 (u w^dag + w u^dag)
+      for (long long e = tid; e < (long long)m * m; e += nt) {
+        const int r = int(e / m), q = int(e - (long long)r * m);
+        cx<T>& x = A[(long long)(c + 1 + r) * n + (c + 1 + q)];
+        const cx<T> t1 = u[r] * conj(w[q]), t2 = w[r] * conj(u[q]);
+        x = x - T(2) * (t1 + t2);
+      }
+      if (tid == 0) {
+        al[c] = cx<T>(T(-phr * nx), T(-phi * nx));
+        dg[c] = A[(long long)c * n + c].re;
+      }
+      // keep u below the subdiagonal for the back-transform
+      for (int r = tid; r < m; r += nt) A[(long long)(c + 1 + r) * n + c] = u[r];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (n >= 2) {
+        dg[n - 2] = A[(long long)(n - 2) * n + (n - 2)].re;
+        al[n - 2] = A[(long long)(n - 1) * n + (n - 2)];
+      }
+      dg[n - 1] = A[(long long)(n - 1) * n + (n - 1)].re;
+      // the last subdiagonal entry is not a reflector: clear it for the back-transform
+      if (n >= 2) A[(long long)(n - 1) * n + (n - 2)] = cx<T>(T(0), T(0));
+    }
+    __syncthreads();
+    // unit phases of the subdiagonal, then their prefix products (serial: cheap)
+    for (int c = tid; c + 1 < n; c += nt) {
+      const T aa = sqrt(abs2(al[c]));
+      od[c] = aa;
+      al[c] = aa > T(0) ? cx<T>(al[c].re / aa, al[c].im / aa) : cx<T>(T(1), T(0));
+    }
+    __syncthreads();
+    if (tid == 0) {
+      cx<T> dcur(T(1), T(0));
+      Dp[0] = dcur;
+      for (int c = 0; c + 1 < n; ++c) {
+        dcur = dcur * al[c];
+        Dp[c + 1] = dcur;
+      }
+      od[n - 1] = T(0);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 3: eigenvalues of T' by bisection on Sturm counts, one thread per
+// (k-point, eigenvalue index), Gershgorin interval.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int sturm_count(const T* dg, const T* od, int n, T x, T pivmin) {
+  int cnt = 0;
+  T q = dg[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < T(0);
+  for (int i = 1; i < n; ++i) {
+    q = dg[i] - x - od[i - 1] * od[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < T(0);
+  }
+  return cnt;
+}
+
+template <typename T>
+__device__ __forceinline__ void gershgorin(const T* dg, const T* od, int n, T& lo, T& hi, T& tn) {
+  lo = T(INFINITY);
+  hi = -T(INFINITY);
+  tn = T(0);
+  for (int i = 0; i < n; ++i) {
+    const T r = (i > 0 ? od[i - 1] : T(0)) + (i + 1 < n ? od[i] : T(0));
+    lo = fmin(lo, dg[i] - r);
+    hi = fmax(hi, dg[i] + r);
+    tn = fmax(tn, fabs(dg[i]) + r);
+  }
+}
+
+template <typename T>
+__global__ void k_lg_bisect(LargeArgs a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.W * a.nval) return;
+  const long long kw = t / a.nval;
+  const int idx = int(t - kw * a.nval), n = a.n;
+  const T* dg = reinterpret_cast<const T*>(a.dg) + kw * n;
+  const T* od = reinterpret_cast<const T*>(a.od) + kw * n;
+  T lo, hi, tn;
+  gershgorin(dg, od, n, lo, hi, tn);
+  const T span = fmax(hi - lo, T(1e-30));
+  lo -= T(4) * lg_eps<T>() * span + T(1e-30);
+  hi += T(4) * lg_eps<T>() * span + T(1e-30);
+  const T pivmin = T(1e-30) * fmax(T(1), tn * tn);
+  for (int it = 0; it < 96; ++it) {
+    const T mid = T(0.5) * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (hi - lo <= T(2) * lg_eps<T>() * fmax(fabs(lo), fabs(hi))) break;
+    if (sturm_count(dg, od, n, mid, pivmin) > idx)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  reinterpret_cast<T*>(a.lam)[kw * a.nval + idx] = T(0.5) * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 4: eigenvectors of T' by inverse iteration.  (T' - lambda) = P L U with
+// partial pivoting (U has two superdiagonals); three solves from a fixed
+// pseudo-random start.  Eigenvalues closer than 1e-3 ||T'|| form a cluster, whose
+// vectors one thread computes in order, orthogonalising each against the earlier
+// ones of its cluster at every iteration.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double hash_unit(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return double(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+template <typename T>
+__device__ void tri_factor(const T* dg, const T* od, int n, T lam, T tiny, T* u0, T* u1, T* u2,
+                           T* l, T* piv) {
+  T c0 = dg[0] - lam, c1 = n > 1 ? od[0] : T(0);
+  for (int i = 0; i + 1 < n; ++i) {
+    const T b = od[i];                 // subdiagonal entry of row i+1
+    const T a1 = dg[i + 1] - lam;      // diagonal of row i+1
+    const T e1 = i + 2 < n ? od[i + 1] : T(0);  // superdiagonal of row i+1
+    if (fabs(b) > fabs(c0)) {          // swap rows i and i+1
+      const T m = c0 / b;
+      u0[i] = b; u1[i] = a1; u2[i] = e1;
+      l[i] = m; piv[i] = T(1);
+      const T r1 = c1 - m * a1, r2 = -m * e1;
+      c0 = r1; c1 = r2;
+      // the remaining row now has entries at columns i+1 (r1) and i+2 (r2)
+    } else {
+      if (c0 == T(0)) c0 = tiny;
+      const T m = b / c0;
+      u0[i] = c0; u1[i] = c1; u2[i] = T(0);
+      l[i] = m; piv[i] = T(0);
+      c0 = a1 - m * c1;
+      c1 = e1;
+    }
+  }
+  u0[n - 1] = c0 == T(0) ? tiny : c0;
+}
+
+template <typename T>
+__device__ void tri_solve(int n, T tiny, const T* u0, const T* u1, const T* u2, const T* l,
+                          const T* piv, T* x) {
+  for (int i = 0; i + 1 < n; ++i) {
+    if (piv[i] != T(0)) {
+      const T t = x[i];
+      x[i] = x[i + 1];
+      x[i + 1] = t;
+    }
+    x[i + 1] -= l[i] * x[i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T s = x[i];
+    if (i + 1 < n) s -= u1[i] * x[i + 1];
+    if (i + 2 < n) s -= u2[i] * x[i + 2];
+    T d = u0[i];
+    if (fabs(d) < tiny) d = d < T(0) ? -tiny : tiny;
+    x[i] = s / d;
+  }
+}
+
+template <typename T>
+__global__ void k_lg_invit(LargeArgs a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.W * a.nvec) return;
+  const long long kw = t / a.nvec;
+  const int idx = int(t - kw * a.nvec), n = a.n;
+  const T* dg = reinterpret_cast<const T*>(a.dg) + kw * n;
+  const T* od = reinterpret_cast<const T*>(a.od) + kw * n;
+  const T* lam = reinterpret_cast<const T*>(a.lam) + kw * a.nval;
+  T lo, hi, tn;
+  gershgorin(dg, od, n, lo, hi, tn);
+  const T tolc = T(1e-3) * tn;
+  if (idx > 0 && lam[idx] - lam[idx - 1] <= tolc) return;  // not the first of its cluster
+  int end = idx;
+  while (end + 1 < a.nvec && lam[end + 1] - lam[end] <= tolc) ++end;
+  T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)a.nvec * n;
+  T* wk = reinterpret_cast<T*>(a.work) + t * 5LL * n;
+  T *u0 = wk, *u1 = wk + n, *u2 = wk + 2 * n, *l = wk + 3 * n, *piv = wk + 4 * n;
+  const T tiny = fmax(lg_eps<T>() * tn, T(1e-30));
+  for (int j = idx; j <= end; ++j) {
+    T* x = Z + (long long)j * n;
+    // a slightly shifted copy of the eigenvalue keeps the factor non-singular
+    tri_factor(dg, od, n, lam[j], tiny, u0, u1, u2, l, piv);
+    for (int r = 0; r < n; ++r) x[r] = T(hash_unit((unsigned long long)j * 1000003ull + r));
+    for (int it = 0; it < 3; ++it) {
+      tri_solve(n, tiny, u0, u1, u2, l, piv, x);
+      for (int q = idx; q < j; ++q) {  // orthogonalise within the cluster
+        const T* y = Z + (long long)q * n;
+        T d = T(0);
+        for (int r = 0; r < n; ++r) d += y[r] * x[r];
+        for (int r = 0; r < n; ++r) x[r] -= d * y[r];
+      }
+      T s = T(0);
+      for (int r = 0; r < n; ++r) s += x[r] * x[r];
+      s = T(1) / sqrt(s);
+      for (int r = 0; r < n; ++r) x[r] *= s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 5: back-transform x = Q D z for the first ncol eigenvectors, Q = P_0 ... P_{n-3}:
+// X = D Z, then X <- P_c X for c = n-3 down to 0 (P_c = I - 2 u_c u_c^dagger).
+// Output X[r][col] with leading dimension ncol, precision To.
+// ---------------------------------------------------------------------------
+template <typename T, typename To>
+__device__ void apply_reflectors(const cx<T>* A, int n, cx<To>* X, int ncol, bool reverse,
+                                 cx<To>* us, cx<To>* wv) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int s = 0; s + 2 < n; ++s) {
+    const int c = reverse ? n - 3 - s : s;
+    const int m = n - c - 1;
+    for (int r = tid; r < m; r += nt) us[r] = ccast<To>(A[(long long)(c + 1 + r) * n + c]);
+    __syncthreads();
+    for (int col = tid; col < ncol; col += nt) {
+      cx<To> acc(To(0), To(0));
+      for (int r = 0; r < m; ++r) cfma_conj(acc, us[r], X[(long long)(c + 1 + r) * ncol + col]);
+      wv[col] = acc;
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)m * ncol; e += nt) {
+      const int r = int(e / ncol), col = int(e - (long long)r * ncol);
+      cx<To>& x = X[(long long)(c + 1 + r) * ncol + col];
+      x = x - To(2) * (us[r] * wv[col]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, typename To>
+__global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_stride, int ncol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  cx<To>* us = reinterpret_cast<cx<To>*>(smem);
+  cx<To>* wv = us + n;
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    const cx<T>* A = reinterpret_cast<const cx<T>*>(a.A) + kw * (long long)n * n;
+    const cx<T>* Dp = reinterpret_cast<const cx<T>*>(a.Dp) + kw * n;
+    const T* Z = reinterpret_cast<const T*>(a.Z) + kw * (long long)a.nvec * n;
+    cx<To>* X = out + kw * out_stride;
+    for (long long e = tid; e < (long long)n * ncol; e += nt) {
+      const int r = int(e / ncol), col = int(e - (long long)r * ncol);
+      const cx<T> d = Dp[r];
+      const T z = Z[(long long)col * n + r];
+      X[e] = cx<To>(To(d.re * z), To(d.im * z));
+    }
+    __syncthreads();
+    apply_reflectors<T, To>(A, n, X, ncol, true, us, wv);
+  }
+}
+
+// FP64 path: direct gap from the bisection eigenvalues.
+__global__ void k_lg_gap64(LargeArgs a) {
+  const long long kw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kw >= a.W) return;
+  const double* lam = reinterpret_cast<const double*>(a.lam) + kw * a.nval;
+  const double g = a.p < a.n ? lam[a.p] - lam[a.p - 1] : INFINITY;
+  a.gap[a.k0 + kw] = g;
+  if (!(g > a.gap_tol)) report(a.status, ST_EGAP, a.k0 + kw, g);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 6 (mixed): one FP64 Newton correction of the occupied block.
+//   Q = X[:, :p] (FP32 eigenvectors, promoted); R_i = H q_i - (q_i^dag H q_i) q_i in
+//   FP64 from the hopping plan's entries; the complement's coefficients
+//   C[a][i] = z_a^T D^dag Q_h^dag R_i / (rho_i - lam_a) through the FP32 reflectors;
+//   Q += Q_h D Z_u C; then Q <- Q (I - (Q^dag Q - I) / 2) (first-order Lowdin
+//   step, exact to second order in the FP32 non-orthogonality).
+//   The gap comes from FP64 Rayleigh quotients of the (p-1)-th and p-th vectors.
+// The off-diagonal part of Q^dag H Q is of the order of the FP32 error; its
+// projection on the complement enters at second order and is dropped.
+// ---------------------------------------------------------------------------
+__global__ void k_lg_refine(LargeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, nbt = a.nbt, tid = threadIdx.x, nt = blockDim.x;
+  const DevModel& md = a.model;
+  c32* us = reinterpret_cast<c32*>(smem);            // n
+  c32* wv = us + n;                                  // p
+  double* rho = reinterpret_cast<double*>(wv + p + (p & 1));  // p + 2
+  double* red = rho + p + 2;                         // 64
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    const long long k = a.k0 + kw;
+    const c32* A = reinterpret_cast<const c32*>(a.A) + kw * (long long)n * n;
+    const c32* Dp = reinterpret_cast<const c32*>(a.Dp) + kw * n;
+    const float* Z = reinterpret_cast<const float*>(a.Z) + kw * (long long)a.nvec * n;
+    const float* lam = reinterpret_cast<const float*>(a.lam) + kw * a.nval;
+    const c32* X = reinterpret_cast<const c32*>(a.X) + kw * (long long)n * nbt;
+    const z64* He = a.Hent + kw * (long long)md.n_ent;
+    z64* Q = a.U + kw * (long long)n * p;
+    z64* R = a.R64 + kw * (long long)n * p;
+    c32* C = a.C32 + kw * (long long)n * p;
+    z64* G = a.G64 + kw * (long long)p * p;
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int r = int(e / p), c = int(e - (long long)r * p);
+      Q[e] = ccast<double>(X[(long long)r * nbt + c]);
+    }
+    __syncthreads();
+    // R = H Q (rows from the plan)
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int r = int(e / p), c = int(e - (long long)r * p);
+      z64 acc(0.0, 0.0);
+      for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) cfma(acc, He[q], Q[(long long)md.ent_col[q] * p + c]);
+      R[e] = acc;
+    }
+    __syncthreads();
+    for (int c = tid; c < p; c += nt) {
+      double s = 0.0;
+      for (int r = 0; r < n; ++r) {
+        const z64 q = Q[(long long)r * p + c], h = R[(long long)r * p + c];
+        s += q.re * h.re + q.im * h.im;
+      }
+      rho[c] = s;
+    }
+    __syncthreads();
+    // R <- R - rho Q, to FP32 (small residual) in C
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int c = int(e % p);
+      C[e] = ccast<float>(R[e] - rho[c] * Q[e]);
+    }
+    __syncthreads();
+    // C <- D^dag Q_h^dag C
+    apply_reflectors<float, float>(A, n, C, p, false, us, wv);
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int r = int(e / p);
+      C[e] = conj(Dp[r]) * C[e];
+    }
+    __syncthreads();
+    // coefficients of the complement, stored in R (FP64 workspace reuse): rows a < n - p
+    const int nu = n - p;
+    for (long long e = tid; e < (long long)nu * p; e += nt) {
+      const int ua = int(e / p), c = int(e - (long long)ua * p);
+      const float* z = Z + (long long)(p + ua) * n;
+      c32 acc(0.f, 0.f);
+      for (int r = 0; r < n; ++r) acc = acc + z[r] * C[(long long)r * p + c];
+      const double den = rho[c] - double(lam[p + ua]);
+      R[e] = (1.0 / den) * ccast<double>(acc);
+    }
+    __syncthreads();
+    // Delta = D Z_u coef (FP32), then Q_h Delta
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int r = int(e / p), c = int(e - (long long)r * p);
+      z64 acc(0.0, 0.0);
+      for (int ua = 0; ua < nu; ++ua) acc = acc + double(Z[(long long)(p + ua) * n + r]) * R[(long long)ua * p + c];
+      C[e] = Dp[r] * ccast<float>(acc);
+    }
+    __syncthreads();
+    apply_reflectors<float, float>(A, n, C, p, true, us, wv);
+    for (long long e = tid; e < (long long)n * p; e += nt) Q[e] = Q[e] + ccast<double>(C[e]);
+    __syncthreads();
+    // G = Q^dag Q - I, then Q <- Q - Q G / 2
+    for (long long e = tid; e < (long long)p * p; e += nt) {
+      const int x = int(e / p), y = int(e - (long long)x * p);
+      z64 acc(0.0, 0.0);
+      for (int r = 0; r < n; ++r) cfma_conj(acc, Q[(long long)r * p + x], Q[(long long)r * p + y]);
+      if (x == y) acc.re -= 1.0;
+      G[e] = acc;
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)n * p; e += nt) {
+      const int r = int(e / p), c = int(e - (long long)r * p);
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) cfma(acc, Q[(long long)r * p + q], G[(long long)q * p + c]);
+      R[e] = acc;
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)n * p; e += nt) Q[e] = Q[e] - 0.5 * R[e];
+    __syncthreads();
+    // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p
+    if (p < n) {
+      double rq[2];
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int col = p - 1 + s2;
+        double num = 0.0, den = 0.0;
+        for (int r = tid; r < n; r += nt) {
+          z64 hv(0.0, 0.0);
+          for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q)
+            cfma(hv, He[q], ccast<double>(X[(long long)md.ent_col[q] * nbt + col]));
+          const z64 v = ccast<double>(X[(long long)r * nbt + col]);
+          num += v.re * hv.re + v.im * hv.im;
+          den += abs2(v);
+        }
+        num = block_sum(num, red);
+        den = block_sum(den, red);
+        rq[s2] = num / den;
+      }
+      if (tid == 0) {
+        const double g = rq[1] - rq[0];
+        a.gap[k] = g;
+        if (!(g > a.gap_tol)) report(a.status, ST_EGAP, k, g);
+      }
+    } else if (tid == 0) {
+      a.gap[k] = INFINITY;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launcher: every stage of one wave, in stream order.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int LG_THREADS = 256;
+
+int lg_grid(long long units) {
+  const long long cap = 152LL * 4;
+  return int(units < cap ? (units > 0 ? units : 1) : cap);
+}
+
+template <typename T>
+cudaError_t lg_common(const LargeArgs& a, cudaStream_t s) {
+  k_lg_build<T><<<lg_grid(a.W), LG_THREADS, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t sm_tri = 3 * size_t(a.n) * sizeof(cx<T>) + 64 * sizeof(double);
+  static size_t cached = 0;
+  if ((e = set_smem_once(k_lg_tridiag<T>, sm_tri, cached)) != cudaSuccess) return e;
+  k_lg_tridiag<T><<<lg_grid(a.W), LG_THREADS, sm_tri, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long nb = a.W * a.nval;
+  k_lg_bisect<T><<<int((nb + 127) / 128), 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long ni = a.W * a.nvec;
+  k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
+  if (a.W <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (!a.mixed) {
+    if ((e = lg_common<double>(a, s)) != cudaSuccess) return e;
+    const size_t sm = 2 * size_t(a.n > a.p ? a.n : a.p) * sizeof(z64);
+    static size_t cached = 0;
+    if ((e = set_smem_once(k_lg_backtransform<double, double>, sm, cached)) != cudaSuccess) return e;
+    k_lg_backtransform<double, double><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
+        a, a.U, (long long)a.n * a.p, a.p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_lg_gap64<<<int((a.W + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
+  const size_t sm = 2 * size_t(a.n > a.nbt ? a.n : a.nbt) * sizeof(c32);
+  static size_t cached = 0;
+  if ((e = set_smem_once(k_lg_backtransform<float, float>, sm, cached)) != cudaSuccess) return e;
+  k_lg_backtransform<float, float><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
+      a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smr = (size_t(a.n) + a.p + 1) * sizeof(c32) + (size_t(a.p) + 2 + 64) * sizeof(double) + 16;
+  static size_t cached_r = 0;
+  if ((e = set_smem_once(k_lg_refine, smr, cached_r)) != cudaSuccess) return e;
+  k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bw

@@ -10,6 +10,8 @@ namespace bw {
 
 // Largest n handled by the shared-memory Jacobi path.
 constexpr int SMALL_N_MAX = 32;
+// Largest n of the tridiagonal (large-n) path.
+constexpr int LARGE_N_MAX = 4096;
 // Largest p handled by the shared-memory loop kernels (Wilson matrix p x p).
 constexpr int LOOP_P_MAX = 64;
 // Distinct translations whose phases are cached in shared memory per k-point.
@@ -92,6 +94,44 @@ inline cudaError_t set_smem_once(Kern kernel, size_t bytes, size_t& cached) {
   if (e == cudaSuccess) cached = bytes;
   return e;
 }
+
+// Large-n occupied states over a wave of W k-points starting at k0 (see large.cu).
+struct LargeArgs {
+  DevModel model;
+  DevPlane plane;
+  const double* f;        // optional explicit k-points (K x 3)
+  int n, p;
+  int nval;               // eigenvalues of T' computed (>= p + 1 when p < n)
+  int nvec;               // eigenvectors of T' computed
+  int nbt;                // columns back-transformed (mixed: p + 1 when p < n)
+  long long k0, W;
+  int mixed;
+  double gap_tol;
+  // wave scratch
+  void* A;                // W x n x n complex (T)
+  void* dg;               // W x n (T)
+  void* od;               // W x n (T)
+  void* Dp;               // W x n complex (T)
+  void* lam;              // W x nval (T)
+  void* Z;                // W x nvec x n (T), vector-contiguous
+  void* work;             // W x nvec x 5 n (T)
+  void* X;                // W x n x nbt complex float (mixed)
+  z64* Hent;              // W x n_ent (mixed)
+  z64* R64;               // W x n x p (mixed)
+  c32* C32;               // W x n x p (mixed)
+  z64* G64;               // W x p x p (mixed)
+  const int* row_ptr;     // n + 1: first entry of each row in the plan
+  // outputs
+  z64* U;                 // W x n x p (wave-relative)
+  double* gap;            // K (absolute k)
+  DevStatus* status;
+};
+
+// Launches every stage of the large-n solver for one wave.
+cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);
+// Projected-spin split of global occupied blocks: U (K x n x p) -> Us (K x n x p/2).
+cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
+                              cudaStream_t s);
 
 cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);

@@ -82,10 +82,10 @@ struct Blob {
 
 struct HostPlan {
   int n = 0, n_R = 0, n_ent = 0;
-  std::vector<int> Rv, ent_row, ent_col, ent_start, hop_r;
+  std::vector<int> Rv, ent_row, ent_col, ent_start, hop_r, row_ptr;
   std::vector<z64> hop_t;
   double tmax = 0.0;
-  size_t o_Rv, o_row, o_col, o_start, o_r, o_t;
+  size_t o_Rv, o_row, o_col, o_start, o_r, o_t, o_rowptr;
 };
 
 bw_status make_plan(bw_ctx* ctx, const bw_model* m, HostPlan& P) {
@@ -172,6 +172,10 @@ bw_status make_plan(bw_ctx* ctx, const bw_model* m, HostPlan& P) {
   }
   P.ent_start.push_back(int(g.size()));
   P.n_ent = int(P.ent_row.size());
+  // first entry of each row (entries are sorted by row)
+  P.row_ptr.assign(n + 1, 0);
+  for (int e = 0; e < P.n_ent; ++e) P.row_ptr[P.ent_row[e] + 1]++;
+  for (int r = 0; r < n; ++r) P.row_ptr[r + 1] += P.row_ptr[r];
   return BW_OK;
 }
 
@@ -182,6 +186,7 @@ void plan_to_blob(HostPlan& P, Blob& b) {
   P.o_start = b.add(P.ent_start);
   P.o_r = b.add(P.hop_r);
   P.o_t = b.add(P.hop_t);
+  P.o_rowptr = b.add(P.row_ptr);
 }
 
 bw::DevModel dev_model(const HostPlan& P, const char* base) {
@@ -390,8 +395,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   if ((st = make_plan(ctx, model, P))) return st;
   const int n = P.n;
   if (p < 1 || p > n) return fail(ctx, BW_EINVAL, "need 1 <= p <= n (p = %d, n = %d)", p, n);
-  if (n > bw::SMALL_N_MAX)
-    return fail(ctx, BW_EINVAL, "n = %d exceeds the largest supported size %d", n, bw::SMALL_N_MAX);
+  if (n > bw::LARGE_N_MAX)
+    return fail(ctx, BW_EINVAL, "n = %d exceeds the largest supported size %d", n, bw::LARGE_N_MAX);
+  const bool large = n > bw::SMALL_N_MAX;
   int p_eff = p;
   HostOp op;
   if (kind == LoopKind::Spin) {
@@ -408,6 +414,8 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     if (!std::isfinite(cut)) return fail(ctx, BW_EINVAL, "cut is not finite");
   }
   if (p_eff > bw::LOOP_P_MAX) return fail(ctx, BW_EINVAL, "p = %d exceeds %d", p_eff, bw::LOOP_P_MAX);
+  if (large && kind == LoopKind::Spin && p > 64)
+    return fail(ctx, BW_EINVAL, "spin-resolved loop for n > %d supports p <= 64 (p = %d)", bw::SMALL_N_MAX, p);
   const Opts o = resolve_opts(opts, P.tmax);
   if (o.unitarise && p_eff > 32) return fail(ctx, BW_EINVAL, "unitarise supports p <= 32");
   const long long K = (long long)plane->N * plane->N_t;
@@ -423,7 +431,30 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const size_t bM = al256(size_t(K) * p_eff * p_eff * sizeof(z64));
   const size_t bW = kind == LoopKind::Nested ? al256(size_t(K) * n * m * sizeof(z64)) : 0;
   const size_t bPso = kind == LoopKind::Spin ? al256(size_t(K) * sizeof(double)) : 0;
-  const size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bPso + 4096;
+  size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bPso + 4096;
+  // large n: per-k-point scratch of the tridiagonal solver, processed in waves
+  const bool mx = prec == BW_MIXED;
+  const size_t ts = mx ? sizeof(float) : sizeof(double);
+  const int nval = mx ? n : std::min(n, p + 1), nvec = mx ? n : p;
+  const int nbt = mx ? std::min(n, p + 1) : p;
+  const size_t sz_A = al256(size_t(n) * n * 2 * ts), sz_v = al256(size_t(n) * ts),
+               sz_D = al256(size_t(n) * 2 * ts), sz_lam = al256(size_t(nval) * ts),
+               sz_Z = al256(size_t(nvec) * n * ts), sz_wk = al256(size_t(nvec) * 5 * n * ts),
+               sz_X = mx ? al256(size_t(n) * nbt * sizeof(bw::c32)) : 0,
+               sz_He = mx ? al256(size_t(P.n_ent) * sizeof(z64)) : 0,
+               sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
+               sz_C = mx ? al256(size_t(n) * p * sizeof(bw::c32)) : 0,
+               sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0,
+               sz_Uf = kind == LoopKind::Spin ? al256(size_t(n) * p * sizeof(z64)) : 0;
+  const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
+                       sz_G + sz_Uf;
+  long long Wv = 0;
+  if (large) {
+    const size_t avail = ctx->budget > total ? (ctx->budget - total) / 2 : 0;
+    Wv = std::min<long long>(K, std::max<long long>(1, (long long)(avail / per_k)));
+    Wv = std::min<long long>(Wv, 2048);
+    total += size_t(Wv) * per_k + 16 * 256;
+  }
   begin_call(ctx, s);
   if ((st = reserve(ctx, total, s))) return st;
   char* dblob = carve(ctx, blob.data.size());
@@ -459,7 +490,47 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   sa.gap = gap;
   sa.status = ctx->status;
   prof_start(ctx, s);
-  BW_CUDA(bw::launch_states_small(sa, p_eff, s), "states kernel");
+  if (!large) {
+    BW_CUDA(bw::launch_states_small(sa, p_eff, s), "states kernel");
+  } else {
+    bw::LargeArgs lg;
+    std::memset(&lg, 0, sizeof(lg));
+    lg.model = sa.model;
+    lg.plane = sa.plane;
+    lg.n = n;
+    lg.p = p;
+    lg.nval = nval;
+    lg.nvec = nvec;
+    lg.nbt = nbt;
+    lg.mixed = mx;
+    lg.gap_tol = o.gap_tol;
+    lg.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
+    lg.gap = gap;
+    lg.status = ctx->status;
+    lg.A = carve(ctx, Wv * sz_A);
+    lg.dg = carve(ctx, Wv * sz_v);
+    lg.od = carve(ctx, Wv * sz_v);
+    lg.Dp = carve(ctx, Wv * sz_D);
+    lg.lam = carve(ctx, Wv * sz_lam);
+    lg.Z = carve(ctx, Wv * sz_Z);
+    lg.work = carve(ctx, Wv * sz_wk);
+    if (mx) {
+      lg.X = carve(ctx, Wv * sz_X);
+      lg.Hent = reinterpret_cast<z64*>(carve(ctx, Wv * sz_He));
+      lg.R64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_R));
+      lg.C32 = reinterpret_cast<bw::c32*>(carve(ctx, Wv * sz_C));
+      lg.G64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_G));
+    }
+    z64* Ufull = reinterpret_cast<z64*>(carve(ctx, Wv * sz_Uf));
+    for (long long k0 = 0; k0 < K; k0 += Wv) {
+      lg.k0 = k0;
+      lg.W = std::min(Wv, K - k0);
+      // the wave's occupied blocks go straight to U, or through the spin split
+      lg.U = kind == LoopKind::Spin ? Ufull : U + k0 * (long long)n * p;
+      BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
+      if (kind == LoopKind::Spin) BW_CUDA(bw::launch_pso_global(sa, Ufull, k0, lg.W, s), "spin split kernel");
+    }
+  }
   prof_mark(ctx, s, "states");
 
   bw::LoopArgs la;

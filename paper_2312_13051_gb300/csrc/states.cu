@@ -524,4 +524,40 @@ cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s) {
   return a.mixed ? eigh_impl<float>(a, n_max, s) : eigh_impl<double>(a, n_max, s);
 }
 
+// ---------------------------------------------------------------------------
+// Projected-spin split of occupied blocks already in global memory (large n):
+// U (n x p per k) -> a.U (n x p/2 per k).  One CTA per k-point.
+// ---------------------------------------------------------------------------
+__global__ void k_pso_global(StatesArgs a, const z64* U, long long k0, long long W) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.model.n, p = a.p;
+  z64* S = reinterpret_cast<z64*>(smem);
+  z64* SV = S + p * p;
+  double* mu = reinterpret_cast<double*>(SV + p * p);
+  int* ord = reinterpret_cast<int*>(mu + p);
+  JacRot<double>* rot = reinterpret_cast<JacRot<double>*>(smem + align16(2 * size_t(p) * p * sizeof(z64) +
+                                                                          p * sizeof(double) + p * sizeof(int)));
+  double* red = reinterpret_cast<double*>(rot + (p / 2 + 2));
+  for (long long kw = blockIdx.x; kw < W; kw += gridDim.x) {
+    const long long k = k0 + kw;
+    pso_split(U + kw * (long long)n * p, a.op, a.sign, n, p, S, SV, ord, mu, rot, red, a.max_sweeps,
+              a.U + k * (long long)n * (p / 2), a.pso_evals ? a.pso_evals + k * p : nullptr,
+              a.pso_gap ? a.pso_gap + k : nullptr, a.pso_gap_tol, a.status, k);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
+                              cudaStream_t s) {
+  if (W <= 0) return cudaSuccess;
+  const int p = a.p;
+  const size_t sm = align16(2 * size_t(p) * p * sizeof(z64) + p * sizeof(double) + p * sizeof(int)) +
+                    (p / 2 + 2) * sizeof(JacRot<double>) + 64 * sizeof(double);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_pso_global, sm, cached);
+  if (e != cudaSuccess) return e;
+  k_pso_global<<<grid_for(W), 128, sm, s>>>(a, U, k0, W);
+  return cudaGetLastError();
+}
+
 }  // namespace bw

@@ -253,3 +253,44 @@ def test_two_streams_same_context(lib, ctx):
     ctx.status()
     for ph, _ in outs:
         assert torch.equal(ph, ref)
+
+
+# ---------------------------------------------------------------- large n (tridiagonal path)
+LARGE = {
+    "random40_p10": (lambda: I.random_hermitian_model(40, 31), P(9, 5), 10),
+    "clean_supercell_L3": (lambda: I.supercell(I.spin_hall(1.0), 3), P(8, 4), 18),
+    "disordered_L4": (lambda: I.supercell(I.spin_hall(1.0), 4, W=2.0, seed=7), P(6, 5), 32),
+    "manyband64": (lambda: I.manyband(64), P(7, 3), 32),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(LARGE))
+def test_large_n_wilson_parity(lib, ctx, case, precision):
+    mk, plane, p = LARGE[case]
+    model = mk()
+    ref, rgap = oracle.wilson_loop(model, plane, p)
+    ph, gap = lib.wilson_loop(model, plane, p, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    rel = np.abs(gap.cpu().numpy() - rgap) / np.maximum(1.0, np.abs(rgap))
+    assert rel.max() <= (1e-9 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_n_spin_and_nested(lib, ctx, precision):
+    sc = I.supercell(I.spin_hall(1.0), 4, W=1.5, seed=3)          # n = 64, p = 32
+    S = np.kron(np.eye(16), I.SPIN_HALL_SZ)
+    plane = P(6, 5)
+    ref, rpso, _, _ = oracle.spin_resolved_wilson_loop(sc, plane, 32, S, -1)
+    ph, pso, _, _ = lib.spin_resolved_wilson_loop(sc, plane, 32, S, -1, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    assert np.abs(pso.cpu().numpy() - rpso).max() <= 1e-8
+    model = I.manyband(32)                                          # n = 64, p = 16, m = 8
+    plane = P(6, 6)
+    try:
+        rph, rn, _, _ = oracle.nested_wilson_loop(model, plane, 16, m=8)
+    except oracle.OracleError as e:
+        pytest.skip(f"oracle: {e}")
+    ph, nest, _, _ = lib.nested_wilson_loop(model, plane, 16, m=8, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), rph) <= TOL[precision]
+    assert circ_err_rows(nest.cpu().numpy(), rn) <= TOL[precision]
