@@ -144,14 +144,19 @@ __device__ int jacobi_eigh(cx<T>* A, cx<T>* V, int n, int ld, int max_sweeps, Ja
   return -1;
 }
 
-// order[rank] = index of the rank-th smallest diagonal entry (stable).
+// Sort key that puts NaN after every number, so that ranks always form a
+// permutation (NaN only appears when the input was not finite).
+template <typename T>
+__device__ __forceinline__ T rank_key(T x) { return isnan(x) ? T(INFINITY) : x; }
+
+// order[rank] = index of the rank-th smallest diagonal entry (stable, NaN last).
 template <typename T>
 __device__ void sort_diag(const cx<T>* A, int n, int ld, int* order) {
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
-    const T la = A[a * ld + a].re;
+    const T la = rank_key(A[a * ld + a].re);
     int rank = 0;
     for (int b = 0; b < n; ++b) {
-      const T lb = A[b * ld + b].re;
+      const T lb = rank_key(A[b * ld + b].re);
       rank += (lb < la) || (lb == la && b < a);
     }
     order[rank] = a;

@@ -9,7 +9,7 @@
 //           kept below the subdiagonal (column c, rows c+1..n-1)
 //   dg, od  diagonal and |off-diagonal| of the real tridiagonal T' = D^dag T D
 //   Dp      the unit phases D (x = Q D z maps eigenvectors z of T' to those of H)
-//   lam, Z  eigenvalues (ascending) and eigenvectors of T' (Z[kw][col][row])
+//   lam, Z  eigenvalues (ascending) and eigenvectors of T' (Z[kw][row][col])
 // T is the working precision of the reduction (double: FP64 path, float: mixed).
 #include <float.h>
 
@@ -269,60 +269,72 @@ __device__ __forceinline__ double hash_unit(unsigned long long x) {
   return double(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
+// Interleaved per-thread arrays: element r of thread t's array a lives at
+// base[(a * n + r) * NT + t], so a warp's accesses to the same r are contiguous.
 template <typename T>
-__device__ void tri_factor(const T* dg, const T* od, int n, T lam, T tiny, T* u0, T* u1, T* u2,
-                           T* l, T* piv) {
+struct Strided {
+  T* base;
+  long long NT;
+  int n;
+  __device__ __forceinline__ T& at(int a, int r, long long t) const { return base[((long long)a * n + r) * NT + t]; }
+};
+
+template <typename T>
+__device__ void tri_factor(const T* dg, const T* od, int n, T lam, T tiny, const Strided<T>& W,
+                           long long t) {
   T c0 = dg[0] - lam, c1 = n > 1 ? od[0] : T(0);
   for (int i = 0; i + 1 < n; ++i) {
-    const T b = od[i];                 // subdiagonal entry of row i+1
-    const T a1 = dg[i + 1] - lam;      // diagonal of row i+1
+    const T b = od[i];                          // subdiagonal entry of row i+1
+    const T a1 = dg[i + 1] - lam;               // diagonal of row i+1
     const T e1 = i + 2 < n ? od[i + 1] : T(0);  // superdiagonal of row i+1
-    if (fabs(b) > fabs(c0)) {          // swap rows i and i+1
+    if (fabs(b) > fabs(c0)) {                   // swap rows i and i+1
       const T m = c0 / b;
-      u0[i] = b; u1[i] = a1; u2[i] = e1;
-      l[i] = m; piv[i] = T(1);
-      const T r1 = c1 - m * a1, r2 = -m * e1;
+      W.at(0, i, t) = b; W.at(1, i, t) = a1; W.at(2, i, t) = e1;
+      W.at(3, i, t) = m; W.at(4, i, t) = T(1);
+      const T r1 = c1 - m * a1, r2 = -m * e1;   // remaining row: columns i+1, i+2
       c0 = r1; c1 = r2;
-      // the remaining row now has entries at columns i+1 (r1) and i+2 (r2)
     } else {
       if (c0 == T(0)) c0 = tiny;
       const T m = b / c0;
-      u0[i] = c0; u1[i] = c1; u2[i] = T(0);
-      l[i] = m; piv[i] = T(0);
+      W.at(0, i, t) = c0; W.at(1, i, t) = c1; W.at(2, i, t) = T(0);
+      W.at(3, i, t) = m; W.at(4, i, t) = T(0);
       c0 = a1 - m * c1;
       c1 = e1;
     }
   }
-  u0[n - 1] = c0 == T(0) ? tiny : c0;
+  W.at(0, n - 1, t) = c0 == T(0) ? tiny : c0;
+  W.at(1, n - 1, t) = T(0);
+  W.at(2, n - 1, t) = T(0);
 }
 
+// Solves (T' - lambda) x = b in place on array 5 of the thread's scratch.
 template <typename T>
-__device__ void tri_solve(int n, T tiny, const T* u0, const T* u1, const T* u2, const T* l,
-                          const T* piv, T* x) {
+__device__ void tri_solve(int n, T tiny, const Strided<T>& W, long long t) {
   for (int i = 0; i + 1 < n; ++i) {
-    if (piv[i] != T(0)) {
-      const T t = x[i];
-      x[i] = x[i + 1];
-      x[i + 1] = t;
-    }
-    x[i + 1] -= l[i] * x[i];
+    T xi = W.at(5, i, t), xn = W.at(5, i + 1, t);
+    if (W.at(4, i, t) != T(0)) { const T q = xi; xi = xn; xn = q; }
+    W.at(5, i, t) = xi;
+    W.at(5, i + 1, t) = xn - W.at(3, i, t) * xi;
   }
+  T x1 = T(0), x2 = T(0);  // x_{i+1}, x_{i+2}
   for (int i = n - 1; i >= 0; --i) {
-    T s = x[i];
-    if (i + 1 < n) s -= u1[i] * x[i + 1];
-    if (i + 2 < n) s -= u2[i] * x[i + 2];
-    T d = u0[i];
+    T sv = W.at(5, i, t) - W.at(1, i, t) * x1 - W.at(2, i, t) * x2;
+    T d = W.at(0, i, t);
     if (fabs(d) < tiny) d = d < T(0) ? -tiny : tiny;
-    x[i] = s / d;
+    const T xi = sv / d;
+    W.at(5, i, t) = xi;
+    x2 = x1;
+    x1 = xi;
   }
 }
 
 template <typename T>
 __global__ void k_lg_invit(LargeArgs a) {
+  const long long NT = a.W * a.nvec;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.W * a.nvec) return;
+  if (t >= NT) return;
   const long long kw = t / a.nvec;
-  const int idx = int(t - kw * a.nvec), n = a.n;
+  const int idx = int(t - kw * a.nvec), n = a.n, nv = a.nvec;
   const T* dg = reinterpret_cast<const T*>(a.dg) + kw * n;
   const T* od = reinterpret_cast<const T*>(a.od) + kw * n;
   const T* lam = reinterpret_cast<const T*>(a.lam) + kw * a.nval;
@@ -331,29 +343,26 @@ __global__ void k_lg_invit(LargeArgs a) {
   const T tolc = T(1e-3) * tn;
   if (idx > 0 && lam[idx] - lam[idx - 1] <= tolc) return;  // not the first of its cluster
   int end = idx;
-  while (end + 1 < a.nvec && lam[end + 1] - lam[end] <= tolc) ++end;
-  T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)a.nvec * n;
-  T* wk = reinterpret_cast<T*>(a.work) + t * 5LL * n;
-  T *u0 = wk, *u1 = wk + n, *u2 = wk + 2 * n, *l = wk + 3 * n, *piv = wk + 4 * n;
+  while (end + 1 < nv && lam[end + 1] - lam[end] <= tolc) ++end;
+  T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)nv * n;   // row-major n x nvec
+  const Strided<T> W{reinterpret_cast<T*>(a.work), NT, n};
   const T tiny = fmax(lg_eps<T>() * tn, T(1e-30));
   for (int j = idx; j <= end; ++j) {
-    T* x = Z + (long long)j * n;
-    // a slightly shifted copy of the eigenvalue keeps the factor non-singular
-    tri_factor(dg, od, n, lam[j], tiny, u0, u1, u2, l, piv);
-    for (int r = 0; r < n; ++r) x[r] = T(hash_unit((unsigned long long)j * 1000003ull + r));
+    tri_factor(dg, od, n, lam[j], tiny, W, t);
+    for (int r = 0; r < n; ++r) W.at(5, r, t) = T(hash_unit((unsigned long long)j * 1000003ull + r));
     for (int it = 0; it < 3; ++it) {
-      tri_solve(n, tiny, u0, u1, u2, l, piv, x);
+      tri_solve(n, tiny, W, t);
       for (int q = idx; q < j; ++q) {  // orthogonalise within the cluster
-        const T* y = Z + (long long)q * n;
         T d = T(0);
-        for (int r = 0; r < n; ++r) d += y[r] * x[r];
-        for (int r = 0; r < n; ++r) x[r] -= d * y[r];
+        for (int r = 0; r < n; ++r) d += Z[(long long)r * nv + q] * W.at(5, r, t);
+        for (int r = 0; r < n; ++r) W.at(5, r, t) -= d * Z[(long long)r * nv + q];
       }
-      T s = T(0);
-      for (int r = 0; r < n; ++r) s += x[r] * x[r];
-      s = T(1) / sqrt(s);
-      for (int r = 0; r < n; ++r) x[r] *= s;
+      T s2 = T(0);
+      for (int r = 0; r < n; ++r) s2 += W.at(5, r, t) * W.at(5, r, t);
+      s2 = T(1) / sqrt(s2);
+      for (int r = 0; r < n; ++r) W.at(5, r, t) *= s2;
     }
+    for (int r = 0; r < n; ++r) Z[(long long)r * nv + j] = W.at(5, r, t);
   }
 }
 
@@ -400,7 +409,7 @@ __global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_strid
     for (long long e = tid; e < (long long)n * ncol; e += nt) {
       const int r = int(e / ncol), col = int(e - (long long)r * ncol);
       const cx<T> d = Dp[r];
-      const T z = Z[(long long)col * n + r];
+      const T z = Z[(long long)r * a.nvec + col];
       X[e] = cx<To>(To(d.re * z), To(d.im * z));
     }
     __syncthreads();
@@ -488,9 +497,8 @@ __global__ void k_lg_refine(LargeArgs a) {
     const int nu = n - p;
     for (long long e = tid; e < (long long)nu * p; e += nt) {
       const int ua = int(e / p), c = int(e - (long long)ua * p);
-      const float* z = Z + (long long)(p + ua) * n;
       c32 acc(0.f, 0.f);
-      for (int r = 0; r < n; ++r) acc = acc + z[r] * C[(long long)r * p + c];
+      for (int r = 0; r < n; ++r) acc = acc + Z[(long long)r * a.nvec + p + ua] * C[(long long)r * p + c];
       const double den = rho[c] - double(lam[p + ua]);
       R[e] = (1.0 / den) * ccast<double>(acc);
     }
@@ -498,9 +506,10 @@ __global__ void k_lg_refine(LargeArgs a) {
     // Delta = D Z_u coef (FP32), then Q_h Delta
     for (long long e = tid; e < (long long)n * p; e += nt) {
       const int r = int(e / p), c = int(e - (long long)r * p);
-      z64 acc(0.0, 0.0);
-      for (int ua = 0; ua < nu; ++ua) acc = acc + double(Z[(long long)(p + ua) * n + r]) * R[(long long)ua * p + c];
-      C[e] = Dp[r] * ccast<float>(acc);
+      c32 acc(0.f, 0.f);
+      const float* zr = Z + (long long)r * a.nvec + p;
+      for (int ua = 0; ua < nu; ++ua) acc = acc + zr[ua] * ccast<float>(R[(long long)ua * p + c]);
+      C[e] = Dp[r] * acc;
     }
     __syncthreads();
     apply_reflectors<float, float>(A, n, C, p, true, us, wv);
@@ -565,22 +574,31 @@ int lg_grid(long long units) {
   return int(units < cap ? (units > 0 ? units : 1) : cap);
 }
 
+void lg_mark(const LargeArgs& a, const char* name) {
+  if (a.mark) a.mark(a.mark_user, name);
+}
+
 template <typename T>
 cudaError_t lg_common(const LargeArgs& a, cudaStream_t s) {
   k_lg_build<T><<<lg_grid(a.W), LG_THREADS, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  lg_mark(a, "lg_build");
   const size_t sm_tri = 3 * size_t(a.n) * sizeof(cx<T>) + 64 * sizeof(double);
   static size_t cached = 0;
   if ((e = set_smem_once(k_lg_tridiag<T>, sm_tri, cached)) != cudaSuccess) return e;
   k_lg_tridiag<T><<<lg_grid(a.W), LG_THREADS, sm_tri, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lg_mark(a, "lg_tridiag");
   const long long nb = a.W * a.nval;
   k_lg_bisect<T><<<int((nb + 127) / 128), 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lg_mark(a, "lg_bisect");
   const long long ni = a.W * a.nvec;
   k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lg_mark(a, "lg_invit");
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -595,8 +613,11 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
     k_lg_backtransform<double, double><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
         a, a.U, (long long)a.n * a.p, a.p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lg_mark(a, "lg_backtransform");
     k_lg_gap64<<<int((a.W + 127) / 128), 128, 0, s>>>(a);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lg_mark(a, "lg_gap");
+    return cudaSuccess;
   }
   if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
   const size_t sm = 2 * size_t(a.n > a.nbt ? a.n : a.nbt) * sizeof(c32);
@@ -605,11 +626,14 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   k_lg_backtransform<float, float><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
       a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lg_mark(a, "lg_backtransform");
   const size_t smr = (size_t(a.n) + a.p + 1) * sizeof(c32) + (size_t(a.p) + 2 + 64) * sizeof(double) + 16;
   static size_t cached_r = 0;
   if ((e = set_smem_once(k_lg_refine, smr, cached_r)) != cudaSuccess) return e;
   k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lg_mark(a, "lg_refine");
+  return cudaSuccess;
 }
 
 }  // namespace bw

@@ -113,8 +113,8 @@ struct LargeArgs {
   void* od;               // W x n (T)
   void* Dp;               // W x n complex (T)
   void* lam;              // W x nval (T)
-  void* Z;                // W x nvec x n (T), vector-contiguous
-  void* work;             // W x nvec x 5 n (T)
+  void* Z;                // W x n x nvec (T), row-major
+  void* work;             // 6 n x (W nvec) (T), interleaved across threads
   void* X;                // W x n x nbt complex float (mixed)
   z64* Hent;              // W x n_ent (mixed)
   z64* R64;               // W x n x p (mixed)
@@ -125,6 +125,9 @@ struct LargeArgs {
   z64* U;                 // W x n x p (wave-relative)
   double* gap;            // K (absolute k)
   DevStatus* status;
+  // optional host callback after each stage launch (per-stage timing)
+  void (*mark)(void*, const char*);
+  void* mark_user;
 };
 
 // Launches every stage of the large-n solver for one wave.

@@ -26,8 +26,11 @@ __device__ __forceinline__ double phase_of(z64 z) { return atan2(z.im, z.re); }
 __device__ void rank_sort(const double* th, int p, int* ord) {
   for (int a = threadIdx.x; a < p; a += blockDim.x) {
     int rank = 0;
-    const double x = th[a];
-    for (int b = 0; b < p; ++b) rank += (th[b] < x) || (th[b] == x && b < a);
+    const double x = rank_key(th[a]);
+    for (int b = 0; b < p; ++b) {
+      const double y = rank_key(th[b]);
+      rank += (y < x) || (y == x && b < a);
+    }
     ord[rank] = a;
   }
   __syncthreads();

@@ -39,8 +39,8 @@ struct bw_ctx {
   // per-kernel timing (bw_set_profiling)
   bool prof = false;
   int prof_n = 0;
-  const char* prof_names[8] = {};
-  cudaEvent_t prof_ev[9] = {};
+  const char* prof_names[128] = {};
+  cudaEvent_t prof_ev[129] = {};
 };
 
 namespace {
@@ -260,7 +260,7 @@ void end_call(bw_ctx* ctx, cudaStream_t s) {
 // Timing marks around kernel launches (recorded as external events under capture,
 // so that replays of a captured graph can be timed too).
 void prof_mark(bw_ctx* ctx, cudaStream_t s, const char* name) {
-  if (!ctx->prof || ctx->prof_n >= 8) return;
+  if (!ctx->prof || ctx->prof_n >= 128) return;
   const int i = ctx->prof_n;
   if (!ctx->prof_ev[0])
     for (auto& e : ctx->prof_ev) cudaEventCreate(&e);
@@ -270,6 +270,16 @@ void prof_mark(bw_ctx* ctx, cudaStream_t s, const char* name) {
 }
 
 // Records the start mark before the first kernel of a call.
+struct MarkHook {
+  bw_ctx* ctx;
+  cudaStream_t s;
+};
+
+void mark_hook(void* user, const char* name) {
+  MarkHook* h = static_cast<MarkHook*>(user);
+  prof_mark(h->ctx, h->s, name);
+}
+
 void prof_start(bw_ctx* ctx, cudaStream_t s) {
   if (!ctx->prof) return;
   if (!ctx->prof_ev[0])
@@ -439,7 +449,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const int nbt = mx ? std::min(n, p + 1) : p;
   const size_t sz_A = al256(size_t(n) * n * 2 * ts), sz_v = al256(size_t(n) * ts),
                sz_D = al256(size_t(n) * 2 * ts), sz_lam = al256(size_t(nval) * ts),
-               sz_Z = al256(size_t(nvec) * n * ts), sz_wk = al256(size_t(nvec) * 5 * n * ts),
+               sz_Z = al256(size_t(nvec) * n * ts), sz_wk = al256(size_t(nvec) * 6 * n * ts),
                sz_X = mx ? al256(size_t(n) * nbt * sizeof(bw::c32)) : 0,
                sz_He = mx ? al256(size_t(P.n_ent) * sizeof(z64)) : 0,
                sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
@@ -522,16 +532,22 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
       lg.G64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_G));
     }
     z64* Ufull = reinterpret_cast<z64*>(carve(ctx, Wv * sz_Uf));
+    MarkHook hook{ctx, s};
+    lg.mark = mark_hook;
+    lg.mark_user = &hook;
     for (long long k0 = 0; k0 < K; k0 += Wv) {
       lg.k0 = k0;
       lg.W = std::min(Wv, K - k0);
       // the wave's occupied blocks go straight to U, or through the spin split
       lg.U = kind == LoopKind::Spin ? Ufull : U + k0 * (long long)n * p;
       BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
-      if (kind == LoopKind::Spin) BW_CUDA(bw::launch_pso_global(sa, Ufull, k0, lg.W, s), "spin split kernel");
+      if (kind == LoopKind::Spin) {
+        BW_CUDA(bw::launch_pso_global(sa, Ufull, k0, lg.W, s), "spin split kernel");
+        prof_mark(ctx, s, "pso_split");
+      }
     }
   }
-  prof_mark(ctx, s, "states");
+  if (!large) prof_mark(ctx, s, "states");
 
   bw::LoopArgs la;
   std::memset(&la, 0, sizeof(la));
@@ -626,21 +642,34 @@ bw_status bw_set_profiling(bw_ctx* ctx, int enable) {
 
 int bw_profile_read(bw_ctx* ctx, int max, char* names, double* ms) {
   if (!ctx || max < 0) return -1;
-  const int n = std::min(ctx->prof_n, max);
-  if (n <= 0) return 0;
+  if (ctx->prof_n <= 0) return 0;
   if (cudaEventSynchronize(ctx->prof_ev[ctx->prof_n]) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
-  for (int i = 0; i < n; ++i) {
+  // durations summed per kernel name, in order of first appearance
+  const char* seen[128];
+  double tot[128];
+  int nu = 0;
+  for (int i = 0; i < ctx->prof_n; ++i) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]) != cudaSuccess) {
       cudaGetLastError();
       return -1;
     }
-    if (ms) ms[i] = double(t);
+    int u = 0;
+    while (u < nu && std::strcmp(seen[u], ctx->prof_names[i]) != 0) ++u;
+    if (u == nu) {
+      seen[nu] = ctx->prof_names[i];
+      tot[nu++] = 0.0;
+    }
+    tot[u] += double(t);
+  }
+  const int n = std::min(nu, max);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = tot[i];
     if (names) {
-      std::strncpy(names + 32 * i, ctx->prof_names[i], 31);
+      std::strncpy(names + 32 * i, seen[i], 31);
       names[32 * i + 31] = 0;
     }
   }

@@ -222,15 +222,20 @@ def supercell(model: HoppingList, L: int, W: float = 0.0, seed: int | None = Non
 
 
 def manyband(norb: int = 128, seed: int = GLOBAL_SEED + 3, decay: float = 1.5,
-             soc: float = 0.1, zeeman: float = 0.05) -> HoppingList:
+             soc: float = 0.1, zeeman: float = 0.05, n_low: int | None = None,
+             e_low: float = -4.0) -> HoppingList:
     """Synthetic Wannier-like spinful model (n = 2 norb), orbital-major, spin-minor.
 
     Translations: shells |R| in {0, 1, sqrt 2, 2} (13 vectors).  For R in a half-space
     t_R = exp(-|R|/decay)/sqrt(norb) [A_R (x) s0 + soc sum_a B_{R,a} (x) s_a] with
     complex Gaussian A, B; t_0 is the Hermitian part of the same form; plus
-    zeeman * I (x) s_z.  The spin-independent part dominates so the projected spin
+    zeeman * I (x) s_z, plus an on-site energy e_low on the first n_low = norb / 4
+    orbitals (low-lying Wannier orbitals).  The offset opens a direct gap at quarter
+    filling wider than the Zeeman splitting, so each spin sector holds half of the
+    occupied states; the spin-independent part dominates so the projected spin
     operator keeps a gap at zero.
     """
+    n_low = norb // 4 if n_low is None else n_low
     rng = np.random.default_rng(seed)
     n = 2 * norb
 
@@ -246,7 +251,9 @@ def manyband(norb: int = 128, seed: int = GLOBAL_SEED + 3, decay: float = 1.5,
             T = T + soc * np.kron(cn((norb, norb)), PAULI[a])
         T = amp * T
         if R == (0, 0):
-            T = 0.5 * (T + T.conj().T) + zeeman * np.kron(np.eye(norb), PAULI[3])
+            low = np.diag((np.arange(norb) < n_low).astype(float))
+            T = 0.5 * (T + T.conj().T) + zeeman * np.kron(np.eye(norb), PAULI[3]) \
+                + e_low * np.kron(low, PAULI[0])
         blocks[R] = T
     return from_blocks(blocks, n, dim=2, name=f"manyband({norb})")
 
