@@ -45,7 +45,7 @@ __device__ __forceinline__ void givens(z64 x, z64 y, double& c, z64& s) {
 // Eigen-decomposition of H (p x p, leading dimension ld), destroyed on output.
 // lam[p] receives the eigenvalues.  With want_vec, Z (p x p) receives the right
 // eigenvectors as unit-norm columns; vec scratch needs p z64.  Returns 0, or -1
-// when the QR iteration cap (40 p sweeps) is reached.
+// when the QR iteration cap (120 p sweeps) is reached.
 __device__ int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64* vec,
                     GeigShared* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -112,7 +112,7 @@ __device__ int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64*
   }
   __syncthreads();
   int iter = 0, total = 0;
-  const int cap = 40 * p + 40;
+  const int cap = 120 * p + 120;
   while (true) {
     if (tid == 0) {
       int hi = sh->hi;
@@ -125,9 +125,22 @@ __device__ int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64*
         }
         int l = hi;
         while (l > 0) {
-          const double sub = zabs(H[l * ld + l - 1]);
-          const double dia = zabs(H[l * ld + l]) + zabs(H[(l - 1) * ld + l - 1]);
-          if (sub <= eps * dia || sub < 1e-300) {
+          const z64 h11 = H[(l - 1) * ld + l - 1], h12 = H[(l - 1) * ld + l];
+          const z64 h21 = H[l * ld + l - 1], h22 = H[l * ld + l];
+          const double sub = zabs(h21);
+          const double dia = zabs(h22) + zabs(h11);
+          bool small = sub <= eps * dia || sub < 1e-300;
+          if (!small && sub <= dia) {
+            // product test (Ahues and Tisseur): the subdiagonal is negligible when its
+            // product with the superdiagonal is small against the local separation
+            const double x = zabs(h12);
+            const double ab = fmax(sub, x), ba = fmin(sub, x);
+            const double y = zabs(h11 - h22);
+            const double aa = fmax(zabs(h22), y), bb = fmin(zabs(h22), y);
+            const double sc = aa + ab;
+            small = ba * (ab / sc) <= fmax(1e-300, eps * (bb * (aa / sc)));
+          }
+          if (small) {
             H[l * ld + l - 1] = z64(0.0, 0.0);
             break;
           }

@@ -6,7 +6,11 @@
 // A complex 2x2 rotation J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] annihilates
 // A[p][q] = |b| e^{i phi}: with tau = (A_qq - A_pp) / (2|b|) and
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c, and
-// A_pp -> A_pp - t|b|, A_qq -> A_qq + t|b|.
+// A_pp -> A_pp - t|b|, A_qq -> A_qq + t|b|.  A rotation is skipped when
+// |A_pq| <= 4 eps sqrt(|A_pp| |A_qq|) (negligible against its diagonal pair); a sweep
+// without any rotation also ends the iteration.  Without that test, clusters of
+// equal eigenvalues keep off-diagonal entries at the rounding level that no
+// rotation removes, and a pure norm test may never be met in FP32.
 #pragma once
 
 #include "common.cuh"
@@ -65,6 +69,7 @@ __device__ int jacobi_eigh(cx<T>* A, cx<T>* V, int n, int ld, int max_sweeps, Ja
   }
   fro = block_sum(fro, red);
   const double tol = 8.0 * double(eps_of<T>()) * sqrt(fro);
+  __shared__ int s_rotated;
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double off = 0.0;
     for (int e = tid; e < n * n; e += nt) {
@@ -74,6 +79,8 @@ __device__ int jacobi_eigh(cx<T>* A, cx<T>* V, int n, int ld, int max_sweeps, Ja
     off = block_sum(off, red);
     if (sqrt(off) <= tol || fro == 0.0) return sweep;
     if (sweep == max_sweeps) break;
+    if (tid == 0) s_rotated = 0;
+    __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
       for (int k = tid; k < npairs; k += nt) {
         int p, q;
@@ -91,7 +98,8 @@ __device__ int jacobi_eigh(cx<T>* A, cx<T>* V, int n, int ld, int max_sweeps, Ja
           const T a = A[p * ld + p].re, d = A[q * ld + q].re;
           R.app = a;
           R.aqq = d;
-          if (ab > T(0)) {
+          if (ab > T(4) * eps_of<T>() * sqrt(fabs(a) * fabs(d)) && ab > T(0)) {
+            s_rotated = 1;
             const T tau = (d - a) / (T(2) * ab);
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
             const T c = T(1) / sqrt(T(1) + t * t);
@@ -140,6 +148,7 @@ __device__ int jacobi_eigh(cx<T>* A, cx<T>* V, int n, int ld, int max_sweeps, Ja
       }
       __syncthreads();
     }
+    if (!s_rotated) return sweep + 1;
   }
   return -1;
 }

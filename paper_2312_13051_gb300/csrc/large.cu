@@ -153,11 +153,10 @@ __global__ void k_lg_tridiag(LargeArgs a) {
       for (int r = tid; r < m; r += nt) w[r] = w[r] - T(kr) * u[r];
       __syncthreads();
       // A22 <- A22 - 2 (u w^dag + w u^dag)
-      for (long long e = tid; e < (long long)m * m; e += nt) {
-        const int r = int(e / m), q = int(e - (long long)r * m);
-        cx<T>& x = A[(long long)(c + 1 + r) * n + (c + 1 + q)];
-        const cx<T> t1 = u[r] * conj(w[q]), t2 = w[r] * conj(u[q]);
-        x = x - T(2) * (t1 + t2);
+      for (int r = warp; r < m; r += nwarp) {
+        cx<T>* row = A + (long long)(c + 1 + r) * n + (c + 1);
+        const cx<T> ur = u[r], wr = w[r];
+        for (int q = lane; q < m; q += 32) row[q] = row[q] - T(2) * (ur * conj(w[q]) + wr * conj(u[q]));
       }
       if (tid == 0) {
         al[c] = cx<T>(T(-phr * nx), T(-phi * nx));
@@ -386,10 +385,10 @@ __device__ void apply_reflectors(const cx<T>* A, int n, cx<To>* X, int ncol, boo
       wv[col] = acc;
     }
     __syncthreads();
-    for (long long e = tid; e < (long long)m * ncol; e += nt) {
-      const int r = int(e / ncol), col = int(e - (long long)r * ncol);
-      cx<To>& x = X[(long long)(c + 1 + r) * ncol + col];
-      x = x - To(2) * (us[r] * wv[col]);
+    for (int r = tid >> 5; r < m; r += nt >> 5) {
+      cx<To>* row = X + (long long)(c + 1 + r) * ncol;
+      const cx<To> ur = To(2) * us[r];
+      for (int col = tid & 31; col < ncol; col += 32) row[col] = row[col] - ur * wv[col];
     }
     __syncthreads();
   }
@@ -406,11 +405,12 @@ __global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_strid
     const cx<T>* Dp = reinterpret_cast<const cx<T>*>(a.Dp) + kw * n;
     const T* Z = reinterpret_cast<const T*>(a.Z) + kw * (long long)a.nvec * n;
     cx<To>* X = out + kw * out_stride;
-    for (long long e = tid; e < (long long)n * ncol; e += nt) {
-      const int r = int(e / ncol), col = int(e - (long long)r * ncol);
+    for (int r = tid >> 5; r < n; r += nt >> 5) {
       const cx<T> d = Dp[r];
-      const T z = Z[(long long)r * a.nvec + col];
-      X[e] = cx<To>(To(d.re * z), To(d.im * z));
+      for (int col = tid & 31; col < ncol; col += 32) {
+        const T z = Z[(long long)r * a.nvec + col];
+        X[(long long)r * ncol + col] = cx<To>(To(d.re * z), To(d.im * z));
+      }
     }
     __syncthreads();
     apply_reflectors<T, To>(A, n, X, ncol, true, us, wv);
@@ -428,19 +428,72 @@ __global__ void k_lg_gap64(LargeArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Stage 6 (mixed): one FP64 Newton correction of the occupied block.
-//   Q = X[:, :p] (FP32 eigenvectors, promoted); R_i = H q_i - (q_i^dag H q_i) q_i in
-//   FP64 from the hopping plan's entries; the complement's coefficients
-//   C[a][i] = z_a^T D^dag Q_h^dag R_i / (rho_i - lam_a) through the FP32 reflectors;
-//   Q += Q_h D Z_u C; then Q <- Q (I - (Q^dag Q - I) / 2) (first-order Lowdin
-//   step, exact to second order in the FP32 non-orthogonality).
-//   The gap comes from FP64 Rayleigh quotients of the (p-1)-th and p-th vectors.
-// The off-diagonal part of Q^dag H Q is of the order of the FP32 error; its
-// projection on the complement enters at second order and is dropped.
+// Compensated FP32 dot products (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is split
+// exactly into a + e with one FMA, the running sum is kept as hi + lo with an
+// error-free two-sum, and the result is as accurate as a sum carried in twice the
+// working precision.  GB300 runs FP32 ~70x faster than FP64, so this is the cheap
+// way to the FP64-grade residuals the Newton correction needs.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);      // exact: a b = p + e
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);  // exact: hi + p = s + err
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ void add(float x) { lo += x; }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+struct CDF {
+  DF re, im;
+  // acc += a * b with a = ah + al (FP64 split into two floats), b FP32
+  __device__ __forceinline__ void add_prod(c32 ah, c32 al, c32 b) {
+    re.add_prod(ah.re, b.re);
+    re.add_prod(-ah.im, b.im);
+    im.add_prod(ah.re, b.im);
+    im.add_prod(ah.im, b.re);
+    re.add(al.re * b.re - al.im * b.im);
+    im.add(al.re * b.im + al.im * b.re);
+  }
+  // acc += conj(a) * b, both FP32
+  __device__ __forceinline__ void add_cprod(c32 a, c32 b) {
+    re.add_prod(a.re, b.re);
+    re.add_prod(a.im, b.im);
+    im.add_prod(a.re, b.im);
+    im.add_prod(-a.im, b.re);
+  }
+  __device__ __forceinline__ z64 value() const { return z64(re.value(), im.value()); }
+};
+
+__device__ __forceinline__ void split64(z64 x, c32& hi, c32& lo) {
+  hi = c32(float(x.re), float(x.im));
+  lo = c32(float(x.re - double(hi.re)), float(x.im - double(hi.im)));
+}
+
+// ---------------------------------------------------------------------------
+// Stage 6 (mixed): one Newton correction of the occupied block.
+//   Q = X[:, :p] holds FP32 eigenvectors (exact FP32 numbers).  H Q from the hopping
+//   plan's FP64 entries with compensated FP32 dot products; rho_c = q_c^dag H q_c and
+//   R = H Q - Q rho in FP64; the complement's coefficients
+//   C[a][c] = z_a^T D^dag Q_h^dag R_c / (rho_c - lam_a) and the update
+//   Q_h D Z_u C in FP32 through the reflectors (R is small, FP32 keeps it to ~1e-7
+//   relative); Q64 = Q + update.  Then one first-order Lowdin step,
+//   Q <- Q - Q (Q^dag Q - I) / 2, with Q32^dag Q32 - I compensated and the small
+//   terms in FP32.  The gap comes from FP64 Rayleigh quotients of the (p-1)-th
+//   and p-th FP32 vectors.  The off-diagonal part of Q^dag H Q is of the order of
+//   the FP32 error; its projection on the complement enters at second order.
 // ---------------------------------------------------------------------------
 __global__ void k_lg_refine(LargeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, p = a.p, nbt = a.nbt, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const DevModel& md = a.model;
   c32* us = reinterpret_cast<c32*>(smem);            // n
   c32* wv = us + n;                                  // p
@@ -455,83 +508,96 @@ __global__ void k_lg_refine(LargeArgs a) {
     const c32* X = reinterpret_cast<const c32*>(a.X) + kw * (long long)n * nbt;
     const z64* He = a.Hent + kw * (long long)md.n_ent;
     z64* Q = a.U + kw * (long long)n * p;
-    z64* R = a.R64 + kw * (long long)n * p;
+    z64* R = a.R64 + kw * (long long)n * p;          // H Q, later FP32 scratch
     c32* C = a.C32 + kw * (long long)n * p;
-    z64* G = a.G64 + kw * (long long)p * p;
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int r = int(e / p), c = int(e - (long long)r * p);
-      Q[e] = ccast<double>(X[(long long)r * nbt + c]);
-    }
-    __syncthreads();
-    // R = H Q (rows from the plan)
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int r = int(e / p), c = int(e - (long long)r * p);
-      z64 acc(0.0, 0.0);
-      for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) cfma(acc, He[q], Q[(long long)md.ent_col[q] * p + c]);
-      R[e] = acc;
+    c32* E = reinterpret_cast<c32*>(a.G64 + kw * (long long)p * p);  // Q^dag Q - I (p x p)
+    // R = H Q32 (compensated), one warp per row, lanes along the columns
+    for (int r = warp; r < n; r += nwarp) {
+      for (int c0 = 0; c0 < p; c0 += 32) {
+        const int c = c0 + lane;
+        CDF acc;
+        for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) {
+          c32 hh, hl;
+          split64(He[q], hh, hl);
+          if (c < p) acc.add_prod(hh, hl, X[(long long)md.ent_col[q] * nbt + c]);
+        }
+        if (c < p) R[(long long)r * p + c] = acc.value();
+      }
     }
     __syncthreads();
     for (int c = tid; c < p; c += nt) {
-      double s = 0.0;
+      double sum = 0.0;
       for (int r = 0; r < n; ++r) {
-        const z64 q = Q[(long long)r * p + c], h = R[(long long)r * p + c];
-        s += q.re * h.re + q.im * h.im;
+        const c32 q = X[(long long)r * nbt + c];
+        const z64 h = R[(long long)r * p + c];
+        sum += double(q.re) * h.re + double(q.im) * h.im;
       }
-      rho[c] = s;
+      rho[c] = sum;
     }
     __syncthreads();
-    // R <- R - rho Q, to FP32 (small residual) in C
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int c = int(e % p);
-      C[e] = ccast<float>(R[e] - rho[c] * Q[e]);
-    }
+    // residual to FP32
+    for (int r = warp; r < n; r += nwarp)
+      for (int c = lane; c < p; c += 32) {
+        const z64 h = R[(long long)r * p + c];
+        const c32 q = X[(long long)r * nbt + c];
+        C[(long long)r * p + c] = c32(float(h.re - rho[c] * double(q.re)), float(h.im - rho[c] * double(q.im)));
+      }
     __syncthreads();
     // C <- D^dag Q_h^dag C
     apply_reflectors<float, float>(A, n, C, p, false, us, wv);
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int r = int(e / p);
-      C[e] = conj(Dp[r]) * C[e];
+    for (int r = warp; r < n; r += nwarp) {
+      const c32 d = conj(Dp[r]);
+      for (int c = lane; c < p; c += 32) C[(long long)r * p + c] = d * C[(long long)r * p + c];
     }
     __syncthreads();
-    // coefficients of the complement, stored in R (FP64 workspace reuse): rows a < n - p
+    // complement coefficients (FP32), kept in the R workspace
+    c32* coef = reinterpret_cast<c32*>(R);
     const int nu = n - p;
-    for (long long e = tid; e < (long long)nu * p; e += nt) {
-      const int ua = int(e / p), c = int(e - (long long)ua * p);
-      c32 acc(0.f, 0.f);
-      for (int r = 0; r < n; ++r) acc = acc + Z[(long long)r * a.nvec + p + ua] * C[(long long)r * p + c];
-      const double den = rho[c] - double(lam[p + ua]);
-      R[e] = (1.0 / den) * ccast<double>(acc);
-    }
+    for (int ua = warp; ua < nu; ua += nwarp)
+      for (int c = lane; c < p; c += 32) {
+        c32 acc(0.f, 0.f);
+        for (int r = 0; r < n; ++r) acc = acc + Z[(long long)r * a.nvec + p + ua] * C[(long long)r * p + c];
+        coef[(long long)ua * p + c] = float(1.0 / (rho[c] - double(lam[p + ua]))) * acc;
+      }
     __syncthreads();
-    // Delta = D Z_u coef (FP32), then Q_h Delta
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int r = int(e / p), c = int(e - (long long)r * p);
-      c32 acc(0.f, 0.f);
+    // update = Q_h D Z_u coef
+    for (int r = warp; r < n; r += nwarp) {
       const float* zr = Z + (long long)r * a.nvec + p;
-      for (int ua = 0; ua < nu; ++ua) acc = acc + zr[ua] * ccast<float>(R[(long long)ua * p + c]);
-      C[e] = Dp[r] * acc;
+      const c32 d = Dp[r];
+      for (int c = lane; c < p; c += 32) {
+        c32 acc(0.f, 0.f);
+        for (int ua = 0; ua < nu; ++ua) acc = acc + zr[ua] * coef[(long long)ua * p + c];
+        C[(long long)r * p + c] = d * acc;
+      }
     }
     __syncthreads();
     apply_reflectors<float, float>(A, n, C, p, true, us, wv);
-    for (long long e = tid; e < (long long)n * p; e += nt) Q[e] = Q[e] + ccast<double>(C[e]);
+    // E = Q^dag Q - I with Q = Q32 + C: Q32^dag Q32 - I compensated, the rest in FP32
+    for (int x = warp; x < p; x += nwarp)
+      for (int y = lane; y < p; y += 32) {
+        CDF acc;
+        c32 small(0.f, 0.f);
+        for (int r = 0; r < n; ++r) {
+          const c32 qx = X[(long long)r * nbt + x], qy = X[(long long)r * nbt + y];
+          const c32 dx = C[(long long)r * p + x], dy = C[(long long)r * p + y];
+          acc.add_cprod(qx, qy);
+          small = small + conj(qx) * dy + conj(dx) * qy + conj(dx) * dy;
+        }
+        z64 v = acc.value();
+        if (x == y) v.re -= 1.0;
+        E[(long long)x * p + y] = c32(float(v.re + double(small.re)), float(v.im + double(small.im)));
+      }
     __syncthreads();
-    // G = Q^dag Q - I, then Q <- Q - Q G / 2
-    for (long long e = tid; e < (long long)p * p; e += nt) {
-      const int x = int(e / p), y = int(e - (long long)x * p);
-      z64 acc(0.0, 0.0);
-      for (int r = 0; r < n; ++r) cfma_conj(acc, Q[(long long)r * p + x], Q[(long long)r * p + y]);
-      if (x == y) acc.re -= 1.0;
-      G[e] = acc;
-    }
-    __syncthreads();
-    for (long long e = tid; e < (long long)n * p; e += nt) {
-      const int r = int(e / p), c = int(e - (long long)r * p);
-      z64 acc(0.0, 0.0);
-      for (int q = 0; q < p; ++q) cfma(acc, Q[(long long)r * p + q], G[(long long)q * p + c]);
-      R[e] = acc;
-    }
-    __syncthreads();
-    for (long long e = tid; e < (long long)n * p; e += nt) Q[e] = Q[e] - 0.5 * R[e];
+    // Q = (Q32 + C) - (Q32 + C) E / 2, the correction in FP32
+    for (int r = warp; r < n; r += nwarp)
+      for (int c = lane; c < p; c += 32) {
+        c32 acc(0.f, 0.f);
+        for (int q = 0; q < p; ++q)
+          acc = acc + (X[(long long)r * nbt + q] + C[(long long)r * p + q]) * E[(long long)q * p + c];
+        const c32 x32 = X[(long long)r * nbt + c], dc = C[(long long)r * p + c];
+        Q[(long long)r * p + c] = z64(double(x32.re) + double(dc.re) - 0.5 * double(acc.re),
+                                      double(x32.im) + double(dc.im) - 0.5 * double(acc.im));
+      }
     __syncthreads();
     // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p
     if (p < n) {

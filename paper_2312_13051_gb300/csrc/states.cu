@@ -682,7 +682,7 @@ cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, l
   static size_t cached = 0;
   cudaError_t e = set_smem_once(k_pso_global, sm, cached);
   if (e != cudaSuccess) return e;
-  k_pso_global<<<grid_for(W), 128, sm, s>>>(a, U, k0, W);
+  k_pso_global<<<grid_for(W), 512, sm, s>>>(a, U, k0, W);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ template <>
 __device__ __forceinline__ float teps<float>() { return 1.1920929e-7f; }
 
 // Serial cyclic Jacobi on a Hermitian NN x NN matrix held in registers; V collects
-// the rotations (same rotation formula as the block solver).  Returns the sweeps
+// the rotations (same rotation formula and skip test as the block solver).  Returns the sweeps
 // used or -1 without convergence.
 template <int NN, typename T>
 __device__ __forceinline__ int jac_serial(cx<T> (&A)[NN][NN], cx<T> (&V)[NN][NN], int max_sweeps) {
@@ -47,14 +47,16 @@ __device__ __forceinline__ int jac_serial(cx<T> (&A)[NN][NN], cx<T> (&V)[NN][NN]
       for (int q = p + 1; q < NN; ++q) off += T(2) * abs2(A[p][q]);
     if (off <= tol2 || fro == T(0)) return sweep;
     if (sweep == max_sweeps) break;
+    bool rotated = false;
 #pragma unroll
     for (int p = 0; p < NN; ++p)
 #pragma unroll
       for (int q = p + 1; q < NN; ++q) {
         const cx<T> b = A[p][q];
         const T ab = sqrt(abs2(b));
-        if (!(ab > T(0))) continue;
         const T a = A[p][p].re, d = A[q][q].re;
+        if (!(ab > T(4) * teps<T>() * sqrt(fabs(a) * fabs(d)) && ab > T(0))) continue;
+        rotated = true;
         const T tau = (d - a) / (T(2) * ab);
         const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
         const T c = T(1) / sqrt(T(1) + t * t);
@@ -80,6 +82,7 @@ __device__ __forceinline__ int jac_serial(cx<T> (&A)[NN][NN], cx<T> (&V)[NN][NN]
         A[p][p] = cx<T>(a - t * ab, T(0));
         A[q][q] = cx<T>(d + t * ab, T(0));
       }
+    if (!rotated) return sweep + 1;
   }
   return -1;
 }
