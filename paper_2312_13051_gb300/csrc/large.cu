@@ -46,6 +46,56 @@ __device__ __forceinline__ void lg_kpoint(const LargeArgs& a, long long k, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Compensated FP32 dot products (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is split
+// exactly into a + e with one FMA, the running sum is kept as hi + lo with an
+// error-free two-sum, and the result is as accurate as a sum carried in twice the
+// working precision.  GB300 runs FP32 ~70x faster than FP64, so this is the cheap
+// way to the FP64-grade residuals the Newton correction needs.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);      // exact: a b = p + e
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);  // exact: hi + p = s + err
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ void add(float x) { lo += x; }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+struct CDF {
+  DF re, im;
+  // acc += a * b with a = ah + al (FP64 split into two floats), b FP32
+  __device__ __forceinline__ void add_prod(c32 ah, c32 al, c32 b) {
+    re.add_prod(ah.re, b.re);
+    re.add_prod(-ah.im, b.im);
+    im.add_prod(ah.re, b.im);
+    im.add_prod(ah.im, b.re);
+    re.add(al.re * b.re - al.im * b.im);
+    im.add(al.re * b.im + al.im * b.re);
+  }
+  // acc += conj(a) * b, both FP32
+  __device__ __forceinline__ void add_cprod(c32 a, c32 b) {
+    re.add_prod(a.re, b.re);
+    re.add_prod(a.im, b.im);
+    im.add_prod(a.re, b.im);
+    im.add_prod(-a.im, b.re);
+  }
+  __device__ __forceinline__ z64 value() const { return z64(re.value(), im.value()); }
+};
+
+__device__ __forceinline__ void split64(z64 x, c32& hi, c32& lo) {
+  hi = c32(float(x.re), float(x.im));
+  lo = c32(float(x.re - double(hi.re)), float(x.im - double(hi.im)));
+}
+
+// ---------------------------------------------------------------------------
 // Stage 1: Bloch Hamiltonian of the wave's k-points (full Hermitian matrix).
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -70,7 +120,13 @@ __global__ void k_lg_build(LargeArgs a) {
         cfma(acc, md.hop_t[h], r < nRs ? phs[r] : bloch_phase(f, md.Rv + 3 * r));
       }
       A[(long long)md.ent_row[e] * n + md.ent_col[e]] = ccast<T>(acc);
-      if (a.Hent) a.Hent[kw * (long long)md.n_ent + e] = acc;
+      if (a.Hent) {  // FP64 entry as an unevaluated sum of two floats (hi, lo)
+        c32 hi, lo;
+        split64(acc, hi, lo);
+        c32* dst = reinterpret_cast<c32*>(a.Hent + kw * (long long)md.n_ent + e);
+        dst[0] = hi;
+        dst[1] = lo;
+      }
     }
     __syncthreads();
   }
@@ -428,56 +484,6 @@ __global__ void k_lg_gap64(LargeArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Compensated FP32 dot products (Ogita, Rump and Oishi, "Accurate sum and dot
-// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is split
-// exactly into a + e with one FMA, the running sum is kept as hi + lo with an
-// error-free two-sum, and the result is as accurate as a sum carried in twice the
-// working precision.  GB300 runs FP32 ~70x faster than FP64, so this is the cheap
-// way to the FP64-grade residuals the Newton correction needs.
-// ---------------------------------------------------------------------------
-struct DF {
-  float hi, lo;
-  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float p = a * b;
-    const float e = fmaf(a, b, -p);      // exact: a b = p + e
-    const float s = hi + p;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (p - bp);  // exact: hi + p = s + err
-    hi = s;
-    lo += err + e;
-  }
-  __device__ __forceinline__ void add(float x) { lo += x; }
-  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
-};
-
-struct CDF {
-  DF re, im;
-  // acc += a * b with a = ah + al (FP64 split into two floats), b FP32
-  __device__ __forceinline__ void add_prod(c32 ah, c32 al, c32 b) {
-    re.add_prod(ah.re, b.re);
-    re.add_prod(-ah.im, b.im);
-    im.add_prod(ah.re, b.im);
-    im.add_prod(ah.im, b.re);
-    re.add(al.re * b.re - al.im * b.im);
-    im.add(al.re * b.im + al.im * b.re);
-  }
-  // acc += conj(a) * b, both FP32
-  __device__ __forceinline__ void add_cprod(c32 a, c32 b) {
-    re.add_prod(a.re, b.re);
-    re.add_prod(a.im, b.im);
-    im.add_prod(a.re, b.im);
-    im.add_prod(-a.im, b.re);
-  }
-  __device__ __forceinline__ z64 value() const { return z64(re.value(), im.value()); }
-};
-
-__device__ __forceinline__ void split64(z64 x, c32& hi, c32& lo) {
-  hi = c32(float(x.re), float(x.im));
-  lo = c32(float(x.re - double(hi.re)), float(x.im - double(hi.im)));
-}
-
-// ---------------------------------------------------------------------------
 // Stage 6 (mixed): one Newton correction of the occupied block.
 //   Q = X[:, :p] holds FP32 eigenvectors (exact FP32 numbers).  H Q from the hopping
 //   plan's FP64 entries with compensated FP32 dot products; rho_c = q_c^dag H q_c and
@@ -517,9 +523,8 @@ __global__ void k_lg_refine(LargeArgs a) {
         const int c = c0 + lane;
         CDF acc;
         for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) {
-          c32 hh, hl;
-          split64(He[q], hh, hl);
-          if (c < p) acc.add_prod(hh, hl, X[(long long)md.ent_col[q] * nbt + c]);
+          const c32* hp = reinterpret_cast<const c32*>(He + q);
+          if (c < p) acc.add_prod(hp[0], hp[1], X[(long long)md.ent_col[q] * nbt + c]);
         }
         if (c < p) R[(long long)r * p + c] = acc.value();
       }
@@ -607,8 +612,11 @@ __global__ void k_lg_refine(LargeArgs a) {
         double num = 0.0, den = 0.0;
         for (int r = tid; r < n; r += nt) {
           z64 hv(0.0, 0.0);
-          for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q)
-            cfma(hv, He[q], ccast<double>(X[(long long)md.ent_col[q] * nbt + col]));
+          for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) {
+            const c32* hp = reinterpret_cast<const c32*>(He + q);
+            const z64 h(double(hp[0].re) + double(hp[1].re), double(hp[0].im) + double(hp[1].im));
+            cfma(hv, h, ccast<double>(X[(long long)md.ent_col[q] * nbt + col]));
+          }
           const z64 v = ccast<double>(X[(long long)r * nbt + col]);
           num += v.re * hv.re + v.im * hv.im;
           den += abs2(v);

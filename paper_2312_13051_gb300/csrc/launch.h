@@ -116,7 +116,7 @@ struct LargeArgs {
   void* Z;                // W x n x nvec (T), row-major
   void* work;             // 6 n x (W nvec) (T), interleaved across threads
   void* X;                // W x n x nbt complex float (mixed)
-  z64* Hent;              // W x n_ent (mixed)
+  z64* Hent;              // W x n_ent (mixed): each slot holds the FP64 entry as two floats (hi, lo)
   z64* R64;               // W x n x p (mixed)
   c32* C32;               // W x n x p (mixed)
   z64* G64;               // W x p x p (mixed)
