@@ -130,7 +130,7 @@ class Context:
     def set_profiling(self, enable: bool = True) -> None:
         self.check(self.lib.bw_set_profiling(self.h, int(enable)))
 
-    def profile_read(self, max_kernels: int = 8):
+    def profile_read(self, max_kernels: int = 32):
         """[(kernel name, ms)] of the most recent profiled call or graph replay."""
         names = C.create_string_buffer(32 * max_kernels)
         ms = (C.c_double * max_kernels)()

@@ -1,0 +1,164 @@
+// Loop kernels for many occupied bands (p > 64, supercells): the Wilson matrix of
+// Eq. 2 no longer fits in shared memory, so the loop is streamed along its k-points.
+//
+//  - k_zgemm:    batched complex FP64 GEMM C_b = op(A_b) B_b, op in {identity,
+//                conjugate transpose}.  It forms the overlaps
+//                M_j = U(k_{j+1})^dagger U(k_j) (Eq. 2) and the running product
+//                W <- M_j W (later k on the left) for every loop of a block at once.
+//  - k_geig_big: one CTA per loop: general complex eigenvalues of W in global
+//                memory (Householder-Hessenberg + shifted QR, the same solver as the
+//                shared-memory path), theta = arg(lambda) sorted ascending, and the
+//                loop's minimum direct gap.
+#include <float.h>
+
+#include <algorithm>
+
+#include "geig.cuh"
+#include "jacobi.cuh"
+#include "launch.h"
+
+namespace bw {
+
+// ---------------------------------------------------------------------------
+// Batched complex GEMM.  CTA tile 64 x 64 of C, 256 threads; thread (ty, tx)
+// owns rows ty + 16 a and columns tx + 16 b (a, b < 4), so that the shared-memory
+// reads of a warp are conflict-free broadcasts or consecutive words.  The k
+// dimension advances in chunks of 16 staged in shared memory, zero-filled past the
+// ragged edges.  FP64 FMA throughput bounds it (GB300: ~1.7 FP64 FMA per clock
+// per SM), far below the shared-memory bandwidth the tile needs.
+// ---------------------------------------------------------------------------
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_zgemm(GemmArgs g) {
+  __shared__ z64 As[GK][GT];
+  __shared__ z64 Bs[GK][GT];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tiles_n = (g.n + GT - 1) / GT;
+  const long long b = g.b0 + blockIdx.y;
+  const long long ba = g.a_next_N > 0 ? (b / g.a_next_N) * g.a_next_N + (b % g.a_next_N + 1) % g.a_next_N : b;
+  const int r0 = (blockIdx.x / tiles_n) * GT, c0 = (blockIdx.x % tiles_n) * GT;
+  const z64* A = g.A + ba * g.sA;
+  const z64* B = g.B + b * g.sB;
+  z64* C = g.C + b * g.sC;
+  z64 acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = z64(0.0, 0.0);
+  for (int k0 = 0; k0 < g.k; k0 += GK) {
+    // stage op(A)[r0 .. r0+64, k0 .. k0+16] as As[kk][r]
+    for (int e = tid; e < GK * GT; e += 256) {
+      int kk, r;
+      if (g.opA) {  // A^dagger: row r of op(A) is column r of A (contiguous in r)
+        kk = e / GT;
+        r = e - kk * GT;
+      } else {      // A: contiguous in kk
+        r = e / GK;
+        kk = e - r * GK;
+      }
+      const int gr = r0 + r, gk = k0 + kk;
+      z64 v(0.0, 0.0);
+      if (gr < g.m && gk < g.k) {
+        if (g.opA) {
+          const z64 t = A[(long long)gk * g.lda + gr];
+          v = z64(t.re, -t.im);
+        } else {
+          v = A[(long long)gr * g.lda + gk];
+        }
+      }
+      As[kk][r] = v;
+    }
+    for (int e = tid; e < GK * GT; e += 256) {
+      const int kk = e / GT, c = e - kk * GT;
+      const int gc = c0 + c, gk = k0 + kk;
+      Bs[kk][c] = (gc < g.n && gk < g.k) ? B[(long long)gk * g.ldb + gc] : z64(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      z64 av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) av[x] = As[kk][ty + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bv[y] = Bs[kk][tx + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) cfma(acc[x][y], av[x], bv[y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int gr = r0 + ty + 16 * x;
+    if (gr >= g.m) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int gc = c0 + tx + 16 * y;
+      if (gc < g.n) C[(long long)gr * g.ldc + gc] = acc[x][y];
+    }
+  }
+}
+
+cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s) {
+  if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
+  const long long tiles = (long long)((g.m + GT - 1) / GT) * ((g.n + GT - 1) / GT);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  for (long long b0 = 0; b0 < g.batch; b0 += 65535) {  // grid.y holds at most 65535
+    GemmArgs h = g;
+    h.b0 = b0;
+    dim3 grid(unsigned(tiles), unsigned(std::min<long long>(65535, g.batch - b0)));
+    k_zgemm<<<grid, 256, 0, s>>>(h);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Eigenphases of the Wilson matrices of a block of loops.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_geig_big(BigEigArgs a) {
+  __shared__ GeigShared sh;
+  __shared__ double red[64];
+  const int p = a.p, tid = threadIdx.x, nt = blockDim.x;
+  for (int l = blockIdx.x; l < a.nl; l += gridDim.x) {
+    const int i = a.i0 + l;  // transverse index of the loop
+    const long long k0 = (long long)i * a.N;
+    if (a.min_gap) {
+      double g = INFINITY;
+      for (int j = tid; j < a.N; j += nt) g = fmin(g, a.gap[k0 + j]);
+      g = block_min(g, red);
+      if (tid == 0) a.min_gap[i] = g;
+    }
+    z64* W = a.W + (long long)l * a.sW;
+    z64* lam = a.lam + (long long)l * p;
+    z64* vec = a.vec + (long long)l * p;
+    double* th = a.th + (long long)l * p;
+    int* ord = a.ord + (long long)l * p;
+    const int rc = geig(W, nullptr, p, p, false, lam, vec, &sh);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+    for (int c = tid; c < p; c += nt) th[c] = atan2(lam[c].im, lam[c].re);
+    __syncthreads();
+    for (int c = tid; c < p; c += nt) {
+      const double x = rank_key(th[c]);
+      int rank = 0;
+      for (int d = 0; d < p; ++d) {
+        const double y = rank_key(th[d]);
+        rank += (y < x) || (y == x && d < c);
+      }
+      ord[rank] = c;
+    }
+    __syncthreads();
+    for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s) {
+  if (a.nl <= 0) return cudaSuccess;
+  k_geig_big<<<a.nl, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bw

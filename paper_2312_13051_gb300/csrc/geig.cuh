@@ -46,7 +46,7 @@ __device__ __forceinline__ void givens(z64 x, z64 y, double& c, z64& s) {
 // lam[p] receives the eigenvalues.  With want_vec, Z (p x p) receives the right
 // eigenvectors as unit-norm columns; vec scratch needs p z64.  Returns 0, or -1
 // when the QR iteration cap (120 p sweeps) is reached.
-__device__ int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64* vec,
+__device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* lam, z64* vec,
                     GeigShared* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const double eps = 2.220446049250313e-16;

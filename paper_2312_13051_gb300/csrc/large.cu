@@ -106,7 +106,7 @@ __global__ void k_lg_build(LargeArgs a) {
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
   const int nRs = min(md.n_R, PHASE_CACHE);
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
-    const long long k = a.k0 + kw;
+    const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     double f[3];
     lg_kpoint(a, k, f);
     for (int r = tid; r < nRs; r += nt) phs[r] = bloch_phase(f, md.Rv + 3 * r);
@@ -479,8 +479,9 @@ __global__ void k_lg_gap64(LargeArgs a) {
   if (kw >= a.W) return;
   const double* lam = reinterpret_cast<const double*>(a.lam) + kw * a.nval;
   const double g = a.p < a.n ? lam[a.p] - lam[a.p - 1] : INFINITY;
-  a.gap[a.k0 + kw] = g;
-  if (!(g > a.gap_tol)) report(a.status, ST_EGAP, a.k0 + kw, g);
+  const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
+  a.gap[k] = g;
+  if (!(g > a.gap_tol)) report(a.status, ST_EGAP, k, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,7 +507,7 @@ __global__ void k_lg_refine(LargeArgs a) {
   double* rho = reinterpret_cast<double*>(wv + p + (p & 1));  // p + 2
   double* red = rho + p + 2;                         // 64
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
-    const long long k = a.k0 + kw;
+    const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     const c32* A = reinterpret_cast<const c32*>(a.A) + kw * (long long)n * n;
     const c32* Dp = reinterpret_cast<const c32*>(a.Dp) + kw * n;
     const float* Z = reinterpret_cast<const float*>(a.Z) + kw * (long long)a.nvec * n;

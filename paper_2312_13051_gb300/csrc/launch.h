@@ -105,6 +105,7 @@ struct LargeArgs {
   int nvec;               // eigenvectors of T' computed
   int nbt;                // columns back-transformed (mixed: p + 1 when p < n)
   long long k0, W;
+  long long kstride;      // k-point of wave slot kw: k0 + kw * kstride (0 means 1)
   int mixed;
   double gap_tol;
   // wave scratch
@@ -129,6 +130,40 @@ struct LargeArgs {
   void (*mark)(void*, const char*);
   void* mark_user;
 };
+
+// Batched complex GEMM C_b = op(A_b) B_b (row-major; op(A) is A or A^dagger), m x n
+// result, inner dimension k; batch b uses A + b' sA, B + b sB, C + b sC, where b' = b,
+// or with a_next_N > 0 the next k-point of the same loop, (b / N) N + (b % N + 1) % N.
+struct GemmArgs {
+  const z64* A;
+  const z64* B;
+  z64* C;
+  int m, n, k;
+  int opA;                // 0: A (m x k), 1: A^dagger (A stored k x m)
+  long long lda, ldb, ldc;
+  long long sA, sB, sC;
+  long long a_next_N;
+  long long batch;
+  long long b0;           // first batch index of this launch (set by launch_zgemm)
+};
+
+// Eigenphases of nl Wilson matrices W (p x p, stride sW), loops i0 .. i0+nl-1.
+struct BigEigArgs {
+  z64* W;
+  long long sW;
+  int p, nl, i0, N;
+  const double* gap;      // K (absolute k = i N + j)
+  double* phases;         // N_t x p
+  double* min_gap;        // N_t (optional)
+  z64* lam;               // nl x p scratch
+  z64* vec;               // nl x p scratch
+  double* th;             // nl x p scratch
+  int* ord;               // nl x p scratch
+  DevStatus* status;
+};
+
+cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s);
 
 // Launches every stage of the large-n solver for one wave.
 cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);

@@ -21,6 +21,9 @@
 
 using bw::z64;
 
+// Timing marks kept per call (kernel launches of one call, in order).
+constexpr int kProfMax = 1024;
+
 struct bw_ctx {
   int device = 0;
   size_t budget = 0;
@@ -39,8 +42,8 @@ struct bw_ctx {
   // per-kernel timing (bw_set_profiling)
   bool prof = false;
   int prof_n = 0;
-  const char* prof_names[128] = {};
-  cudaEvent_t prof_ev[129] = {};
+  const char* prof_names[kProfMax] = {};
+  cudaEvent_t prof_ev[kProfMax + 1] = {};
 };
 
 namespace {
@@ -260,7 +263,7 @@ void end_call(bw_ctx* ctx, cudaStream_t s) {
 // Timing marks around kernel launches (recorded as external events under capture,
 // so that replays of a captured graph can be timed too).
 void prof_mark(bw_ctx* ctx, cudaStream_t s, const char* name) {
-  if (!ctx->prof || ctx->prof_n >= 128) return;
+  if (!ctx->prof || ctx->prof_n >= kProfMax) return;
   const int i = ctx->prof_n;
   if (!ctx->prof_ev[0])
     for (auto& e : ctx->prof_ev) cudaEventCreate(&e);
@@ -387,6 +390,148 @@ bw::DevPlane dev_plane(const bw_plane* pl) {
   return d;
 }
 
+// Plain Wilson loop with many occupied bands (p > LOOP_P_MAX, n > SMALL_N_MAX).  The
+// Wilson matrix no longer fits in shared memory, so the loop runs as batched GEMMs:
+// for a block of nl loops (their k-points are contiguous, k = i N + j) the states are
+// solved in waves of up to 2048 k-points, one GEMM forms every overlap
+// M_j = U(k_{j+1})^dagger U(k_j) of the block (closing on U(k_0), Eq. 2), N - 1 GEMMs
+// form W = M_{N-1} ... M_0 for all loops of the block at once, and one CTA per loop
+// takes the eigenphases.  Memory per loop: N n x p states, N + 2 p x p matrices;
+// the solver's per-k-point scratch is per wave.  The block shrinks to fit the budget.
+bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const bw_plane* plane,
+                       int p, bool mx, const Opts& o, double* phases, double* min_gap,
+                       cudaStream_t s) {
+  const int n = P.n, N = plane->N, Nt = plane->N_t;
+  const long long K = (long long)N * Nt;
+  const size_t ts = mx ? sizeof(float) : sizeof(double);
+  const int nval = mx ? n : std::min(n, p + 1), nvec = mx ? n : p;
+  const int nbt = mx ? std::min(n, p + 1) : p;
+  const size_t sz_A = al256(size_t(n) * n * 2 * ts), sz_v = al256(size_t(n) * ts),
+               sz_D = al256(size_t(n) * 2 * ts), sz_lam = al256(size_t(nval) * ts),
+               sz_Z = al256(size_t(nvec) * n * ts), sz_wk = al256(size_t(nvec) * 6 * n * ts),
+               sz_X = mx ? al256(size_t(n) * nbt * sizeof(bw::c32)) : 0,
+               sz_He = mx ? al256(size_t(P.n_ent) * sizeof(z64)) : 0,
+               sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
+               sz_C = mx ? al256(size_t(n) * p * sizeof(bw::c32)) : 0,
+               sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0;
+  const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C + sz_G;
+  const size_t bUk = size_t(n) * p * sizeof(z64), bPk = size_t(p) * p * sizeof(z64);
+  const size_t bEl = size_t(p) * (2 * sizeof(z64) + sizeof(double) + sizeof(int));
+  const size_t per_loop = size_t(N) * (bUk + bPk) + 2 * bPk + bEl;
+  size_t total = al256(blob.data.size()) + al256(size_t(K) * sizeof(double)) + 32 * 256;
+  const size_t avail = ctx->budget > total ? ctx->budget - total : 0;
+  long long Wv = std::min<long long>(K, 2048);
+  while (Wv > 1 && size_t(Wv) * per_k + per_loop > avail) Wv /= 2;
+  const size_t left = avail > size_t(Wv) * per_k ? avail - size_t(Wv) * per_k : 0;
+  const int nl_max = int(std::min<long long>(Nt, std::max<long long>(1, (long long)(left / per_loop))));
+  Wv = std::min<long long>(Wv, (long long)nl_max * N);
+  total += size_t(Wv) * per_k + size_t(nl_max) * per_loop;
+  bw_status st;
+  if ((st = reserve(ctx, total, s))) return st;
+  char* dblob = carve(ctx, blob.data.size());
+  double* gap = reinterpret_cast<double*>(carve(ctx, size_t(K) * sizeof(double)));
+  if ((st = upload(ctx, blob, dblob, s))) return st;
+  z64* Ublk = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * N * bUk));
+  z64* Mblk = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * N * bPk));
+  z64* Wbuf[2];
+  for (auto& w : Wbuf) w = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * bPk));
+  z64* e_lam = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(p) * sizeof(z64)));
+  z64* e_vec = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(p) * sizeof(z64)));
+  double* e_th = reinterpret_cast<double*>(carve(ctx, nl_max * size_t(p) * sizeof(double)));
+  int* e_ord = reinterpret_cast<int*>(carve(ctx, nl_max * size_t(p) * sizeof(int)));
+
+  bw::LargeArgs lg;
+  std::memset(&lg, 0, sizeof(lg));
+  lg.model = dev_model(P, dblob);
+  lg.plane = dev_plane(plane);
+  lg.n = n;
+  lg.p = p;
+  lg.nval = nval;
+  lg.nvec = nvec;
+  lg.nbt = nbt;
+  lg.mixed = mx;
+  lg.gap_tol = o.gap_tol;
+  lg.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
+  lg.gap = gap;
+  lg.status = ctx->status;
+  lg.A = carve(ctx, Wv * sz_A);
+  lg.dg = carve(ctx, Wv * sz_v);
+  lg.od = carve(ctx, Wv * sz_v);
+  lg.Dp = carve(ctx, Wv * sz_D);
+  lg.lam = carve(ctx, Wv * sz_lam);
+  lg.Z = carve(ctx, Wv * sz_Z);
+  lg.work = carve(ctx, Wv * sz_wk);
+  if (mx) {
+    lg.X = carve(ctx, Wv * sz_X);
+    lg.Hent = reinterpret_cast<z64*>(carve(ctx, Wv * sz_He));
+    lg.R64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_R));
+    lg.C32 = reinterpret_cast<bw::c32*>(carve(ctx, Wv * sz_C));
+    lg.G64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_G));
+  }
+  MarkHook hook{ctx, s};
+  lg.mark = mark_hook;
+  lg.mark_user = &hook;
+  prof_start(ctx, s);
+  const long long sU = (long long)n * p, sP = (long long)p * p;
+  for (int i0 = 0; i0 < Nt; i0 += nl_max) {
+    const int nl = std::min(nl_max, Nt - i0);
+    const long long kb = (long long)i0 * N, Kb = (long long)nl * N;
+    for (long long w0 = 0; w0 < Kb; w0 += Wv) {
+      lg.k0 = kb + w0;
+      lg.W = std::min(Wv, Kb - w0);
+      lg.U = Ublk + w0 * sU;
+      BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
+    }
+    // every overlap of the block: batch b = l N + j, A = U(k_{j+1}) (closing on j = 0)
+    bw::GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = Ublk; g.B = Ublk; g.C = Mblk;
+    g.m = p; g.n = p; g.k = n; g.opA = 1;
+    g.lda = p; g.ldb = p; g.ldc = p;
+    g.sA = sU; g.sB = sU; g.sC = sP;
+    g.a_next_N = N;
+    g.batch = Kb;
+    BW_CUDA(bw::launch_zgemm(g, s), "overlap GEMM");
+    prof_mark(ctx, s, "overlaps");
+    // W = M_{N-1} ... M_0 for the nl loops at once
+    const z64* Wcur = Mblk;  // M_0 of loop l at Mblk + l N p^2
+    long long sWcur = (long long)N * sP;
+    for (int j = 1; j < N; ++j) {
+      z64* Wout = Wbuf[j & 1];
+      std::memset(&g, 0, sizeof(g));
+      g.A = Mblk + (long long)j * sP; g.B = Wcur; g.C = Wout;
+      g.m = p; g.n = p; g.k = p; g.opA = 0;
+      g.lda = p; g.ldb = p; g.ldc = p;
+      g.sA = (long long)N * sP; g.sB = sWcur; g.sC = sP;
+      g.batch = nl;
+      BW_CUDA(bw::launch_zgemm(g, s), "loop-product GEMM");
+      Wcur = Wout;
+      sWcur = sP;
+    }
+    if (N > 1) prof_mark(ctx, s, "loops");
+    bw::BigEigArgs e;
+    std::memset(&e, 0, sizeof(e));
+    e.W = const_cast<z64*>(Wcur);
+    e.sW = sWcur;
+    e.p = p;
+    e.nl = nl;
+    e.i0 = i0;
+    e.N = N;
+    e.gap = gap;
+    e.phases = phases;
+    e.min_gap = min_gap;
+    e.lam = e_lam;
+    e.vec = e_vec;
+    e.th = e_th;
+    e.ord = e_ord;
+    e.status = ctx->status;
+    BW_CUDA(bw::launch_geig_big(e, s), "eigenphase kernel");
+    prof_mark(ctx, s, "eigenphases");
+  }
+  end_call(ctx, s);
+  return BW_OK;
+}
+
 // Shared driver of the three loop entry points.
 enum class LoopKind { Plain, Nested, Spin };
 
@@ -423,7 +568,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
                   first + m, p);
     if (!std::isfinite(cut)) return fail(ctx, BW_EINVAL, "cut is not finite");
   }
-  if (p_eff > bw::LOOP_P_MAX) return fail(ctx, BW_EINVAL, "p = %d exceeds %d", p_eff, bw::LOOP_P_MAX);
+  const bool big = p_eff > bw::LOOP_P_MAX;
+  if (big && kind != LoopKind::Plain)
+    return fail(ctx, BW_EINVAL, "%s loop supports p <= %d (p = %d)",
+                kind == LoopKind::Spin ? "spin-resolved" : "nested", bw::LOOP_P_MAX, p_eff);
   if (large && kind == LoopKind::Spin && p > 64)
     return fail(ctx, BW_EINVAL, "spin-resolved loop for n > %d supports p <= 64 (p = %d)", bw::SMALL_N_MAX, p);
   const Opts o = resolve_opts(opts, P.tmax);
@@ -431,6 +579,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const long long K = (long long)plane->N * plane->N_t;
   Blob blob;
   plan_to_blob(P, blob);
+  if (big) {
+    begin_call(ctx, s);
+    return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s);
+  }
   if (kind == LoopKind::Spin) {
     op.o_row = blob.add(op.row);
     op.o_col = blob.add(op.col);

@@ -294,3 +294,41 @@ def test_large_n_spin_and_nested(lib, ctx, precision):
     ph, nest, _, _ = lib.nested_wilson_loop(model, plane, 16, m=8, precision=precision, ctx=ctx)
     assert circ_err_rows(ph.cpu().numpy(), rph) <= TOL[precision]
     assert circ_err_rows(nest.cpu().numpy(), rn) <= TOL[precision]
+
+
+# ---------------------------------------------------------------- many occupied bands (p > 64)
+MANY = {
+    "flux_L6": (lambda: I.supercell(I.spin_hall(1.0), 6, W=1.0, seed=11, flux=True), P(6, 4), 72),
+    "random160_p80": (lambda: I.random_hermitian_model(160, 41), P(5, 3), 80),
+    "disordered_L10": (lambda: I.supercell(I.spin_hall(1.0), 10, W=2.0, seed=5), P(4, 3), 200),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(MANY))
+def test_many_band_wilson_parity(lib, ctx, case, precision):
+    """Streamed loop (GEMM overlaps and products, global-memory eigenphases) vs the oracle."""
+    mk, plane, p = MANY[case]
+    model = mk()
+    ref, rgap = oracle.wilson_loop(model, plane, p)
+    ph, gap = lib.wilson_loop(model, plane, p, precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    rel = np.abs(gap.cpu().numpy() - rgap) / np.maximum(1.0, np.abs(rgap))
+    assert rel.max() <= (1e-9 if precision == "fp64" else 1e-6)
+
+
+def test_many_band_blocks_of_loops(lib):
+    """A budget that holds a few loops and a few k-points at a time (several blocks of
+    loops, several solver waves per block) gives the same phases as one block."""
+    torch = pytest.importorskip("torch")
+    model = I.supercell(I.spin_hall(1.0), 6, W=1.0, seed=11, flux=True)   # n = 144, p = 72
+    plane = P(5, 5)
+    big = lib.Context(0)
+    small = lib.Context(0, 8 << 20)
+    try:
+        a, ga = lib.wilson_loop(model, plane, 72, precision="mixed", ctx=big)
+        b, gb = lib.wilson_loop(model, plane, 72, precision="mixed", ctx=small)
+        assert torch.equal(a, b) and torch.equal(ga, gb)
+    finally:
+        big.close()
+        small.close()
