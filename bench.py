@@ -364,6 +364,93 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    """Config-4 serving stream through the request server (continuous batching).
+
+    Poisson arrivals (seeded) of Wilson-loop requests on flux-threaded, disordered
+    spin-Hall supercells (L from --sides, W ~ U[0, 4], nk x nk grid, p = n/2), each
+    submitted at its arrival time; the server admits them as slots and device memory
+    free up.  Reports achieved throughput and p50/p99 latency (submit -> results in
+    host memory) for the mixed and the FP64 path, and the phase error of sampled
+    requests against the oracle.
+    """
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2312_13051_gb300 import build as B
+    B.build()
+    from paper_2312_13051_gb300 import _lib as lib
+    from paper_2312_13051_gb300 import inputs as I
+    import oracle
+
+    sides = tuple(int(x) for x in args.sides.split(","))
+    reqs = I.serving_requests(args.requests, rate=args.rate, sides=sides,
+                              nk_range=(args.nk_min, args.nk_max))
+    models = [I.serving_model(r) for r in reqs]
+    planes = [I.Plane(r["nk"], r["nk"]) for r in reqs]
+    clocks = ClockSampler(0)
+    out = {}
+    clocks.start()
+    for prec in ("mixed", "fp64"):
+        srv = lib.Server(0, max_slots=args.slots)
+        # warm-up: one small request per precision (library load, first launches)
+        w = srv.submit(I.spin_hall(1.0), I.Plane(4, 4), 2, prec)
+        srv.wait(w)
+        done, results = {}, {}
+        t0 = time.perf_counter()
+        nxt = 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+                m = models[nxt]
+                rid = srv.submit(m, planes[nxt], m.n // 2, prec)
+                results[rid] = nxt
+                nxt += 1
+            for rid, info, ph, gap in srv.poll():
+                done[results[rid]] = (info, ph)
+            if nxt < len(reqs):
+                time.sleep(max(0.0, min(0.002, reqs[nxt]["arrival"] - (time.perf_counter() - t0))))
+            else:
+                time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array([done[i][0]["latency_ms"] for i in range(len(reqs))])
+        ok = [i for i in range(len(reqs)) if done[i][0]["status"] == "OK"]
+        kpts = sum(reqs[i]["nk"] ** 2 for i in ok)
+        failed = {}
+        for i in range(len(reqs)):
+            st = done[i][0]["status"]
+            if st != "OK":
+                failed[st] = failed.get(st, 0) + 1
+        out[prec] = dict(wall_s=wall, requests_per_s=len(reqs) / wall, kpoints_per_s=kpts / wall,
+                         p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                         ok=len(ok), failed=failed,
+                         device_ms_sum=float(sum(done[i][0]["device_ms"] for i in range(len(reqs)))))
+        # parity on the smallest successful requests (one transverse row each, oracle FP64)
+        errs = []
+        for i in sorted(ok, key=lambda i: models[i].n * reqs[i]["nk"])[:args.parity_samples]:
+            pl = planes[i]
+            row = 1 % pl.N_t
+            plr = I.Plane(pl.N, 1, origin=tuple(np.array(pl.trans_dir) * row / pl.N_t))
+            ref, _ = oracle.wilson_loop(models[i], plr, models[i].n // 2)
+            errs.append(oracle.circular_match_error(done[i][1][row], ref[0]))
+        out[prec]["phase_err_rad"] = max(errs) if errs else None
+        out[prec]["parity_samples"] = len(errs)
+    clk = clocks.stop()
+    line = {
+        "metric": "Wilson-loop serving: k-points/s and p50/p99 latency (submit -> host results)",
+        "value": out["mixed"]["kpoints_per_s"], "unit": UNIT, "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving stream: flux-threaded disordered spin-Hall supercells",
+                   "requests": len(reqs), "rate_per_s": args.rate, "sides": list(sides),
+                   "nk_range": [args.nk_min, args.nk_max], "slots": args.slots, "p": "n/2"},
+        "mixed": out["mixed"], "fp64": out["fp64"],
+        "mixed_over_fp64": out["mixed"]["kpoints_per_s"] / max(out["fp64"]["kpoints_per_s"], 1e-30),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,12 +459,23 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving stream (request server) instead of the step bench")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--sides", default="8,12,16")
+    ap.add_argument("--nk-min", type=int, default=8)
+    ap.add_argument("--nk-max", type=int, default=24)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--parity-samples", type=int, default=3)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         log("warmup raised to 3")
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     return run_ours(args)
 
 

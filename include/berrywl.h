@@ -209,6 +209,62 @@ bw_status bw_wilson_loop_noalloc(const bw_model* model, const bw_plane* plane, i
                                  bw_precision prec, const bw_opts* opts, double* phases,
                                  double* min_gap, void* stream, char* err, size_t err_len);
 
+/* Scratch bytes bw_wilson_loop would reserve on this context for the problem (the
+ * context's memory budget bounds it: a smaller budget runs the loops in smaller
+ * blocks).  Validates the arguments like bw_wilson_loop; no device work. */
+bw_status bw_wilson_loop_workspace(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
+                                   int32_t p, bw_precision prec, const bw_opts* opts,
+                                   size_t* bytes);
+
+/* ---------------------------------------------------------------------------
+ * Request server (no counterpart in the paper: serving many Wilson-loop requests,
+ * e.g. disorder realisations and supercells of different sizes, on one GPU).
+ *
+ * The server owns one device memory pool (allocated once at creation), up to
+ * max_slots contexts with one CUDA stream each, and a worker thread.  A submitted
+ * request is validated and sized on the caller's thread, queued, and admitted when
+ * a slot is free and the pool holds its scratch and outputs (at most half of the
+ * pool per request); requests arriving while others run are admitted as soon as
+ * slots and memory free up, and their kernels overlap on the GPU.  A request that
+ * does not fit yet lets later, smaller ones through.  Each request computes exactly
+ * what bw_wilson_loop computes; its results are copied to the caller's HOST buffers,
+ * which must stay valid until the request is collected by bw_server_poll or
+ * bw_server_wait.  The server functions may be called from any one host thread.
+ * --------------------------------------------------------------------------- */
+typedef struct bw_server bw_server;
+
+typedef struct {
+  int64_t id;
+  int32_t status;         /* bw_status of the request (argument, device or CUDA error) */
+  int32_t reserved;
+  int64_t k_index;        /* k-point index of a device-side status, else -1         */
+  double latency_ms;      /* submit -> results in the caller's buffers                */
+  double queue_ms;        /* submit -> admission                                      */
+  double device_ms;       /* first to last operation on the slot's stream             */
+  char message[128];      /* error text (empty when status is BW_OK)                  */
+} bw_request_info;
+
+/* mem_budget_bytes = 0: 80 % of the free device memory.  1 <= max_slots <= 64. */
+bw_status bw_server_create(bw_server** out, int device, int32_t max_slots,
+                           size_t mem_budget_bytes);
+/* Stops admitting, waits for the requests on the GPU, drops queued ones. */
+void bw_server_destroy(bw_server* server);
+const char* bw_server_last_error(const bw_server* server);
+/* Queues a Wilson loop (arguments as bw_wilson_loop; model copied).  phases: HOST,
+ * N_t x p doubles; min_gap: HOST, N_t doubles (may be NULL).  *id receives the
+ * request id.  Returns argument errors and BW_ENOMEM (larger than the pool). */
+bw_status bw_server_submit(bw_server* server, const bw_model* model, const bw_plane* plane,
+                           int32_t p, bw_precision prec, const bw_opts* opts,
+                           double* phases, double* min_gap, int64_t* id);
+/* Collects up to max finished requests (in completion order) without blocking;
+ * returns their number, or -1 on bad arguments. */
+int bw_server_poll(bw_server* server, bw_request_info* done, int max);
+/* Blocks until request id finishes (BW_ETIMEOUT after timeout_s seconds) and
+ * collects it into *info (may be NULL). */
+bw_status bw_server_wait(bw_server* server, int64_t id, double timeout_s, bw_request_info* info);
+/* Requests queued or running. */
+int64_t bw_server_outstanding(bw_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,12 @@ class bw_opts(C.Structure):
                 ("max_sweeps", C.c_int32)]
 
 
+class bw_request_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("k_index", C.c_int64), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("device_ms", C.c_double), ("message", C.c_char * 128)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -81,6 +87,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_wilson_loop_noalloc": (i32, [C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
                                              C.POINTER(bw_opts), vp, vp, vp, C.c_char_p,
                                              C.c_size_t]),
+            "bw_wilson_loop_workspace": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32,
+                                               i32, C.POINTER(bw_opts), C.POINTER(C.c_size_t)]),
+            "bw_server_create": (i32, [C.POINTER(vp), C.c_int, i32, C.c_size_t]),
+            "bw_server_destroy": (None, [vp]),
+            "bw_server_last_error": (C.c_char_p, [vp]),
+            "bw_server_submit": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
+                                       C.POINTER(bw_opts), vp, vp, C.POINTER(i64)]),
+            "bw_server_poll": (C.c_int, [vp, C.POINTER(bw_request_info), C.c_int]),
+            "bw_server_wait": (i32, [vp, i64, dbl, C.POINTER(bw_request_info)]),
+            "bw_server_outstanding": (i64, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -94,7 +110,9 @@ def exported_symbols():
     return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
             "bw_profile_read", "bw_build_hk",
             "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
-            "bw_spin_resolved_wilson_loop", "bw_wilson_loop_noalloc"]
+            "bw_spin_resolved_wilson_loop", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
+            "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
+            "bw_server_poll", "bw_server_wait", "bw_server_outstanding"]
 
 
 class Context:
@@ -334,3 +352,92 @@ def wilson_loop_noalloc(model, plane, p: int, precision: str = "fp64", out=None,
     if rc != 0:
         raise BWError(rc, err.value.decode())
     return ph, gap
+
+
+def wilson_loop_workspace(model, plane, p: int, precision: str = "fp64",
+                          ctx: Context | None = None, **opts) -> int:
+    """Device scratch bytes ``wilson_loop`` reserves for this problem on ``ctx``."""
+    ctx = ctx or context()
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    nb = C.c_size_t(0)
+    ctx.check(ctx.lib.bw_wilson_loop_workspace(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
+                                               PRECISION[precision], C.byref(o), C.byref(nb)))
+    return int(nb.value)
+
+
+class Server:
+    """``bw_server``: memory-admitted continuous batching of Wilson-loop requests.
+
+    ``submit`` returns a request id; the results land in host numpy arrays owned by
+    this object until the request is collected with ``poll`` or ``wait``, which
+    return ``(id, info, phases[N_t, p], min_gap[N_t])``.
+    """
+
+    def __init__(self, device: int = 0, max_slots: int = 4, mem_budget_bytes: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.bw_server_create(C.byref(h), device, int(max_slots), int(mem_budget_bytes))
+        if rc != 0:
+            raise BWError(rc, f"bw_server_create(device={device}) failed")
+        self.h = h
+        self._out = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bw_server_destroy(self.h)
+            self.h = None
+            self._out.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, model, plane, p: int, precision: str = "fp64", **opts) -> int:
+        hm = _HostModel(model)
+        pl = _plane(plane)
+        o = _opts(**opts)
+        ph = np.empty((plane.N_t, p), np.float64)
+        gap = np.empty((plane.N_t,), np.float64)
+        rid = C.c_int64(0)
+        rc = self.lib.bw_server_submit(self.h, C.byref(hm.s), C.byref(pl), int(p),
+                                       PRECISION[precision], C.byref(o),
+                                       ph.ctypes.data_as(C.c_void_p),
+                                       gap.ctypes.data_as(C.c_void_p), C.byref(rid))
+        if rc != 0:
+            raise BWError(rc, self.lib.bw_server_last_error(self.h).decode())
+        self._out[int(rid.value)] = (ph, gap)
+        return int(rid.value)
+
+    @staticmethod
+    def _info(i: bw_request_info) -> dict:
+        return dict(id=int(i.id), status=STATUS_NAMES[i.status] if 0 <= i.status < len(STATUS_NAMES)
+                    else str(i.status), k_index=int(i.k_index), latency_ms=i.latency_ms,
+                    queue_ms=i.queue_ms, device_ms=i.device_ms, message=i.message.decode())
+
+    def poll(self, max_requests: int = 64):
+        buf = (bw_request_info * max_requests)()
+        n = self.lib.bw_server_poll(self.h, buf, max_requests)
+        if n < 0:
+            raise BWError(1, "bw_server_poll failed")
+        out = []
+        for k in range(n):
+            info = self._info(buf[k])
+            ph, gap = self._out.pop(info["id"])
+            out.append((info["id"], info, ph, gap))
+        return out
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        info = bw_request_info()
+        rc = self.lib.bw_server_wait(self.h, int(rid), float(timeout_s), C.byref(info))
+        if rc != 0:
+            raise BWError(rc, self.lib.bw_server_last_error(self.h).decode())
+        inf = self._info(info)
+        ph, gap = self._out.pop(int(rid))
+        return int(rid), inf, ph, gap
+
+    def outstanding(self) -> int:
+        return int(self.lib.bw_server_outstanding(self.h))

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libberrywl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["states.cu", "tiny.cu", "large.cu", "loops.cu", "bigloop.cu", "runtime.cu"]
+SOURCES = ["states.cu", "tiny.cu", "large.cu", "loops.cu", "bigloop.cu", "runtime.cu", "server.cu"]
 
 
 def nvcc() -> str:
@@ -58,7 +58,7 @@ def build(force: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, hdr), SOURCES))
     if os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -56,53 +56,59 @@ __device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* la
       Z[r * ld + c] = z64(double(r == c), 0.0);
     }
   __syncthreads();
-  // --- Householder reduction to Hessenberg form
+  // --- Householder reduction to Hessenberg form.  Column norms are block
+  // reductions; the left update runs one thread per column and the right update one
+  // warp per row, so that consecutive threads touch consecutive entries.
+  __shared__ double hred[32];
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   for (int c = 0; c + 2 < p; ++c) {
-    if (tid == 0) {
-      double nrm2 = 0.0;
-      for (int r = c + 1; r < p; ++r) nrm2 += abs2(H[r * ld + c]);
-      double tail = nrm2 - abs2(H[(c + 1) * ld + c]);
-      sh->active = (tail > 0.0);
-      if (sh->active) {
-        const z64 x0 = H[(c + 1) * ld + c];
-        const double nx = sqrt(nrm2), ax0 = zabs(x0);
-        const z64 ph = ax0 > 0.0 ? z64(x0.re / ax0, x0.im / ax0) : z64(1.0, 0.0);
-        const z64 alpha = -nx * ph;
-        for (int r = c + 1; r < p; ++r) vec[r] = H[r * ld + c];
-        vec[c + 1] = vec[c + 1] - alpha;
-        double nv = 0.0;
-        for (int r = c + 1; r < p; ++r) nv += abs2(vec[r]);
-        nv = 1.0 / sqrt(nv);
-        for (int r = c + 1; r < p; ++r) vec[r] = nv * vec[r];
-        sh->mu = alpha;
-      }
+    double nrm2 = 0.0;
+    for (int r = c + 1 + tid; r < p; r += nt) nrm2 += abs2(H[r * ld + c]);
+    nrm2 = block_sum(nrm2, hred);
+    const z64 x0 = H[(c + 1) * ld + c];
+    const double tail = nrm2 - abs2(x0);
+    if (!(tail > 0.0)) {
+      __syncthreads();
+      continue;
     }
+    const double nx = sqrt(nrm2), ax0 = zabs(x0);
+    const z64 ph = ax0 > 0.0 ? z64(x0.re / ax0, x0.im / ax0) : z64(1.0, 0.0);
+    // v = x - alpha e1, alpha = -|x| ph: v_0 = ph (|x0| + |x|), |v|^2 = (|x0| + |x|)^2 + tail
+    const double v0m = ax0 + nx, nv = 1.0 / sqrt(v0m * v0m + tail);
+    for (int r = c + 1 + tid; r < p; r += nt)
+      vec[r] = r == c + 1 ? z64(nv * v0m * ph.re, nv * v0m * ph.im) : nv * H[r * ld + c];
+    if (tid == 0) sh->mu = -nx * ph;
     __syncthreads();
-    if (!sh->active) continue;
-    // left: H <- (I - 2 v v^dagger) H on rows c+1.., columns c..
-    for (int col = c + tid; col < p; col += nt) {
+    // left: H <- (I - 2 v v^dagger) H on rows c+1.., columns c+1.. (column c is set below)
+    for (int col = c + 1 + tid; col < p; col += nt) {
       z64 w(0.0, 0.0);
       for (int r = c + 1; r < p; ++r) cfma_conj(w, vec[r], H[r * ld + col]);
       for (int r = c + 1; r < p; ++r) H[r * ld + col] = H[r * ld + col] - 2.0 * (vec[r] * w);
     }
     __syncthreads();
     // right: H <- H (I - 2 v v^dagger) on columns c+1..; Z likewise
-    for (int row = tid; row < p; row += nt) {
+    for (int row = warp; row < p; row += nwarp) {
+      z64* hr = H + row * ld;
       z64 w(0.0, 0.0);
-      for (int k = c + 1; k < p; ++k) cfma(w, H[row * ld + k], vec[k]);
-      for (int k = c + 1; k < p; ++k) H[row * ld + k] = H[row * ld + k] - 2.0 * (w * conj(vec[k]));
+      for (int k = c + 1 + lane; k < p; k += 32) cfma(w, hr[k], vec[k]);
+      for (int o = 16; o > 0; o >>= 1) {
+        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+      }
+      for (int k = c + 1 + lane; k < p; k += 32) hr[k] = hr[k] - 2.0 * (w * conj(vec[k]));
       if (want_vec) {
+        z64* zr = Z + row * ld;
         z64 wz(0.0, 0.0);
-        for (int k = c + 1; k < p; ++k) cfma(wz, Z[row * ld + k], vec[k]);
-        for (int k = c + 1; k < p; ++k)
-          Z[row * ld + k] = Z[row * ld + k] - 2.0 * (wz * conj(vec[k]));
+        for (int k = c + 1 + lane; k < p; k += 32) cfma(wz, zr[k], vec[k]);
+        for (int o = 16; o > 0; o >>= 1) {
+          wz.re += __shfl_xor_sync(0xffffffffu, wz.re, o);
+          wz.im += __shfl_xor_sync(0xffffffffu, wz.im, o);
+        }
+        for (int k = c + 1 + lane; k < p; k += 32) zr[k] = zr[k] - 2.0 * (wz * conj(vec[k]));
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      H[(c + 1) * ld + c] = sh->mu;
-      for (int r = c + 2; r < p; ++r) H[r * ld + c] = z64(0.0, 0.0);
-    }
+    for (int r = c + 1 + tid; r < p; r += nt) H[r * ld + c] = r == c + 1 ? sh->mu : z64(0.0, 0.0);
     __syncthreads();
   }
   // --- shifted QR on the Hessenberg matrix

@@ -23,6 +23,8 @@ using bw::z64;
 
 // Timing marks kept per call (kernel launches of one call, in order).
 constexpr int kProfMax = 1024;
+// Internal status returned by reserve() in a workspace query (never reaches a caller).
+constexpr bw_status kQueryDone = bw_status(100);
 
 struct bw_ctx {
   int device = 0;
@@ -39,6 +41,11 @@ struct bw_ctx {
   cudaStream_t last_stream = nullptr;
   bool have_last = false;
   std::string err;
+  // arena supplied by the owner (a server slot): never grown or freed here
+  bool external_arena = false;
+  // workspace query: reserve() records the bytes and stops the call
+  bool query_only = false;
+  size_t query_bytes = 0;
   // per-kernel timing (bw_set_profiling)
   bool prof = false;
   int prof_n = 0;
@@ -292,6 +299,13 @@ void prof_start(bw_ctx* ctx, cudaStream_t s) {
 
 // Makes sure the arena holds `bytes`; growing it waits for outstanding work.
 bw_status reserve(bw_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (ctx->query_only) {
+    ctx->query_bytes = bytes;
+    return kQueryDone;
+  }
+  if (ctx->external_arena && bytes > ctx->arena_cap)
+    return fail(ctx, BW_ENOMEM, "call needs %zu bytes of scratch, the attached arena holds %zu", bytes,
+                ctx->arena_cap);
   if (bytes > ctx->budget)
     return fail(ctx, BW_ENOMEM, "call needs %zu bytes of scratch, budget is %zu", bytes, ctx->budget);
   if (bytes <= ctx->arena_cap) return BW_OK;
@@ -774,7 +788,7 @@ void bw_destroy(bw_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->arena && !ctx->external_arena) cudaFree(ctx->arena);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->upload_ev) cudaEventDestroy(ctx->upload_ev);
@@ -1104,3 +1118,61 @@ extern "C" bw_status bw_wilson_loop_noalloc(const bw_model* model, const bw_plan
   }
   return st;
 }
+
+extern "C" bw_status bw_wilson_loop_workspace(bw_ctx* ctx, const bw_model* model,
+                                              const bw_plane* plane, int32_t p, bw_precision prec,
+                                              const bw_opts* opts, size_t* bytes) {
+  if (!ctx || !bytes) return BW_EINVAL;
+  double dummy = 0.0;
+  ctx->query_only = true;
+  ctx->query_bytes = 0;
+  const bw_status st = run_loop(ctx, LoopKind::Plain, model, plane, p, prec, opts, nullptr, 0, 0.0, 0,
+                                0, &dummy, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  ctx->query_only = false;
+  if (st == kQueryDone) {
+    *bytes = ctx->query_bytes;
+    return BW_OK;
+  }
+  return st == BW_OK ? BW_EINVAL : st;
+}
+
+namespace bw_internal {
+
+bw_status attach_arena(bw_ctx* ctx, void* base, size_t cap) {
+  if (!ctx) return BW_EINVAL;
+  if (ctx->arena && !ctx->external_arena) {
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->arena);
+  }
+  ctx->arena = static_cast<char*>(base);
+  ctx->arena_cap = cap;
+  ctx->external_arena = true;
+  ctx->budget = cap;
+  return BW_OK;
+}
+
+bw_status reserve_staging(bw_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->staging_cap) return BW_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->staging) cudaFreeHost(ctx->staging);
+  ctx->staging = nullptr;
+  ctx->staging_cap = 0;
+  BW_CUDA(cudaMallocHost(&ctx->staging, bytes), "cudaMallocHost");
+  ctx->staging_cap = bytes;
+  return BW_OK;
+}
+
+bw_status clear_status_async(bw_ctx* ctx, cudaStream_t s) {
+  BW_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(bw::DevStatus), s), "cudaMemsetAsync status");
+  return BW_OK;
+}
+
+bw_status status_to_host_async(bw_ctx* ctx, void* pinned_dst, cudaStream_t s) {
+  BW_CUDA(cudaMemcpyAsync(pinned_dst, ctx->status, sizeof(bw::DevStatus), cudaMemcpyDeviceToHost, s),
+          "cudaMemcpyAsync status");
+  return BW_OK;
+}
+
+const char* last_error(const bw_ctx* ctx) { return ctx->err.c_str(); }
+
+}  // namespace bw_internal
