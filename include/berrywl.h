@@ -132,12 +132,15 @@ bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64
 
 /* Step 2, exact diagonalisation (Sec. I), batched with uneven sizes.
  * H: DEVICE, matrices packed back to back (matrix b holds n_per[b]^2 complex128,
- * row-major, Hermitian; only its lower triangle is read for n > 32 ... the full
- * matrix for n <= 32).  n_per: HOST, batch sizes.  evals: DEVICE, sum(n_per)
+ * row-major, Hermitian; for n > 32 only the lower triangle is read, for n <= 32 the
+ * full matrix).  n_per: HOST, batch sizes.  evals: DEVICE, sum(n_per)
  * doubles, ascending per matrix.  evecs: DEVICE, sum(n_per[b] * n_vec) complex128,
  * matrix b's lowest n_vec eigenvectors as an n x n_vec row-major block (NULL: values
  * only).  BW_MIXED: FP32 solve, lowest n_vec block refined in FP64 (needs
- * n_vec < n and a gap above it).  1 <= n <= 1024, 0 <= n_vec <= n. */
+ * n_vec < n and a gap above it; for n > 32 also n_vec <= 64), the other eigenvalues
+ * to FP32 accuracy.  n <= 32: one shared-memory Jacobi solve per matrix; n > 32:
+ * Householder tridiagonalisation, bisection and inverse iteration, matrices of equal
+ * size in waves.  1 <= n <= 4096, 0 <= n_vec <= n. */
 bw_status bw_eigh_batched(bw_ctx* ctx, const void* H, const int32_t* n_per, int64_t batch,
                           int32_t n_vec, bw_precision prec, double* evals, void* evecs,
                           void* stream);

@@ -13,6 +13,8 @@
 // T is the working precision of the reduction (double: FP64 path, float: mixed).
 #include <float.h>
 
+#include <algorithm>
+
 #include "jacobi.cuh"
 #include "launch.h"
 
@@ -106,6 +108,29 @@ __global__ void k_lg_build(LargeArgs a) {
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
   const int nRs = min(md.n_R, PHASE_CACHE);
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    if (a.Hin) {  // explicit matrix: lower triangle mirrored, FP64 entries kept for the refinement
+      const z64* Hm = a.Hin + a.h_off[a.idx[a.k0 + kw]];
+      cx<T>* A = reinterpret_cast<cx<T>*>(a.A) + kw * (long long)n * n;
+      c32* He = a.Hent ? reinterpret_cast<c32*>(a.Hent + kw * (long long)n * n) : nullptr;
+      for (int r = tid >> 5; r < n; r += nt >> 5)
+        for (int q = tid & 31; q <= r; q += 32) {
+          z64 h = Hm[(long long)r * n + q];
+          if (q == r) h.im = 0.0;
+          A[(long long)r * n + q] = ccast<T>(h);
+          A[(long long)q * n + r] = ccast<T>(conj(h));
+          if (He) {
+            c32 hi, lo;
+            split64(h, hi, lo);
+            He[2 * ((long long)r * n + q)] = hi;
+            He[2 * ((long long)r * n + q) + 1] = lo;
+            split64(conj(h), hi, lo);
+            He[2 * ((long long)q * n + r)] = hi;
+            He[2 * ((long long)q * n + r) + 1] = lo;
+          }
+        }
+      __syncthreads();
+      continue;
+    }
     const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     double f[3];
     lg_kpoint(a, k, f);
@@ -232,6 +257,201 @@ __global__ void k_lg_tridiag(LargeArgs a) {
       if (n >= 2) A[(long long)(n - 1) * n + (n - 2)] = cx<T>(T(0), T(0));
     }
     __syncthreads();
+    // unit phases of the subdiagonal, then their prefix products (serial: cheap)
+    for (int c = tid; c + 1 < n; c += nt) {
+      const T aa = sqrt(abs2(al[c]));
+      od[c] = aa;
+      al[c] = aa > T(0) ? cx<T>(al[c].re / aa, al[c].im / aa) : cx<T>(T(1), T(0));
+    }
+    __syncthreads();
+    if (tid == 0) {
+      cx<T> dcur(T(1), T(0));
+      Dp[0] = dcur;
+      for (int c = 0; c + 1 < n; ++c) {
+        dcur = dcur * al[c];
+        Dp[c + 1] = dcur;
+      }
+      od[n - 1] = T(0);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2, lower-triangle form (used when its shared memory fits, see the launcher).
+// Same reflectors and T' as k_lg_tridiag, one pass over the trailing lower triangle
+// per column: the column c+1 of the updated matrix is formed first, its reflector
+// u' built, and then the rank-2 update of step c and the product p' = A' u' of step
+// c+1 run in the same sweep.  A' u' takes A'_rq u'_q from the stored lower triangle
+// and conj(A'_rq) u'_r for the mirrored upper one; the mirrored terms go to one
+// accumulator array per warp (lane-private entries: entry q of a warp's array is
+// only touched by lane (q - lo) mod 32), summed over warps in a fixed order, so the
+// result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+
+// Turns xs[c+1..n) (column c below the diagonal) into the unit reflector u with
+// (I - 2 u u^dag) x = alpha e_1 and returns alpha; u = 0 when nothing lies below the
+// subdiagonal.  Block-wide.
+template <typename T>
+__device__ cx<T> lg_reflector(cx<T>* xs, int c, int n, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double s = 0.0;
+  for (int r = c + 1 + tid; r < n; r += nt) s += double(abs2(xs[r]));
+  s = block_sum(s, red);
+  const cx<T> x0 = xs[c + 1];
+  const double ax0 = hypot(double(x0.re), double(x0.im)), tail = s - ax0 * ax0;
+  __syncthreads();
+  if (!(tail > 0.0)) {
+    for (int r = c + 1 + tid; r < n; r += nt) xs[r] = cx<T>(T(0), T(0));
+    __syncthreads();
+    return x0;
+  }
+  const double nx = sqrt(s);
+  const double phr = ax0 > 0.0 ? double(x0.re) / ax0 : 1.0, phi = ax0 > 0.0 ? double(x0.im) / ax0 : 0.0;
+  const double v0m = ax0 + nx;
+  const T inv = T(1.0 / sqrt(v0m * v0m + tail));
+  for (int r = c + 1 + tid; r < n; r += nt) {
+    const cx<T> v = r == c + 1 ? cx<T>(T(phr * v0m), T(phi * v0m)) : xs[r];
+    xs[r] = inv * v;
+  }
+  __syncthreads();
+  return cx<T>(T(-phr * nx), T(-phi * nx));
+}
+
+// Rows and columns lo..n-1 of the lower triangle: with upd, A <- A - 2 (u w^dag + w u^dag);
+// then pa = A u2 (pw: per-warp accumulators, stride n).  A warp takes RW rows at a
+// time (r, r + nwarp, ...) and walks their columns together, so that RW loads per
+// lane are in flight even when the rows are short.  Ends with pa complete.
+template <typename T>
+__device__ void lg_hpass(cx<T>* A, int n, int lo, bool upd, const cx<T>* u, const cx<T>* w,
+                         const cx<T>* u2, cx<T>* pw, cx<T>* pa) {
+  constexpr int RW = sizeof(T) == 4 ? 8 : 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < nwarp * (n - lo); e += blockDim.x) {
+    const int ww = e / (n - lo), q = lo + (e - ww * (n - lo));
+    pw[ww * n + q] = cx<T>(T(0), T(0));
+  }
+  __syncthreads();
+  cx<T>* acc_w = pw + warp * n;
+  const cx<T> zero(T(0), T(0));
+  for (int r0 = lo + warp; r0 < n; r0 += RW * nwarp) {
+    int rr[RW];
+    cx<T> ur[RW], wr[RW], u2r[RW], acc[RW];
+    int rmax = r0;
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+      rr[i] = r0 + i * nwarp;
+      const bool ok = rr[i] < n;
+      if (ok) rmax = rr[i];
+      ur[i] = ok && upd ? u[rr[i]] : zero;
+      wr[i] = ok && upd ? w[rr[i]] : zero;
+      u2r[i] = ok ? u2[rr[i]] : zero;
+      acc[i] = zero;
+      if (!ok) rr[i] = -1;
+    }
+    for (int q = lo + lane; q <= rmax; q += 32) {
+      cx<T> v[RW];
+#pragma unroll
+      for (int i = 0; i < RW; ++i)
+        v[i] = q <= rr[i] ? A[(long long)rr[i] * n + q] : zero;
+      const cx<T> wq = upd ? w[q] : zero, uq = upd ? u[q] : zero, u2q = u2[q];
+      cx<T> tq = zero;
+#pragma unroll
+      for (int i = 0; i < RW; ++i) {
+        if (q > rr[i]) continue;
+        cx<T> x = v[i];
+        if (upd) {
+          x = x - T(2) * (ur[i] * conj(wq) + wr[i] * conj(uq));
+          if (q == rr[i]) x.im = T(0);
+          A[(long long)rr[i] * n + q] = x;
+        }
+        cfma(acc[i], x, u2q);
+        if (q < rr[i]) tq = tq + conj(x) * u2r[i];
+      }
+      acc_w[q] = acc_w[q] + tq;
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+      const cx<T> t = warp_csum(acc[i]);
+      // entry r belongs to lane (r - lo) mod 32 of this warp's array
+      if (rr[i] >= 0 && lane == ((rr[i] - lo) & 31)) acc_w[rr[i]] = acc_w[rr[i]] + t;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = lo + threadIdx.x; q < n; q += blockDim.x) {
+    cx<T> t(T(0), T(0));
+    for (int ww = 0; ww < nwarp; ++ww) t = t + pw[ww * n + q];
+    pa[q] = t;
+  }
+  __syncthreads();
+}
+
+// w = p - (u^dag p) u on lo..n-1 (p in pa).
+template <typename T>
+__device__ void lg_make_w(const cx<T>* u, const cx<T>* pa, cx<T>* w, int lo, int n, double* red) {
+  double kr = 0.0;
+  for (int r = lo + threadIdx.x; r < n; r += blockDim.x)
+    kr += double(u[r].re) * double(pa[r].re) + double(u[r].im) * double(pa[r].im);
+  kr = block_sum(kr, red);
+  for (int r = lo + threadIdx.x; r < n; r += blockDim.x) w[r] = pa[r] - T(kr) * u[r];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_lg_tridiag_h(LargeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  cx<T>* u = reinterpret_cast<cx<T>*>(smem);  // reflector of the current step
+  cx<T>* w = u + n;
+  cx<T>* u2 = w + n;                          // reflector of the next step
+  cx<T>* pa = u2 + n;                         // A u2
+  cx<T>* al = pa + n;                         // complex subdiagonal
+  cx<T>* pw = al + n;                         // (blockDim / 32) x n per-warp accumulators
+  double* red = reinterpret_cast<double*>(pw + (nt >> 5) * n);
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    cx<T>* A = reinterpret_cast<cx<T>*>(a.A) + kw * (long long)n * n;
+    T* dg = reinterpret_cast<T*>(a.dg) + kw * n;
+    T* od = reinterpret_cast<T*>(a.od) + kw * n;
+    cx<T>* Dp = reinterpret_cast<cx<T>*>(a.Dp) + kw * n;
+    // step 0: reflector of column 0 and p = A22 u
+    for (int r = 1 + tid; r < n; r += nt) u[r] = A[(long long)r * n];
+    __syncthreads();
+    cx<T> alpha = lg_reflector(u, 0, n, red);
+    if (tid == 0) {
+      al[0] = alpha;
+      dg[0] = A[0].re;
+    }
+    for (int r = 1 + tid; r < n; r += nt) A[(long long)r * n] = u[r];
+    __syncthreads();
+    lg_hpass<T>(A, n, 1, false, nullptr, nullptr, u, pw, pa);
+    lg_make_w(u, pa, w, 1, n, red);
+    for (int c = 0; c + 2 < n; ++c) {
+      // column c+1 of A - 2 (u w^dag + w u^dag), rows c+1..n-1
+      const cx<T> uc = u[c + 1], wc = w[c + 1];
+      for (int r = c + 1 + tid; r < n; r += nt)
+        u2[r] = A[(long long)r * n + c + 1] - T(2) * (u[r] * conj(wc) + w[r] * conj(uc));
+      __syncthreads();
+      if (tid == 0) dg[c + 1] = u2[c + 1].re;
+      if (c + 3 == n) {  // last 2 x 2 block: its subdiagonal and diagonal, no reflector
+        if (tid == 0) {
+          al[n - 2] = u2[n - 1];
+          const cx<T> un = u[n - 1], wn = w[n - 1];
+          dg[n - 1] = A[(long long)(n - 1) * n + n - 1].re - T(4) * (un.re * wn.re + un.im * wn.im);
+          A[(long long)(n - 1) * n + n - 2] = cx<T>(T(0), T(0));
+        }
+        __syncthreads();
+        break;
+      }
+      alpha = lg_reflector(u2, c + 1, n, red);
+      if (tid == 0) al[c + 1] = alpha;
+      for (int r = c + 2 + tid; r < n; r += nt) A[(long long)r * n + c + 1] = u2[r];
+      __syncthreads();
+      lg_hpass<T>(A, n, c + 2, true, u, w, u2, pw, pa);
+      lg_make_w(u2, pa, w, c + 2, n, red);
+      for (int r = c + 2 + tid; r < n; r += nt) u[r] = u2[r];
+      __syncthreads();
+    }
     // unit phases of the subdiagonal, then their prefix products (serial: cheap)
     for (int c = tid; c + 1 < n; c += nt) {
       const T aa = sqrt(abs2(al[c]));
@@ -513,7 +733,8 @@ __global__ void k_lg_refine(LargeArgs a) {
     const float* Z = reinterpret_cast<const float*>(a.Z) + kw * (long long)a.nvec * n;
     const float* lam = reinterpret_cast<const float*>(a.lam) + kw * a.nval;
     const c32* X = reinterpret_cast<const c32*>(a.X) + kw * (long long)n * nbt;
-    const z64* He = a.Hent + kw * (long long)md.n_ent;
+    const bool dense = a.Hin != nullptr;  // explicit matrix: entries r n + q, all columns
+    const z64* He = a.Hent + kw * (long long)(dense ? n * n : md.n_ent);
     z64* Q = a.U + kw * (long long)n * p;
     z64* R = a.R64 + kw * (long long)n * p;          // H Q, later FP32 scratch
     c32* C = a.C32 + kw * (long long)n * p;
@@ -523,9 +744,11 @@ __global__ void k_lg_refine(LargeArgs a) {
       for (int c0 = 0; c0 < p; c0 += 32) {
         const int c = c0 + lane;
         CDF acc;
-        for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) {
+        const int q0 = dense ? r * n : a.row_ptr[r], q1 = dense ? (r + 1) * n : a.row_ptr[r + 1];
+        for (int q = q0; q < q1; ++q) {
           const c32* hp = reinterpret_cast<const c32*>(He + q);
-          if (c < p) acc.add_prod(hp[0], hp[1], X[(long long)md.ent_col[q] * nbt + c]);
+          const int col = dense ? q - q0 : md.ent_col[q];
+          if (c < p) acc.add_prod(hp[0], hp[1], X[(long long)col * nbt + c]);
         }
         if (c < p) R[(long long)r * p + c] = acc.value();
       }
@@ -613,10 +836,11 @@ __global__ void k_lg_refine(LargeArgs a) {
         double num = 0.0, den = 0.0;
         for (int r = tid; r < n; r += nt) {
           z64 hv(0.0, 0.0);
-          for (int q = a.row_ptr[r]; q < a.row_ptr[r + 1]; ++q) {
+          const int q0 = dense ? r * n : a.row_ptr[r], q1 = dense ? (r + 1) * n : a.row_ptr[r + 1];
+          for (int q = q0; q < q1; ++q) {
             const c32* hp = reinterpret_cast<const c32*>(He + q);
             const z64 h(double(hp[0].re) + double(hp[1].re), double(hp[0].im) + double(hp[1].im));
-            cfma(hv, h, ccast<double>(X[(long long)md.ent_col[q] * nbt + col]));
+            cfma(hv, h, ccast<double>(X[(long long)(dense ? q - q0 : md.ent_col[q]) * nbt + col]));
           }
           const z64 v = ccast<double>(X[(long long)r * nbt + col]);
           num += v.re * hv.re + v.im * hv.im;
@@ -659,10 +883,29 @@ cudaError_t lg_common(const LargeArgs& a, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   lg_mark(a, "lg_build");
-  const size_t sm_tri = 3 * size_t(a.n) * sizeof(cx<T>) + 64 * sizeof(double);
-  static size_t cached = 0;
-  if ((e = set_smem_once(k_lg_tridiag<T>, sm_tri, cached)) != cudaSuccess) return e;
-  k_lg_tridiag<T><<<lg_grid(a.W), LG_THREADS, sm_tri, s>>>(a);
+  // lower-triangle kernel: 5 n + (warps) n complex values of shared memory, with up
+  // to 16 warps and at least 4; one CTA per SM keeps the matrices being reduced
+  // resident in L2 (n = 256: 152 x 512 KB in complex64)
+  const size_t vec_b = size_t(a.n) * sizeof(cx<T>), lim = size_t(200) << 10;
+  const size_t fixed = 5 * vec_b + 64 * sizeof(double);
+  // Each step waits on a few dependent L2 round trips, so several k-points per SM
+  // (more CTAs with fewer warps each) hide more latency than more warps on one
+  // k-point; a small wave gives each of its CTAs more warps instead.
+  const int fit = fixed < lim ? int(std::min<size_t>(16, (lim - fixed) / vec_b)) : 0;
+  const int want = a.W >= 4 * 152 ? 4 : (a.W >= 2 * 152 ? 8 : 16);
+  const int warps = std::min(fit, want);
+  if (warps >= 4) {
+    const size_t sm_h = fixed + size_t(warps) * vec_b;
+    static size_t cached_h = 0;
+    if ((e = set_smem_once(k_lg_tridiag_h<T>, sm_h, cached_h)) != cudaSuccess) return e;
+    const long long ctas = std::min<long long>(a.W, 152LL * (16 / warps));
+    k_lg_tridiag_h<T><<<int(ctas), 32 * warps, sm_h, s>>>(a);
+  } else {
+    const size_t sm_tri = 3 * size_t(a.n) * sizeof(cx<T>) + 64 * sizeof(double);
+    static size_t cached = 0;
+    if ((e = set_smem_once(k_lg_tridiag<T>, sm_tri, cached)) != cudaSuccess) return e;
+    k_lg_tridiag<T><<<lg_grid(a.W), LG_THREADS, sm_tri, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_tridiag");
   const long long nb = a.W * a.nval;
@@ -670,9 +913,11 @@ cudaError_t lg_common(const LargeArgs& a, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_bisect");
   const long long ni = a.W * a.nvec;
-  k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  lg_mark(a, "lg_invit");
+  if (ni > 0) {
+    k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lg_mark(a, "lg_invit");
+  }
   return cudaSuccess;
 }
 }  // namespace
@@ -682,6 +927,7 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   cudaError_t e;
   if (!a.mixed) {
     if ((e = lg_common<double>(a, s)) != cudaSuccess) return e;
+    if (a.p == 0) return cudaSuccess;  // values only
     const size_t sm = 2 * size_t(a.n > a.p ? a.n : a.p) * sizeof(z64);
     static size_t cached = 0;
     if ((e = set_smem_once(k_lg_backtransform<double, double>, sm, cached)) != cudaSuccess) return e;
@@ -689,12 +935,14 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
         a, a.U, (long long)a.n * a.p, a.p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lg_mark(a, "lg_backtransform");
+    if (a.Hin) return cudaSuccess;  // batched eigensolve: every eigenvalue is returned, no gap test
     k_lg_gap64<<<int((a.W + 127) / 128), 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lg_mark(a, "lg_gap");
     return cudaSuccess;
   }
   if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
+  if (a.no_refine) return cudaSuccess;
   const size_t sm = 2 * size_t(a.n > a.nbt ? a.n : a.nbt) * sizeof(c32);
   static size_t cached = 0;
   if ((e = set_smem_once(k_lg_backtransform<float, float>, sm, cached)) != cudaSuccess) return e;
@@ -709,6 +957,109 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_refine");
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Batched eigensolve of explicit matrices: FP64 Rayleigh-Ritz of the refined block
+// (mixed path, p <= 64) and the scatter of eigenvalues / eigenvectors to the
+// caller's packed layout.
+// ---------------------------------------------------------------------------
+__global__ void k_eigh_ritz(LargeArgs a, double* ritz) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  z64* G = reinterpret_cast<z64*>(smem);    // p x p
+  z64* V = G + p * p;                       // p x p
+  JacRot<double>* rot = reinterpret_cast<JacRot<double>*>(V + p * p);
+  double* red = reinterpret_cast<double*>(rot + (p / 2 + 2));
+  int* ord = reinterpret_cast<int*>(red + 64);
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    const c32* He = reinterpret_cast<const c32*>(a.Hent + kw * (long long)n * n);
+    z64* Q = a.U + kw * (long long)n * p;
+    z64* HQ = a.R64 + kw * (long long)n * p;
+    for (int r = warp; r < n; r += nwarp)  // H Q in FP64 (H from its float-pair split)
+      for (int c = lane; c < p; c += 32) {
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < n; ++q) {
+          const c32 hi = He[2 * ((long long)r * n + q)], lo = He[2 * ((long long)r * n + q) + 1];
+          cfma(acc, z64(double(hi.re) + double(lo.re), double(hi.im) + double(lo.im)), Q[(long long)q * p + c]);
+        }
+        HQ[(long long)r * p + c] = acc;
+      }
+    __syncthreads();
+    for (int e = tid; e < p * p; e += nt) {
+      const int x = e / p, y = e - x * p;
+      z64 acc(0.0, 0.0);
+      for (int r = 0; r < n; ++r) cfma_conj(acc, Q[(long long)r * p + x], HQ[(long long)r * p + y]);
+      G[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < p * p; e += nt) {  // Hermitian part
+      const int x = e / p, y = e - x * p;
+      if (x < y) {
+        const z64 h = 0.5 * (G[x * p + y] + conj(G[y * p + x]));
+        G[x * p + y] = h;
+        G[y * p + x] = conj(h);
+      } else if (x == y) {
+        G[e] = z64(G[e].re, 0.0);
+      }
+    }
+    __syncthreads();
+    const int sw = jacobi_eigh<double>(G, V, p, p, 40, rot, red);
+    if (sw < 0 && tid == 0) report(a.status, ST_ENOCONV, a.k0 + kw, 0.0);
+    sort_diag(G, p, p, ord);
+    for (int c = tid; c < p; c += nt) ritz[kw * p + c] = G[ord[c] * p + ord[c]].re;
+    // Q <- Q V (columns in ascending order), row by row through HQ as scratch
+    for (int r = warp; r < n; r += nwarp)
+      for (int c = lane; c < p; c += 32) {
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < p; ++q) cfma(acc, Q[(long long)r * p + q], V[q * p + ord[c]]);
+        HQ[(long long)r * p + c] = acc;
+      }
+    __syncthreads();
+    for (long long e = tid; e < (long long)n * p; e += nt) Q[e] = HQ[e];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_eigh_ritz(const LargeArgs& a, double* ritz, cudaStream_t s) {
+  if (a.W <= 0 || a.p <= 0) return cudaSuccess;
+  if (a.p > 64) return cudaErrorInvalidValue;
+  const size_t sm = 2 * size_t(a.p) * a.p * sizeof(z64) + (a.p / 2 + 2) * sizeof(JacRot<double>) +
+                    64 * sizeof(double) + size_t(a.p) * sizeof(int) + 16;
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_eigh_ritz, sm, cached);
+  if (e != cudaSuccess) return e;
+  k_eigh_ritz<<<lg_grid(a.W), LG_THREADS, sm, s>>>(a, ritz);
+  return cudaGetLastError();
+}
+
+__global__ void k_eigh_scatter(EighScatterArgs e) {
+  for (long long kw = blockIdx.x; kw < e.W; kw += gridDim.x) {
+    const int b = e.idx[e.k0 + kw];
+    double* ev = e.evals + e.e_off[b];
+    for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+      double v;
+      if (e.ritz && i < e.p)
+        v = e.ritz[kw * e.p + i];
+      else if (e.mixed)
+        v = double(reinterpret_cast<const float*>(e.lam)[kw * e.nval + i]);
+      else
+        v = reinterpret_cast<const double*>(e.lam)[kw * e.nval + i];
+      ev[i] = v;
+    }
+    if (e.evecs && e.p > 0) {
+      const z64* src = e.U + kw * (long long)e.n * e.p;
+      z64* dst = e.evecs + e.v_off[b];
+      for (long long x = threadIdx.x; x < (long long)e.n * e.p; x += blockDim.x) dst[x] = src[x];
+    }
+  }
+}
+
+cudaError_t launch_eigh_scatter(const EighScatterArgs& e, cudaStream_t s) {
+  if (e.W <= 0) return cudaSuccess;
+  k_eigh_scatter<<<lg_grid(e.W), 256, 0, s>>>(e);
+  return cudaGetLastError();
 }
 
 }  // namespace bw

@@ -129,7 +129,33 @@ struct LargeArgs {
   // optional host callback after each stage launch (per-stage timing)
   void (*mark)(void*, const char*);
   void* mark_user;
+  // explicit Hermitian matrices instead of a model (batched eigensolve): wave slot kw
+  // holds matrix idx[k0 + kw] at Hin + h_off[that] (lower triangle read); the
+  // refinement uses the dense matrix, and gap[k0 + kw] receives its gap
+  const z64* Hin;
+  const long long* h_off;
+  const int* idx;
+  int no_refine;          // mixed path without a block to refine (p = 0)
 };
+
+// Outputs of the batched eigensolve for one wave of the large path.
+struct EighScatterArgs {
+  const int* idx;         // wave slot -> matrix index (from idx + k0)
+  long long k0, W;
+  int n, nval, p, mixed;
+  const void* lam;        // W x nval (T)
+  const z64* U;           // W x n x p (refined / back-transformed block)
+  const double* ritz;     // W x p (mixed: FP64 Ritz values), or NULL
+  const long long* e_off;
+  const long long* v_off;
+  double* evals;
+  z64* evecs;             // NULL: values only
+};
+
+// FP64 Rayleigh-Ritz of the refined block of explicit matrices (p <= 64):
+// U <- U V, ritz = eigenvalues of U^dag H U (ascending).
+cudaError_t launch_eigh_ritz(const LargeArgs& a, double* ritz, cudaStream_t s);
+cudaError_t launch_eigh_scatter(const EighScatterArgs& e, cudaStream_t s);
 
 // Batched complex GEMM C_b = op(A_b) B_b (row-major; op(A) is A or A^dagger), m x n
 // result, inner dimension k; batch b uses A + b' sA, B + b sB, C + b sC, where b' = b,

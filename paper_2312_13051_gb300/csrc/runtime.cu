@@ -899,47 +899,173 @@ bw_status bw_eigh_batched(bw_ctx* ctx, const void* H, const int32_t* n_per, int6
   if (!H || !n_per || !evals) return fail(ctx, BW_EINVAL, "H, n_per or evals is NULL");
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision");
   if (n_vec < 0) return fail(ctx, BW_EINVAL, "n_vec < 0");
-  int n_max = 0;
+  const bool mx = prec == BW_MIXED;
+  int n_max_small = 0;
   std::vector<long long> ho(batch), eo(batch), vo(batch);
+  std::vector<long long> ho_s, eo_s, vo_s;
+  std::vector<int> np_s, large_idx;
   long long h = 0, ev = 0, vv = 0;
   for (int64_t b = 0; b < batch; ++b) {
     const int n = n_per[b];
-    if (n < 1 || n > bw::SMALL_N_MAX)
-      return fail(ctx, BW_EINVAL, "matrix %lld has n = %d outside [1, %d]", (long long)b, n, bw::SMALL_N_MAX);
+    if (n < 1 || n > bw::LARGE_N_MAX)
+      return fail(ctx, BW_EINVAL, "matrix %lld has n = %d outside [1, %d]", (long long)b, n, bw::LARGE_N_MAX);
     if (n_vec > n) return fail(ctx, BW_EINVAL, "n_vec = %d exceeds n = %d of matrix %lld", n_vec, n, (long long)b);
-    n_max = std::max(n_max, n);
+    if (n > bw::SMALL_N_MAX && mx && n_vec > 0 && (n_vec >= n || n_vec > 64))
+      return fail(ctx, BW_EINVAL, "mixed precision for n > %d needs n_vec < n and n_vec <= 64 "
+                  "(matrix %lld: n = %d, n_vec = %d)", bw::SMALL_N_MAX, (long long)b, n, n_vec);
     ho[b] = h;
     eo[b] = ev;
     vo[b] = vv;
+    if (n <= bw::SMALL_N_MAX) {
+      n_max_small = std::max(n_max_small, n);
+      ho_s.push_back(h);
+      eo_s.push_back(ev);
+      vo_s.push_back(vv);
+      np_s.push_back(n);
+    } else {
+      large_idx.push_back(int(b));
+    }
     h += (long long)n * n;
     ev += n;
     vv += (long long)n * n_vec;
   }
-  std::vector<int> np(n_per, n_per + batch);
+  // large matrices grouped by size (one solver configuration per size)
+  std::stable_sort(large_idx.begin(), large_idx.end(),
+                   [&](int x, int y) { return n_per[x] < n_per[y]; });
   Blob blob;
-  const size_t o_h = blob.add(ho), o_e = blob.add(eo), o_v = blob.add(vo), o_n = blob.add(np);
+  const size_t o_h = blob.add(ho_s), o_e = blob.add(eo_s), o_v = blob.add(vo_s), o_n = blob.add(np_s);
+  const size_t o_ha = blob.add(ho), o_ea = blob.add(eo), o_va = blob.add(vo), o_li = blob.add(large_idx);
+  // scratch of the largest group's wave
+  struct Group { int n, first, count; };
+  std::vector<Group> groups;
+  for (size_t g = 0; g < large_idx.size();) {
+    size_t e = g;
+    while (e < large_idx.size() && n_per[large_idx[e]] == n_per[large_idx[g]]) ++e;
+    groups.push_back({n_per[large_idx[g]], int(g), int(e - g)});
+    g = e;
+  }
+  auto per_k_bytes = [&](int n) {
+    const int p = n_vec;
+    const bool refine = mx && p > 0;
+    const size_t ts = mx ? sizeof(float) : sizeof(double);
+    const int nval = n, nvec = mx ? (refine ? n : 0) : p, nbt = refine ? p + 1 : p;
+    size_t b = al256(size_t(n) * n * 2 * ts) + 2 * al256(size_t(n) * ts) + al256(size_t(n) * 2 * ts) +
+               al256(size_t(nval) * ts) + al256(size_t(nvec) * n * ts) + al256(size_t(nvec) * 6 * n * ts);
+    if (refine)
+      b += al256(size_t(n) * nbt * sizeof(bw::c32)) + al256(size_t(n) * n * sizeof(z64)) +
+           al256(size_t(n) * p * sizeof(z64)) + al256(size_t(n) * p * sizeof(bw::c32)) +
+           al256(size_t(p) * p * sizeof(z64));
+    b += al256(size_t(n) * std::max(p, 1) * sizeof(z64)) + al256(sizeof(double)) +
+         al256(size_t(std::max(p, 1)) * sizeof(double));
+    return b;
+  };
+  const size_t fixed = al256(blob.data.size()) + 4096;
+  long long Wv = 0;
+  size_t wave_bytes = 0;
+  for (const Group& g : groups) {
+    const size_t pk = per_k_bytes(g.n);
+    const size_t avail = ctx->budget > fixed ? (ctx->budget - fixed) / 2 : 0;
+    long long w = std::min<long long>(g.count, std::min<long long>(2048, (long long)(avail / pk)));
+    w = std::max<long long>(w, 1);
+    Wv = std::max(Wv, w);
+    wave_bytes = std::max(wave_bytes, size_t(w) * (pk + 24 * 256));
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   begin_call(ctx, s);
   bw_status st;
-  if ((st = reserve(ctx, al256(blob.data.size()) + 4096, s))) return st;
+  if ((st = reserve(ctx, fixed + wave_bytes, s))) return st;
   char* d = carve(ctx, blob.data.size());
   if ((st = upload(ctx, blob, d, s))) return st;
-  bw::EighArgs a;
-  a.H = static_cast<const z64*>(H);
-  a.h_off = reinterpret_cast<const long long*>(d + o_h);
-  a.e_off = reinterpret_cast<const long long*>(d + o_e);
-  a.v_off = reinterpret_cast<const long long*>(d + o_v);
-  a.n_per = reinterpret_cast<const int*>(d + o_n);
-  a.batch = batch;
-  a.n_vec = n_vec;
-  a.mixed = prec == BW_MIXED;
-  a.max_sweeps = 30;
-  a.evals = evals;
-  a.evecs = static_cast<z64*>(evecs);
-  a.status = ctx->status;
   prof_start(ctx, s);
-  BW_CUDA(bw::launch_eigh_small(a, n_max, s), "eigh kernel");
-  prof_mark(ctx, s, "eigh");
+  if (!np_s.empty()) {
+    bw::EighArgs a;
+    a.H = static_cast<const z64*>(H);
+    a.h_off = reinterpret_cast<const long long*>(d + o_h);
+    a.e_off = reinterpret_cast<const long long*>(d + o_e);
+    a.v_off = reinterpret_cast<const long long*>(d + o_v);
+    a.n_per = reinterpret_cast<const int*>(d + o_n);
+    a.batch = (long long)np_s.size();
+    a.n_vec = n_vec;
+    a.mixed = mx;
+    a.max_sweeps = 30;
+    a.evals = evals;
+    a.evecs = static_cast<z64*>(evecs);
+    a.status = ctx->status;
+    BW_CUDA(bw::launch_eigh_small(a, n_max_small, s), "eigh kernel");
+    prof_mark(ctx, s, "eigh");
+  }
+  const size_t mark = ctx->arena_off;
+  for (const Group& g : groups) {
+    ctx->arena_off = mark;
+    const int n = g.n, p = n_vec;
+    const bool refine = mx && p > 0;
+    const size_t ts = mx ? sizeof(float) : sizeof(double);
+    const size_t pk = per_k_bytes(n);
+    const size_t avail = ctx->budget > fixed ? (ctx->budget - fixed) / 2 : 0;
+    const long long W = std::max<long long>(1, std::min<long long>(g.count, std::min<long long>(2048, (long long)(avail / pk))));
+    bw::LargeArgs lg;
+    std::memset(&lg, 0, sizeof(lg));
+    lg.model.n = n;
+    lg.n = n;
+    lg.p = p;
+    lg.nval = n;
+    lg.nvec = mx ? (refine ? n : 0) : p;
+    lg.nbt = refine ? p + 1 : p;
+    lg.mixed = mx;
+    lg.no_refine = mx && !refine;
+    lg.gap_tol = 0.0;
+    lg.status = ctx->status;
+    lg.Hin = static_cast<const z64*>(H);
+    lg.h_off = reinterpret_cast<const long long*>(d + o_ha);
+    lg.idx = reinterpret_cast<const int*>(d + o_li);
+    lg.A = carve(ctx, W * al256(size_t(n) * n * 2 * ts));
+    lg.dg = carve(ctx, W * al256(size_t(n) * ts));
+    lg.od = carve(ctx, W * al256(size_t(n) * ts));
+    lg.Dp = carve(ctx, W * al256(size_t(n) * 2 * ts));
+    lg.lam = carve(ctx, W * al256(size_t(n) * ts));
+    lg.Z = carve(ctx, W * al256(size_t(lg.nvec) * n * ts));
+    lg.work = carve(ctx, W * al256(size_t(lg.nvec) * 6 * n * ts));
+    if (refine) {
+      lg.X = carve(ctx, W * al256(size_t(n) * lg.nbt * sizeof(bw::c32)));
+      lg.Hent = reinterpret_cast<z64*>(carve(ctx, W * al256(size_t(n) * n * sizeof(z64))));
+      lg.R64 = reinterpret_cast<z64*>(carve(ctx, W * al256(size_t(n) * p * sizeof(z64))));
+      lg.C32 = reinterpret_cast<bw::c32*>(carve(ctx, W * al256(size_t(n) * p * sizeof(bw::c32))));
+      lg.G64 = reinterpret_cast<z64*>(carve(ctx, W * al256(size_t(p) * p * sizeof(z64))));
+    }
+    lg.U = reinterpret_cast<z64*>(carve(ctx, W * al256(size_t(n) * std::max(p, 1) * sizeof(z64))));
+    // the refinement's gap test uses gap[k0 + kw]: one slot per matrix of the group
+    lg.gap = reinterpret_cast<double*>(carve(ctx, size_t(large_idx.size()) * sizeof(double)));
+    double* ritz = reinterpret_cast<double*>(carve(ctx, W * al256(size_t(std::max(p, 1)) * sizeof(double))));
+    MarkHook hook{ctx, s};
+    lg.mark = mark_hook;
+    lg.mark_user = &hook;
+    for (long long w0 = 0; w0 < g.count; w0 += W) {
+      lg.k0 = g.first + w0;
+      lg.W = std::min<long long>(W, g.count - w0);
+      BW_CUDA(bw::launch_states_large(lg, s), "large-n eigensolver kernels");
+      if (refine) {
+        BW_CUDA(bw::launch_eigh_ritz(lg, ritz, s), "Rayleigh-Ritz kernel");
+        prof_mark(ctx, s, "eigh_ritz");
+      }
+      bw::EighScatterArgs e;
+      e.idx = lg.idx;
+      e.k0 = lg.k0;
+      e.W = lg.W;
+      e.n = n;
+      e.nval = n;
+      e.p = p;
+      e.mixed = mx;
+      e.lam = lg.lam;
+      e.U = lg.U;
+      e.ritz = refine ? ritz : nullptr;
+      e.e_off = reinterpret_cast<const long long*>(d + o_ea);
+      e.v_off = reinterpret_cast<const long long*>(d + o_va);
+      e.evals = evals;
+      e.evecs = static_cast<z64*>(evecs);
+      BW_CUDA(bw::launch_eigh_scatter(e, s), "eigh scatter kernel");
+      prof_mark(ctx, s, "eigh_scatter");
+    }
+  }
   end_call(ctx, s);
   return BW_OK;
 }

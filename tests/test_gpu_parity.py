@@ -332,3 +332,39 @@ def test_many_band_blocks_of_loops(lib):
     finally:
         big.close()
         small.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n_vec", [0, 3])
+def test_eigh_batched_large_ragged(lib, ctx, precision, n_vec):
+    """Uneven sizes across the shared-memory (n <= 32) and tridiagonal (n > 32) solvers
+    in one batch; the upper triangle of the large matrices is garbage (only the lower
+    one is read)."""
+    torch = _torch()
+    sizes = [5, 40, 33, 64, 40, 100, 7, 129]
+    mats = I.random_hermitian_batch(sizes, seed=17)
+    packed = []
+    for A, n in zip(mats, sizes):
+        B = A.copy()
+        if n > 32:
+            B[np.triu_indices(n, 1)] = 7.0 + 3.0j
+        packed.append(B.reshape(-1))
+    H = torch.tensor(np.concatenate(packed), device="cuda")
+    ev, vec = lib.eigh_batched(H, sizes, n_vec, precision=precision, ctx=ctx)
+    ev = ev.cpu().numpy()
+    vec = vec.cpu().numpy() if vec is not None else None
+    eo = vo = 0
+    for A, n in zip(mats, sizes):
+        ref = np.linalg.eigvalsh(A)
+        got = ev[eo:eo + n]
+        scale = max(1.0, np.abs(ref).max())
+        tol_v = 1e-12 if precision == "fp64" else 2e-5
+        assert np.abs(got - ref).max() <= tol_v * scale, (n, np.abs(got - ref).max())
+        assert np.abs(got[:n_vec] - ref[:n_vec]).max(initial=0) <= 1e-12 * scale
+        if n_vec:
+            V = vec[vo:vo + n * n_vec].reshape(n, n_vec)
+            res = A @ V - V * got[:n_vec]
+            assert np.abs(res).max() <= 1e-11 * scale, (n, np.abs(res).max())
+            assert np.abs(V.conj().T @ V - np.eye(n_vec)).max() <= 1e-12
+        eo += n
+        vo += n * n_vec
