@@ -95,6 +95,7 @@ struct DevModel {
   const int* ent_start;  // n_ent + 1
   const int* hop_r;      // translation id per hopping (sorted by entry)
   const z64* hop_t;
+  const float* hop_tdf;  // hop_t as double-float pairs: (re hi, re lo, im hi, im lo)
 };
 
 // Sparse operator (spin operator): entries (row, col, value).

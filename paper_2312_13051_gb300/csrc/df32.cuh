@@ -1,0 +1,110 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits (unit roundoff ~ 2^-47), computed
+// on the FP32 pipe.  Built from error-free transformations: Knuth's TwoSum and
+// Dekker's FastTwoSum for sums, the exact product a b = p + fma(a, b, -p) for
+// products (Dekker 1971, "A floating-point technique for extending the available
+// precision"), and one Newton correction of the float quotient / square root.
+//
+// GB300 runs FP32 about 70x faster than FP64; where the mixed path needs FP64-grade
+// accuracy (the refinement residual) on data that fits the float exponent range,
+// these operations take the FP32 pipe instead of the FP64 one.
+#pragma once
+
+#include "common.cuh"
+
+namespace bw {
+
+struct df {
+  float hi, lo;
+  __host__ __device__ df() = default;
+  __host__ __device__ constexpr df(float h, float l = 0.f) : hi(h), lo(l) {}
+};
+
+// s + e = a + b exactly (any magnitudes).
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return df(s, e);
+}
+
+// s + e = a + b exactly when |a| >= |b| (or a = 0).
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return df(s, b - (s - a));
+}
+
+__device__ __forceinline__ df df_from_double(double x) {
+  const float h = float(x);
+  return df(h, float(x - double(h)));
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return double(x.hi) + double(x.lo); }
+
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+
+// Accurate sum: both parts through TwoSum, then renormalised.
+__device__ __forceinline__ df operator+(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  const df t = df_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df operator*(float a, df b) {
+  const float p = a * b.hi;
+  float e = fmaf(a, b.hi, -p);
+  e = fmaf(a, b.lo, e);
+  return df_fast_two_sum(p, e);
+}
+
+// q = a / b: float quotient, corrected once from the double-float remainder.
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q0 = a.hi / b.hi;
+  const df r = a - q0 * b;
+  const float q1 = r.hi / b.hi;
+  return df_fast_two_sum(q0, q1);
+}
+
+// sqrt(a), a >= 0: float root, corrected once (Newton step on s^2 = a).
+__device__ __forceinline__ df df_sqrt(df a) {
+  if (!(a.hi > 0.f)) return df(0.f, 0.f);
+  const float s0 = sqrtf(a.hi);
+  const float p = s0 * s0;
+  const df r = a - df(p, fmaf(s0, s0, -p));  // a - s0^2, s0^2 exact
+  const float s1 = r.hi / (2.f * s0);
+  return df_fast_two_sum(s0, s1);
+}
+
+// Complex double-float.
+struct cdf {
+  df re, im;
+  __host__ __device__ cdf() = default;
+  __host__ __device__ constexpr cdf(df r, df i) : re(r), im(i) {}
+};
+
+__device__ __forceinline__ cdf cdf_from(z64 z) { return cdf(df_from_double(z.re), df_from_double(z.im)); }
+__device__ __forceinline__ cdf cdf_from(c32 z) { return cdf(df(z.re), df(z.im)); }
+__device__ __forceinline__ z64 cdf_to_z64(cdf z) { return z64(df_to_double(z.re), df_to_double(z.im)); }
+__device__ __forceinline__ cdf conj(cdf a) { return cdf(a.re, -a.im); }
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return cdf(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cdf operator*(cdf a, cdf b) {
+  return cdf(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ cdf operator*(df s, cdf b) { return cdf(s * b.re, s * b.im); }
+// |a|^2
+__device__ __forceinline__ df abs2(cdf a) { return a.re * a.re + a.im * a.im; }
+
+}  // namespace bw

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 
+#include "df32.cuh"
 #include "jacobi.cuh"
 #include "launch.h"
 
@@ -134,9 +135,31 @@ __global__ void k_lg_build(LargeArgs a) {
     const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     double f[3];
     lg_kpoint(a, k, f);
-    for (int r = tid; r < nRs; r += nt) phs[r] = bloch_phase(f, md.Rv + 3 * r);
     cx<T>* A = reinterpret_cast<cx<T>*>(a.A) + kw * (long long)n * n;
     for (long long e = tid; e < (long long)n * n; e += nt) A[e] = cx<T>(T(0), T(0));
+    if (a.Hent && md.hop_tdf) {
+      // mixed path: entries in double-float on the FP32 pipe (FP64-grade for the
+      // refinement's residual, the FP32 matrix is the high part)
+      cdf* phd = reinterpret_cast<cdf*>(phs);
+      for (int r = tid; r < nRs; r += nt) phd[r] = cdf_from(bloch_phase(f, md.Rv + 3 * r));
+      __syncthreads();
+      for (int e = tid; e < md.n_ent; e += nt) {
+        cdf acc(df(0.f), df(0.f));
+        for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h) {
+          const int r = md.hop_r[h];
+          const float* t4 = md.hop_tdf + 4 * h;
+          acc = acc + cdf(df(t4[0], t4[1]), df(t4[2], t4[3])) *
+                          (r < nRs ? phd[r] : cdf_from(bloch_phase(f, md.Rv + 3 * r)));
+        }
+        A[(long long)md.ent_row[e] * n + md.ent_col[e]] = cx<T>(T(acc.re.hi), T(acc.im.hi));
+        c32* dst = reinterpret_cast<c32*>(a.Hent + kw * (long long)md.n_ent + e);
+        dst[0] = c32(acc.re.hi, acc.im.hi);
+        dst[1] = c32(acc.re.lo, acc.im.lo);
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int r = tid; r < nRs; r += nt) phs[r] = bloch_phase(f, md.Rv + 3 * r);
     __syncthreads();
     for (int e = tid; e < md.n_ent; e += nt) {
       z64 acc(0.0, 0.0);

@@ -95,7 +95,7 @@ struct HostPlan {
   std::vector<int> Rv, ent_row, ent_col, ent_start, hop_r, row_ptr;
   std::vector<z64> hop_t;
   double tmax = 0.0;
-  size_t o_Rv, o_row, o_col, o_start, o_r, o_t, o_rowptr;
+  size_t o_Rv, o_row, o_col, o_start, o_r, o_t, o_tdf, o_rowptr;
 };
 
 bw_status make_plan(bw_ctx* ctx, const bw_model* m, HostPlan& P) {
@@ -196,6 +196,16 @@ void plan_to_blob(HostPlan& P, Blob& b) {
   P.o_start = b.add(P.ent_start);
   P.o_r = b.add(P.hop_r);
   P.o_t = b.add(P.hop_t);
+  std::vector<float> tdf(4 * P.hop_t.size());
+  for (size_t h = 0; h < P.hop_t.size(); ++h) {
+    const double v[2] = {P.hop_t[h].re, P.hop_t[h].im};
+    for (int c = 0; c < 2; ++c) {
+      const float hi = float(v[c]);
+      tdf[4 * h + 2 * c] = hi;
+      tdf[4 * h + 2 * c + 1] = float(v[c] - double(hi));
+    }
+  }
+  P.o_tdf = b.add(tdf);
   P.o_rowptr = b.add(P.row_ptr);
 }
 
@@ -210,6 +220,7 @@ bw::DevModel dev_model(const HostPlan& P, const char* base) {
   d.ent_start = reinterpret_cast<const int*>(base + P.o_start);
   d.hop_r = reinterpret_cast<const int*>(base + P.o_r);
   d.hop_t = reinterpret_cast<const z64*>(base + P.o_t);
+  d.hop_tdf = reinterpret_cast<const float*>(base + P.o_tdf);
   return d;
 }
 

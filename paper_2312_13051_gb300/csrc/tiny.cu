@@ -1,6 +1,6 @@
 // One thread per k-point for few-band models (n = 2 or 4): Bloch Hamiltonian,
-// exact diagonalisation, optional FP64 refinement and projected-spin sector, all
-// in registers (Sec. I "exact diagonalization", Eq. 1, Sec. IV).
+// exact diagonalisation in FP64 and projected-spin sector, all in registers
+// (Sec. I "exact diagonalization", Eq. 1, Sec. IV).
 //
 // GB300's FP64 pipe serves a whole warp instruction at a time, so a kernel that
 // gives one small matrix to a CTA pays for 32 lanes and uses a few.  Here every
@@ -9,7 +9,7 @@
 // tables: with an integer loop direction and an integer transverse direction,
 // f(j, i).R = origin.R + j (loop.R) / N + i (trans.R) / N_t, so
 // exp(i 2pi f.R) = exp(i 2pi origin.R) w_N^{(j loop.R) mod N} w_Nt^{(i trans.R) mod N_t}
-// with w_M = exp(i 2pi / M) tabulated once per CTA.
+// with w_M = exp(i 2pi / M) tabulated once per CTA (in two levels for long grids).
 #include <float.h>
 
 #include "launch.h"
@@ -112,101 +112,60 @@ __device__ __forceinline__ void sort_eig(const cx<T> (&A)[NN][NN], const cx<T> (
   }
 }
 
-// One Cholesky-QR pass on the columns of Q (NN x PP) in FP64; false on breakdown.
-template <int NN, int PP>
-__device__ __forceinline__ bool cholqr_serial(z64 (&Q)[NN][PP]) {
-  z64 L[PP][PP];
-#pragma unroll
-  for (int a = 0; a < PP; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      z64 g(0.0, 0.0);
-#pragma unroll
-      for (int r = 0; r < NN; ++r) cfma_conj(g, Q[r][b], Q[r][a]);  // G[a][b] = q_b^dag q_a ... conj
-      L[a][b] = conj(g);                                            // G[a][b] = q_a^dag q_b
-    }
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < PP; ++j) {
-    double d = L[j][j].re;
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= abs2(L[j][k]);
-    ok = ok && (d > 0.0);
-    d = sqrt(fmax(d, 1e-300));
-    L[j][j] = z64(d, 0.0);
-#pragma unroll
-    for (int i = j + 1; i < PP; ++i) {
-      z64 s = L[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s = s - L[i][k] * conj(L[j][k]);
-      L[i][j] = (1.0 / d) * s;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NN; ++r) {
-    // row x of the new Q solves x L^dagger = q: L y = q^dagger, x = y^dagger
-    z64 y[PP];
-#pragma unroll
-    for (int j = 0; j < PP; ++j) {
-      z64 v = conj(Q[r][j]);
-#pragma unroll
-      for (int k = 0; k < j; ++k) v = v - L[j][k] * y[k];
-      y[j] = (1.0 / L[j][j].re) * v;
-    }
-#pragma unroll
-    for (int j = 0; j < PP; ++j) Q[r][j] = conj(y[j]);
-  }
-  return ok;
-}
-
-
 constexpr int TINY_THREADS = 32;
+// Above this many points a direction's phase table is split in two levels
+// (w^m = w^{B (m / B)} w^{m mod B}, B ~ sqrt(M)), so that long grids keep the
+// shared memory per CTA small.
+constexpr int TAB_SPLIT = 512;
 
 __device__ __forceinline__ int pmod(long long x, int m) {
   long long r = x % m;
   return int(r < 0 ? r + m : r);
 }
 
-// FP64 Rayleigh quotient v^dagger H v / v^dagger v of an FP32 vector.
-template <int NN>
-__device__ __forceinline__ double rq(const z64 (&H)[NN][NN], const c32 (&V)[NN][NN], int col) {
-  double num = 0.0, den = 0.0;
-#pragma unroll
-  for (int r = 0; r < NN; ++r) {
-    z64 hv(0.0, 0.0);
-#pragma unroll
-    for (int c = 0; c < NN; ++c) cfma(hv, H[r][c], ccast<double>(V[c][col]));
-    const z64 v = ccast<double>(V[r][col]);
-    num += v.re * hv.re + v.im * hv.im;
-    den += abs2(v);
-  }
-  return num / den;
+struct TabShape {
+  int B, H;  // low-level entries (w^0 .. w^{B-1}), high-level entries (w^{0}, w^{B}, ...)
+};
+
+__host__ __device__ inline TabShape tab_shape(int M) {
+  if (M <= TAB_SPLIT) return {M, 0};
+  int B = 1;
+  while (B * B < M) ++B;
+  return {B, (M + B - 1) / B};
 }
 
-template <int NN, int PP, bool MIXED>
+// Fills lo[0..B) and hi[0..H) with exp(i 2pi m / M).
+__device__ void fill_tab(z64* lo, z64* hi, int M, TabShape t) {
+  for (int m = threadIdx.x; m < t.B + t.H; m += blockDim.x) {
+    const long long e = m < t.B ? m : (long long)(m - t.B) * t.B;
+    double sn, cs;
+    sincospi(2.0 * double(e) / double(M), &sn, &cs);
+    *(m < t.B ? lo + m : hi + (m - t.B)) = z64(cs, sn);
+  }
+}
+
+__device__ __forceinline__ z64 tab_at(const z64* lo, const z64* hi, TabShape t, int m) {
+  if (t.H == 0) return lo[m];
+  return hi[m / t.B] * lo[m % t.B];
+}
+
+template <int NN, int PP>
 __global__ void __launch_bounds__(TINY_THREADS)
 k_states_tiny(StatesArgs a, int use_tab) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevModel& md = a.model;
   const int tid = threadIdx.x, bd = blockDim.x, nR = md.n_R;
   const int N = a.plane.N, Nt = a.plane.N_t;
+  const TabShape tN = tab_shape(N), tT = tab_shape(Nt);
   z64* cache = reinterpret_cast<z64*>(smem);             // nR x bd
-  z64* tabN = cache + nR * bd;                             // N
-  z64* tabNt = tabN + (use_tab ? N : 0);                   // N_t
-  z64* oph = tabNt + (use_tab ? Nt : 0);                   // nR
+  z64* tabN = cache + nR * bd;                             // tN.B + tN.H
+  z64* tabNt = tabN + (use_tab ? tN.B + tN.H : 0);         // tT.B + tT.H
+  z64* oph = tabNt + (use_tab ? tT.B + tT.H : 0);          // nR
   int* lR = reinterpret_cast<int*>(oph + (use_tab ? nR : 0));
   int* tR = lR + (use_tab ? nR : 0);
   if (use_tab) {
-    for (int m = tid; m < N; m += bd) {
-      double s, c;
-      sincospi(2.0 * double(m) / double(N), &s, &c);
-      tabN[m] = z64(c, s);
-    }
-    for (int m = tid; m < Nt; m += bd) {
-      double s, c;
-      sincospi(2.0 * double(m) / double(Nt), &s, &c);
-      tabNt[m] = z64(c, s);
-    }
+    fill_tab(tabN, tabN + tN.B, N, tN);
+    fill_tab(tabNt, tabNt + tT.B, Nt, tT);
     for (int r = tid; r < nR; r += bd) {
       const int* R = md.Rv + 3 * r;
       double x = 0.0;
@@ -216,9 +175,9 @@ k_states_tiny(StatesArgs a, int use_tab) {
         l += int(a.plane.loop_dir[d]) * R[d];
         t += int(a.plane.trans_dir[d]) * R[d];
       }
-      double s, c;
-      sincospi(2.0 * x, &s, &c);
-      oph[r] = z64(c, s);
+      double sn, cs;
+      sincospi(2.0 * x, &sn, &cs);
+      oph[r] = z64(cs, sn);
       lR[r] = l;
       tR[r] = t;
     }
@@ -229,9 +188,10 @@ k_states_tiny(StatesArgs a, int use_tab) {
   const int i = int(k / N), j = int(k - (long long)i * N);
   // Bloch phases of the distinct translations at this k-point
   if (use_tab) {
-    for (int r = 0; r < nR; ++r)
-      cache[r * bd + tid] = oph[r] * tabN[pmod((long long)j * lR[r], N)] *
-                            tabNt[pmod((long long)i * tR[r], Nt)];
+    for (int r = 0; r < nR; ++r) {
+      const int mN = pmod((long long)j * lR[r], N), mT = pmod((long long)i * tR[r], Nt);
+      cache[r * bd + tid] = oph[r] * tab_at(tabN, tabN + tN.B, tN, mN) * tab_at(tabNt, tabNt + tT.B, tT, mT);
+    }
   } else {
     double f[3];
     if (a.f) {
@@ -241,83 +201,29 @@ k_states_tiny(StatesArgs a, int use_tab) {
     }
     for (int r = 0; r < nR; ++r) cache[r * bd + tid] = bloch_phase(f, md.Rv + 3 * r);
   }
-  // H(k) in FP64 registers
-  z64 H[NN][NN];
-#pragma unroll
-  for (int r = 0; r < NN; ++r)
-#pragma unroll
-    for (int c = 0; c < NN; ++c) H[r][c] = z64(0.0, 0.0);
-  for (int e = 0; e < md.n_ent; ++e) {
-    z64 acc(0.0, 0.0);
-    for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h)
-      cfma(acc, md.hop_t[h], cache[md.hop_r[h] * bd + tid]);
-    const int row = md.ent_row[e], col = md.ent_col[e];
-#pragma unroll
-    for (int r = 0; r < NN; ++r)
-#pragma unroll
-      for (int c = 0; c < NN; ++c)
-        if (row == r && col == c) H[r][c] = acc;
-  }
   z64 Q[NN][PP];
   double gap = INFINITY;
   bool ok = true;
-  if (MIXED) {
-    c32 A[NN][NN], V[NN][NN], Vs[NN][NN];
-    float lam[NN];
+  {
+    // H(k) in FP64.  The mixed-precision request takes this FP64 solve as well: at
+    // n <= 4 one thread's FP64 Jacobi costs no more than an FP32 solve plus the
+    // FP64-grade refinement of its occupied block (measured), at full accuracy.
+    z64 H[NN][NN];
 #pragma unroll
     for (int r = 0; r < NN; ++r)
 #pragma unroll
-      for (int c = 0; c < NN; ++c) A[r][c] = ccast<float>(H[r][c]);
-    ok = jac_serial<NN, float>(A, V, a.max_sweeps) >= 0;
-    sort_eig<NN, float>(A, V, Vs, lam);
-#pragma unroll
-    for (int r = 0; r < NN; ++r)
-#pragma unroll
-      for (int c = 0; c < PP; ++c) Q[r][c] = ccast<double>(Vs[r][c]);
-    ok = cholqr_serial<NN, PP>(Q) && ok;
-    if (PP < NN) {
-      // one Newton correction from the FP32 eigenbasis (see the block refinement)
-      z64 HQ[NN][PP], G[PP][PP];
+      for (int c = 0; c < NN; ++c) H[r][c] = z64(0.0, 0.0);
+    for (int e = 0; e < md.n_ent; ++e) {
+      z64 acc(0.0, 0.0);
+      for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h)
+        cfma(acc, md.hop_t[h], cache[md.hop_r[h] * bd + tid]);
+      const int row = md.ent_row[e], col = md.ent_col[e];
 #pragma unroll
       for (int r = 0; r < NN; ++r)
 #pragma unroll
-        for (int c = 0; c < PP; ++c) {
-          z64 acc(0.0, 0.0);
-#pragma unroll
-          for (int q = 0; q < NN; ++q) cfma(acc, H[r][q], Q[q][c]);
-          HQ[r][c] = acc;
-        }
-#pragma unroll
-      for (int x = 0; x < PP; ++x)
-#pragma unroll
-        for (int y = 0; y < PP; ++y) {
-          z64 acc(0.0, 0.0);
-#pragma unroll
-          for (int r = 0; r < NN; ++r) cfma_conj(acc, Q[r][x], HQ[r][y]);
-          G[x][y] = acc;
-        }
-#pragma unroll
-      for (int r = 0; r < NN; ++r)
-#pragma unroll
-        for (int c = 0; c < PP; ++c) {
-#pragma unroll
-          for (int q = 0; q < PP; ++q) HQ[r][c] = HQ[r][c] - Q[r][q] * G[q][c];
-        }
-#pragma unroll
-      for (int u = PP; u < NN; ++u)
-#pragma unroll
-        for (int c = 0; c < PP; ++c) {
-          z64 acc(0.0, 0.0);
-#pragma unroll
-          for (int r = 0; r < NN; ++r) cfma_conj(acc, ccast<double>(Vs[r][u]), HQ[r][c]);
-          acc = (1.0 / (G[c][c].re - double(lam[u]))) * acc;
-#pragma unroll
-          for (int r = 0; r < NN; ++r) cfma(Q[r][c], ccast<double>(Vs[r][u]), acc);
-        }
-      ok = cholqr_serial<NN, PP>(Q) && ok;
-      gap = rq<NN>(H, Vs, PP) - rq<NN>(H, Vs, PP - 1);
+        for (int c = 0; c < NN; ++c)
+          if (row == r && col == c) H[r][c] = acc;
     }
-  } else {
     z64 A[NN][NN], V[NN][NN], Vs[NN][NN];
     double lam[NN];
 #pragma unroll
@@ -412,20 +318,14 @@ k_states_tiny(StatesArgs a, int use_tab) {
   }
 }
 
-template <int NN, int PP, bool MIXED>
-cudaError_t tiny_launch(const StatesArgs& a, int use_tab, size_t smem, cudaStream_t s) {
-  static size_t cached = 0;
-  cudaError_t e = set_smem_once(k_states_tiny<NN, PP, MIXED>, smem, cached);
-  if (e != cudaSuccess) return e;
-  const long long blocks = (a.K + TINY_THREADS - 1) / TINY_THREADS;
-  k_states_tiny<NN, PP, MIXED><<<int(blocks), TINY_THREADS, smem, s>>>(a, use_tab);
-  return cudaGetLastError();
-}
-
 template <int NN, int PP>
 cudaError_t tiny_prec(const StatesArgs& a, int use_tab, size_t smem, cudaStream_t s) {
-  return a.mixed ? tiny_launch<NN, PP, true>(a, use_tab, smem, s)
-                 : tiny_launch<NN, PP, false>(a, use_tab, smem, s);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_states_tiny<NN, PP>, smem, cached);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (a.K + TINY_THREADS - 1) / TINY_THREADS;
+  k_states_tiny<NN, PP><<<int(blocks), TINY_THREADS, smem, s>>>(a, use_tab);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -441,9 +341,11 @@ cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, b
   bool integer_plane = a.f == nullptr;
   for (int d = 0; d < 3; ++d)
     integer_plane = integer_plane && a.plane.trans_dir[d] == double((long long)a.plane.trans_dir[d]);
-  const bool use_tab = integer_plane && (size_t(N) + Nt) <= 8192;
+  const TabShape tN = tab_shape(N), tT = tab_shape(Nt);
+  const size_t tab = size_t(tN.B) + tN.H + tT.B + tT.H;
+  const bool use_tab = integer_plane && tab <= 4096;
   size_t smem = size_t(a.model.n_R) * TINY_THREADS * sizeof(z64);
-  if (use_tab) smem += (size_t(N) + Nt + a.model.n_R) * sizeof(z64) + 2 * a.model.n_R * sizeof(int);
+  if (use_tab) smem += (tab + a.model.n_R) * sizeof(z64) + 2 * a.model.n_R * sizeof(int);
   *handled = true;
   if (n == 2) {
     return p == 1 ? tiny_prec<2, 1>(a, use_tab, smem, s) : tiny_prec<2, 2>(a, use_tab, smem, s);
