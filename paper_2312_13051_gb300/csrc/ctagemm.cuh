@@ -1,0 +1,249 @@
+// CTA-level building blocks of the large-n refinement: a tiled complex GEMM (plain
+// FP32, or with compensated sums for FP64-grade results) and the application of a
+// sequence of Householder reflectors to a column panel held in shared memory.  Both
+// keep operand reuse in shared memory instead of L2.
+#pragma once
+
+#include "common.cuh"
+
+namespace bw {
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 dot products (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is split
+// exactly into a + e with one FMA, the running sum is kept as hi + lo with an
+// error-free two-sum, and the result is as accurate as a sum carried in twice the
+// working precision.  GB300 runs FP32 ~70x faster than FP64, so this is the cheap
+// way to the FP64-grade residuals the Newton correction needs.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);      // exact: a b = p + e
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);  // exact: hi + p = s + err
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ void add(float x) { lo += x; }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+struct CDF {
+  DF re, im;
+  // acc += a * b with a = ah + al (FP64 split into two floats), b FP32
+  __device__ __forceinline__ void add_prod(c32 ah, c32 al, c32 b) {
+    re.add_prod(ah.re, b.re);
+    re.add_prod(-ah.im, b.im);
+    im.add_prod(ah.re, b.im);
+    im.add_prod(ah.im, b.re);
+    re.add(al.re * b.re - al.im * b.im);
+    im.add(al.re * b.im + al.im * b.re);
+  }
+  // acc += conj(a) * b, both FP32
+  __device__ __forceinline__ void add_cprod(c32 a, c32 b) {
+    re.add_prod(a.re, b.re);
+    re.add_prod(a.im, b.im);
+    im.add_prod(a.re, b.im);
+    im.add_prod(-a.im, b.re);
+  }
+  __device__ __forceinline__ z64 value() const { return z64(re.value(), im.value()); }
+};
+
+
+// Operand and accumulator policies of cta_gemm.
+struct GemmPlain {  // C = A B in FP32
+  using TA = c32;
+  using TB = c32;
+  using Acc = c32;
+  static __device__ __forceinline__ TA zero_a() { return c32(0.f, 0.f); }
+  static __device__ __forceinline__ Acc zero() { return c32(0.f, 0.f); }
+  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
+};
+struct SplitC {  // an FP64 value as the float pair hi + lo
+  c32 hi, lo;
+};
+struct GemmSplitComp {  // C = A B, A an FP64 matrix as float pairs, compensated sums
+  using TA = SplitC;
+  using TB = c32;
+  using Acc = CDF;
+  static __device__ __forceinline__ TA zero_a() { return SplitC{c32(0.f, 0.f), c32(0.f, 0.f)}; }
+  static __device__ __forceinline__ Acc zero() { return CDF(); }
+  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { c.add_prod(a.hi, a.lo, b); }
+};
+struct GemmGramComp {  // C = A^dag B (A passed unconjugated), compensated sums
+  using TA = c32;
+  using TB = c32;
+  using Acc = CDF;
+  static __device__ __forceinline__ TA zero_a() { return c32(0.f, 0.f); }
+  static __device__ __forceinline__ Acc zero() { return CDF(); }
+  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { c.add_cprod(a, b); }
+};
+
+constexpr int CG_TILE = 64, CG_K = 16;
+// Shared memory used by cta_gemm<Pol> (a 16 x 64 tile of each operand).
+template <class Pol>
+__host__ __device__ constexpr size_t cg_smem() {
+  return CG_K * CG_TILE * (sizeof(typename Pol::TA) + sizeof(typename Pol::TB));
+}
+constexpr size_t CG_SMEM = CG_K * CG_TILE * (sizeof(SplitC) + sizeof(c32));  // the largest policy
+
+// C(m, c) = sum_k A(m, k) B(k, c) (the policy's product and accumulator) for m < M,
+// c < Ncol, k < K, computed by all blockDim.x == 256 threads of the CTA in 64 x 64
+// output tiles (thread (ty, tx) owns rows ty + 16 i and columns tx + 16 j).
+// la(m, k) and lb(k, c) return the operands (out-of-range indices are never
+// requested); st(m, c, acc) consumes each result once.  A_K_CONTIG / B_C_CONTIG say
+// which index of the operand is contiguous in memory, so that the staging loads
+// are coalesced.  sm: cg_smem<Pol>() bytes.
+template <class Pol, bool A_K_CONTIG, bool B_C_CONTIG, class LA, class LB, class ST>
+__device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned char* sm) {
+  using TA = typename Pol::TA;
+  using TB = typename Pol::TB;
+  TA(*As)[CG_TILE] = reinterpret_cast<TA(*)[CG_TILE]>(sm);
+  TB(*Bs)[CG_TILE] = reinterpret_cast<TB(*)[CG_TILE]>(sm + CG_K * CG_TILE * sizeof(TA));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += CG_TILE)
+    for (int c0 = 0; c0 < Ncol; c0 += CG_TILE) {
+      typename Pol::Acc acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Pol::zero();
+      for (int k0 = 0; k0 < K; k0 += CG_K) {
+        for (int e = tid; e < CG_K * CG_TILE; e += 256) {
+          int kk, mm;
+          if (A_K_CONTIG) {
+            mm = e / CG_K;
+            kk = e - mm * CG_K;
+          } else {
+            kk = e / CG_TILE;
+            mm = e - kk * CG_TILE;
+          }
+          const int gm = m0 + mm, gk = k0 + kk;
+          As[kk][mm] = (gm < M && gk < K) ? la(gm, gk) : Pol::zero_a();
+        }
+        for (int e = tid; e < CG_K * CG_TILE; e += 256) {
+          int kk, cc;
+          if (B_C_CONTIG) {
+            kk = e / CG_TILE;
+            cc = e - kk * CG_TILE;
+          } else {
+            cc = e / CG_K;
+            kk = e - cc * CG_K;
+          }
+          const int gc = c0 + cc, gk = k0 + kk;
+          Bs[kk][cc] = (gc < Ncol && gk < K) ? lb(gk, gc) : c32(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int kk = 0; kk < CG_K; ++kk) {
+          TA av[4];
+          TB bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Pol::mac(acc[i][j], av[i], bv[j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gm = m0 + ty + 16 * i, gc = c0 + tx + 16 * j;
+          if (gm < M && gc < Ncol) st(gm, gc, acc[i][j]);
+        }
+    }
+}
+
+template <bool A_K_CONTIG, bool B_C_CONTIG, class LA, class LB, class ST>
+__device__ void cta_cgemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned char* sm) {
+  cta_gemm<GemmPlain, A_K_CONTIG, B_C_CONTIG>(M, Ncol, K, la, lb, st, sm);
+}
+
+// Applies the reflectors P_c = I - 2 u_c u_c^dag, c = 0 .. n-3 (u_c in column c of
+// A below the diagonal, rows c+1..n-1), to X (n x ncol, leading dimension ldx, in
+// global memory): X <- P_{n-3} ... P_0 X (forward) or X <- P_0 ... P_{n-3} X
+// (reverse).  X is processed in panels of PW columns held in shared memory; each
+// reflector is read once per panel.  sm: reflect_smem<TX>(n, PW) bytes.
+template <class TX>
+__host__ __device__ inline size_t reflect_smem(int n, int PW) {
+  return (size_t(n) * PW + n + 8 * size_t(PW)) * sizeof(cx<TX>);
+}
+
+template <int PW, class TA, class TX>
+__device__ void cta_reflect_pw(const cx<TA>* A, int n, cx<TX>* X, int ncol, long long ldx, bool reverse,
+                               unsigned char* smraw) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  cx<TX>* P = reinterpret_cast<cx<TX>*>(smraw);  // n x PW panel
+  cx<TX>* us = P + n * PW;                       // n
+  cx<TX>* part = us + n;                         // nwarp (<= 8) x PW partial dot products
+  for (int j0 = 0; j0 < ncol; j0 += PW) {
+    const int w = min(PW, ncol - j0);
+    for (int e = tid; e < n * PW; e += nt) {
+      const int r = e / PW, j = e - r * PW;
+      P[e] = j < w ? X[(long long)r * ldx + j0 + j] : cx<TX>(TX(0), TX(0));
+    }
+    for (int s = 0; s + 2 < n; ++s) {
+      const int c = reverse ? n - 3 - s : s;
+      for (int r = c + 1 + tid; r < n; r += nt) {
+        const cx<TA> v = A[(long long)r * n + c];
+        us[r] = cx<TX>(TX(v.re), TX(v.im));
+      }
+      __syncthreads();
+      // partial w_j = sum_r conj(u_r) P[r][j]: warp k takes rows c+1+k, c+1+k+nwarp, ...
+      if (lane < PW) {
+        cx<TX> acc(TX(0), TX(0));
+        for (int r = c + 1 + warp; r < n; r += nwarp) cfma_conj(acc, us[r], P[r * PW + lane]);
+        part[warp * PW + lane] = acc;
+      }
+      __syncthreads();
+      if (tid < PW) {
+        cx<TX> t(TX(0), TX(0));
+        for (int k = 0; k < nwarp; ++k) t = t + part[k * PW + tid];
+        part[tid] = TX(2) * t;
+      }
+      __syncthreads();
+      for (int e = (c + 1) * PW + tid; e < n * PW; e += nt) {
+        const int r = e / PW, j = e - r * PW;
+        P[e] = P[e] - us[r] * part[j];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < n * PW; e += nt) {
+      const int r = e / PW, j = e - r * PW;
+      if (j < w) X[(long long)r * ldx + j0 + j] = P[e];
+    }
+    __syncthreads();
+  }
+}
+
+// Panel width that fits `bytes` of shared memory (0: none fits).
+template <class TX>
+__host__ __device__ inline int reflect_pw(int n, size_t bytes) {
+  for (int pw = 32; pw >= 1; pw >>= 1)
+    if (reflect_smem<TX>(n, pw) <= bytes) return pw;
+  return 0;
+}
+
+template <class TA, class TX>
+__device__ void cta_reflect(const cx<TA>* A, int n, cx<TX>* X, int ncol, long long ldx, bool reverse,
+                            unsigned char* sm, int pw) {
+  switch (pw) {
+    case 32: cta_reflect_pw<32>(A, n, X, ncol, ldx, reverse, sm); break;
+    case 16: cta_reflect_pw<16>(A, n, X, ncol, ldx, reverse, sm); break;
+    case 8: cta_reflect_pw<8>(A, n, X, ncol, ldx, reverse, sm); break;
+    case 4: cta_reflect_pw<4>(A, n, X, ncol, ldx, reverse, sm); break;
+    case 2: cta_reflect_pw<2>(A, n, X, ncol, ldx, reverse, sm); break;
+    default: cta_reflect_pw<1>(A, n, X, ncol, ldx, reverse, sm); break;
+  }
+}
+
+}  // namespace bw

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 
+#include "ctagemm.cuh"
 #include "df32.cuh"
 #include "jacobi.cuh"
 #include "launch.h"
@@ -47,51 +48,6 @@ __device__ __forceinline__ void lg_kpoint(const LargeArgs& a, long long k, doubl
     plane_f(a.plane, i, j, f);
   }
 }
-
-// ---------------------------------------------------------------------------
-// Compensated FP32 dot products (Ogita, Rump and Oishi, "Accurate sum and dot
-// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is split
-// exactly into a + e with one FMA, the running sum is kept as hi + lo with an
-// error-free two-sum, and the result is as accurate as a sum carried in twice the
-// working precision.  GB300 runs FP32 ~70x faster than FP64, so this is the cheap
-// way to the FP64-grade residuals the Newton correction needs.
-// ---------------------------------------------------------------------------
-struct DF {
-  float hi, lo;
-  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float p = a * b;
-    const float e = fmaf(a, b, -p);      // exact: a b = p + e
-    const float s = hi + p;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (p - bp);  // exact: hi + p = s + err
-    hi = s;
-    lo += err + e;
-  }
-  __device__ __forceinline__ void add(float x) { lo += x; }
-  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
-};
-
-struct CDF {
-  DF re, im;
-  // acc += a * b with a = ah + al (FP64 split into two floats), b FP32
-  __device__ __forceinline__ void add_prod(c32 ah, c32 al, c32 b) {
-    re.add_prod(ah.re, b.re);
-    re.add_prod(-ah.im, b.im);
-    im.add_prod(ah.re, b.im);
-    im.add_prod(ah.im, b.re);
-    re.add(al.re * b.re - al.im * b.im);
-    im.add(al.re * b.im + al.im * b.re);
-  }
-  // acc += conj(a) * b, both FP32
-  __device__ __forceinline__ void add_cprod(c32 a, c32 b) {
-    re.add_prod(a.re, b.re);
-    re.add_prod(a.im, b.im);
-    im.add_prod(a.re, b.im);
-    im.add_prod(-a.im, b.re);
-  }
-  __device__ __forceinline__ z64 value() const { return z64(re.value(), im.value()); }
-};
 
 __device__ __forceinline__ void split64(z64 x, c32& hi, c32& lo) {
   hi = c32(float(x.re), float(x.im));
@@ -315,30 +271,50 @@ __global__ void k_lg_tridiag(LargeArgs a) {
 // Turns xs[c+1..n) (column c below the diagonal) into the unit reflector u with
 // (I - 2 u u^dag) x = alpha e_1 and returns alpha; u = 0 when nothing lies below the
 // subdiagonal.  Block-wide.
+// Block-wide sum in the working precision (FP32 for the mixed solve: GB300's FP64
+// pipe is ~70x narrower, and these per-step reductions would otherwise cost as much
+// as the sweep over the matrix).
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  T* r = reinterpret_cast<T*>(red);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) r[w] = v;
+  __syncthreads();
+  T s = T(0);
+  for (int k = 0; k < nw; ++k) s += r[k];
+  __syncthreads();
+  return s;
+}
+
+// Turns xs[c+1..n) (column c below the diagonal) into the unit reflector u with
+// (I - 2 u u^dag) x = alpha e_1 and returns alpha; u = 0 when nothing lies below the
+// subdiagonal.  Block-wide, in the working precision T.
 template <typename T>
 __device__ cx<T> lg_reflector(cx<T>* xs, int c, int n, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  double s = 0.0;
-  for (int r = c + 1 + tid; r < n; r += nt) s += double(abs2(xs[r]));
-  s = block_sum(s, red);
+  T s = T(0);
+  for (int r = c + 1 + tid; r < n; r += nt) s += abs2(xs[r]);
+  s = block_sum_t(s, red);
   const cx<T> x0 = xs[c + 1];
-  const double ax0 = hypot(double(x0.re), double(x0.im)), tail = s - ax0 * ax0;
+  const T ax0 = sqrt(abs2(x0)), tail = s - ax0 * ax0;
   __syncthreads();
-  if (!(tail > 0.0)) {
+  if (!(tail > T(0))) {
     for (int r = c + 1 + tid; r < n; r += nt) xs[r] = cx<T>(T(0), T(0));
     __syncthreads();
     return x0;
   }
-  const double nx = sqrt(s);
-  const double phr = ax0 > 0.0 ? double(x0.re) / ax0 : 1.0, phi = ax0 > 0.0 ? double(x0.im) / ax0 : 0.0;
-  const double v0m = ax0 + nx;
-  const T inv = T(1.0 / sqrt(v0m * v0m + tail));
+  const T nx = sqrt(s);
+  const T phr = ax0 > T(0) ? x0.re / ax0 : T(1), phi = ax0 > T(0) ? x0.im / ax0 : T(0);
+  const T v0m = ax0 + nx;
+  const T inv = T(1) / sqrt(v0m * v0m + tail);
   for (int r = c + 1 + tid; r < n; r += nt) {
-    const cx<T> v = r == c + 1 ? cx<T>(T(phr * v0m), T(phi * v0m)) : xs[r];
+    const cx<T> v = r == c + 1 ? cx<T>(phr * v0m, phi * v0m) : xs[r];
     xs[r] = inv * v;
   }
   __syncthreads();
-  return cx<T>(T(-phr * nx), T(-phi * nx));
+  return cx<T>(-phr * nx, -phi * nx);
 }
 
 // Rows and columns lo..n-1 of the lower triangle: with upd, A <- A - 2 (u w^dag + w u^dag);
@@ -413,11 +389,10 @@ __device__ void lg_hpass(cx<T>* A, int n, int lo, bool upd, const cx<T>* u, cons
 // w = p - (u^dag p) u on lo..n-1 (p in pa).
 template <typename T>
 __device__ void lg_make_w(const cx<T>* u, const cx<T>* pa, cx<T>* w, int lo, int n, double* red) {
-  double kr = 0.0;
-  for (int r = lo + threadIdx.x; r < n; r += blockDim.x)
-    kr += double(u[r].re) * double(pa[r].re) + double(u[r].im) * double(pa[r].im);
-  kr = block_sum(kr, red);
-  for (int r = lo + threadIdx.x; r < n; r += blockDim.x) w[r] = pa[r] - T(kr) * u[r];
+  T kr = T(0);
+  for (int r = lo + threadIdx.x; r < n; r += blockDim.x) kr += u[r].re * pa[r].re + u[r].im * pa[r].im;
+  kr = block_sum_t(kr, red);
+  for (int r = lo + threadIdx.x; r < n; r += blockDim.x) w[r] = pa[r] - kr * u[r];
   __syncthreads();
 }
 
@@ -670,35 +645,9 @@ __global__ void k_lg_invit(LargeArgs a) {
 // Output X[r][col] with leading dimension ncol, precision To.
 // ---------------------------------------------------------------------------
 template <typename T, typename To>
-__device__ void apply_reflectors(const cx<T>* A, int n, cx<To>* X, int ncol, bool reverse,
-                                 cx<To>* us, cx<To>* wv) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int s = 0; s + 2 < n; ++s) {
-    const int c = reverse ? n - 3 - s : s;
-    const int m = n - c - 1;
-    for (int r = tid; r < m; r += nt) us[r] = ccast<To>(A[(long long)(c + 1 + r) * n + c]);
-    __syncthreads();
-    for (int col = tid; col < ncol; col += nt) {
-      cx<To> acc(To(0), To(0));
-      for (int r = 0; r < m; ++r) cfma_conj(acc, us[r], X[(long long)(c + 1 + r) * ncol + col]);
-      wv[col] = acc;
-    }
-    __syncthreads();
-    for (int r = tid >> 5; r < m; r += nt >> 5) {
-      cx<To>* row = X + (long long)(c + 1 + r) * ncol;
-      const cx<To> ur = To(2) * us[r];
-      for (int col = tid & 31; col < ncol; col += 32) row[col] = row[col] - ur * wv[col];
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T, typename To>
-__global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_stride, int ncol) {
+__global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_stride, int ncol, int pw) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
-  cx<To>* us = reinterpret_cast<cx<To>*>(smem);
-  cx<To>* wv = us + n;
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
     const cx<T>* A = reinterpret_cast<const cx<T>*>(a.A) + kw * (long long)n * n;
     const cx<T>* Dp = reinterpret_cast<const cx<T>*>(a.Dp) + kw * n;
@@ -712,7 +661,7 @@ __global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_strid
       }
     }
     __syncthreads();
-    apply_reflectors<T, To>(A, n, X, ncol, true, us, wv);
+    cta_reflect<T, To>(A, n, X, ncol, ncol, true, smem, pw);
   }
 }
 
@@ -725,6 +674,10 @@ __global__ void k_lg_gap64(LargeArgs a) {
   const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
   a.gap[k] = g;
   if (!(g > a.gap_tol)) report(a.status, ST_EGAP, k, g);
+}
+
+__host__ __device__ inline size_t refine_work_offset(int p) {
+  return ((size_t(p) + 66) * sizeof(double) + 15) & ~size_t(15);
 }
 
 // ---------------------------------------------------------------------------
@@ -740,15 +693,14 @@ __global__ void k_lg_gap64(LargeArgs a) {
 //   and p-th FP32 vectors.  The off-diagonal part of Q^dag H Q is of the order of
 //   the FP32 error; its projection on the complement enters at second order.
 // ---------------------------------------------------------------------------
-__global__ void k_lg_refine(LargeArgs a) {
+__global__ void k_lg_refine(LargeArgs a, int pw) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, p = a.p, nbt = a.nbt, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const DevModel& md = a.model;
-  c32* us = reinterpret_cast<c32*>(smem);            // n
-  c32* wv = us + n;                                  // p
-  double* rho = reinterpret_cast<double*>(wv + p + (p & 1));  // p + 2
+  double* rho = reinterpret_cast<double*>(smem);     // p + 2
   double* red = rho + p + 2;                         // 64
+  unsigned char* work = smem + refine_work_offset(p);  // reflector panels / GEMM tiles
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
     const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     const c32* A = reinterpret_cast<const c32*>(a.A) + kw * (long long)n * n;
@@ -762,7 +714,17 @@ __global__ void k_lg_refine(LargeArgs a) {
     z64* R = a.R64 + kw * (long long)n * p;          // H Q, later FP32 scratch
     c32* C = a.C32 + kw * (long long)n * p;
     c32* E = reinterpret_cast<c32*>(a.G64 + kw * (long long)p * p);  // Q^dag Q - I (p x p)
-    // R = H Q32 (compensated), one warp per row, lanes along the columns
+    // R = H Q32 (compensated): a tiled GEMM when H is dense, else one warp per row
+    if (dense || md.n_ent == n * n) {
+      cta_gemm<GemmSplitComp, true, true>(
+          n, p, n,
+          [&](int r, int q) {
+            const c32* hp = reinterpret_cast<const c32*>(He + (long long)r * n + q);
+            return SplitC{hp[0], hp[1]};
+          },
+          [&](int q, int c) { return X[(long long)q * nbt + c]; },
+          [&](int r, int c, const CDF& acc) { R[(long long)r * p + c] = acc.value(); }, work);
+    } else
     for (int r = warp; r < n; r += nwarp) {
       for (int c0 = 0; c0 < p; c0 += 32) {
         const int c = c0 + lane;
@@ -796,7 +758,7 @@ __global__ void k_lg_refine(LargeArgs a) {
       }
     __syncthreads();
     // C <- D^dag Q_h^dag C
-    apply_reflectors<float, float>(A, n, C, p, false, us, wv);
+    cta_reflect<float, float>(A, n, C, p, p, false, work, pw);
     for (int r = warp; r < n; r += nwarp) {
       const c32 d = conj(Dp[r]);
       for (int c = lane; c < p; c += 32) C[(long long)r * p + c] = d * C[(long long)r * p + c];
@@ -805,51 +767,56 @@ __global__ void k_lg_refine(LargeArgs a) {
     // complement coefficients (FP32), kept in the R workspace
     c32* coef = reinterpret_cast<c32*>(R);
     const int nu = n - p;
-    for (int ua = warp; ua < nu; ua += nwarp)
-      for (int c = lane; c < p; c += 32) {
-        c32 acc(0.f, 0.f);
-        for (int r = 0; r < n; ++r) acc = acc + Z[(long long)r * a.nvec + p + ua] * C[(long long)r * p + c];
-        coef[(long long)ua * p + c] = float(1.0 / (rho[c] - double(lam[p + ua]))) * acc;
-      }
+    const int nvec = a.nvec;
+    // coef[ua][c] = (Z_u^T C)[ua][c] / (rho_c - lam_{p+ua})
+    cta_cgemm<false, true>(
+        nu, p, n, [&](int ua, int r) { return c32(Z[(long long)r * nvec + p + ua], 0.f); },
+        [&](int r, int c) { return C[(long long)r * p + c]; },
+        [&](int ua, int c, c32 v) {
+          coef[(long long)ua * p + c] = float(1.0 / (rho[c] - double(lam[p + ua]))) * v;
+        },
+        work);
     __syncthreads();
     // update = Q_h D Z_u coef
-    for (int r = warp; r < n; r += nwarp) {
-      const float* zr = Z + (long long)r * a.nvec + p;
-      const c32 d = Dp[r];
-      for (int c = lane; c < p; c += 32) {
-        c32 acc(0.f, 0.f);
-        for (int ua = 0; ua < nu; ++ua) acc = acc + zr[ua] * coef[(long long)ua * p + c];
-        C[(long long)r * p + c] = d * acc;
-      }
-    }
+    cta_cgemm<true, true>(
+        n, p, nu, [&](int r, int ua) { return c32(Z[(long long)r * nvec + p + ua], 0.f); },
+        [&](int ua, int c) { return coef[(long long)ua * p + c]; },
+        [&](int r, int c, c32 v) { C[(long long)r * p + c] = Dp[r] * v; }, work);
     __syncthreads();
-    apply_reflectors<float, float>(A, n, C, p, true, us, wv);
-    // E = Q^dag Q - I with Q = Q32 + C: Q32^dag Q32 - I compensated, the rest in FP32
-    for (int x = warp; x < p; x += nwarp)
-      for (int y = lane; y < p; y += 32) {
-        CDF acc;
-        c32 small(0.f, 0.f);
-        for (int r = 0; r < n; ++r) {
-          const c32 qx = X[(long long)r * nbt + x], qy = X[(long long)r * nbt + y];
-          const c32 dx = C[(long long)r * p + x], dy = C[(long long)r * p + y];
-          acc.add_cprod(qx, qy);
-          small = small + conj(qx) * dy + conj(dx) * qy + conj(dx) * dy;
-        }
-        z64 v = acc.value();
-        if (x == y) v.re -= 1.0;
-        E[(long long)x * p + y] = c32(float(v.re + double(small.re)), float(v.im + double(small.im)));
-      }
+    cta_reflect<float, float>(A, n, C, p, p, true, work, pw);
+    // E = Q^dag Q - I with Q = Q32 + C: Q32^dag Q32 - I compensated (the FP32 basis is
+    // orthonormal to ~1e-7, so the difference needs the extra precision), then the
+    // small terms Q32^dag C + C^dag (Q32 + C) in FP32 as one GEMM over 2 n rows
+    cta_gemm<GemmGramComp, false, true>(
+        p, p, n, [&](int x, int r) { return X[(long long)r * nbt + x]; },
+        [&](int r, int y) { return X[(long long)r * nbt + y]; },
+        [&](int x, int y, const CDF& acc) {
+          z64 v = acc.value();
+          if (x == y) v.re -= 1.0;
+          E[(long long)x * p + y] = c32(float(v.re), float(v.im));
+        },
+        work);
+    __syncthreads();
+    cta_cgemm<false, true>(
+        p, p, 2 * n,
+        [&](int x, int k) {
+          return conj(k < n ? X[(long long)k * nbt + x] : C[(long long)(k - n) * p + x]);
+        },
+        [&](int k, int y) {
+          return k < n ? C[(long long)k * p + y] : X[(long long)(k - n) * nbt + y] + C[(long long)(k - n) * p + y];
+        },
+        [&](int x, int y, c32 v) { E[(long long)x * p + y] = E[(long long)x * p + y] + v; }, work);
     __syncthreads();
     // Q = (Q32 + C) - (Q32 + C) E / 2, the correction in FP32
-    for (int r = warp; r < n; r += nwarp)
-      for (int c = lane; c < p; c += 32) {
-        c32 acc(0.f, 0.f);
-        for (int q = 0; q < p; ++q)
-          acc = acc + (X[(long long)r * nbt + q] + C[(long long)r * p + q]) * E[(long long)q * p + c];
-        const c32 x32 = X[(long long)r * nbt + c], dc = C[(long long)r * p + c];
-        Q[(long long)r * p + c] = z64(double(x32.re) + double(dc.re) - 0.5 * double(acc.re),
-                                      double(x32.im) + double(dc.im) - 0.5 * double(acc.im));
-      }
+    cta_cgemm<true, true>(
+        n, p, p, [&](int r, int q) { return X[(long long)r * nbt + q] + C[(long long)r * p + q]; },
+        [&](int q, int c) { return E[(long long)q * p + c]; },
+        [&](int r, int c, c32 v) {
+          const c32 x32 = X[(long long)r * nbt + c], dc = C[(long long)r * p + c];
+          Q[(long long)r * p + c] = z64(double(x32.re) + double(dc.re) - 0.5 * double(v.re),
+                                        double(x32.im) + double(dc.im) - 0.5 * double(v.im));
+        },
+        work);
     __syncthreads();
     // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p
     if (p < n) {
@@ -890,6 +857,8 @@ __global__ void k_lg_refine(LargeArgs a) {
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int LG_THREADS = 256;
+// shared memory for a reflector panel (the panel width adapts to n)
+constexpr size_t kReflectSmem = size_t(200) << 10;
 
 int lg_grid(long long units) {
   const long long cap = 152LL * 4;
@@ -951,11 +920,13 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   if (!a.mixed) {
     if ((e = lg_common<double>(a, s)) != cudaSuccess) return e;
     if (a.p == 0) return cudaSuccess;  // values only
-    const size_t sm = 2 * size_t(a.n > a.p ? a.n : a.p) * sizeof(z64);
+    const int pw = reflect_pw<double>(a.n, kReflectSmem);
+    if (pw == 0) return cudaErrorInvalidValue;
+    const size_t sm = reflect_smem<double>(a.n, pw);
     static size_t cached = 0;
     if ((e = set_smem_once(k_lg_backtransform<double, double>, sm, cached)) != cudaSuccess) return e;
     k_lg_backtransform<double, double><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
-        a, a.U, (long long)a.n * a.p, a.p);
+        a, a.U, (long long)a.n * a.p, a.p, pw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lg_mark(a, "lg_backtransform");
     if (a.Hin) return cudaSuccess;  // batched eigensolve: every eigenvalue is returned, no gap test
@@ -966,17 +937,19 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   }
   if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
   if (a.no_refine) return cudaSuccess;
-  const size_t sm = 2 * size_t(a.n > a.nbt ? a.n : a.nbt) * sizeof(c32);
+  const int pw = reflect_pw<float>(a.n, kReflectSmem - refine_work_offset(a.p));
+  if (pw == 0) return cudaErrorInvalidValue;
+  const size_t sm = reflect_smem<float>(a.n, pw);
   static size_t cached = 0;
   if ((e = set_smem_once(k_lg_backtransform<float, float>, sm, cached)) != cudaSuccess) return e;
   k_lg_backtransform<float, float><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
-      a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt);
+      a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt, pw);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_backtransform");
-  const size_t smr = (size_t(a.n) + a.p + 1) * sizeof(c32) + (size_t(a.p) + 2 + 64) * sizeof(double) + 16;
+  const size_t smr = refine_work_offset(a.p) + std::max(reflect_smem<float>(a.n, pw), CG_SMEM);
   static size_t cached_r = 0;
   if ((e = set_smem_once(k_lg_refine, smr, cached_r)) != cudaSuccess) return e;
-  k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a);
+  k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a, pw);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_refine");
   return cudaSuccess;
