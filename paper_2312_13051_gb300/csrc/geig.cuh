@@ -297,4 +297,56 @@ __device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* la
   return 0;
 }
 
+// Principal complex square root.
+__device__ __forceinline__ z64 csqrt64(z64 z) {
+  const double r = zabs(z);
+  if (r == 0.0) return z64(0.0, 0.0);
+  const double t = sqrt(0.5 * (r + fabs(z.re)));
+  if (z.re >= 0.0) return z64(t, z.im / (2.0 * t));
+  return z64(fabs(z.im) / (2.0 * t), z.im >= 0.0 ? t : -t);
+}
+
+// Closed-form eigen-decomposition of a 2 x 2 complex matrix H = [[a, b], [c, d]]
+// (leading dimension ld), one thread: lam[0..2), and with Z the unit right
+// eigenvectors as columns.  lambda = (a + d)/2 +- sqrt(((a - d)/2)^2 + b c); the
+// root of larger magnitude comes from the formula and the other from
+// det / lambda_1, which avoids cancellation.  Eigenvector of lambda: (b, lambda - a)
+// or (lambda - d, c), whichever is longer (e_1, e_2 when H is a multiple of I).
+__device__ inline void eig2_closed(const z64* H, int ld, z64* lam, z64* Z, bool want_vec) {
+  const z64 a = H[0], b = H[1], c = H[ld], d = H[ld + 1];
+  const z64 mid = 0.5 * (a + d), half = 0.5 * (a - d);
+  const z64 sq = csqrt64(half * half + b * c);
+  const z64 l1p = mid + sq, l1m = mid - sq;
+  const z64 l1 = abs2(l1p) >= abs2(l1m) ? l1p : l1m;
+  const z64 det = a * d - b * c;
+  z64 l2;
+  if (abs2(l1) > 0.0) {
+    const double den = abs2(l1);
+    l2 = z64((det.re * l1.re + det.im * l1.im) / den, (det.im * l1.re - det.re * l1.im) / den);
+  } else {
+    l2 = z64(0.0, 0.0);
+  }
+  lam[0] = l1;
+  lam[1] = l2;
+  if (!want_vec) return;
+  for (int k = 0; k < 2; ++k) {
+    const z64 l = lam[k];
+    z64 v0 = b, v1 = l - a;
+    const z64 w0 = l - d, w1 = c;
+    if (abs2(w0) + abs2(w1) > abs2(v0) + abs2(v1)) {
+      v0 = w0;
+      v1 = w1;
+    }
+    double nv = abs2(v0) + abs2(v1);
+    if (!(nv > 0.0)) {
+      v0 = z64(k == 0 ? 1.0 : 0.0, 0.0);
+      v1 = z64(k == 0 ? 0.0 : 1.0, 0.0);
+      nv = 1.0;
+    }
+    const double inv = 1.0 / sqrt(nv);
+    Z[0 * ld + k] = inv * v0;
+    Z[1 * ld + k] = inv * v1;
+  }
+}
+
 }  // namespace bw

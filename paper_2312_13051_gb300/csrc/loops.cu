@@ -469,8 +469,13 @@ __global__ void k_loops_scan(LoopArgs a) {
     z64* Pf = prefix_products(S, T, N, p);
     for (int e = tid; e < pp; e += nt) X[e] = Pf[(N - 1) * pp + e];
     __syncthreads();
-    const int rc = geig(X, Y, p, p, a.nested != 0, lam, vec, sh);
-    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+    if (p == 2) {  // closed form: the general solver's serial QR sweeps dominate at p = 2
+      if (tid == 0) eig2_closed(X, 2, lam, Y, a.nested != 0);
+      __syncthreads();
+    } else {
+      const int rc = geig(X, Y, p, p, a.nested != 0, lam, vec, sh);
+      if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+    }
     for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
     __syncthreads();
     rank_sort(th, p, ord);
