@@ -21,6 +21,7 @@ constexpr int TINY_R_MAX = 16;
 
 struct StatesArgs {
   DevModel model;
+  const int* row_ptr;   // n + 1: first plan entry of each row (entries sorted by row)
   DevPlane plane;       // used when f == nullptr
   const double* f;      // optional explicit k-points (K x 3)
   long long K;

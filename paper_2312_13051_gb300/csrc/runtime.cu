@@ -655,6 +655,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   bw::StatesArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.model = dev_model(P, dblob);
+  sa.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
   sa.plane = dev_plane(plane);
   sa.f = nullptr;
   sa.K = K;
@@ -1199,6 +1200,7 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
   bw::StatesArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.model = dev_model(P, dblob);
+  sa.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
   sa.plane = dev_plane(plane);
   sa.K = K;
   sa.p = p;
