@@ -202,6 +202,8 @@ cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);
 cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, bool* handled);
 cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s);
+// True when the loop kernel forms the overlaps itself (launch_overlaps then does nothing).
+bool loops_form_overlaps(const LoopArgs& a);
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s);
 cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s);
 cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s);

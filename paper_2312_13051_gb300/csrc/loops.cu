@@ -462,8 +462,19 @@ __global__ void k_loops_scan(LoopArgs a) {
         if (a.min_pso_gap) a.min_pso_gap[i] = gp;
       }
     }
-    const z64* Mg = a.M + k0 * pp;
-    for (int e = tid; e < N * pp; e += nt) S[e] = Mg[e];
+    if (a.unitarise) {
+      const z64* Mg = a.M + k0 * pp;
+      for (int e = tid; e < N * pp; e += nt) S[e] = Mg[e];
+    } else {  // the overlaps of this loop, M_j = U(k_{j+1})^dagger U(k_j), closing on j = 0
+      for (int e = tid; e < N * pp; e += nt) {
+        const int jj = e / pp, rc = e - jj * pp, r = rc / p, c = rc - r * p;
+        const z64* Uh = a.U + (k0 + jj) * (long long)n * p;
+        const z64* Un = a.U + (k0 + (jj + 1 == N ? 0 : jj + 1)) * (long long)n * p;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < n; ++q) cfma_conj(acc, Un[q * p + r], Uh[q * p + c]);
+        S[e] = acc;
+      }
+    }
     __syncthreads();
     // P[j] = M_j ... M_0; the loop matrix is P[N-1]
     z64* Pf = prefix_products(S, T, N, p);
@@ -584,9 +595,11 @@ static bool scan_nested_fit(const LoopArgs& a) {
 // ---------------------------------------------------------------------------
 static int loop_threads(int p) { return p <= 4 ? 32 : (p <= 16 ? 64 : 128); }
 
+bool loops_form_overlaps(const LoopArgs& a) { return !a.unitarise && scan_loops_fit(a); }
+
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
   const long long K = (long long)a.N * a.N_t;
-  if (K <= 0) return cudaSuccess;
+  if (K <= 0 || loops_form_overlaps(a)) return cudaSuccess;
   const size_t sm = a.unitarise ? (4 * size_t(a.p) * a.p * sizeof(z64) +
                                    (a.p / 2 + 2) * sizeof(JacRot<double>) + 64 * sizeof(double))
                                 : 0;

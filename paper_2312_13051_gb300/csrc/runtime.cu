@@ -753,8 +753,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     la.min_wannier_gap = min_wgap;
     la.nested_out = nested_out;
   }
-  BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
-  prof_mark(ctx, s, "overlaps");
+  if (!bw::loops_form_overlaps(la)) {
+    BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
+    prof_mark(ctx, s, "overlaps");
+  }
   BW_CUDA(bw::launch_loops(la, s), "loop kernel");
   prof_mark(ctx, s, "loops");
   if (kind == LoopKind::Nested) {
