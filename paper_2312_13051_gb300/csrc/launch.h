@@ -81,6 +81,7 @@ struct LoopArgs {
   int first, m;
   double wannier_gap_tol;
   z64* w;                // N x N_t x n x m
+  z64* nu_buf;           // N x N_t x p x m transported sector bases (sequential loop path), or NULL
   double* min_wannier_gap;  // N_t (optional)
   double* nested_out;    // N x m
   DevStatus* status;
@@ -207,5 +208,10 @@ bool loops_form_overlaps(const LoopArgs& a);
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s);
 cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s);
 cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s);
+// True when the nested loop kernel only transports the sector bases (into nu_buf)
+// and launch_wannier forms the Wannier states.
+bool loops_transport_only(const LoopArgs& a);
+// Orthonormalised Wannier states w from the transported bases in nu_buf (no-op without).
+cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s);
 
 }  // namespace bw

@@ -129,44 +129,6 @@ __host__ __device__ inline LoopSmem loop_layout(int p, int m) {
   return L;
 }
 
-// One Cholesky-QR pass on nu (p x m) with Gram scratch G (m x m).
-__device__ void cholqr_small(z64* nu, z64* G, int p, int m, int* flag) {
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int a = e / m, b = e - a * m;
-    z64 acc(0.0, 0.0);
-    for (int r = 0; r < p; ++r) cfma_conj(acc, nu[r * m + a], nu[r * m + b]);
-    G[e] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    for (int j = 0; j < m && ok; ++j) {
-      double d = G[j * m + j].re;
-      for (int k = 0; k < j; ++k) d -= abs2(G[j * m + k]);
-      if (!(d > 0.0)) { ok = 0; break; }
-      d = sqrt(d);
-      G[j * m + j] = z64(d, 0.0);
-      for (int i = j + 1; i < m; ++i) {
-        z64 s = G[i * m + j];
-        for (int k = 0; k < j; ++k) s = s - G[i * m + k] * conj(G[j * m + k]);
-        G[i * m + j] = (1.0 / d) * s;
-      }
-    }
-    *flag = ok;
-  }
-  __syncthreads();
-  if (!*flag) return;
-  for (int r = threadIdx.x; r < p; r += blockDim.x) {
-    z64* q = nu + r * m;
-    for (int j = 0; j < m; ++j) {
-      z64 y = conj(q[j]);
-      for (int k = 0; k < j; ++k) y = y - G[j * m + k] * conj(q[k]);
-      q[j] = conj((1.0 / G[j * m + j].re) * y);
-    }
-  }
-  __syncthreads();
-}
-
 __global__ void k_loops(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
@@ -174,7 +136,6 @@ __global__ void k_loops(LoopArgs a) {
   const LoopSmem L = loop_layout(p, m);
   z64* X = reinterpret_cast<z64*>(smem + L.X);
   z64* Y = reinterpret_cast<z64*>(smem + L.Y);
-  z64* G = reinterpret_cast<z64*>(smem + L.G);
   z64* lam = reinterpret_cast<z64*>(smem + L.lam);
   z64* vec = reinterpret_cast<z64*>(smem + L.vec);
   double* th = reinterpret_cast<double*>(smem + L.th);
@@ -182,7 +143,6 @@ __global__ void k_loops(LoopArgs a) {
   int* ord = reinterpret_cast<int*>(smem + L.ord);
   GeigShared* sh = reinterpret_cast<GeigShared*>(smem + L.sh);
   double* red = reinterpret_cast<double*>(smem + L.red);
-  int* flag = reinterpret_cast<int*>(red + 40);
 
   for (int i = blockIdx.x; i < a.N_t; i += gridDim.x) {
     const long long k0 = (long long)i * N;
@@ -268,16 +228,20 @@ __global__ void k_loops(LoopArgs a) {
     __syncthreads();
     z64* nx = Zm;  // scratch for nu_{j+1}
     for (int j = 0; j < N; ++j) {
-      cholqr_small(nu, G, p, m, flag);
-      cholqr_small(nu, G, p, m, flag);
-      const z64* Uk = a.U + (k0 + j) * (long long)n * p;
-      z64* w = a.w + ((long long)j * a.N_t + i) * (long long)n * m;
-      for (int e = tid; e < n * m; e += nt) {
-        const int r = e / m, c = e - r * m;
-        z64 acc(0.0, 0.0);
-        for (int q = 0; q < p; ++q) cfma(acc, Uk[r * p + q], nu[q * m + c]);
-        w[e] = acc;
+      // transport only; the sector basis of every base point is orthonormalised and
+      // lifted to Wannier states by k_wannier, in parallel over all k-points (any
+      // basis of the transported span is valid: the nested phases are gauge
+      // invariant).  Columns are rescaled to unit norm so that the product cannot
+      // drift in scale along the loop.
+      for (int c = tid; c < m; c += nt) {
+        double s2 = 0.0;
+        for (int r = 0; r < p; ++r) s2 += abs2(nu[r * m + c]);
+        const double inv = 1.0 / sqrt(s2);
+        for (int r = 0; r < p; ++r) nu[r * m + c] = inv * nu[r * m + c];
       }
+      __syncthreads();
+      z64* dst = a.nu_buf + ((long long)j * a.N_t + i) * (long long)p * m;
+      for (int e = tid; e < p * m; e += nt) dst[e] = nu[e];
       const z64* M = a.M + (k0 + j) * (long long)p * p;
       for (int e = tid; e < p * m; e += nt) {
         const int r = e / m, c = e - r * m;
@@ -290,6 +254,94 @@ __global__ void k_loops(LoopArgs a) {
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Wannier states of every (base point j, transverse index i): the transported sector
+// basis nu (p x m) orthonormalised by two Cholesky-QR passes (Gram matrix by the
+// whole CTA, Cholesky factor by one warp, triangular solves one row per thread),
+// then w = U(k_ij) nu.  One CTA per pair, all pairs independent.
+// ---------------------------------------------------------------------------
+// nu <- nu L^{-dagger} with G = nu^dagger nu = L L^dagger (L lower triangular, kept in
+// the lower triangle of G); *ok = 0 on breakdown.
+__device__ void cholqr_par(z64* nu, z64* G, int p, int m, int* ok) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  for (int e = tid; e < m * m; e += nt) {
+    const int x = e / m, y = e - x * m;
+    z64 acc(0.0, 0.0);
+    for (int r = 0; r < p; ++r) cfma_conj(acc, nu[r * m + x], nu[r * m + y]);
+    G[e] = acc;  // G[x][y] = nu_x^dag nu_y
+  }
+  __syncthreads();
+  if (tid < 32) {  // Cholesky by one warp, column by column, lanes along the rows
+    for (int j = 0; j < m; ++j) {
+      double part = 0.0;
+      for (int k = lane; k < j; k += 32) part += abs2(G[j * m + k]);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const double d2 = G[j * m + j].re - part;
+      if (!(d2 > 0.0) && lane == 0) *ok = 0;
+      const double d = sqrt(fmax(d2, 1e-300));
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        z64 v = G[i * m + j];
+        for (int k = 0; k < j; ++k) v = v - G[i * m + k] * conj(G[j * m + k]);
+        G[i * m + j] = (1.0 / d) * v;
+      }
+      __syncwarp();
+      if (lane == 0) G[j * m + j] = z64(d, 0.0);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // row q of nu: x L^dagger = q, i.e. L y = q^dagger (forward substitution), x = y^dagger
+  for (int r = tid; r < p; r += nt) {
+    z64* q = nu + r * m;
+    for (int j = 0; j < m; ++j) {
+      z64 y = conj(q[j]);
+      for (int k = 0; k < j; ++k) y = y - G[j * m + k] * conj(q[k]);
+      q[j] = conj((1.0 / G[j * m + j].re) * y);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_wannier(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, m = a.m, N = a.N, tid = threadIdx.x, nt = blockDim.x;
+  z64* nu = reinterpret_cast<z64*>(smem);  // p x m
+  z64* G = nu + p * m;                     // m x m
+  __shared__ int ok;
+  const long long K = (long long)N * a.N_t;
+  for (long long b = blockIdx.x; b < K; b += gridDim.x) {
+    const int j = int(b / a.N_t), i = int(b - (long long)j * a.N_t);
+    const z64* src = a.nu_buf + b * (long long)p * m;
+    for (int e = tid; e < p * m; e += nt) nu[e] = src[e];
+    if (tid == 0) ok = 1;
+    __syncthreads();
+    cholqr_par(nu, G, p, m, &ok);
+    cholqr_par(nu, G, p, m, &ok);
+    if (!ok && tid == 0) report(a.status, ST_ENOCONV, (long long)i * N + j, 0.0);
+    const z64* Uk = a.U + ((long long)i * N + j) * (long long)n * p;
+    z64* w = a.w + b * (long long)n * m;
+    for (int e = tid; e < n * m; e += nt) {
+      const int r = e / m, c = e - r * m;
+      z64 acc(0.0, 0.0);
+      for (int q = 0; q < p; ++q) cfma(acc, Uk[r * p + q], nu[q * m + c]);
+      w[e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s) {
+  const long long K = (long long)a.N * a.N_t;
+  if (K <= 0 || !a.nu_buf) return cudaSuccess;
+  const size_t sm = (size_t(a.p) * a.m + size_t(a.m) * a.m) * sizeof(z64);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_wannier, sm, cached);
+  if (e != cudaSuccess) return e;
+  const long long cap = 152LL * 8;
+  k_wannier<<<int(K < cap ? K : cap), 256, sm, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -596,6 +648,8 @@ static bool scan_nested_fit(const LoopArgs& a) {
 static int loop_threads(int p) { return p <= 4 ? 32 : (p <= 16 ? 64 : 128); }
 
 bool loops_form_overlaps(const LoopArgs& a) { return !a.unitarise && scan_loops_fit(a); }
+
+bool loops_transport_only(const LoopArgs& a) { return a.nested && !scan_loops_fit(a); }
 
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
   const long long K = (long long)a.N * a.N_t;

@@ -617,8 +617,21 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const size_t bGap = al256(size_t(K) * sizeof(double));
   const size_t bM = al256(size_t(K) * p_eff * p_eff * sizeof(z64));
   const size_t bW = kind == LoopKind::Nested ? al256(size_t(K) * n * m * sizeof(z64)) : 0;
+  bool transport_only = false;
+  if (kind == LoopKind::Nested) {
+    bw::LoopArgs q;
+    std::memset(&q, 0, sizeof(q));
+    q.n = n;
+    q.p = p_eff;
+    q.N = plane->N;
+    q.N_t = plane->N_t;
+    q.nested = 1;
+    q.m = m;
+    transport_only = bw::loops_transport_only(q);
+  }
+  const size_t bNu = transport_only ? al256(size_t(K) * p_eff * m * sizeof(z64)) : 0;
   const size_t bPso = kind == LoopKind::Spin ? al256(size_t(K) * sizeof(double)) : 0;
-  size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bPso + 4096;
+  size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bNu + bPso + 4096;
   // large n: per-k-point scratch of the tridiagonal solver, processed in waves
   const bool mx = prec == BW_MIXED;
   const size_t ts = mx ? sizeof(float) : sizeof(double);
@@ -649,6 +662,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   double* gap = reinterpret_cast<double*>(carve(ctx, bGap));
   z64* M = reinterpret_cast<z64*>(carve(ctx, bM));
   z64* w = bW ? reinterpret_cast<z64*>(carve(ctx, bW)) : nullptr;
+  z64* nu_buf = bNu ? reinterpret_cast<z64*>(carve(ctx, bNu)) : nullptr;
   double* psog = bPso ? reinterpret_cast<double*>(carve(ctx, bPso)) : nullptr;
   if ((st = upload(ctx, blob, dblob, s))) return st;
 
@@ -750,6 +764,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     la.m = m;
     la.wannier_gap_tol = o.wannier_gap_tol;
     la.w = w;
+    la.nu_buf = nu_buf;
     la.min_wannier_gap = min_wgap;
     la.nested_out = nested_out;
   }
@@ -759,6 +774,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   }
   BW_CUDA(bw::launch_loops(la, s), "loop kernel");
   prof_mark(ctx, s, "loops");
+  if (la.nu_buf) {
+    BW_CUDA(bw::launch_wannier(la, s), "Wannier-state kernel");
+    prof_mark(ctx, s, "wannier");
+  }
   if (kind == LoopKind::Nested) {
     BW_CUDA(bw::launch_nested(la, s), "nested kernel");
     prof_mark(ctx, s, "nested");
