@@ -152,4 +152,33 @@ __device__ __forceinline__ double block_min(double v, double* red) {
   return s;
 }
 
+// In-place lower Cholesky factor of the Hermitian p x p matrix G (row-major, lower
+// triangle read and overwritten: G = L L^dagger), by the first warp of the CTA,
+// column by column with the lanes along the rows.  *flag = 0 when a pivot is not
+// positive.  Every thread must call it; it ends with a block barrier.
+__device__ inline void chol_lower_warp(z64* G, int p, int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) *flag = 1;
+  __syncthreads();
+  if (tid < 32) {
+    for (int j = 0; j < p; ++j) {
+      double part = 0.0;
+      for (int k = lane; k < j; k += 32) part += abs2(G[j * p + k]);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const double d2 = G[j * p + j].re - part;
+      if (!(d2 > 0.0) && lane == 0) *flag = 0;
+      const double d = sqrt(fmax(d2, 1e-300));
+      for (int i = j + 1 + lane; i < p; i += 32) {
+        z64 v = G[i * p + j];
+        for (int k = 0; k < j; ++k) v = v - G[i * p + k] * conj(G[j * p + k]);
+        G[i * p + j] = (1.0 / d) * v;
+      }
+      __syncwarp();
+      if (lane == 0) G[j * p + j] = z64(d, 0.0);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace bw

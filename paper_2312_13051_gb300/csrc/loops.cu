@@ -265,7 +265,7 @@ __global__ void k_loops(LoopArgs a) {
 // nu <- nu L^{-dagger} with G = nu^dagger nu = L L^dagger (L lower triangular, kept in
 // the lower triangle of G); *ok = 0 on breakdown.
 __device__ void cholqr_par(z64* nu, z64* G, int p, int m, int* ok) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < m * m; e += nt) {
     const int x = e / m, y = e - x * m;
     z64 acc(0.0, 0.0);
@@ -273,25 +273,9 @@ __device__ void cholqr_par(z64* nu, z64* G, int p, int m, int* ok) {
     G[e] = acc;  // G[x][y] = nu_x^dag nu_y
   }
   __syncthreads();
-  if (tid < 32) {  // Cholesky by one warp, column by column, lanes along the rows
-    for (int j = 0; j < m; ++j) {
-      double part = 0.0;
-      for (int k = lane; k < j; k += 32) part += abs2(G[j * m + k]);
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const double d2 = G[j * m + j].re - part;
-      if (!(d2 > 0.0) && lane == 0) *ok = 0;
-      const double d = sqrt(fmax(d2, 1e-300));
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        z64 v = G[i * m + j];
-        for (int k = 0; k < j; ++k) v = v - G[i * m + k] * conj(G[j * m + k]);
-        G[i * m + j] = (1.0 / d) * v;
-      }
-      __syncwarp();
-      if (lane == 0) G[j * m + j] = z64(d, 0.0);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
+  __shared__ int chol_ok;
+  chol_lower_warp(G, m, &chol_ok);  // warp-parallel factor, ends with a barrier
+  if (!chol_ok && tid == 0) *ok = 0;
   // row q of nu: x L^dagger = q, i.e. L y = q^dagger (forward substitution), x = y^dagger
   for (int r = tid; r < p; r += nt) {
     z64* q = nu + r * m;

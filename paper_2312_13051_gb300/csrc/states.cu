@@ -112,23 +112,7 @@ __device__ void gram(const z64* Q, z64* G, int n, int p) {
 // Returns false when the Gram matrix is not positive definite.
 __device__ bool cholqr(z64* Q, z64* G, int n, int p, int* flag) {
   gram(Q, G, n, p);
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    for (int j = 0; j < p && ok; ++j) {
-      double d = G[j * p + j].re;
-      for (int k = 0; k < j; ++k) d -= abs2(G[j * p + k]);
-      if (!(d > 0.0)) { ok = 0; break; }
-      d = sqrt(d);
-      G[j * p + j] = z64(d, 0.0);
-      for (int i = j + 1; i < p; ++i) {
-        z64 s = G[i * p + j];
-        for (int k = 0; k < j; ++k) s = s - G[i * p + k] * conj(G[j * p + k]);
-        G[i * p + j] = (1.0 / d) * s;
-      }
-    }
-    *flag = ok;
-  }
-  __syncthreads();
+  chol_lower_warp(G, p, flag);
   if (!*flag) return false;
   // each row x of Q: solve x L^dagger = q, i.e. L y = q^dagger with x = y^dagger
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
