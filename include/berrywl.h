@@ -187,6 +187,19 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
                                        double* phases, double* pso_evals,
                                        double* min_pso_gap, double* min_gap, void* stream);
 
+/* Winding of the hybrid Wannier centres over the transverse direction (Sec. II B,
+ * Eq. 6: C = sum_n xbar_n(k_y = 2 pi) - sum_n xbar_n(k_y = 0), in units of the
+ * lattice constant).  For the rows of `phases` (N_t x p, as written by the loop
+ * entry points, theta in radians) s_i = sum_c theta[i][c] / 2pi, and the winding is
+ * sum_i wrap(s_{i+1} - s_i) over the cyclic transverse grid (row N_t - 1 steps to
+ * row 0), wrap(d) = d - rint(d).  It is the Chern number of the loop's bands (of the
+ * PSO sector for the spin-resolved loop) when the grid resolves each step of the
+ * summed centre to less than half a lattice constant; the result is an integer up to
+ * rounding.  phases: DEVICE.  sums: DEVICE, N_t doubles (may be NULL).  winding:
+ * DEVICE, one double.  Asynchronous on `stream`; no scratch memory. */
+bw_status bw_winding(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, double* sums,
+                     double* winding, void* stream);
+
 /* Allocation-free Wilson loop (no counterpart in the paper: it serves callers).
  * Some callers cannot let a library allocate device memory: programs that give all
  * device memory to their own pool under a hard cap, plugins running inside another

@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_spin_resolved_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane),
                                                    i32, vp, i32, i32, C.POINTER(bw_opts), vp,
                                                    vp, vp, vp, vp]),
+            "bw_winding": (i32, [vp, vp, i32, i32, vp, vp, vp]),
             "bw_wilson_loop_noalloc": (i32, [C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
                                              C.POINTER(bw_opts), vp, vp, vp, C.c_char_p,
                                              C.c_size_t]),
@@ -110,7 +111,7 @@ def exported_symbols():
     return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
             "bw_profile_read", "bw_build_hk",
             "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
-            "bw_spin_resolved_wilson_loop", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
+            "bw_spin_resolved_wilson_loop", "bw_winding", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
             "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
             "bw_server_poll", "bw_server_wait", "bw_server_outstanding"]
 
@@ -330,6 +331,25 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     if check:
         ctx.status()
     return ph, pso, pg, gap
+
+
+def winding(phases, ctx: Context | None = None, check=True, want_sums=False):
+    """Winding of the summed Wannier centres of ``phases`` (CUDA float64 N_t x p) over
+    the transverse grid (Eq. 6).  Returns a CUDA float64 scalar tensor, or
+    (winding, sums[N_t]) with ``want_sums``."""
+    import torch
+    ctx = ctx or context()
+    if not (phases.is_cuda and phases.dtype == torch.float64 and phases.is_contiguous()
+            and phases.dim() == 2):
+        raise BWError(1, "phases must be a contiguous CUDA float64 tensor of shape (N_t, p)")
+    Nt, p = phases.shape
+    w = _empty((), torch.float64, phases.device)
+    sums = _empty((Nt,), torch.float64, phases.device) if want_sums else None
+    ctx.check(ctx.lib.bw_winding(ctx.h, _ptr(phases), int(Nt), int(p), _ptr(sums), _ptr(w),
+                                 _stream_ptr()))
+    if check:
+        ctx.status()
+    return (w, sums) if want_sums else w
 
 
 def wilson_loop_noalloc(model, plane, p: int, precision: str = "fp64", out=None, **opts):

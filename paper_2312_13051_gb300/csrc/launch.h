@@ -199,6 +199,10 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);
 cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
                               cudaStream_t s);
 
+// Winding of the summed Wannier centres over the transverse direction (Eq. 6).
+cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,
+                           cudaStream_t s);
+
 cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);
 cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, bool* handled);

@@ -12,6 +12,8 @@
 //                Wannier states w = U(k_j) nu_j.
 //  - k_nested:   one CTA per base point: product of w(i+1)^dagger w(i) along the
 //                transverse direction (closed on i = 0) and its eigenphases.
+//  - k_winding:  the winding of the summed Wannier centres over the transverse
+//                direction (Eq. 6).
 #include <float.h>
 
 #include "geig.cuh"
@@ -665,6 +667,41 @@ cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
   cudaError_t e = set_smem_once(k_loops, L.total, cached);
   if (e != cudaSuccess) return e;
   k_loops<<<a.N_t, loop_threads(a.p), L.total, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Winding of the hybrid Wannier centres (Eq. 6): s_i = sum_c theta[i][c] / 2pi is the
+// total Wannier centre of row i in units of the lattice constant; the Chern (or
+// spin-Chern) number is its net change across the transverse period, accumulated
+// as sum_i wrap(s_{i+1} - s_i) over the cyclic grid (i = N_t - 1 steps to 0), where
+// wrap(d) = d - rint(d) takes each increment to [-1/2, 1/2].  One CTA; the block
+// sum runs in a fixed order, so the result is reproducible.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double wcc_row_sum(const double* phases, int i, int p) {
+  double s = 0.0;
+  for (int c = 0; c < p; ++c) s += phases[(long long)i * p + c];
+  return s / 6.283185307179586;
+}
+
+__global__ void k_winding(const double* phases, int Nt, int p, double* sums, double* winding) {
+  __shared__ double red[64];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) {
+    const double s0 = wcc_row_sum(phases, i, p);
+    const double s1 = wcc_row_sum(phases, i + 1 == Nt ? 0 : i + 1, p);
+    double d = s1 - s0;
+    d -= rint(d);
+    acc += d;
+    if (sums) sums[i] = s0;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *winding = acc;
+}
+
+cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,
+                           cudaStream_t s) {
+  k_winding<<<1, 256, 0, s>>>(phases, Nt, p, sums, winding);
   return cudaGetLastError();
 }
 

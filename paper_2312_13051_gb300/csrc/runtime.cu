@@ -922,6 +922,21 @@ bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64
   return BW_OK;
 }
 
+bw_status bw_winding(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, double* sums,
+                     double* winding, void* stream) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  if (N_t < 1 || p < 1) return fail(ctx, BW_EINVAL, "need N_t >= 1 and p >= 1 (N_t = %d, p = %d)", N_t, p);
+  if (!phases || !winding) return fail(ctx, BW_EINVAL, "phases or winding is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  begin_call(ctx, s);
+  prof_start(ctx, s);
+  BW_CUDA(bw::launch_winding(phases, N_t, p, sums, winding, s), "winding kernel");
+  prof_mark(ctx, s, "winding");
+  end_call(ctx, s);
+  return BW_OK;
+}
+
 bw_status bw_eigh_batched(bw_ctx* ctx, const void* H, const int32_t* n_per, int64_t batch,
                           int32_t n_vec, bw_precision prec, double* evals, void* evecs,
                           void* stream) {

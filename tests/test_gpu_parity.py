@@ -368,3 +368,26 @@ def test_eigh_batched_large_ragged(lib, ctx, precision, n_vec):
             assert np.abs(V.conj().T @ V - np.eye(n_vec)).max() <= 1e-12
         eo += n
         vo += n * n_vec
+
+
+# ---------------------------------------------------------------- winding (Eq. 6)
+def test_winding_parity(lib, ctx):
+    """bw_winding against the oracle's winding: loop outputs of the spin-Hall model
+    (total 0, sectors -1 / +1), Eq. 4 (+1), and seeded random phase tables, including
+    one row and one band."""
+    torch = _torch()
+    wl = I.config_spin_hall()
+    for sign in (-1, 1):
+        ph, _, _, _ = lib.spin_resolved_wilson_loop(wl.model, wl.plane, 2, wl.spin_op, sign, ctx=ctx)
+        w, sums = lib.winding(ph, ctx=ctx, want_sums=True)
+        ref = oracle.winding(ph.cpu().numpy())
+        assert abs(w.item() - ref) < 1e-12 and abs(w.item() - sign) < 1e-6
+        assert np.abs(sums.cpu().numpy() - ph.cpu().numpy().sum(axis=1) / (2 * np.pi)).max() < 1e-14
+    ph, _ = lib.wilson_loop(I.chern_eq4(), P(24, 24), 1, ctx=ctx)
+    assert abs(lib.winding(ph, ctx=ctx).item() - oracle.winding(ph.cpu().numpy())) < 1e-12
+    assert abs(lib.winding(ph, ctx=ctx).item() - 1) < 1e-6
+    rng = np.random.default_rng(11)
+    for Nt, p in ((1, 1), (7, 1), (300, 3), (1000, 16)):
+        th = rng.uniform(-np.pi, np.pi, size=(Nt, p))
+        w = lib.winding(torch.tensor(th, device="cuda"), ctx=ctx).item()
+        assert abs(w - oracle.winding(th)) < 1e-11, (Nt, p)
