@@ -373,6 +373,8 @@ def run_ours(args):
     pk = res["mixed"]["per_kernel"]
     if "overlaps" not in pk:      # formed inside the loop kernel
         flops["loops"] += flops["overlaps"]
+    if "states" not in pk:        # solved inside the loop kernel
+        flops["loops"] += flops["states"]
     dom = max(pk, key=pk.get)
     avg_ms = pk[dom] / args.steps
     achieved = flops[dom] / (avg_ms * 1e-3) / 1e12
@@ -416,6 +418,8 @@ def run_ours(args):
                "k_points_per_call": Ks}
         if "overlaps" not in sat_res["mixed"]["per_kernel"]:
             fl_s["loops"] += fl_s["overlaps"]
+        if "states" not in sat_res["mixed"]["per_kernel"]:
+            fl_s["loops"] += fl_s["states"]
         for prec, r in sat_res.items():
             pks = r["per_kernel"]
             d = max(pks, key=pks.get)

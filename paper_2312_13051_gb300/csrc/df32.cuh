@@ -107,4 +107,51 @@ __device__ __forceinline__ cdf operator*(df s, cdf b) { return cdf(s * b.re, s *
 // |a|^2
 __device__ __forceinline__ df abs2(cdf a) { return a.re * a.re + a.im * a.im; }
 
+// a b + c: the product exactly (hi part) plus its first-order terms, one TwoSum with
+// c and a final TwoSum; absolute error about 2^-46 (|a b| + |c|).
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const df s = df_two_sum(p, c.hi);
+  return df_two_sum(s.hi, s.lo + (e + c.lo));
+}
+
+// acc += a b and acc += conj(a) b in double-float.
+__device__ __forceinline__ void cfma(cdf& acc, cdf a, cdf b) {
+  acc.re = df_fma(a.re, b.re, acc.re);
+  acc.re = df_fma(-a.im, b.im, acc.re);
+  acc.im = df_fma(a.re, b.im, acc.im);
+  acc.im = df_fma(a.im, b.re, acc.im);
+}
+
+__device__ __forceinline__ void cfma_conj(cdf& acc, cdf a, cdf b) {
+  acc.re = df_fma(a.re, b.re, acc.re);
+  acc.re = df_fma(a.im, b.im, acc.re);
+  acc.im = df_fma(a.re, b.im, acc.im);
+  acc.im = df_fma(-a.im, b.re, acc.im);
+}
+
+// 1 / sqrt(a), a > 0: float estimate, one Newton step y <- y (3 - a y^2) / 2 in
+// double-float.
+__device__ __forceinline__ df df_rsqrt(df a) {
+  const float y0 = rsqrtf(a.hi);
+  const df y(y0, 0.f);
+  const df t = a * (y * y);  // ~1
+  const df corr = df(0.5f) * (df(3.f) - t);
+  return y * corr;
+}
+
+__device__ __forceinline__ cdf cdf_zero() { return cdf(df(0.f, 0.f), df(0.f, 0.f)); }
+
+// Warp shuffle of a complex double-float.
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
+  return cdf(df(__shfl_sync(0xffffffffu, v.re.hi, src), __shfl_sync(0xffffffffu, v.re.lo, src)),
+             df(__shfl_sync(0xffffffffu, v.im.hi, src), __shfl_sync(0xffffffffu, v.im.lo, src)));
+}
+
+__device__ __forceinline__ df shfl_xor_df(df v, int m) {
+  return df(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
 }  // namespace bw

@@ -39,6 +39,7 @@ struct StatesArgs {
   double* pso_evals;    // K x p (optional)
   double* pso_gap;      // K (optional)
   DevStatus* status;
+  int want_df;          // write U as complex double-float (states_df_eligible() holds)
 };
 
 struct EighArgs {
@@ -85,6 +86,7 @@ struct LoopArgs {
   double* min_wannier_gap;  // N_t (optional)
   double* nested_out;    // N x m
   DevStatus* status;
+  int u_df;              // U and w hold complex double-float (loops_accept_df() holds)
 };
 
 // Raises a kernel's dynamic shared-memory limit only when a launch needs more than
@@ -206,6 +208,9 @@ cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, do
 cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);
 cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, bool* handled);
+// True when the mixed-precision double-float states kernel (n = 4) can serve the
+// problem; with want_df set it writes U as complex double-float.
+bool states_df_eligible(const StatesArgs& a, int p_out);
 cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s);
 // True when the loop kernel forms the overlaps itself (launch_overlaps then does nothing).
 bool loops_form_overlaps(const LoopArgs& a);
@@ -215,6 +220,14 @@ cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s);
 // True when the nested loop kernel only transports the sector bases (into nu_buf)
 // and launch_wannier forms the Wannier states.
 bool loops_transport_only(const LoopArgs& a);
+// True when the scan kernels serve both loops (no unitarised overlaps): they then
+// also accept U in complex double-float (u_df).
+bool loops_accept_df(const LoopArgs& a);
+// Mixed precision, n = 4, p = 2, N <= 64 with the scan kernels: one kernel solves each
+// loop's states and runs the loop (replaces launch_states_small + launch_loops; sa as
+// for launch_states_small with want_df, a as for launch_loops with u_df).
+bool loops_fused_eligible(const LoopArgs& a);
+cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s);
 // Orthonormalised Wannier states w from the transported bases in nu_buf (no-op without).
 cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s);
 

@@ -16,9 +16,11 @@
 //                direction (Eq. 6).
 #include <float.h>
 
+#include "df32.cuh"
 #include "geig.cuh"
 #include "jacobi.cuh"
 #include "launch.h"
+#include "quad.cuh"
 
 namespace bw {
 
@@ -388,10 +390,34 @@ __global__ void k_nested(LoopArgs a) {
 constexpr int SCAN_P_MAX = 4;
 constexpr size_t SCAN_SMEM_MAX = 96 * 1024;
 
+// Element arithmetic of the scan kernels: complex FP64 (z64), or complex
+// double-float (cdf) on the FP32 pipe for the mixed-precision few-band path, whose
+// states arrive as double-float.  Eigenvalues of the final small matrices are taken
+// in FP64 either way.
+template <typename E>
+struct Arith;
+template <>
+struct Arith<z64> {
+  using R = double;
+  __device__ static z64 zero() { return z64(0.0, 0.0); }
+  __device__ static z64 from(z64 v) { return v; }
+  __device__ static z64 to64(z64 v) { return v; }
+  __device__ static double rsqrt(double x) { return 1.0 / sqrt(x); }
+};
+template <>
+struct Arith<cdf> {
+  using R = df;
+  __device__ static cdf zero() { return cdf_zero(); }
+  __device__ static cdf from(z64 v) { return cdf_from(v); }
+  __device__ static z64 to64(cdf v) { return cdf_to_z64(v); }
+  __device__ static df rsqrt(df x) { return df_rsqrt(x); }
+};
+
 // In-place inclusive prefix product over L matrices of size q x q, later index on the
 // left: on return S[j] = A_j A_{j-1} ... A_0.  T is scratch of the same size.
 // Returns the buffer holding the result (S or T).
-__device__ z64* prefix_products(z64* S, z64* T, int L, int q) {
+template <typename E>
+__device__ E* prefix_products(E* S, E* T, int L, int q) {
   const int qq = q * q;
   for (int d = 1; d < L; d <<= 1) {
     for (int e = threadIdx.x; e < L * qq; e += blockDim.x) {
@@ -399,15 +425,15 @@ __device__ z64* prefix_products(z64* S, z64* T, int L, int q) {
       if (j < d) {
         T[e] = S[e];
       } else {
-        const z64* A = S + j * qq;
-        const z64* B = S + (j - d) * qq;
-        z64 acc(0.0, 0.0);
+        const E* A = S + j * qq;
+        const E* B = S + (j - d) * qq;
+        E acc = Arith<E>::zero();
         for (int k = 0; k < q; ++k) cfma(acc, A[r * q + k], B[k * q + c]);
         T[e] = acc;
       }
     }
     __syncthreads();
-    z64* t = S; S = T; T = t;
+    E* t = S; S = T; T = t;
   }
   return S;
 }
@@ -467,14 +493,21 @@ __device__ void nested_sector(const LoopArgs& a, const double* th, int p, int m,
   }
 }
 
-__global__ void k_loops_scan(LoopArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// One loop (transverse index i) of the scan kernels: overlaps from the loop's states
+// Ul (N x n x p, global or shared memory), prefix products, eigenphases and, for the
+// nested loop, the transported sector bases and Wannier states.  gl / pgl: the
+// loop's N direct / PSO gaps (may be NULL).  Every thread of the CTA calls it.
+template <typename E>
+__device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const double* gl,
+                              const double* pgl, unsigned char* smem) {
+  using A = Arith<E>;
   const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
   const int m = a.nested ? a.m : 1;
   const ScanSmem Z = scan_layout(N, p, a.nested ? N * p * m : 1);
-  z64* S = reinterpret_cast<z64*>(smem + Z.S);
-  z64* T = reinterpret_cast<z64*>(smem + Z.T);
-  z64* Nu = reinterpret_cast<z64*>(smem + Z.Nu);
+  E* S = reinterpret_cast<E*>(smem + Z.S);
+  E* T = reinterpret_cast<E*>(smem + Z.T);
+  E* Nu = reinterpret_cast<E*>(smem + Z.Nu);
+  E* wg = reinterpret_cast<E*>(a.w);
   z64* X = reinterpret_cast<z64*>(smem + Z.X);
   z64* Y = reinterpret_cast<z64*>(smem + Z.Y);
   z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
@@ -485,13 +518,13 @@ __global__ void k_loops_scan(LoopArgs a) {
   GeigShared* sh = reinterpret_cast<GeigShared*>(smem + Z.sh);
   double* red = reinterpret_cast<double*>(smem + Z.red);
   const int pp = p * p;
-  for (int i = blockIdx.x; i < a.N_t; i += gridDim.x) {
+  {
     const long long k0 = (long long)i * N;
     if (a.min_gap || a.min_pso_gap) {
       double g = INFINITY, gp = INFINITY;
       for (int j = tid; j < N; j += nt) {
-        if (a.gap) g = fmin(g, a.gap[k0 + j]);
-        if (a.pso_gap) gp = fmin(gp, a.pso_gap[k0 + j]);
+        if (gl) g = fmin(g, gl[j]);
+        if (pgl) gp = fmin(gp, pgl[j]);
       }
       g = block_min(g, red);
       gp = block_min(gp, red);
@@ -502,21 +535,21 @@ __global__ void k_loops_scan(LoopArgs a) {
     }
     if (a.unitarise) {
       const z64* Mg = a.M + k0 * pp;
-      for (int e = tid; e < N * pp; e += nt) S[e] = Mg[e];
+      for (int e = tid; e < N * pp; e += nt) S[e] = A::from(Mg[e]);
     } else {  // the overlaps of this loop, M_j = U(k_{j+1})^dagger U(k_j), closing on j = 0
       for (int e = tid; e < N * pp; e += nt) {
         const int jj = e / pp, rc = e - jj * pp, r = rc / p, c = rc - r * p;
-        const z64* Uh = a.U + (k0 + jj) * (long long)n * p;
-        const z64* Un = a.U + (k0 + (jj + 1 == N ? 0 : jj + 1)) * (long long)n * p;
-        z64 acc(0.0, 0.0);
+        const E* Uh = Ul + jj * (long long)n * p;
+        const E* Un = Ul + (jj + 1 == N ? 0 : jj + 1) * (long long)n * p;
+        E acc = A::zero();
         for (int q = 0; q < n; ++q) cfma_conj(acc, Un[q * p + r], Uh[q * p + c]);
         S[e] = acc;
       }
     }
     __syncthreads();
     // P[j] = M_j ... M_0; the loop matrix is P[N-1]
-    z64* Pf = prefix_products(S, T, N, p);
-    for (int e = tid; e < pp; e += nt) X[e] = Pf[(N - 1) * pp + e];
+    E* Pf = prefix_products(S, T, N, p);
+    for (int e = tid; e < pp; e += nt) X[e] = A::to64(Pf[(N - 1) * pp + e]);
     __syncthreads();
     if (p == 2) {  // closed form: the general solver's serial QR sweeps dominate at p = 2
       if (tid == 0) eig2_closed(X, 2, lam, Y, a.nested != 0);
@@ -530,33 +563,33 @@ __global__ void k_loops_scan(LoopArgs a) {
     rank_sort(th, p, ord);
     for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
     __syncthreads();
-    if (!a.nested) continue;
+    if (!a.nested) return;
     nested_sector(a, th, p, m, key, ord, red, i, k0);
     // nu_j = P[j-1] nu_0 (nu_0 = Y[:, sector]), one thread per base point j:
     // normalise the columns, then modified Gram-Schmidt (m <= SCAN_P_MAX)
     for (int j = tid; j < N; j += nt) {
-      z64* nu = Nu + (size_t)j * p * m;
+      E* nu = Nu + (size_t)j * p * m;
       for (int r = 0; r < p; ++r)
         for (int c = 0; c < m; ++c) {
           const int col = ord[a.first + c];
-          z64 acc(0.0, 0.0);
+          E acc = A::zero();
           if (j == 0) {
-            acc = Y[r * p + col];
+            acc = A::from(Y[r * p + col]);
           } else {
-            const z64* P = Pf + (size_t)(j - 1) * pp;
-            for (int q = 0; q < p; ++q) cfma(acc, P[r * p + q], Y[q * p + col]);
+            const E* P = Pf + (size_t)(j - 1) * pp;
+            for (int q = 0; q < p; ++q) cfma(acc, P[r * p + q], A::from(Y[q * p + col]));
           }
           nu[r * m + c] = acc;
         }
       for (int c = 0; c < m; ++c) {
         for (int c2 = 0; c2 < c; ++c2) {
-          z64 d(0.0, 0.0);
+          E d = A::zero();
           for (int r = 0; r < p; ++r) cfma_conj(d, nu[r * m + c2], nu[r * m + c]);
           for (int r = 0; r < p; ++r) nu[r * m + c] = nu[r * m + c] - nu[r * m + c2] * d;
         }
-        double s = 0.0;
-        for (int r = 0; r < p; ++r) s += abs2(nu[r * m + c]);
-        s = 1.0 / sqrt(s);
+        typename A::R s = abs2(nu[c]);
+        for (int r = 1; r < p; ++r) s = s + abs2(nu[r * m + c]);
+        s = A::rsqrt(s);
         for (int r = 0; r < p; ++r) nu[r * m + c] = s * nu[r * m + c];
       }
     }
@@ -564,25 +597,156 @@ __global__ void k_loops_scan(LoopArgs a) {
     // Wannier states w(j, i) = U(k_j) nu_j
     for (int e = tid; e < N * n * m; e += nt) {
       const int j = e / (n * m), rc2 = e - j * n * m, r = rc2 / m, c = rc2 - r * m;
-      const z64* Uk = a.U + (k0 + j) * (long long)n * p;
-      const z64* nu = Nu + (size_t)j * p * m;
-      z64 acc(0.0, 0.0);
+      const E* Uk = Ul + j * (long long)n * p;
+      const E* nu = Nu + (size_t)j * p * m;
+      E acc = A::zero();
       for (int q = 0; q < p; ++q) cfma(acc, Uk[r * p + q], nu[q * m + c]);
-      a.w[((long long)j * a.N_t + i) * n * m + rc2] = acc;
+      wg[((long long)j * a.N_t + i) * n * m + rc2] = acc;
     }
     __syncthreads();
   }
 }
 
+template <typename E>
+__global__ void k_loops_scan(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const E* Ug = reinterpret_cast<const E*>(a.U);
+  for (int i = blockIdx.x; i < a.N_t; i += gridDim.x) {
+    const long long k0 = (long long)i * a.N;
+    scan_one_loop<E>(a, i, Ug + k0 * a.n * a.p, a.gap ? a.gap + k0 : nullptr,
+                     a.pso_gap ? a.pso_gap + k0 : nullptr, smem);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision, four bands, two occupied, N <= 64: one CTA per loop solves the
+// loop's N k-points (four lanes each, quad_df_occupied: double-float H(k), FP32
+// Jacobi, double-float Newton refinement) into shared memory and runs the scan loop
+// on them, so that the states never leave the SM.  The Bloch phases of the loop
+// factor as exp(i 2pi (origin.R + (i trans.R mod N_t) / N_t)) exp(i 2pi (j loop.R
+// mod N) / N): one table of N entries and one factor per translation, per CTA.
+// ---------------------------------------------------------------------------
+constexpr int FUSED_THREADS = 256;
+
+struct FusedSmem {
+  size_t U, g, cache, tab, rowf, lR, total;
+};
+
+__host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int nR) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  FusedSmem F;
+  size_t o = Z.total;
+  F.U = o; o = al(o + size_t(N) * 4 * 2 * sizeof(cdf));
+  F.g = o; o = al(o + size_t(N) * sizeof(double));
+  F.cache = o; o = al(o + size_t(nR) * (FUSED_THREADS / 4) * sizeof(cdf));
+  F.tab = o; o = al(o + size_t(N) * sizeof(cdf));
+  F.rowf = o; o = al(o + size_t(nR) * sizeof(cdf));
+  F.lR = o; o = al(o + size_t(nR) * sizeof(int));
+  F.total = o;
+  return F;
+}
+
+__global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa, LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevModel& md = sa.model;
+  const int N = a.N, Nt = a.N_t, nR = md.n_R, tid = threadIdx.x, nt = blockDim.x;
+  constexpr int KPB = FUSED_THREADS / 4;
+  const ScanSmem Z = scan_layout(N, 2, a.nested ? N * 2 * a.m : 1);
+  const FusedSmem F = fused_layout(Z, N, nR);
+  cdf* Us = reinterpret_cast<cdf*>(smem + F.U);
+  double* gs = reinterpret_cast<double*>(smem + F.g);
+  cdf* cache = reinterpret_cast<cdf*>(smem + F.cache);
+  cdf* tab = reinterpret_cast<cdf*>(smem + F.tab);
+  cdf* rowf = reinterpret_cast<cdf*>(smem + F.rowf);
+  int* lR = reinterpret_cast<int*>(smem + F.lR);
+  for (int m = tid; m < N; m += nt) {
+    double sn, cs;
+    sincospi(2.0 * double(m) / double(N), &sn, &cs);
+    tab[m] = cdf_from(z64(cs, sn));
+  }
+  const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
+  const bool active = kl < N;
+  const int j = active ? kl : N - 1;  // idle groups recompute the last k-point
+  for (int i = blockIdx.x; i < Nt; i += gridDim.x) {
+    for (int r = tid; r < nR; r += nt) {
+      const int* Rv = md.Rv + 3 * r;
+      double x = 0.0;
+      int lq = 0, tq = 0;
+      for (int dd = 0; dd < 3; ++dd) {
+        x += sa.plane.origin[dd] * double(Rv[dd]);
+        lq += int(sa.plane.loop_dir[dd]) * Rv[dd];
+        tq += int(sa.plane.trans_dir[dd]) * Rv[dd];
+      }
+      x += double(pmod((long long)i * tq, Nt)) / double(Nt);
+      double sn, cs;
+      sincospi(2.0 * x, &sn, &cs);
+      rowf[r] = cdf_from(z64(cs, sn));
+      lR[r] = lq;
+    }
+    __syncthreads();
+    for (int r = l; r < nR; r += 4) cache[r * KPB + kl] = rowf[r] * tab[pmod((long long)j * lR[r], N)];
+    __syncwarp();
+    // row l of H(k) in double-float
+    cdf Hr[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Hr[c] = cdf_zero();
+    for (int e = sa.row_ptr[l]; e < sa.row_ptr[l + 1]; ++e) {
+      cdf acc = cdf_zero();
+      for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h) {
+        const float* t4 = md.hop_tdf + 4 * h;
+        cfma(acc, cdf(df(t4[0], t4[1]), df(t4[2], t4[3])), cache[md.hop_r[h] * KPB + kl]);
+      }
+      const int col = md.ent_col[e];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c == col) Hr[c] = acc;
+    }
+    cdf Qf[2];
+    double gap;
+    const int sweeps = quad_df_occupied(Hr, l, base, sa.max_sweeps, Qf[0], Qf[1], gap);
+    if (active) {
+      Us[(j * 4 + l) * 2] = Qf[0];
+      Us[(j * 4 + l) * 2 + 1] = Qf[1];
+      if (l == 0) {
+        const long long k = (long long)i * N + j;
+        gs[j] = gap;
+        if (sweeps < 0) report(sa.status, ST_ENOCONV, k, 0.0);
+        if (!(gap > sa.gap_tol)) report(sa.status, ST_EGAP, k, gap);
+      }
+    }
+    __syncthreads();
+    scan_one_loop<cdf>(a, i, Us, gs, nullptr, smem);
+    __syncthreads();
+  }
+}
+
+bool loops_fused_eligible(const LoopArgs& a) {
+  return a.n == 4 && a.p == 2 && a.N >= 1 && 4 * a.N <= FUSED_THREADS && loops_accept_df(a);
+}
+
+cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s) {
+  if (a.N_t <= 0) return cudaSuccess;
+  const ScanSmem Z = scan_layout(a.N, 2, a.nested ? a.N * 2 * a.m : 1);
+  const FusedSmem F = fused_layout(Z, a.N, sa.model.n_R);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_loops_fused_df, F.total, cached);
+  if (e != cudaSuccess) return e;
+  k_loops_fused_df<<<a.N_t, FUSED_THREADS, F.total, s>>>(sa, a);
+  return cudaGetLastError();
+}
+
 // Nested loop for small m: one CTA per base point, all Wannier states of the base
 // point in shared memory, overlaps in parallel, product by prefix scan.
+template <typename E>
 __global__ void k_nested_scan(LoopArgs a) {
+  using A = Arith<E>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, m = a.m, Nt = a.N_t, tid = threadIdx.x, nt = blockDim.x;
   const ScanSmem Z = scan_layout(Nt, m, Nt * n * m);
-  z64* S = reinterpret_cast<z64*>(smem + Z.S);
-  z64* T = reinterpret_cast<z64*>(smem + Z.T);
-  z64* Wn = reinterpret_cast<z64*>(smem + Z.Nu);
+  E* S = reinterpret_cast<E*>(smem + Z.S);
+  E* T = reinterpret_cast<E*>(smem + Z.T);
+  E* Wn = reinterpret_cast<E*>(smem + Z.Nu);
   z64* X = reinterpret_cast<z64*>(smem + Z.X);
   z64* Y = reinterpret_cast<z64*>(smem + Z.Y);
   z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
@@ -592,21 +756,21 @@ __global__ void k_nested_scan(LoopArgs a) {
   GeigShared* sh = reinterpret_cast<GeigShared*>(smem + Z.sh);
   const int mm2 = m * m, nm = n * m;
   for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
-    const z64* wj = a.w + (long long)j * Nt * nm;
+    const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * nm;
     for (int e = tid; e < Nt * nm; e += nt) Wn[e] = wj[e];
     __syncthreads();
     // A_i = w(i+1)^dagger w(i), closed on i = 0
     for (int e = tid; e < Nt * mm2; e += nt) {
       const int i = e / mm2, rc = e - i * mm2, r = rc / m, c = rc - r * m;
-      const z64* wa = Wn + (size_t)i * nm;
-      const z64* wb = Wn + (size_t)(i + 1 == Nt ? 0 : i + 1) * nm;
-      z64 acc(0.0, 0.0);
+      const E* wa = Wn + (size_t)i * nm;
+      const E* wb = Wn + (size_t)(i + 1 == Nt ? 0 : i + 1) * nm;
+      E acc = A::zero();
       for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q * m + r], wa[q * m + c]);
       S[e] = acc;
     }
     __syncthreads();
-    z64* Pf = prefix_products(S, T, Nt, m);
-    for (int e = tid; e < mm2; e += nt) X[e] = Pf[(Nt - 1) * mm2 + e];
+    E* Pf = prefix_products(S, T, Nt, m);
+    for (int e = tid; e < mm2; e += nt) X[e] = A::to64(Pf[(Nt - 1) * mm2 + e]);
     __syncthreads();
     const int rc = geig(X, Y, m, m, false, lam, vec, sh);
     if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, j, 0.0);
@@ -637,6 +801,10 @@ bool loops_form_overlaps(const LoopArgs& a) { return !a.unitarise && scan_loops_
 
 bool loops_transport_only(const LoopArgs& a) { return a.nested && !scan_loops_fit(a); }
 
+bool loops_accept_df(const LoopArgs& a) {
+  return !a.unitarise && scan_loops_fit(a) && (!a.nested || scan_nested_fit(a));
+}
+
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
   const long long K = (long long)a.N * a.N_t;
   if (K <= 0 || loops_form_overlaps(a)) return cudaSuccess;
@@ -656,10 +824,17 @@ cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
   if (a.N_t <= 0) return cudaSuccess;
   if (scan_loops_fit(a)) {
     const ScanSmem Z = scan_layout(a.N, a.p, a.nested ? a.N * a.p * a.m : 1);
+    if (a.u_df) {
+      static size_t cached_df = 0;
+      cudaError_t e = set_smem_once(k_loops_scan<cdf>, Z.total, cached_df);
+      if (e != cudaSuccess) return e;
+      k_loops_scan<cdf><<<a.N_t, 128, Z.total, s>>>(a);
+      return cudaGetLastError();
+    }
     static size_t cached_scan = 0;
-    cudaError_t e = set_smem_once(k_loops_scan, Z.total, cached_scan);
+    cudaError_t e = set_smem_once(k_loops_scan<z64>, Z.total, cached_scan);
     if (e != cudaSuccess) return e;
-    k_loops_scan<<<a.N_t, 128, Z.total, s>>>(a);
+    k_loops_scan<z64><<<a.N_t, 128, Z.total, s>>>(a);
     return cudaGetLastError();
   }
   const LoopSmem L = loop_layout(a.p, a.nested ? a.m : 1);
@@ -709,10 +884,17 @@ cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
   if (scan_nested_fit(a)) {
     const ScanSmem Z = scan_layout(a.N_t, a.m, a.N_t * a.n * a.m);
+    if (a.u_df) {
+      static size_t cached_df = 0;
+      cudaError_t e = set_smem_once(k_nested_scan<cdf>, Z.total, cached_df);
+      if (e != cudaSuccess) return e;
+      k_nested_scan<cdf><<<a.N, 128, Z.total, s>>>(a);
+      return cudaGetLastError();
+    }
     static size_t cached_scan = 0;
-    cudaError_t e = set_smem_once(k_nested_scan, Z.total, cached_scan);
+    cudaError_t e = set_smem_once(k_nested_scan<z64>, Z.total, cached_scan);
     if (e != cudaSuccess) return e;
-    k_nested_scan<<<a.N, 128, Z.total, s>>>(a);
+    k_nested_scan<z64><<<a.N, 128, Z.total, s>>>(a);
     return cudaGetLastError();
   }
   const LoopSmem L = loop_layout(a.m, 1);

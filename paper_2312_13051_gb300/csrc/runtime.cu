@@ -691,8 +691,27 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   sa.U = U;
   sa.gap = gap;
   sa.status = ctx->status;
+  // Mixed precision with four bands and the scan loop kernels: states, overlaps and
+  // loop products in double-float on the FP32 pipe (U and w as complex double-float)
+  bool use_df = false, fused = false;
+  if (!large && sa.mixed && kind != LoopKind::Spin) {
+    bw::LoopArgs q;
+    std::memset(&q, 0, sizeof(q));
+    q.n = n;
+    q.p = p_eff;
+    q.N = plane->N;
+    q.N_t = plane->N_t;
+    q.unitarise = o.unitarise;
+    q.nested = kind == LoopKind::Nested;
+    q.m = m;
+    use_df = bw::loops_accept_df(q) && bw::states_df_eligible(sa, p_eff);
+    fused = use_df && bw::loops_fused_eligible(q);
+  }
+  sa.want_df = use_df ? 1 : 0;
   prof_start(ctx, s);
-  if (!large) {
+  if (fused) {
+    // states are solved inside the loop kernel below
+  } else if (!large) {
     BW_CUDA(bw::launch_states_small(sa, p_eff, s), "states kernel");
   } else {
     bw::LargeArgs lg;
@@ -739,7 +758,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
       }
     }
   }
-  if (!large) prof_mark(ctx, s, "states");
+  if (!large && !fused) prof_mark(ctx, s, "states");
 
   bw::LoopArgs la;
   std::memset(&la, 0, sizeof(la));
@@ -757,6 +776,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.min_gap = min_gap;
   la.min_pso_gap = min_pso_gap;
   la.status = ctx->status;
+  la.u_df = use_df ? 1 : 0;
   if (kind == LoopKind::Nested) {
     la.nested = 1;
     la.cut = cut;
@@ -768,11 +788,15 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     la.min_wannier_gap = min_wgap;
     la.nested_out = nested_out;
   }
-  if (!bw::loops_form_overlaps(la)) {
-    BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
-    prof_mark(ctx, s, "overlaps");
+  if (fused) {
+    BW_CUDA(bw::launch_loops_fused_df(sa, la, s), "fused states and loop kernel");
+  } else {
+    if (!bw::loops_form_overlaps(la)) {
+      BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
+      prof_mark(ctx, s, "overlaps");
+    }
+    BW_CUDA(bw::launch_loops(la, s), "loop kernel");
   }
-  BW_CUDA(bw::launch_loops(la, s), "loop kernel");
   prof_mark(ctx, s, "loops");
   if (la.nu_buf) {
     BW_CUDA(bw::launch_wannier(la, s), "Wannier-state kernel");

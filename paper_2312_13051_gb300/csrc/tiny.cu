@@ -13,16 +13,10 @@
 #include <float.h>
 
 #include "launch.h"
+#include "quad.cuh"
 
 namespace bw {
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T teps();
-template <>
-__device__ __forceinline__ double teps<double>() { return 2.220446049250313e-16; }
-template <>
-__device__ __forceinline__ float teps<float>() { return 1.1920929e-7f; }
 
 // Serial cyclic Jacobi on a Hermitian NN x NN matrix held in registers; V collects
 // the rotations (same rotation formula and skip test as the block solver).  Returns the sweeps
@@ -117,15 +111,6 @@ constexpr int TINY_THREADS = 32;
 // (w^m = w^{B (m / B)} w^{m mod B}, B ~ sqrt(M)), so that long grids keep the
 // shared memory per CTA small.
 constexpr int TAB_SPLIT = 512;
-
-__device__ __forceinline__ int pmod(long long x, int m) {
-  long long r = x % m;
-  return int(r < 0 ? r + m : r);
-}
-
-struct TabShape {
-  int B, H;  // low-level entries (w^0 .. w^{B-1}), high-level entries (w^{0}, w^{B}, ...)
-};
 
 __host__ __device__ inline TabShape tab_shape(int M) {
   if (M <= TAB_SPLIT) return {M, 0};
@@ -331,90 +316,6 @@ k_states_tiny(StatesArgs a, int use_tab) {
 // ---------------------------------------------------------------------------
 constexpr int QUAD_THREADS = 128;  // 32 k-points per CTA
 
-__device__ __forceinline__ z64 shfl_z(z64 v, int src) {
-  return z64(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
-}
-
-// x[i] for a runtime i in [0, 4) without dynamic register indexing.
-__device__ __forceinline__ z64 sel4(const z64 (&x)[4], int i) {
-  z64 r = x[0];
-  if (i == 1) r = x[1];
-  if (i == 2) r = x[2];
-  if (i == 3) r = x[3];
-  return r;
-}
-
-// Rotation of the Hermitian 2 x 2 block (a, b; conj b, d): c, s e^{i phi} and t as in
-// the one-thread solver; false when the off-diagonal entry is negligible.
-__device__ __forceinline__ bool quad_angle(double a, double d, z64 b, double& c, z64& sc, double& t,
-                                           double& ab) {
-  ab = sqrt(abs2(b));
-  if (!(ab > 4.0 * teps<double>() * sqrt(fabs(a) * fabs(d)) && ab > 0.0)) return false;
-  const double tau = (d - a) / (2.0 * ab);
-  t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  const double s = t * c / ab;
-  sc = z64(s * b.re, s * b.im);
-  return true;
-}
-
-template <int R>
-__device__ __forceinline__ bool quad_round(z64 (&Ar)[4], z64 (&Vr)[4], int l, int base) {
-  constexpr int Q = R == 1 ? 2 : 1;          // a lane of the other pair is l ^ Q
-  constexpr int A0 = 0, A1 = R;              // pair containing index 0
-  constexpr int B0 = R == 1 ? 2 : 1, B1 = R == 3 ? 2 : 3;  // the other pair
-  const int partner = l ^ R;
-  const bool is_p = l < partner;
-  const double own_d = sel4(Ar, l).re;
-  const double par_d = __shfl_sync(0xffffffffu, own_d, base + partner);
-  const z64 bo = sel4(Ar, partner);
-  const z64 b = is_p ? bo : conj(bo);        // A[p][q] from either row (exact Hermitian storage)
-  const double a = is_p ? own_d : par_d, d = is_p ? par_d : own_d;
-  double c = 1.0, t = 0.0, ab = 0.0;
-  z64 sc(0.0, 0.0);
-  const bool rot = quad_angle(a, d, b, c, sc, t, ab);
-  // rows: own row with the partner's
-  z64 other[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) other[k] = shfl_z(Ar[k], base + partner);
-  if (rot) {
-    const z64 beta = is_p ? z64(-sc.re, -sc.im) : conj(sc);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) Ar[k] = c * Ar[k] + beta * other[k];
-  }
-  // columns: both rotations of the round on the own row of A and of V
-  const double c2 = __shfl_sync(0xffffffffu, c, base + (l ^ Q));
-  const z64 sc2 = shfl_z(sc, base + (l ^ Q));
-  const bool mine_a = (l == A0 || l == A1);
-  const double cA = mine_a ? c : c2, cB = mine_a ? c2 : c;
-  const z64 sA = mine_a ? sc : sc2, sB = mine_a ? sc2 : sc;
-  {
-    const z64 ap = Ar[A0], aq = Ar[A1];
-    Ar[A0] = cA * ap - aq * conj(sA);
-    Ar[A1] = ap * sA + cA * aq;
-    const z64 vp = Vr[A0], vq = Vr[A1];
-    Vr[A0] = cA * vp - vq * conj(sA);
-    Vr[A1] = vp * sA + cA * vq;
-  }
-  {
-    const z64 ap = Ar[B0], aq = Ar[B1];
-    Ar[B0] = cB * ap - aq * conj(sB);
-    Ar[B1] = ap * sB + cB * aq;
-    const z64 vp = Vr[B0], vq = Vr[B1];
-    Vr[B0] = cB * vp - vq * conj(sB);
-    Vr[B1] = vp * sB + cB * vq;
-  }
-  if (rot) {  // the annihilated entry and the new diagonal, as in the one-thread solver
-    const z64 dnew(is_p ? a - t * ab : d + t * ab, 0.0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k == partner) Ar[k] = z64(0.0, 0.0);
-      if (k == l) Ar[k] = dnew;
-    }
-  }
-  return rot;
-}
-
 template <int PP>
 __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -473,36 +374,7 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
     for (int c = 0; c < 4; ++c)
       if (c == col) Ar[c] = acc;
   }
-  double fro = 0.0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) fro += abs2(Ar[c]);
-  fro += __shfl_xor_sync(0xffffffffu, fro, 1);
-  fro += __shfl_xor_sync(0xffffffffu, fro, 2);
-  const double eps = teps<double>();
-  const double tol2 = 64.0 * eps * eps * fro;
-  int sweeps = -1;
-  for (int sweep = 0; sweep <= a.max_sweeps; ++sweep) {
-    double off = 0.0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c != l) off += abs2(Ar[c]);
-    off += __shfl_xor_sync(0xffffffffu, off, 1);
-    off += __shfl_xor_sync(0xffffffffu, off, 2);
-    if (off <= tol2 || fro == 0.0) {
-      sweeps = sweep;
-      break;
-    }
-    if (sweep == a.max_sweeps) break;
-    int rot = quad_round<1>(Ar, Vr, l, base);
-    rot |= quad_round<2>(Ar, Vr, l, base);
-    rot |= quad_round<3>(Ar, Vr, l, base);
-    rot |= __shfl_xor_sync(0xffffffffu, rot, 1);
-    rot |= __shfl_xor_sync(0xffffffffu, rot, 2);
-    if (!rot) {
-      sweeps = sweep + 1;
-      break;
-    }
-  }
+  const int sweeps = quad_jacobi(Ar, Vr, l, base, a.max_sweeps);
   // eigenvalues of the group, ascending (stable)
   const double own = sel4(Ar, l).re;
   double lam[4];
@@ -539,6 +411,113 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision, four lanes per k-point (n = 4, p = 2, no spin split), with every step on
+// the FP32 pipe: GB300 issues FP32 about 70x faster than FP64, and at small grids
+// the FP64 kernel above is bound by its FP64 instruction count.
+//  - Bloch phases and H(k) in double-float (two-level phase tables, exact products
+//    of the double-float hopping amplitudes with the phases);
+//  - FP32 Jacobi on the float part of H, made exactly Hermitian;
+//  - one Newton correction of the occupied block Q in the FP32 eigenbasis, with the
+//    residual R = H Q - Q rho in double-float: for each unoccupied FP32 vector z_a,
+//    Q_c += z_a (z_a^dag R_c) / (rho_c - lam_a), rho_c = q_c^dag H q_c;
+//  - one first-order Lowdin step Q <- Q - Q (Q^dag Q - I) / 2 with the Gram matrix
+//    in double-float;
+//  - the gap from double-float Ritz values of the refined occupied pair and of the
+//    re-orthonormalised unoccupied pair (errors quadratic in the subspace errors,
+//    whatever the splitting inside each pair).
+// The occupied block leaves as complex double-float (hi, lo per part, 16 bytes like
+// a complex128), accurate to about 1e-13, for the double-float loop kernels.
+// ---------------------------------------------------------------------------
+size_t quad_df_smem(int nR, int N, int Nt) {
+  const TabShape tN = tab_shape_split(N), tT = tab_shape_split(Nt);
+  return (size_t(nR) * (QUAD_THREADS / 4) + tN.B + tN.H + tT.B + tT.H + nR) * sizeof(cdf) +
+         2 * size_t(nR) * sizeof(int);
+}
+
+template <int PP>
+__global__ void __launch_bounds__(QUAD_THREADS) k_states_quad_df(StatesArgs a) {
+  static_assert(PP == 2, "the double-float four-lane kernel serves two occupied bands");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevModel& md = a.model;
+  const int tid = threadIdx.x, nR = md.n_R;
+  const int N = a.plane.N, Nt = a.plane.N_t;
+  const TabShape tN = tab_shape_split(N), tT = tab_shape_split(Nt);
+  constexpr int KPB = QUAD_THREADS / 4;
+  cdf* cache = reinterpret_cast<cdf*>(smem);   // nR x KPB
+  cdf* tabN = cache + nR * KPB;
+  cdf* tabNt = tabN + tN.B + tN.H;
+  cdf* oph = tabNt + tT.B + tT.H;
+  int* lR = reinterpret_cast<int*>(oph + nR);
+  int* tR = lR + nR;
+  fill_tab_df(tabN, tabN + tN.B, N, tN);
+  fill_tab_df(tabNt, tabNt + tT.B, Nt, tT);
+  for (int r = tid; r < nR; r += blockDim.x) {
+    const int* Rv = md.Rv + 3 * r;
+    double x = 0.0;
+    int lq = 0, tq = 0;
+    for (int dd = 0; dd < 3; ++dd) {
+      x += a.plane.origin[dd] * double(Rv[dd]);
+      lq += int(a.plane.loop_dir[dd]) * Rv[dd];
+      tq += int(a.plane.trans_dir[dd]) * Rv[dd];
+    }
+    double sn, cs;
+    sincospi(2.0 * x, &sn, &cs);
+    oph[r] = cdf_from(z64(cs, sn));
+    lR[r] = lq;
+    tR[r] = tq;
+  }
+  __syncthreads();
+  const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
+  const long long kraw = (long long)blockIdx.x * KPB + kl;
+  const bool active = kraw < a.K;
+  const long long k = active ? kraw : a.K - 1;  // idle groups recompute the last k-point
+  const int i = int(k / N), j = int(k - (long long)i * N);
+  for (int r = l; r < nR; r += 4) {
+    const int mN = pmod((long long)j * lR[r], N), mT = pmod((long long)i * tR[r], Nt);
+    cache[r * KPB + kl] = oph[r] * tab_at_df(tabN, tabN + tN.B, tN, mN) *
+                          tab_at_df(tabNt, tabNt + tT.B, tT, mT);
+  }
+  __syncwarp();
+  // row l of H(k) in double-float
+  cdf Hr[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Hr[c] = cdf_zero();
+  for (int e = a.row_ptr[l]; e < a.row_ptr[l + 1]; ++e) {
+    cdf acc = cdf_zero();
+    for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h) {
+      const float* t4 = md.hop_tdf + 4 * h;
+      cfma(acc, cdf(df(t4[0], t4[1]), df(t4[2], t4[3])), cache[md.hop_r[h] * KPB + kl]);
+    }
+    const int col = md.ent_col[e];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c == col) Hr[c] = acc;
+  }
+  cdf Qf[PP];
+  double gap;
+  const int sweeps = quad_df_occupied(Hr, l, base, a.max_sweeps, Qf[0], Qf[1], gap);
+  if (!active) return;
+  cdf* out = reinterpret_cast<cdf*>(a.U) + k * 4LL * PP + l * PP;
+#pragma unroll
+  for (int c = 0; c < PP; ++c) out[c] = Qf[c];
+  if (l == 0) {
+    a.gap[k] = gap;
+    if (sweeps < 0) report(a.status, ST_ENOCONV, k, 0.0);
+    if (!(gap > a.gap_tol)) report(a.status, ST_EGAP, k, gap);
+  }
+}
+
+template <int PP>
+cudaError_t quad_df_launch(const StatesArgs& a, size_t smem, cudaStream_t s) {
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_states_quad_df<PP>, smem, cached);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (a.K + QUAD_THREADS / 4 - 1) / (QUAD_THREADS / 4);
+  k_states_quad_df<PP><<<int(blocks), QUAD_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int PP>
 cudaError_t quad_launch(const StatesArgs& a, size_t smem, cudaStream_t s) {
   static size_t cached = 0;
@@ -561,6 +540,17 @@ cudaError_t tiny_prec(const StatesArgs& a, int use_tab, size_t smem, cudaStream_
 
 }  // namespace
 
+// The double-float four-lane kernel applies: mixed precision, n = 4, p = 2, no spin split,
+// an integer plane (phase tables) and a small grid.
+bool states_df_eligible(const StatesArgs& a, int p_out) {
+  if (!a.mixed || a.f != nullptr || a.op.nnz > 0 || a.model.n != 4 || a.p != 2 ||
+      p_out != a.p || a.model.n_R > TINY_R_MAX || a.K <= 0 || a.K > 8192 || !a.row_ptr)
+    return false;
+  for (int d = 0; d < 3; ++d)
+    if (a.plane.trans_dir[d] != double((long long)a.plane.trans_dir[d])) return false;
+  return quad_df_smem(a.model.n_R, a.plane.N, a.plane.N_t) <= 48 * 1024;
+}
+
 // Few-band path: n in {2, 4}, at most TINY_R_MAX distinct translations.  Sets
 // *handled = false (and launches nothing) when the problem is outside it.
 cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, bool* handled) {
@@ -578,6 +568,8 @@ cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, b
   size_t smem = size_t(a.model.n_R) * TINY_THREADS * sizeof(z64);
   if (use_tab) smem += (tab + a.model.n_R) * sizeof(z64) + 2 * a.model.n_R * sizeof(int);
   *handled = true;
+  if (a.want_df)  // the caller checked states_df_eligible()
+    return quad_df_launch<2>(a, quad_df_smem(a.model.n_R, N, Nt), s);
   // Small grids (under ~2 warps per SM partition with one thread per k-point) are
   // latency-bound: four lanes per k-point halve the FP64 instructions per lane.
   // Large grids are FP64-throughput-bound, where the one-thread kernel does less

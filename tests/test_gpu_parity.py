@@ -391,3 +391,45 @@ def test_winding_parity(lib, ctx):
         th = rng.uniform(-np.pi, np.pi, size=(Nt, p))
         w = lib.winding(torch.tensor(th, device="cuda"), ctx=ctx).item()
         assert abs(w - oracle.winding(th)) < 1e-11, (Nt, p)
+
+
+# ---------------------------------------------------------------- mixed, four bands
+# The mixed request with n = 4 and p = 2 runs states, overlaps and loop products in
+# double-float on the FP32 pipe; its phases stay within 1e-9 rad of the FP64 oracle
+# (far inside the 1e-6 rad the mixed path promises) and its gaps, Ritz values of
+# the refined pairs, within 1e-9 relative even with degenerate bands (Eq. 9, BBH).
+# The other occupied counts take the FP64 four-lane kernel and meet the same bounds.
+DF_TOL = 1e-9
+DF_CASES = {
+    "random4_p1": (lambda: I.random_hermitian_model(4, 31), P(13, 7, origin=(0.1, 0.2, 0.0)), 1),
+    "random4_p2": (lambda: I.random_hermitian_model(4, 32), P(13, 7), 2),
+    "random4_p3": (lambda: I.random_hermitian_model(4, 33, shells=((1, 0), (0, 1), (1, 1))),
+                   P(11, 5, origin=(0.3, 0.0, 0.0)), 3),
+    "random4_p4": (lambda: I.random_hermitian_model(4, 34), P(9, 3), 4),
+    "spin_hall_51": (lambda: I.spin_hall(1.0), P(51, 51), 2),
+    "choti_kz": (lambda: I.choti_eq9(1.0), P(20, 9, origin=(0, 0, 0.3)), 2),
+}
+
+
+@pytest.mark.parametrize("case", sorted(DF_CASES))
+def test_mixed_four_band_double_float(lib, ctx, case):
+    mk, plane, p = DF_CASES[case]
+    model = mk()
+    ref, rgap = oracle.wilson_loop(model, plane, p)
+    ph, gap = lib.wilson_loop(model, plane, p, precision="mixed", ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= DF_TOL
+    g = gap.cpu().numpy()
+    fin = np.isfinite(rgap)
+    assert np.all(np.isfinite(g) == fin)
+    assert np.abs(g[fin] - rgap[fin]).max(initial=0) <= 1e-9 * max(1, np.abs(rgap[fin]).max(initial=1))
+
+
+def test_mixed_four_band_nested_double_float(lib, ctx):
+    for model, plane, p, m in ((I.bbh(0.5, 0.5), P(60, 60), 2, 1),
+                               (I.bbh(1.5, 1.5), P(12, 10), 2, 1),
+                               (I.choti_eq9(1.0), P(12, 12, origin=(0, 0, 0.25)), 2, 1)):
+        ref_ph, ref_n, ref_wg, _ = oracle.nested_wilson_loop(model, plane, p, m=m)
+        ph, nest, wg, _ = lib.nested_wilson_loop(model, plane, p, m=m, precision="mixed", ctx=ctx)
+        assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= DF_TOL
+        assert circ_err_rows(nest.cpu().numpy(), ref_n) <= DF_TOL
+        assert abs(wg.cpu().numpy().min() - ref_wg) <= 1e-8
