@@ -212,41 +212,56 @@ def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
         for _ in range(max(warmup, 3)):
             call()
     ctx.status(s)
-    ctx.set_profiling(True)
+
+    def replay_steps(g, per_kernel):
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                g.replay()
+            t_end = time.perf_counter() + 0.5          # untimed soak so clocks settle
+            while time.perf_counter() < t_end:
+                g.replay()
+        torch.cuda.synchronize(dev)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier(dev)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(s):
+            for k in range(steps):
+                flush.add_(1)                              # write > L2 between steps
+                ev0[k].record(s)
+                g.replay()
+                ev1[k].record(s)
+                if per_kernel is not None:
+                    ev1[k].synchronize()
+                    for name, ms in ctx.profile_read():
+                        per_kernel[name] = per_kernel.get(name, 0.0) + ms
+        torch.cuda.synchronize(dev)
+        barrier(dev)
+        return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+    # the timed graph carries no timing marks; a second capture with per-kernel
+    # CUDA-event marks gives the breakdown
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         call()
     ctx.status(s)
-    with torch.cuda.stream(s):
-        for _ in range(warmup):
-            g.replay()
-        t_end = time.perf_counter() + 0.5          # untimed soak so clocks settle
-        while time.perf_counter() < t_end:
-            g.replay()
-    torch.cuda.synchronize(dev)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    per_step = replay_steps(g, None)
+    total = sum(per_step)
+    ctx.status(s)
+    outs = [o.cpu().numpy() for o in out]
+    del g
+    ctx.set_profiling(True)
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp, stream=s):
+        call()
+    ctx.status(s)
     per_kernel = {}
-    barrier(dev)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(s):
-        for k in range(steps):
-            flush.add_(1)                              # write > L2 between steps
-            ev0[k].record(s)
-            g.replay()
-            ev1[k].record(s)
-            ev1[k].synchronize()
-            for name, ms in ctx.profile_read():
-                per_kernel[name] = per_kernel.get(name, 0.0) + ms
-    torch.cuda.synchronize(dev)
-    barrier(dev)
-    total = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    replay_steps(gp, per_kernel)
     ctx.status(s)
     ctx.set_profiling(False)
     launches = len(per_kernel)
-    del g
-    return total, per_kernel, launches, [o.cpu().numpy() for o in out], \
-        [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    del gp
+    return total, per_kernel, launches, outs, per_step
 
 
 def time_e2e(lib, ctx, wl, precision, steps, warmup, dev):

@@ -89,6 +89,7 @@ struct DevModel {
   int n;
   int n_R;            // distinct translations
   int n_ent;          // distinct (row, col) pairs
+  int n_hop;          // grouped hoppings (ent_start[n_ent])
   const int* Rv;      // n_R x 3
   const int* ent_row;
   const int* ent_col;

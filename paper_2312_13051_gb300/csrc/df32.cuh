@@ -144,6 +144,61 @@ __device__ __forceinline__ df df_rsqrt(df a) {
 
 __device__ __forceinline__ cdf cdf_zero() { return cdf(df(0.f, 0.f), df(0.f, 0.f)); }
 
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? -a : a; }
+__device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+// Principal complex square root: t = sqrt((|z| + |Re z|) / 2), then Im z / (2 t).
+__device__ __forceinline__ cdf csqrt_df(cdf z) {
+  const df r = df_sqrt(abs2(z));
+  if (!(r.hi > 0.f)) return cdf_zero();
+  const df t = df_sqrt(df(0.5f) * (r + df_abs(z.re)));
+  const df two_t = df(2.f) * t;
+  if (z.re.hi >= 0.f) return cdf(t, df_div(z.im, two_t));
+  return cdf(df_div(df_abs(z.im), two_t), z.im.hi >= 0.f ? t : -t);
+}
+
+// Closed-form eigen-decomposition of the 2 x 2 complex matrix H = [[a, b], [c, d]]
+// (row-major) in double-float, one thread: lambda = (a + d)/2 +- sqrt(((a - d)/2)^2
+// + b c); the root of larger magnitude from the formula, the other as det / lambda_1
+// (no cancellation).  With want_vec, Z (row-major 2 x 2) receives unit right
+// eigenvectors as columns: (b, lambda - a) or (lambda - d, c), whichever is longer
+// (e_1, e_2 when H is a multiple of I).
+__device__ inline void eig2_closed_df(const cdf* H, cdf* lam, cdf* Z, bool want_vec) {
+  const cdf a = H[0], b = H[1], c = H[2], d = H[3];
+  const cdf mid = df(0.5f) * (a + d), half = df(0.5f) * (a - d);
+  const cdf sq = csqrt_df(half * half + b * c);
+  const cdf l1p = mid + sq, l1m = mid - sq;
+  const cdf l1 = df_gt(abs2(l1m), abs2(l1p)) ? l1m : l1p;
+  const cdf det = a * d - b * c;
+  cdf l2 = cdf_zero();
+  const df den = abs2(l1);
+  if (den.hi > 0.f) {
+    const cdf num = det * conj(l1);
+    l2 = cdf(df_div(num.re, den), df_div(num.im, den));
+  }
+  lam[0] = l1;
+  lam[1] = l2;
+  if (!want_vec) return;
+  for (int k = 0; k < 2; ++k) {
+    const cdf l = lam[k];
+    cdf v0 = b, v1 = l - a;
+    const cdf w0 = l - d, w1 = c;
+    if (df_gt(abs2(w0) + abs2(w1), abs2(v0) + abs2(v1))) {
+      v0 = w0;
+      v1 = w1;
+    }
+    df nv = abs2(v0) + abs2(v1);
+    if (!(nv.hi > 0.f)) {
+      v0 = cdf(df(k == 0 ? 1.f : 0.f), df(0.f));
+      v1 = cdf(df(k == 0 ? 0.f : 1.f), df(0.f));
+      nv = df(1.f);
+    }
+    const df inv = df_rsqrt(nv);
+    Z[k] = inv * v0;
+    Z[2 + k] = inv * v1;
+  }
+}
+
 // Warp shuffle of a complex double-float.
 __device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
   return cdf(df(__shfl_sync(0xffffffffu, v.re.hi, src), __shfl_sync(0xffffffffu, v.re.lo, src)),

@@ -226,7 +226,7 @@ bool loops_accept_df(const LoopArgs& a);
 // Mixed precision, n = 4, p = 2, N <= 64 with the scan kernels: one kernel solves each
 // loop's states and runs the loop (replaces launch_states_small + launch_loops; sa as
 // for launch_states_small with want_df, a as for launch_loops with u_df).
-bool loops_fused_eligible(const LoopArgs& a);
+bool loops_fused_eligible(const LoopArgs& a, const DevModel& md);
 cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s);
 // Orthonormalised Wannier states w from the transported bases in nu_buf (no-op without).
 cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s);

@@ -16,6 +16,8 @@
 //                direction (Eq. 6).
 #include <float.h>
 
+#include <type_traits>
+
 #include "df32.cuh"
 #include "geig.cuh"
 #include "jacobi.cuh"
@@ -464,32 +466,38 @@ __host__ __device__ inline ScanSmem scan_layout(int L, int q, int n_nu) {
 
 // Orders the eigenphases th[0..p) by their distance from `cut` (mod 2pi, stable),
 // writes the Wannier gap of the sector [first, first+m) for loop i and reports a
-// closed gap.  ord receives the ordering.  Every thread must call it.
+// closed gap.  ord receives the ordering.  Every thread must call it.  The host
+// passes cut reduced to [0, 2pi), so theta - cut lies in (-3pi, pi] and wraps by
+// adding 2pi at most twice; two phases in (-pi, pi] differ by at most 2pi.  One warp
+// takes the gap.
 __device__ void nested_sector(const LoopArgs& a, const double* th, int p, int m, double* key,
-                              int* ord, double* red, int i, long long k0) {
+                              int* ord, int i, long long k0) {
   const double two_pi = 6.283185307179586;
   for (int c = threadIdx.x; c < p; c += blockDim.x) {
-    double x = fmod(th[c] - a.cut, two_pi);
+    double x = th[c] - a.cut;
+    if (x < 0.0) x += two_pi;
     if (x < 0.0) x += two_pi;
     if (x >= two_pi) x = 0.0;
     key[c] = x;
   }
   __syncthreads();
   rank_sort(key, p, ord);
-  double wg = INFINITY;
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int s = e / p, r = e - s * p;
-    const bool in_s = s >= a.first && s < a.first + m;
-    const bool in_r = !(r >= a.first && r < a.first + m);
-    if (in_s && in_r) {
-      double d = fmod(fabs(th[ord[s]] - th[ord[r]]), two_pi);
-      wg = fmin(wg, fmin(d, two_pi - d));
+  if (threadIdx.x < 32) {
+    double wg = INFINITY;
+    for (int e = threadIdx.x; e < p * p; e += 32) {
+      const int s = e / p, r = e - s * p;
+      const bool in_s = s >= a.first && s < a.first + m;
+      const bool in_r = !(r >= a.first && r < a.first + m);
+      if (in_s && in_r) {
+        const double d = fabs(th[ord[s]] - th[ord[r]]);
+        wg = fmin(wg, fmin(d, two_pi - d));
+      }
     }
-  }
-  wg = block_min(wg, red);
-  if (threadIdx.x == 0) {
-    if (a.min_wannier_gap) a.min_wannier_gap[i] = wg;
-    if (!(wg > a.wannier_gap_tol)) report(a.status, ST_EWANGAP, k0, wg);
+    for (int o = 16; o > 0; o >>= 1) wg = fmin(wg, __shfl_xor_sync(0xffffffffu, wg, o));
+    if (threadIdx.x == 0) {
+      if (a.min_wannier_gap) a.min_wannier_gap[i] = wg;
+      if (!(wg > a.wannier_gap_tol)) report(a.status, ST_EWANGAP, k0, wg);
+    }
   }
 }
 
@@ -520,17 +528,21 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
   const int pp = p * p;
   {
     const long long k0 = (long long)i * N;
-    if (a.min_gap || a.min_pso_gap) {
-      double g = INFINITY, gp = INFINITY;
-      for (int j = tid; j < N; j += nt) {
-        if (gl) g = fmin(g, gl[j]);
-        if (pgl) gp = fmin(gp, pgl[j]);
-      }
-      g = block_min(g, red);
-      gp = block_min(gp, red);
-      if (tid == 0) {
-        if (a.min_gap) a.min_gap[i] = g;
-        if (a.min_pso_gap) a.min_pso_gap[i] = gp;
+    if (a.min_gap || a.min_pso_gap) {  // one warp
+      if (tid < 32) {
+        double g = INFINITY, gp = INFINITY;
+        for (int j = tid; j < N; j += 32) {
+          if (gl) g = fmin(g, gl[j]);
+          if (pgl) gp = fmin(gp, pgl[j]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          g = fmin(g, __shfl_xor_sync(0xffffffffu, g, o));
+          gp = fmin(gp, __shfl_xor_sync(0xffffffffu, gp, o));
+        }
+        if (tid == 0) {
+          if (a.min_gap) a.min_gap[i] = g;
+          if (a.min_pso_gap) a.min_pso_gap[i] = gp;
+        }
       }
     }
     if (a.unitarise) {
@@ -549,14 +561,36 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
     __syncthreads();
     // P[j] = M_j ... M_0; the loop matrix is P[N-1]
     E* Pf = prefix_products(S, T, N, p);
-    for (int e = tid; e < pp; e += nt) X[e] = A::to64(Pf[(N - 1) * pp + e]);
-    __syncthreads();
-    if (p == 2) {  // closed form: the general solver's serial QR sweeps dominate at p = 2
-      if (tid == 0) eig2_closed(X, 2, lam, Y, a.nested != 0);
+    // eigenvalues (and for the nested loop right eigenvectors) of W = P[N-1]; at
+    // p = 2 in closed form in the element arithmetic (the general solver's serial QR
+    // sweeps dominate there), else by the FP64 general solver.  Ye: eigenvectors
+    // as E for the transport.
+    constexpr bool kDf = std::is_same<E, cdf>::value;
+    E* Ye = reinterpret_cast<E*>(smem + Z.Y);
+    if (p == 2) {
+      if (tid == 0) {
+        if constexpr (kDf) {
+          cdf l2[2];
+          eig2_closed_df(Pf + (N - 1) * pp, l2, Ye, a.nested != 0);
+          lam[0] = cdf_to_z64(l2[0]);
+          lam[1] = cdf_to_z64(l2[1]);
+        } else {
+          eig2_closed(Pf + (N - 1) * pp, 2, lam, Y, a.nested != 0);
+        }
+      }
       __syncthreads();
     } else {
+      for (int e = tid; e < pp; e += nt) X[e] = A::to64(Pf[(N - 1) * pp + e]);
+      __syncthreads();
       const int rc = geig(X, Y, p, p, a.nested != 0, lam, vec, sh);
       if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, k0, 0.0);
+      if constexpr (kDf) {  // convert in place (same element size)
+        __syncthreads();
+        for (int e = tid; e < pp; e += nt) {
+          const z64 v = Y[e];
+          Ye[e] = A::from(v);
+        }
+      }
     }
     for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
     __syncthreads();
@@ -564,7 +598,7 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
     for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
     __syncthreads();
     if (!a.nested) return;
-    nested_sector(a, th, p, m, key, ord, red, i, k0);
+    nested_sector(a, th, p, m, key, ord, i, k0);
     // nu_j = P[j-1] nu_0 (nu_0 = Y[:, sector]), one thread per base point j:
     // normalise the columns, then modified Gram-Schmidt (m <= SCAN_P_MAX)
     for (int j = tid; j < N; j += nt) {
@@ -574,10 +608,10 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
           const int col = ord[a.first + c];
           E acc = A::zero();
           if (j == 0) {
-            acc = A::from(Y[r * p + col]);
+            acc = Ye[r * p + col];
           } else {
             const E* P = Pf + (size_t)(j - 1) * pp;
-            for (int q = 0; q < p; ++q) cfma(acc, P[r * p + q], A::from(Y[q * p + col]));
+            for (int q = 0; q < p; ++q) cfma(acc, P[r * p + q], Ye[q * p + col]);
           }
           nu[r * m + c] = acc;
         }
@@ -630,10 +664,14 @@ __global__ void k_loops_scan(LoopArgs a) {
 constexpr int FUSED_THREADS = 256;
 
 struct FusedSmem {
-  size_t U, g, cache, tab, rowf, lR, total;
+  size_t U, g, cache, tab, rowf, lR, rowp, ent, col, hr, ht, total;
 };
 
-__host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int nR) {
+// The model plan (row pointers, entries, grouped hoppings) is staged in shared memory:
+// each k-point walks it once, and global loads would put an L2 round trip on every
+// step of that walk.
+__host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int nR, int n_ent,
+                                                  int n_hop) {
   auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
   FusedSmem F;
   size_t o = Z.total;
@@ -643,6 +681,11 @@ __host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int 
   F.tab = o; o = al(o + size_t(N) * sizeof(cdf));
   F.rowf = o; o = al(o + size_t(nR) * sizeof(cdf));
   F.lR = o; o = al(o + size_t(nR) * sizeof(int));
+  F.rowp = o; o = al(o + 5 * sizeof(int));
+  F.ent = o; o = al(o + size_t(n_ent + 1) * sizeof(int));
+  F.col = o; o = al(o + size_t(n_ent) * sizeof(int));
+  F.hr = o; o = al(o + size_t(n_hop) * sizeof(int));
+  F.ht = o; o = al(o + size_t(n_hop) * 4 * sizeof(float));
   F.total = o;
   return F;
 }
@@ -653,23 +696,39 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
   const int N = a.N, Nt = a.N_t, nR = md.n_R, tid = threadIdx.x, nt = blockDim.x;
   constexpr int KPB = FUSED_THREADS / 4;
   const ScanSmem Z = scan_layout(N, 2, a.nested ? N * 2 * a.m : 1);
-  const FusedSmem F = fused_layout(Z, N, nR);
+  const FusedSmem F = fused_layout(Z, N, nR, md.n_ent, md.n_hop);
   cdf* Us = reinterpret_cast<cdf*>(smem + F.U);
+  int* s_rowp = reinterpret_cast<int*>(smem + F.rowp);
+  int* s_ent = reinterpret_cast<int*>(smem + F.ent);
+  int* s_col = reinterpret_cast<int*>(smem + F.col);
+  int* s_hr = reinterpret_cast<int*>(smem + F.hr);
+  float4* s_ht = reinterpret_cast<float4*>(smem + F.ht);
+  for (int e = tid; e < 5; e += nt) s_rowp[e] = sa.row_ptr[e];
+  for (int e = tid; e <= md.n_ent; e += nt) s_ent[e] = md.ent_start[e];
+  for (int e = tid; e < md.n_ent; e += nt) s_col[e] = md.ent_col[e];
+  for (int h = tid; h < md.n_hop; h += nt) {
+    s_hr[h] = md.hop_r[h];
+    s_ht[h] = make_float4(md.hop_tdf[4 * h], md.hop_tdf[4 * h + 1], md.hop_tdf[4 * h + 2],
+                          md.hop_tdf[4 * h + 3]);
+  }
   double* gs = reinterpret_cast<double*>(smem + F.g);
   cdf* cache = reinterpret_cast<cdf*>(smem + F.cache);
   cdf* tab = reinterpret_cast<cdf*>(smem + F.tab);
   cdf* rowf = reinterpret_cast<cdf*>(smem + F.rowf);
   int* lR = reinterpret_cast<int*>(smem + F.lR);
+  const double inv_N = 2.0 / double(N);
   for (int m = tid; m < N; m += nt) {
     double sn, cs;
-    sincospi(2.0 * double(m) / double(N), &sn, &cs);
+    sincospi(double(m) * inv_N, &sn, &cs);
     tab[m] = cdf_from(z64(cs, sn));
   }
   const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
   const bool active = kl < N;
   const int j = active ? kl : N - 1;  // idle groups recompute the last k-point
+  // the translation factors on the last warps, in parallel with the table above
+  const int rbase = nt - 32 * ((nR + 31) / 32);
   for (int i = blockIdx.x; i < Nt; i += gridDim.x) {
-    for (int r = tid; r < nR; r += nt) {
+    for (int r = tid - rbase; r >= 0 && r < nR; r += nt) {
       const int* Rv = md.Rv + 3 * r;
       double x = 0.0;
       int lq = 0, tq = 0;
@@ -691,13 +750,13 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
     cdf Hr[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) Hr[c] = cdf_zero();
-    for (int e = sa.row_ptr[l]; e < sa.row_ptr[l + 1]; ++e) {
+    for (int e = s_rowp[l]; e < s_rowp[l + 1]; ++e) {
       cdf acc = cdf_zero();
-      for (int h = md.ent_start[e]; h < md.ent_start[e + 1]; ++h) {
-        const float* t4 = md.hop_tdf + 4 * h;
-        cfma(acc, cdf(df(t4[0], t4[1]), df(t4[2], t4[3])), cache[md.hop_r[h] * KPB + kl]);
+      for (int h = s_ent[e]; h < s_ent[e + 1]; ++h) {
+        const float4 t4 = s_ht[h];
+        cfma(acc, cdf(df(t4.x, t4.y), df(t4.z, t4.w)), cache[s_hr[h] * KPB + kl]);
       }
-      const int col = md.ent_col[e];
+      const int col = s_col[e];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (c == col) Hr[c] = acc;
@@ -721,14 +780,17 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
   }
 }
 
-bool loops_fused_eligible(const LoopArgs& a) {
-  return a.n == 4 && a.p == 2 && a.N >= 1 && 4 * a.N <= FUSED_THREADS && loops_accept_df(a);
+bool loops_fused_eligible(const LoopArgs& a, const DevModel& md) {
+  if (!(a.n == 4 && a.p == 2 && a.N >= 1 && 4 * a.N <= FUSED_THREADS && loops_accept_df(a)))
+    return false;
+  const ScanSmem Z = scan_layout(a.N, 2, a.nested ? a.N * 2 * a.m : 1);
+  return fused_layout(Z, a.N, md.n_R, md.n_ent, md.n_hop).total <= 96 * 1024;
 }
 
 cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s) {
   if (a.N_t <= 0) return cudaSuccess;
   const ScanSmem Z = scan_layout(a.N, 2, a.nested ? a.N * 2 * a.m : 1);
-  const FusedSmem F = fused_layout(Z, a.N, sa.model.n_R);
+  const FusedSmem F = fused_layout(Z, a.N, sa.model.n_R, sa.model.n_ent, sa.model.n_hop);
   static size_t cached = 0;
   cudaError_t e = set_smem_once(k_loops_fused_df, F.total, cached);
   if (e != cudaSuccess) return e;

@@ -214,6 +214,7 @@ bw::DevModel dev_model(const HostPlan& P, const char* base) {
   d.n = P.n;
   d.n_R = P.n_R;
   d.n_ent = P.n_ent;
+  d.n_hop = int(P.hop_t.size());
   d.Rv = reinterpret_cast<const int*>(base + P.o_Rv);
   d.ent_row = reinterpret_cast<const int*>(base + P.o_row);
   d.ent_col = reinterpret_cast<const int*>(base + P.o_col);
@@ -705,7 +706,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     q.nested = kind == LoopKind::Nested;
     q.m = m;
     use_df = bw::loops_accept_df(q) && bw::states_df_eligible(sa, p_eff);
-    fused = use_df && bw::loops_fused_eligible(q);
+    fused = use_df && bw::loops_fused_eligible(q, sa.model);
   }
   sa.want_df = use_df ? 1 : 0;
   prof_start(ctx, s);
@@ -779,7 +780,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.u_df = use_df ? 1 : 0;
   if (kind == LoopKind::Nested) {
     la.nested = 1;
-    la.cut = cut;
+    // the kernels measure phases from cut as (theta - cut) wrapped into [0, 2 pi)
+    double cr = std::fmod(cut, 6.283185307179586);
+    if (cr < 0.0) cr += 6.283185307179586;
+    la.cut = cr;
     la.first = first;
     la.m = m;
     la.wannier_gap_tol = o.wannier_gap_tol;

@@ -541,10 +541,10 @@ cudaError_t tiny_prec(const StatesArgs& a, int use_tab, size_t smem, cudaStream_
 }  // namespace
 
 // The double-float four-lane kernel applies: mixed precision, n = 4, p = 2, no spin split,
-// an integer plane (phase tables) and a small grid.
+// an integer plane (phase tables), at most TINY_R_MAX translations.
 bool states_df_eligible(const StatesArgs& a, int p_out) {
   if (!a.mixed || a.f != nullptr || a.op.nnz > 0 || a.model.n != 4 || a.p != 2 ||
-      p_out != a.p || a.model.n_R > TINY_R_MAX || a.K <= 0 || a.K > 8192 || !a.row_ptr)
+      p_out != a.p || a.model.n_R > TINY_R_MAX || a.K <= 0 || !a.row_ptr)
     return false;
   for (int d = 0; d < 3; ++d)
     if (a.plane.trans_dir[d] != double((long long)a.plane.trans_dir[d])) return false;
