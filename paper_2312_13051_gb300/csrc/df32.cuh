@@ -157,13 +157,11 @@ __device__ __forceinline__ cdf csqrt_df(cdf z) {
   return cdf(df_div(df_abs(z.im), two_t), z.im.hi >= 0.f ? t : -t);
 }
 
-// Closed-form eigen-decomposition of the 2 x 2 complex matrix H = [[a, b], [c, d]]
-// (row-major) in double-float, one thread: lambda = (a + d)/2 +- sqrt(((a - d)/2)^2
-// + b c); the root of larger magnitude from the formula, the other as det / lambda_1
-// (no cancellation).  With want_vec, Z (row-major 2 x 2) receives unit right
-// eigenvectors as columns: (b, lambda - a) or (lambda - d, c), whichever is longer
-// (e_1, e_2 when H is a multiple of I).
-__device__ inline void eig2_closed_df(const cdf* H, cdf* lam, cdf* Z, bool want_vec) {
+// Closed-form eigenvalues of the 2 x 2 complex matrix H = [[a, b], [c, d]]
+// (row-major) in double-float: lambda = (a + d)/2 +- sqrt(((a - d)/2)^2 + b c); the
+// root of larger magnitude from the formula, the other as det / lambda_1 (no
+// cancellation).
+__device__ inline void eig2_values_df(const cdf* H, cdf* lam) {
   const cdf a = H[0], b = H[1], c = H[2], d = H[3];
   const cdf mid = df(0.5f) * (a + d), half = df(0.5f) * (a - d);
   const cdf sq = csqrt_df(half * half + b * c);
@@ -178,25 +176,28 @@ __device__ inline void eig2_closed_df(const cdf* H, cdf* lam, cdf* Z, bool want_
   }
   lam[0] = l1;
   lam[1] = l2;
-  if (!want_vec) return;
-  for (int k = 0; k < 2; ++k) {
-    const cdf l = lam[k];
-    cdf v0 = b, v1 = l - a;
-    const cdf w0 = l - d, w1 = c;
-    if (df_gt(abs2(w0) + abs2(w1), abs2(v0) + abs2(v1))) {
-      v0 = w0;
-      v1 = w1;
-    }
-    df nv = abs2(v0) + abs2(v1);
-    if (!(nv.hi > 0.f)) {
-      v0 = cdf(df(k == 0 ? 1.f : 0.f), df(0.f));
-      v1 = cdf(df(k == 0 ? 0.f : 1.f), df(0.f));
-      nv = df(1.f);
-    }
-    const df inv = df_rsqrt(nv);
-    Z[k] = inv * v0;
-    Z[2 + k] = inv * v1;
+}
+
+// Unit right eigenvector of H for its eigenvalue l, written as column k of the
+// row-major 2 x 2 Z: (b, l - a) or (l - d, c), whichever is longer (e_k when H is a
+// multiple of I).
+__device__ inline void eig2_vector_df(const cdf* H, cdf l, int k, cdf* Z) {
+  const cdf a = H[0], b = H[1], c = H[2], d = H[3];
+  cdf v0 = b, v1 = l - a;
+  const cdf w0 = l - d, w1 = c;
+  if (df_gt(abs2(w0) + abs2(w1), abs2(v0) + abs2(v1))) {
+    v0 = w0;
+    v1 = w1;
   }
+  df nv = abs2(v0) + abs2(v1);
+  if (!(nv.hi > 0.f)) {
+    v0 = cdf(df(k == 0 ? 1.f : 0.f), df(0.f));
+    v1 = cdf(df(k == 0 ? 0.f : 1.f), df(0.f));
+    nv = df(1.f);
+  }
+  const df inv = df_rsqrt(nv);
+  Z[k] = inv * v0;
+  Z[2 + k] = inv * v1;
 }
 
 // Warp shuffle of a complex double-float.

@@ -402,6 +402,10 @@ template <>
 struct Arith<z64> {
   using R = double;
   __device__ static z64 zero() { return z64(0.0, 0.0); }
+  __device__ static z64 one() { return z64(1.0, 0.0); }
+  __device__ static z64 shfl_xor(z64 v, int o) {
+    return z64(__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o));
+  }
   __device__ static z64 from(z64 v) { return v; }
   __device__ static z64 to64(z64 v) { return v; }
   __device__ static double rsqrt(double x) { return 1.0 / sqrt(x); }
@@ -410,6 +414,10 @@ template <>
 struct Arith<cdf> {
   using R = df;
   __device__ static cdf zero() { return cdf_zero(); }
+  __device__ static cdf one() { return cdf(df(1.f), df(0.f)); }
+  __device__ static cdf shfl_xor(cdf v, int o) {
+    return cdf(shfl_xor_df(v.re, o), shfl_xor_df(v.im, o));
+  }
   __device__ static cdf from(z64 v) { return cdf_from(v); }
   __device__ static z64 to64(cdf v) { return cdf_to_z64(v); }
   __device__ static df rsqrt(df x) { return df_rsqrt(x); }
@@ -568,15 +576,20 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
     constexpr bool kDf = std::is_same<E, cdf>::value;
     E* Ye = reinterpret_cast<E*>(smem + Z.Y);
     if (p == 2) {
-      if (tid == 0) {
-        if constexpr (kDf) {
-          cdf l2[2];
-          eig2_closed_df(Pf + (N - 1) * pp, l2, Ye, a.nested != 0);
-          lam[0] = cdf_to_z64(l2[0]);
-          lam[1] = cdf_to_z64(l2[1]);
-        } else {
-          eig2_closed(Pf + (N - 1) * pp, 2, lam, Y, a.nested != 0);
+      if constexpr (kDf) {
+        // eigenvalues on one thread; then the two eigenvectors (warp 0) and the two
+        // phases (warp 1) in parallel
+        cdf* lamd = reinterpret_cast<cdf*>(smem + Z.vec);
+        const E* Wl = Pf + (N - 1) * pp;
+        if (tid == 0) eig2_values_df(Wl, lamd);
+        __syncthreads();
+        if (tid < 2 && a.nested) eig2_vector_df(Wl, lamd[tid], tid, Ye);
+        if (tid >= 32 && tid < 34) {
+          lam[tid - 32] = cdf_to_z64(lamd[tid - 32]);
+          th[tid - 32] = phase_of(lam[tid - 32]);
         }
+      } else {
+        if (tid == 0) eig2_closed(Pf + (N - 1) * pp, 2, lam, Y, a.nested != 0);
       }
       __syncthreads();
     } else {
@@ -592,7 +605,8 @@ __device__ void scan_one_loop(const LoopArgs& a, int i, const E* Ul, const doubl
         }
       }
     }
-    for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
+    if (!(kDf && p == 2))
+      for (int c = tid; c < p; c += nt) th[c] = phase_of(lam[c]);
     __syncthreads();
     rank_sort(th, p, ord);
     for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
@@ -819,6 +833,23 @@ __global__ void k_nested_scan(LoopArgs a) {
   const int mm2 = m * m, nm = n * m;
   for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
     const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * nm;
+    if (m == 1) {
+      // one Wannier band: the loop matrix is the product of the scalar overlaps
+      // (any order), taken by one warp straight from global memory
+      if (tid < 32) {
+        E prod = A::one();
+        for (int i = tid; i < Nt; i += 32) {
+          const E* wa = wj + (size_t)i * n;
+          const E* wb = wj + (size_t)(i + 1 == Nt ? 0 : i + 1) * n;
+          E acc = A::zero();
+          for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q], wa[q]);
+          prod = prod * acc;
+        }
+        for (int o = 16; o > 0; o >>= 1) prod = prod * A::shfl_xor(prod, o);
+        if (tid == 0) a.nested_out[j] = phase_of(A::to64(prod));
+      }
+      continue;
+    }
     for (int e = tid; e < Nt * nm; e += nt) Wn[e] = wj[e];
     __syncthreads();
     // A_i = w(i+1)^dagger w(i), closed on i = 0
