@@ -390,6 +390,8 @@ def run_ours(args):
         flops["loops"] += flops["overlaps"]
     if "states" not in pk:        # solved inside the loop kernel
         flops["loops"] += flops["states"]
+    if "nested" not in pk:        # nested loops in the same (cooperative) launch
+        flops["loops"] += flops["nested"]
     dom = max(pk, key=pk.get)
     avg_ms = pk[dom] / args.steps
     achieved = flops[dom] / (avg_ms * 1e-3) / 1e12

@@ -147,14 +147,25 @@ __device__ __forceinline__ cdf cdf_zero() { return cdf(df(0.f, 0.f), df(0.f, 0.f
 __device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? -a : a; }
 __device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
+// Out-of-line copies of the larger operations for code that runs once per loop on
+// one thread (the 2 x 2 eigen-decomposition below): called rather than inlined, each
+// exists once in the kernel, so a cold instruction cache fetches less of it.
+static __device__ __noinline__ cdf cmul_ool(cdf a, cdf b) { return a * b; }
+static __device__ __noinline__ cdf cadd_ool(cdf a, cdf b) { return a + b; }
+static __device__ __noinline__ cdf csub_ool(cdf a, cdf b) { return a - b; }
+static __device__ __noinline__ df abs2_ool(cdf a) { return abs2(a); }
+static __device__ __noinline__ df dfadd_ool(df a, df b) { return a + b; }
+static __device__ __noinline__ df dfdiv_ool(df a, df b) { return df_div(a, b); }
+static __device__ __noinline__ df dfsqrt_ool(df a) { return df_sqrt(a); }
+
 // Principal complex square root: t = sqrt((|z| + |Re z|) / 2), then Im z / (2 t).
-__device__ __forceinline__ cdf csqrt_df(cdf z) {
-  const df r = df_sqrt(abs2(z));
+__device__ inline cdf csqrt_df(cdf z) {
+  const df r = dfsqrt_ool(abs2_ool(z));
   if (!(r.hi > 0.f)) return cdf_zero();
-  const df t = df_sqrt(df(0.5f) * (r + df_abs(z.re)));
+  const df t = dfsqrt_ool(df(0.5f) * dfadd_ool(r, df_abs(z.re)));
   const df two_t = df(2.f) * t;
-  if (z.re.hi >= 0.f) return cdf(t, df_div(z.im, two_t));
-  return cdf(df_div(df_abs(z.im), two_t), z.im.hi >= 0.f ? t : -t);
+  if (z.re.hi >= 0.f) return cdf(t, dfdiv_ool(z.im, two_t));
+  return cdf(dfdiv_ool(df_abs(z.im), two_t), z.im.hi >= 0.f ? t : -t);
 }
 
 // Closed-form eigenvalues of the 2 x 2 complex matrix H = [[a, b], [c, d]]
@@ -163,16 +174,16 @@ __device__ __forceinline__ cdf csqrt_df(cdf z) {
 // cancellation).
 __device__ inline void eig2_values_df(const cdf* H, cdf* lam) {
   const cdf a = H[0], b = H[1], c = H[2], d = H[3];
-  const cdf mid = df(0.5f) * (a + d), half = df(0.5f) * (a - d);
-  const cdf sq = csqrt_df(half * half + b * c);
-  const cdf l1p = mid + sq, l1m = mid - sq;
-  const cdf l1 = df_gt(abs2(l1m), abs2(l1p)) ? l1m : l1p;
-  const cdf det = a * d - b * c;
+  const cdf mid = df(0.5f) * cadd_ool(a, d), half = df(0.5f) * csub_ool(a, d);
+  const cdf sq = csqrt_df(cadd_ool(cmul_ool(half, half), cmul_ool(b, c)));
+  const cdf l1p = cadd_ool(mid, sq), l1m = csub_ool(mid, sq);
+  const cdf l1 = df_gt(abs2_ool(l1m), abs2_ool(l1p)) ? l1m : l1p;
+  const cdf det = csub_ool(cmul_ool(a, d), cmul_ool(b, c));
   cdf l2 = cdf_zero();
-  const df den = abs2(l1);
+  const df den = abs2_ool(l1);
   if (den.hi > 0.f) {
-    const cdf num = det * conj(l1);
-    l2 = cdf(df_div(num.re, den), df_div(num.im, den));
+    const cdf num = cmul_ool(det, conj(l1));
+    l2 = cdf(dfdiv_ool(num.re, den), dfdiv_ool(num.im, den));
   }
   lam[0] = l1;
   lam[1] = l2;
@@ -183,13 +194,13 @@ __device__ inline void eig2_values_df(const cdf* H, cdf* lam) {
 // multiple of I).
 __device__ inline void eig2_vector_df(const cdf* H, cdf l, int k, cdf* Z) {
   const cdf a = H[0], b = H[1], c = H[2], d = H[3];
-  cdf v0 = b, v1 = l - a;
-  const cdf w0 = l - d, w1 = c;
-  if (df_gt(abs2(w0) + abs2(w1), abs2(v0) + abs2(v1))) {
+  cdf v0 = b, v1 = csub_ool(l, a);
+  const cdf w0 = csub_ool(l, d), w1 = c;
+  if (df_gt(dfadd_ool(abs2_ool(w0), abs2_ool(w1)), dfadd_ool(abs2_ool(v0), abs2_ool(v1)))) {
     v0 = w0;
     v1 = w1;
   }
-  df nv = abs2(v0) + abs2(v1);
+  df nv = dfadd_ool(abs2_ool(v0), abs2_ool(v1));
   if (!(nv.hi > 0.f)) {
     v0 = cdf(df(k == 0 ? 1.f : 0.f), df(0.f));
     v1 = cdf(df(k == 0 ? 0.f : 1.f), df(0.f));

@@ -227,7 +227,10 @@ bool loops_accept_df(const LoopArgs& a);
 // loop's states and runs the loop (replaces launch_states_small + launch_loops; sa as
 // for launch_states_small with want_df, a as for launch_loops with u_df).
 bool loops_fused_eligible(const LoopArgs& a, const DevModel& md);
-cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s);
+// *nested_done: the launch also ran the nested loops (one Wannier band, cooperative
+// launch with the whole grid resident), so launch_nested must not run.
+cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s,
+                                  bool* nested_done);
 // Orthonormalised Wannier states w from the transported bases in nu_buf (no-op without).
 cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s);
 

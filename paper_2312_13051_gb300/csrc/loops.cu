@@ -16,6 +16,7 @@
 //                direction (Eq. 6).
 #include <float.h>
 
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "df32.cuh"
@@ -667,6 +668,27 @@ __global__ void k_loops_scan(LoopArgs a) {
   }
 }
 
+// Nested loop of one Wannier band at base point j: the loop matrix is the product
+// of the scalar overlaps w(i+1)^dagger w(i) (any order), taken by the CTA's first
+// warp straight from global memory; the other threads return at once.
+template <typename E>
+__device__ void nested_base_m1(const LoopArgs& a, int j) {
+  using A = Arith<E>;
+  const int n = a.n, Nt = a.N_t, tid = threadIdx.x;
+  if (tid >= 32) return;
+  const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * n;
+  E prod = A::one();
+  for (int i = tid; i < Nt; i += 32) {
+    const E* wa = wj + (size_t)i * n;
+    const E* wb = wj + (size_t)(i + 1 == Nt ? 0 : i + 1) * n;
+    E acc = A::zero();
+    for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q], wa[q]);
+    prod = prod * acc;
+  }
+  for (int o = 16; o > 0; o >>= 1) prod = prod * A::shfl_xor(prod, o);
+  if (tid == 0) a.nested_out[j] = phase_of(A::to64(prod));
+}
+
 // ---------------------------------------------------------------------------
 // Mixed precision, four bands, two occupied, N <= 64: one CTA per loop solves the
 // loop's N k-points (four lanes each, quad_df_occupied: double-float H(k), FP32
@@ -704,6 +726,7 @@ __host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int 
   return F;
 }
 
+template <bool kNested1>
 __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa, LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevModel& md = sa.model;
@@ -792,6 +815,13 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
     scan_one_loop<cdf>(a, i, Us, gs, nullptr, smem);
     __syncthreads();
   }
+  if constexpr (kNested1) {
+    // cooperative launch: every loop's Wannier states are written once the grid
+    // has passed this barrier; then the nested loops of one Wannier band
+    __threadfence();
+    cooperative_groups::this_grid().sync();
+    for (int j = blockIdx.x; j < a.N; j += gridDim.x) nested_base_m1<cdf>(a, j);
+  }
 }
 
 bool loops_fused_eligible(const LoopArgs& a, const DevModel& md) {
@@ -801,14 +831,44 @@ bool loops_fused_eligible(const LoopArgs& a, const DevModel& md) {
   return fused_layout(Z, a.N, md.n_R, md.n_ent, md.n_hop).total <= 96 * 1024;
 }
 
-cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s) {
+cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s,
+                                  bool* nested_done) {
+  *nested_done = false;
   if (a.N_t <= 0) return cudaSuccess;
   const ScanSmem Z = scan_layout(a.N, 2, a.nested ? a.N * 2 * a.m : 1);
   const FusedSmem F = fused_layout(Z, a.N, sa.model.n_R, sa.model.n_ent, sa.model.n_hop);
+  cudaError_t e;
+  if (a.nested && a.m == 1) {
+    // one cooperative launch for the loops and the nested loops when the whole grid
+    // is resident at once (one CTA per loop)
+    static size_t cached_c = 0;
+    if ((e = set_smem_once(k_loops_fused_df<true>, F.total, cached_c)) != cudaSuccess) return e;
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df<true>, FUSED_THREADS,
+                                                           F.total)) != cudaSuccess)
+      return e;
+    if (coop && (long long)per_sm * sms >= a.N_t) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(a.N_t);
+      cfg.blockDim = dim3(FUSED_THREADS);
+      cfg.dynamicSmemBytes = F.total;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if ((e = cudaLaunchKernelEx(&cfg, k_loops_fused_df<true>, sa, a)) != cudaSuccess) return e;
+      *nested_done = true;
+      return cudaSuccess;
+    }
+  }
   static size_t cached = 0;
-  cudaError_t e = set_smem_once(k_loops_fused_df, F.total, cached);
-  if (e != cudaSuccess) return e;
-  k_loops_fused_df<<<a.N_t, FUSED_THREADS, F.total, s>>>(sa, a);
+  if ((e = set_smem_once(k_loops_fused_df<false>, F.total, cached)) != cudaSuccess) return e;
+  k_loops_fused_df<false><<<a.N_t, FUSED_THREADS, F.total, s>>>(sa, a);
   return cudaGetLastError();
 }
 
@@ -834,20 +894,7 @@ __global__ void k_nested_scan(LoopArgs a) {
   for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
     const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * nm;
     if (m == 1) {
-      // one Wannier band: the loop matrix is the product of the scalar overlaps
-      // (any order), taken by one warp straight from global memory
-      if (tid < 32) {
-        E prod = A::one();
-        for (int i = tid; i < Nt; i += 32) {
-          const E* wa = wj + (size_t)i * n;
-          const E* wb = wj + (size_t)(i + 1 == Nt ? 0 : i + 1) * n;
-          E acc = A::zero();
-          for (int q = 0; q < n; ++q) cfma_conj(acc, wb[q], wa[q]);
-          prod = prod * acc;
-        }
-        for (int o = 16; o > 0; o >>= 1) prod = prod * A::shfl_xor(prod, o);
-        if (tid == 0) a.nested_out[j] = phase_of(A::to64(prod));
-      }
+      nested_base_m1<E>(a, j);
       continue;
     }
     for (int e = tid; e < Nt * nm; e += nt) Wn[e] = wj[e];

@@ -60,6 +60,29 @@ __device__ __forceinline__ bool quad_angle(T a, T d, cx<T> b, T& c, cx<T>& sc, T
   return true;
 }
 
+// FP32 rotation from hardware reciprocal square roots and reciprocals (about 2 ulp):
+// the FP32 sweeps only seed the double-float refinement, whose result does not
+// depend on the last bits of the rotations.  The skip test compares squares.
+template <>
+__device__ __forceinline__ bool quad_angle<float>(float a, float d, c32 b, float& c, c32& sc, float& t,
+                                                  float& ab) {
+  const float b2 = abs2(b);
+  const float e4 = 4.f * teps<float>();
+  if (!(b2 > e4 * e4 * fabsf(a) * fabsf(d) && b2 > 0.f)) {
+    ab = 0.f;
+    return false;
+  }
+  const float inv_ab = rsqrtf(b2);
+  ab = b2 * inv_ab;
+  const float tau = 0.5f * (d - a) * inv_ab;
+  t = copysignf(__frcp_rn(fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
+  if (tau == 0.f) t = 1.f;
+  c = rsqrtf(fmaf(t, t, 1.f));
+  const float s = t * c * inv_ab;
+  sc = c32(s * b.re, s * b.im);
+  return true;
+}
+
 template <int R, typename T>
 __device__ __forceinline__ bool quad_round(cx<T> (&Ar)[4], cx<T> (&Vr)[4], int l, int base,
                                            bool frozen) {

@@ -792,8 +792,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     la.min_wannier_gap = min_wgap;
     la.nested_out = nested_out;
   }
+  bool nested_done = false;
   if (fused) {
-    BW_CUDA(bw::launch_loops_fused_df(sa, la, s), "fused states and loop kernel");
+    BW_CUDA(bw::launch_loops_fused_df(sa, la, s, &nested_done), "fused states and loop kernel");
   } else {
     if (!bw::loops_form_overlaps(la)) {
       BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
@@ -806,7 +807,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     BW_CUDA(bw::launch_wannier(la, s), "Wannier-state kernel");
     prof_mark(ctx, s, "wannier");
   }
-  if (kind == LoopKind::Nested) {
+  if (kind == LoopKind::Nested && !nested_done) {
     BW_CUDA(bw::launch_nested(la, s), "nested kernel");
     prof_mark(ctx, s, "nested");
   }
