@@ -355,6 +355,29 @@ def run_ours(args):
             ctx.set_profiling(False)
             ctx.status()
             mb_res[prec] = dict(ms=e0.elapsed_time(e1), stages=stages, phases=ph.cpu().numpy())
+        # the spin-resolved (C_down sector) and nested (lower Wannier band) loops of the
+        # same plane, mixed request, one call each
+        kinds = [k for k in args.manyband_kinds.split(",") if k in ("spin", "nested")]
+        for kind in kinds:
+            if kind == "spin":
+                call = lambda: lib.spin_resolved_wilson_loop(mb.model, mb.plane, mb.p, mb.spin_op, -1,
+                                                             precision="mixed", ctx=ctx, want_pso=False)
+            else:
+                call = lambda: lib.nested_wilson_loop(mb.model, mb.plane, mb.p, m=mb.nested_m,
+                                                      precision="mixed", ctx=ctx)
+            call()
+            ctx.status()
+            ctx.set_profiling(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            call()
+            e1.record()
+            e1.synchronize()
+            stages = dict(ctx.profile_read())
+            ctx.set_profiling(False)
+            ctx.status()
+            mb_res[kind + "_mixed"] = dict(ms=e0.elapsed_time(e1), stages=stages)
     clk = clocks.stop()
     e2e_s, lat, h2d, d2h = time_e2e(lib, ctx, wl, "mixed", args.steps, args.warmup, dev)
 
@@ -370,7 +393,7 @@ def run_ours(args):
             row = 37
             plr = I.Plane(mb.plane.N, 1, origin=tuple(np.array(mb.plane.trans_dir) * row / mb.plane.N_t))
             ref_mb, _ = oracle.wilson_loop(mb.model, plr, mb.p)
-            for prec in mb_res:
+            for prec in ("mixed", "fp64"):
                 mb_res[prec]["phase_err_rad"] = oracle.circular_match_error(mb_res[prec]["phases"][row], ref_mb[0])
         for prec in sat_res:   # rows 64 i of the fine grid are the k-points of row i
             ph = sat_res[prec]["phases"]
@@ -460,8 +483,9 @@ def run_ours(args):
                "k_points_per_call": Km}
         for prec, r in mb_res.items():
             blk[prec] = {"value": Km / (r["ms"] * 1e-3), "ms_per_call": r["ms"],
-                         "phase_err_rad_sampled_row": r.get("phase_err_rad"),
                          "stage_ms": {k: round(v, 3) for k, v in r["stages"].items()}}
+            if "phase_err_rad" in r:
+                blk[prec]["phase_err_rad_sampled_row"] = r["phase_err_rad"]
         blk["mixed_over_fp64"] = blk["mixed"]["value"] / blk["fp64"]["value"]
         line["manyband"] = blk
     if world == 1 and not args.no_cpu_baseline:
@@ -568,17 +592,18 @@ def run_profile_case(args):
     ctx = lib.Context(0)
     wl = I.config_bbh()
     case = args.profile_case
+    prec = args.profile_precision
     for _ in range(args.warmup):
         if case == "bench":
-            lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m, precision="mixed", ctx=ctx)
+            lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m, precision=prec, ctx=ctx)
         elif case == "saturated":
-            lib.wilson_loop(wl.model, I.Plane(60, 3840), wl.p, precision="mixed", ctx=ctx)
+            lib.wilson_loop(wl.model, I.Plane(60, 3840), wl.p, precision=prec, ctx=ctx)
         elif case == "manyband":
             mb = I.config_manyband(N=24)
-            lib.wilson_loop(mb.model, mb.plane, mb.p, precision="mixed", ctx=ctx)
+            lib.wilson_loop(mb.model, mb.plane, mb.p, precision=prec, ctx=ctx)
         elif case == "supercell":
             m10 = I.supercell(I.spin_hall(1.0), 10, W=2.0, seed=5)
-            lib.wilson_loop(m10, I.Plane(16, 16), 200, precision="mixed", ctx=ctx)
+            lib.wilson_loop(m10, I.Plane(16, 16), 200, precision=prec, ctx=ctx)
     torch.cuda.synchronize()
     ctx.status()
     print("profile case done:", case, flush=True)
@@ -604,6 +629,10 @@ def main(argv=None):
     ap.add_argument("--parity-samples", type=int, default=3)
     ap.add_argument("--no-manyband", action="store_true",
                     help="skip the many-band (n = 256) mixed-vs-FP64 measurement")
+    ap.add_argument("--manyband-kinds", default="wilson",
+                    help="comma list of many-band loops to time: wilson (always), spin, nested")
+    ap.add_argument("--profile-precision", choices=["mixed", "fp64"], default="mixed",
+                    help="precision of the --profile-case calls")
     ap.add_argument("--no-saturated", action="store_true",
                     help="skip the saturated-batch measurement (230 400 k-points per call)")
     ap.add_argument("--profile-case", choices=["bench", "saturated", "manyband", "supercell"],
