@@ -176,7 +176,9 @@ bw_status bw_nested_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_pla
  * S_occ = U^dagger s U (p x p), is diagonalised; its eigenvectors with eigenvalue
  * of sign `sign` (-1: C_down, +1: C_up) form the sector U_s = U V_s, which must
  * hold p/2 states at every k with min |eigenvalue| > pso_gap_tol (else
- * BW_EPSOGAP).  The Wilson loop of U_s as in bw_wilson_loop.
+ * BW_EPSOGAP).  The Wilson loop of U_s as in bw_wilson_loop.  For n > 32 and
+ * p > 64, S_occ is formed by a batched GEMM and diagonalised in FP64 on the
+ * tridiagonal path in both precisions, and the loop runs as batched GEMMs.
  * spin_op: HOST, n x n complex128 Hermitian (e.g. diag(1,-1,-1,1) = s3 (x) t3).
  * phases: DEVICE, N_t x p/2.  pso_evals: DEVICE, K x p ascending (may be NULL).
  * min_pso_gap, min_gap: DEVICE, N_t doubles each (may be NULL).  p even. */

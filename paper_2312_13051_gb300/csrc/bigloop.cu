@@ -131,6 +131,12 @@ __global__ void __launch_bounds__(256) k_geig_big(BigEigArgs a) {
       g = block_min(g, red);
       if (tid == 0) a.min_gap[i] = g;
     }
+    if (a.min_pso_gap && a.pso_gap) {
+      double g = INFINITY;
+      for (int j = tid; j < a.N; j += nt) g = fmin(g, a.pso_gap[k0 + j]);
+      g = block_min(g, red);
+      if (tid == 0) a.min_pso_gap[i] = g;
+    }
     z64* W = a.W + (long long)l * a.sW;
     z64* lam = a.lam + (long long)l * p;
     z64* vec = a.vec + (long long)l * p;
@@ -153,6 +159,74 @@ __global__ void __launch_bounds__(256) k_geig_big(BigEigArgs a) {
     for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Spin-resolved loop with many occupied bands (Sec. IV).  The occupied-space spin
+// operator S = U^dagger s U of a wave comes from one sparse application Y = sigma s U
+// and one batched GEMM U^dagger Y; its eigen-decomposition runs on the tridiagonal
+// path in FP64 (sigma = +1 for the sector s < 0, -1 for s > 0, so that the sector
+// is always the lowest p/2 eigenvectors of sigma S); the sector states U V then go
+// through the same batched-GEMM loop as the plain Wilson loop.
+// ---------------------------------------------------------------------------
+__global__ void k_spin_apply(const z64* U, z64* Y, long long W, int n, int p, const int* rowp,
+                             const int* col, const z64* val, double sigma) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= W * n * p) return;
+  const long long kw = e / ((long long)n * p);
+  const int rc = int(e - kw * n * p), r = rc / p, c = rc - r * p;
+  const z64* Uk = U + kw * (long long)n * p;
+  z64 acc(0.0, 0.0);
+  for (int q = rowp[r]; q < rowp[r + 1]; ++q) cfma(acc, val[q], Uk[(long long)col[q] * p + c]);
+  Y[e] = sigma * acc;
+}
+
+cudaError_t launch_spin_apply(const z64* U, z64* Y, long long W, int n, int p, const int* rowp,
+                              const int* col, const z64* val, double sigma, cudaStream_t s) {
+  const long long tot = W * n * p;
+  if (tot <= 0) return cudaSuccess;
+  const long long blocks = (tot + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_spin_apply<<<unsigned(blocks), 256, 0, s>>>(U, Y, W, n, p, rowp, col, val, sigma);
+  return cudaGetLastError();
+}
+
+__global__ void k_pso_post(const double* nu, int nval, long long W, long long k0, int p,
+                           double sigma, double tol, double* pso_evals, double* pso_gap,
+                           DevStatus* status) {
+  const long long kw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kw >= W) return;
+  const double* v = nu + kw * nval;
+  const int h = p / 2;
+  const long long k = k0 + kw;
+  const double lo = v[h - 1], hi = v[h];
+  const double g = fmin(fabs(lo), fabs(hi));
+  if (pso_gap) pso_gap[k] = g;
+  if (pso_evals)
+    for (int c = 0; c < p; ++c) pso_evals[k * p + c] = sigma > 0.0 ? v[c] : -v[p - 1 - c];
+  if (!(lo < 0.0 && hi > 0.0 && g > tol)) report(status, ST_EPSOGAP, k, g);
+}
+
+cudaError_t launch_pso_post(const double* nu, int nval, long long W, long long k0, int p,
+                            double sigma, double tol, double* pso_evals, double* pso_gap,
+                            DevStatus* status, cudaStream_t s) {
+  if (W <= 0) return cudaSuccess;
+  k_pso_post<<<unsigned((W + 127) / 128), 128, 0, s>>>(nu, nval, W, k0, p, sigma, tol, pso_evals,
+                                                       pso_gap, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_iota(long long* off, int* idx, long long W, long long stride) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= W) return;
+  off[t] = t * stride;
+  idx[t] = int(t);
+}
+
+cudaError_t launch_iota(long long* off, int* idx, long long W, long long stride, cudaStream_t s) {
+  if (W <= 0) return cudaSuccess;
+  k_iota<<<unsigned((W + 255) / 256), 256, 0, s>>>(off, idx, W, stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s) {

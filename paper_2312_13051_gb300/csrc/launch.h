@@ -183,14 +183,32 @@ struct BigEigArgs {
   long long sW;
   int p, nl, i0, N;
   const double* gap;      // K (absolute k = i N + j)
+  const double* pso_gap;  // K (spin-resolved loop), or NULL
   double* phases;         // N_t x p
   double* min_gap;        // N_t (optional)
+  double* min_pso_gap;    // N_t (optional)
   z64* lam;               // nl x p scratch
   z64* vec;               // nl x p scratch
   double* th;             // nl x p scratch
   int* ord;               // nl x p scratch
   DevStatus* status;
 };
+
+// Spin-resolved loop with many occupied bands (bigloop.cu).
+// Y = sigma s U for a wave of W occupied blocks (n x p each), s a sparse operator in
+// CSR form (rowp n + 1, col, val).
+cudaError_t launch_spin_apply(const z64* U, z64* Y, long long W, int n, int p, const int* rowp,
+                              const int* col, const z64* val, double sigma, cudaStream_t s);
+// From the ascending eigenvalues nu (W x nval) of sigma S_occ per wave slot: the PSO
+// eigenvalues mu = sigma nu ascending into pso_evals (K x p, optional, needs nval = p),
+// min |mu| around the split into pso_gap[k] and BW_EPSOGAP unless nu_{h-1} < 0 < nu_h
+// with min |nu| > tol (h = p / 2).
+cudaError_t launch_pso_post(const double* nu, int nval, long long W, long long k0, int p,
+                            double sigma, double tol, double* pso_evals, double* pso_gap,
+                            DevStatus* status, cudaStream_t s);
+
+// off[t] = t stride, idx[t] = t for t < W (wave slot -> explicit matrix).
+cudaError_t launch_iota(long long* off, int* idx, long long W, long long stride, cudaStream_t s);
 
 cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s);

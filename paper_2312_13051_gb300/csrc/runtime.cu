@@ -226,9 +226,9 @@ bw::DevModel dev_model(const HostPlan& P, const char* base) {
 }
 
 struct HostOp {
-  std::vector<int> row, col;
+  std::vector<int> row, col, rowp;  // entries sorted by row; rowp: CSR row pointers (n + 1)
   std::vector<z64> val;
-  size_t o_row, o_col, o_val;
+  size_t o_row, o_col, o_val, o_rowp;
 };
 
 bw_status make_op(bw_ctx* ctx, const bw_c128* S, int n, HostOp& op) {
@@ -250,6 +250,9 @@ bw_status make_op(bw_ctx* ctx, const bw_c128* S, int n, HostOp& op) {
       }
     }
   if (op.val.empty()) return fail(ctx, BW_EINVAL, "spin operator is zero");
+  op.rowp.assign(n + 1, 0);
+  for (int r : op.row) op.rowp[r + 1]++;
+  for (int r = 0; r < n; ++r) op.rowp[r + 1] += op.rowp[r];
   return BW_OK;
 }
 
@@ -416,7 +419,7 @@ bw::DevPlane dev_plane(const bw_plane* pl) {
   return d;
 }
 
-// Plain Wilson loop with many occupied bands (p > LOOP_P_MAX, n > SMALL_N_MAX).  The
+// Wilson loop with many occupied bands (p > LOOP_P_MAX, n > SMALL_N_MAX).  The
 // Wilson matrix no longer fits in shared memory, so the loop runs as batched GEMMs:
 // for a block of nl loops (their k-points are contiguous, k = i N + j) the states are
 // solved in waves of up to 2048 k-points, one GEMM forms every overlap
@@ -424,10 +427,19 @@ bw::DevPlane dev_plane(const bw_plane* pl) {
 // form W = M_{N-1} ... M_0 for all loops of the block at once, and one CTA per loop
 // takes the eigenphases.  Memory per loop: N n x p states, N + 2 p x p matrices;
 // the solver's per-k-point scratch is per wave.  The block shrinks to fit the budget.
+// With a spin operator (Sec. IV) each wave also forms S = U^dagger (sigma s U) by
+// one sparse application and one GEMM, diagonalises it in FP64 on the tridiagonal
+// path (sigma = +1 for the sector s < 0, -1 for s > 0: the sector is the lowest p/2
+// eigenvectors V of sigma S), checks the PSO gap, and keeps the sector states U V;
+// the loop then runs on those p/2 columns.
 bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const bw_plane* plane,
                        int p, bool mx, const Opts& o, double* phases, double* min_gap,
-                       cudaStream_t s) {
+                       cudaStream_t s, const HostOp* op = nullptr, int sign = -1,
+                       double* pso_evals = nullptr, double* min_pso_gap = nullptr) {
   const int n = P.n, N = plane->N, Nt = plane->N_t;
+  const bool spin = op != nullptr;
+  const int pl = spin ? p / 2 : p;  // columns the loop runs on
+  const double sigma = sign < 0 ? 1.0 : -1.0;
   const long long K = (long long)N * Nt;
   const size_t ts = mx ? sizeof(float) : sizeof(double);
   const int nval = mx ? n : std::min(n, p + 1), nvec = mx ? n : p;
@@ -440,11 +452,24 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
                sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
                sz_C = mx ? al256(size_t(n) * p * sizeof(bw::c32)) : 0,
                sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0;
-  const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C + sz_G;
-  const size_t bUk = size_t(n) * p * sizeof(z64), bPk = size_t(p) * p * sizeof(z64);
-  const size_t bEl = size_t(p) * (2 * sizeof(z64) + sizeof(double) + sizeof(int));
+  // spin split, per wave slot: the occupied block, sigma s U, S, the sector vectors and
+  // the FP64 tridiagonal solver's scratch for the p x p problem
+  const int pnval = pso_evals ? p : pl + 1;
+  const size_t d8 = sizeof(double);
+  const size_t sp_U = spin ? al256(size_t(n) * p * sizeof(z64)) : 0,
+               sp_S = spin ? al256(size_t(p) * p * sizeof(z64)) : 0,
+               sp_V = spin ? al256(size_t(p) * pl * sizeof(z64)) : 0,
+               sp_v = spin ? al256(size_t(p) * d8) : 0, sp_D = spin ? al256(size_t(p) * 2 * d8) : 0,
+               sp_lam = spin ? al256(size_t(pnval) * d8) : 0,
+               sp_Z = spin ? al256(size_t(pl) * p * d8) : 0,
+               sp_wk = spin ? al256(size_t(pl) * 6 * p * d8) : 0;
+  const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
+                       sz_G + 2 * sp_U + 2 * sp_S + sp_V + 2 * sp_v + sp_D + sp_lam + sp_Z + sp_wk +
+                       (spin ? sizeof(long long) + sizeof(int) : 0);
+  const size_t bUk = size_t(n) * pl * sizeof(z64), bPk = size_t(pl) * pl * sizeof(z64);
+  const size_t bEl = size_t(pl) * (2 * sizeof(z64) + sizeof(double) + sizeof(int));
   const size_t per_loop = size_t(N) * (bUk + bPk) + 2 * bPk + bEl;
-  size_t total = al256(blob.data.size()) + al256(size_t(K) * sizeof(double)) + 32 * 256;
+  size_t total = al256(blob.data.size()) + (spin ? 2 : 1) * al256(size_t(K) * sizeof(double)) + 40 * 256;
   const size_t avail = ctx->budget > total ? ctx->budget - total : 0;
   long long Wv = std::min<long long>(K, 2048);
   while (Wv > 1 && size_t(Wv) * per_k + per_loop > avail) Wv /= 2;
@@ -456,15 +481,16 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
   if ((st = reserve(ctx, total, s))) return st;
   char* dblob = carve(ctx, blob.data.size());
   double* gap = reinterpret_cast<double*>(carve(ctx, size_t(K) * sizeof(double)));
+  double* psog = spin ? reinterpret_cast<double*>(carve(ctx, size_t(K) * sizeof(double))) : nullptr;
   if ((st = upload(ctx, blob, dblob, s))) return st;
   z64* Ublk = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * N * bUk));
   z64* Mblk = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * N * bPk));
   z64* Wbuf[2];
   for (auto& w : Wbuf) w = reinterpret_cast<z64*>(carve(ctx, size_t(nl_max) * bPk));
-  z64* e_lam = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(p) * sizeof(z64)));
-  z64* e_vec = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(p) * sizeof(z64)));
-  double* e_th = reinterpret_cast<double*>(carve(ctx, nl_max * size_t(p) * sizeof(double)));
-  int* e_ord = reinterpret_cast<int*>(carve(ctx, nl_max * size_t(p) * sizeof(int)));
+  z64* e_lam = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(pl) * sizeof(z64)));
+  z64* e_vec = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(pl) * sizeof(z64)));
+  double* e_th = reinterpret_cast<double*>(carve(ctx, nl_max * size_t(pl) * sizeof(double)));
+  int* e_ord = reinterpret_cast<int*>(carve(ctx, nl_max * size_t(pl) * sizeof(int)));
 
   bw::LargeArgs lg;
   std::memset(&lg, 0, sizeof(lg));
@@ -497,37 +523,103 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
   MarkHook hook{ctx, s};
   lg.mark = mark_hook;
   lg.mark_user = &hook;
+  // spin split of a wave: U (wave), sigma s U, S and the FP64 eigensolve of S
+  z64 *Uw = nullptr, *Yw = nullptr, *Sw = nullptr, *Vw = nullptr;
+  bw::LargeArgs ps;
+  std::memset(&ps, 0, sizeof(ps));
+  const int* op_rowp = nullptr;
+  const int* op_col = nullptr;
+  const z64* op_val = nullptr;
+  if (spin) {
+    Uw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_U));
+    Yw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_U));
+    Sw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_S));
+    Vw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_V));
+    long long* h_off = reinterpret_cast<long long*>(carve(ctx, Wv * sizeof(long long)));
+    int* idx = reinterpret_cast<int*>(carve(ctx, Wv * sizeof(int)));
+    BW_CUDA(bw::launch_iota(h_off, idx, Wv, (long long)p * p, s), "index kernel");
+    ps.model = lg.model;
+    ps.plane = lg.plane;
+    ps.n = p;
+    ps.p = pl;
+    ps.nval = pnval;
+    ps.nvec = pl;
+    ps.nbt = pl;
+    ps.mixed = 0;
+    ps.gap = psog;
+    ps.status = ctx->status;
+    ps.A = carve(ctx, Wv * sp_S);
+    ps.dg = carve(ctx, Wv * sp_v);
+    ps.od = carve(ctx, Wv * sp_v);
+    ps.Dp = carve(ctx, Wv * sp_D);
+    ps.lam = carve(ctx, Wv * sp_lam);
+    ps.Z = carve(ctx, Wv * sp_Z);
+    ps.work = carve(ctx, Wv * sp_wk);
+    ps.U = Vw;
+    ps.Hin = Sw;
+    ps.h_off = h_off;
+    ps.idx = idx;
+    op_rowp = reinterpret_cast<const int*>(dblob + op->o_rowp);
+    op_col = reinterpret_cast<const int*>(dblob + op->o_col);
+    op_val = reinterpret_cast<const z64*>(dblob + op->o_val);
+  }
   prof_start(ctx, s);
-  const long long sU = (long long)n * p, sP = (long long)p * p;
+  const long long sU = (long long)n * pl, sP = (long long)pl * pl;
   for (int i0 = 0; i0 < Nt; i0 += nl_max) {
     const int nl = std::min(nl_max, Nt - i0);
     const long long kb = (long long)i0 * N, Kb = (long long)nl * N;
     for (long long w0 = 0; w0 < Kb; w0 += Wv) {
+      const long long Wn = std::min(Wv, Kb - w0);
       lg.k0 = kb + w0;
-      lg.W = std::min(Wv, Kb - w0);
-      lg.U = Ublk + w0 * sU;
+      lg.W = Wn;
+      lg.U = spin ? Uw : Ublk + w0 * sU;
       BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
+      if (!spin) continue;
+      BW_CUDA(bw::launch_spin_apply(Uw, Yw, Wn, n, p, op_rowp, op_col, op_val, sigma, s),
+              "spin operator kernel");
+      bw::GemmArgs g;
+      std::memset(&g, 0, sizeof(g));
+      g.A = Uw; g.B = Yw; g.C = Sw;
+      g.m = p; g.n = p; g.k = n; g.opA = 1;
+      g.lda = p; g.ldb = p; g.ldc = p;
+      g.sA = (long long)n * p; g.sB = (long long)n * p; g.sC = (long long)p * p;
+      g.batch = Wn;
+      BW_CUDA(bw::launch_zgemm(g, s), "spin operator GEMM");
+      ps.k0 = 0;
+      ps.W = Wn;
+      BW_CUDA(bw::launch_states_large(ps, s), "spin operator eigensolve");
+      BW_CUDA(bw::launch_pso_post(reinterpret_cast<const double*>(ps.lam), pnval, Wn, kb + w0, p, sigma,
+                                  o.pso_gap_tol, pso_evals, psog, ctx->status, s),
+              "spin sector check");
+      std::memset(&g, 0, sizeof(g));
+      g.A = Uw; g.B = Vw; g.C = Ublk + w0 * sU;
+      g.m = n; g.n = pl; g.k = p; g.opA = 0;
+      g.lda = p; g.ldb = pl; g.ldc = pl;
+      g.sA = (long long)n * p; g.sB = (long long)p * pl; g.sC = sU;
+      g.batch = Wn;
+      BW_CUDA(bw::launch_zgemm(g, s), "sector states GEMM");
+      prof_mark(ctx, s, "pso_split");
     }
     // every overlap of the block: batch b = l N + j, A = U(k_{j+1}) (closing on j = 0)
     bw::GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.A = Ublk; g.B = Ublk; g.C = Mblk;
-    g.m = p; g.n = p; g.k = n; g.opA = 1;
-    g.lda = p; g.ldb = p; g.ldc = p;
+    g.m = pl; g.n = pl; g.k = n; g.opA = 1;
+    g.lda = pl; g.ldb = pl; g.ldc = pl;
     g.sA = sU; g.sB = sU; g.sC = sP;
     g.a_next_N = N;
     g.batch = Kb;
     BW_CUDA(bw::launch_zgemm(g, s), "overlap GEMM");
     prof_mark(ctx, s, "overlaps");
     // W = M_{N-1} ... M_0 for the nl loops at once
-    const z64* Wcur = Mblk;  // M_0 of loop l at Mblk + l N p^2
+    const z64* Wcur = Mblk;  // M_0 of loop l at Mblk + l N pl^2
     long long sWcur = (long long)N * sP;
     for (int j = 1; j < N; ++j) {
       z64* Wout = Wbuf[j & 1];
       std::memset(&g, 0, sizeof(g));
       g.A = Mblk + (long long)j * sP; g.B = Wcur; g.C = Wout;
-      g.m = p; g.n = p; g.k = p; g.opA = 0;
-      g.lda = p; g.ldb = p; g.ldc = p;
+      g.m = pl; g.n = pl; g.k = pl; g.opA = 0;
+      g.lda = pl; g.ldb = pl; g.ldc = pl;
       g.sA = (long long)N * sP; g.sB = sWcur; g.sC = sP;
       g.batch = nl;
       BW_CUDA(bw::launch_zgemm(g, s), "loop-product GEMM");
@@ -539,13 +631,15 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
     std::memset(&e, 0, sizeof(e));
     e.W = const_cast<z64*>(Wcur);
     e.sW = sWcur;
-    e.p = p;
+    e.p = pl;
     e.nl = nl;
     e.i0 = i0;
     e.N = N;
     e.gap = gap;
+    e.pso_gap = psog;
     e.phases = phases;
     e.min_gap = min_gap;
+    e.min_pso_gap = min_pso_gap;
     e.lam = e_lam;
     e.vec = e_vec;
     e.th = e_th;
@@ -594,25 +688,29 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
                   first + m, p);
     if (!std::isfinite(cut)) return fail(ctx, BW_EINVAL, "cut is not finite");
   }
-  const bool big = p_eff > bw::LOOP_P_MAX;
-  if (big && kind != LoopKind::Plain)
-    return fail(ctx, BW_EINVAL, "%s loop supports p <= %d (p = %d)",
-                kind == LoopKind::Spin ? "spin-resolved" : "nested", bw::LOOP_P_MAX, p_eff);
-  if (large && kind == LoopKind::Spin && p > 64)
-    return fail(ctx, BW_EINVAL, "spin-resolved loop for n > %d supports p <= 64 (p = %d)", bw::SMALL_N_MAX, p);
+  if (kind == LoopKind::Nested && p_eff > bw::LOOP_P_MAX)
+    return fail(ctx, BW_EINVAL, "nested loop supports p <= %d (p = %d)", bw::LOOP_P_MAX, p_eff);
+  // many occupied bands: batched-GEMM loops (the spin-resolved one from p > 64 at
+  // large n, where the split runs on the tridiagonal path)
+  const bool big = (kind == LoopKind::Plain && p_eff > bw::LOOP_P_MAX) ||
+                   (kind == LoopKind::Spin && large && p > 64);
   const Opts o = resolve_opts(opts, P.tmax);
   if (o.unitarise && p_eff > 32) return fail(ctx, BW_EINVAL, "unitarise supports p <= 32");
   const long long K = (long long)plane->N * plane->N_t;
   Blob blob;
   plan_to_blob(P, blob);
-  if (big) {
-    begin_call(ctx, s);
-    return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s);
-  }
   if (kind == LoopKind::Spin) {
     op.o_row = blob.add(op.row);
     op.o_col = blob.add(op.col);
     op.o_val = blob.add(op.val);
+    op.o_rowp = blob.add(op.rowp);
+  }
+  if (big) {
+    begin_call(ctx, s);
+    if (kind == LoopKind::Spin)
+      return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s, &op, sign,
+                          pso_evals, min_pso_gap);
+    return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s);
   }
   const size_t bU = al256(size_t(K) * n * p_eff * sizeof(z64));
   const size_t bGap = al256(size_t(K) * sizeof(double));

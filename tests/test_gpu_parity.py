@@ -433,3 +433,41 @@ def test_mixed_four_band_nested_double_float(lib, ctx):
         assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= DF_TOL
         assert circ_err_rows(nest.cpu().numpy(), ref_n) <= DF_TOL
         assert abs(wg.cpu().numpy().min() - ref_wg) <= 1e-8
+
+
+# ---------------------------------------------------------------- spin-resolved, p > 64
+# Spin-resolved loop with many occupied bands: S = U^dagger s U by GEMM, its FP64
+# eigensolve on the tridiagonal path, the sector states U V through the batched loop.
+SPIN_MANY = {
+    # disordered spin-Hall supercell (s_z conserved: PSO eigenvalues exactly +-1,
+    # 36-fold degenerate), n = 144, p = 72
+    "disordered_L6": (lambda: I.supercell(I.spin_hall(1.0), 6, W=2.0, seed=7),
+                      lambda: np.kron(np.eye(36), I.SPIN_HALL_SZ), P(6, 5), 72),
+    # Eq. 9 supercell with s3 (x) t3 (a spread PSO spectrum), n = 144, p = 72
+    "choti_L6": (lambda: I.supercell(I.choti_eq9(1.0), 6),
+                 lambda: np.kron(np.eye(36), np.diag([1.0, -1.0, -1.0, 1.0])), P(5, 4, origin=(0, 0, 0.1)), 72),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(SPIN_MANY))
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_spin_resolved_many_bands(lib, ctx, case, precision, sign):
+    mk, mkS, plane, p = SPIN_MANY[case]
+    model, S = mk(), mkS()
+    ref, rpso, rpg, _ = oracle.spin_resolved_wilson_loop(model, plane, p, S, sign)
+    ph, pso, pg, _ = lib.spin_resolved_wilson_loop(model, plane, p, S, sign, precision=precision,
+                                                   ctx=ctx)
+    assert ph.shape == (plane.N_t, p // 2)
+    assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+    assert np.abs(pso.cpu().numpy() - rpso).max() <= 1e-9
+    assert abs(pg.cpu().numpy().min() - rpg) <= 1e-9
+
+
+def test_spin_resolved_many_bands_status(lib, ctx):
+    """A spin operator whose projected spectrum has no gap at zero fails with EPSOGAP."""
+    model = I.supercell(I.spin_hall(1.0), 6, W=2.0, seed=7)
+    S = np.kron(np.eye(36), np.diag([1.0, 1.0, 1.0, 1.0]))   # every PSO eigenvalue is +1
+    with pytest.raises(lib.BWError) as e:
+        lib.spin_resolved_wilson_loop(model, P(4, 3), 72, S, -1, ctx=ctx)
+    assert e.value.status == "EPSOGAP"
