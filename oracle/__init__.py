@@ -16,4 +16,5 @@ from .wilson import (  # noqa: F401
     overlap, polar_factor, wilson_matrix, eigenphases, wilson_loop,
     projected_spin_sector, spin_resolved_wilson_loop, nested_wilson_loop,
     cyclic_wilson_matrix, winding, circular_match_error, eigh_batched,
+    plaquette_flux, plaquette_corners, plaquette_matrix,
 )

@@ -23,7 +23,8 @@ def _all_pins():
             functools.partial(pins.test_bbh_nested_polarisation, 0.5, np.pi),
             pins.test_choti_eq9_paper_statements, pins.test_eigenphases_known_spectrum,
             pins.test_two_band_closed_form_eigenvectors,
-            pins.test_eigh_against_independent_jacobi]
+            pins.test_eigh_against_independent_jacobi, pins.test_plaquette_flux_chern_eq4,
+            pins.test_plaquette_flux_spin_sectors]
     return out
 
 
@@ -71,6 +72,10 @@ def _highest_bands(H, p):
     return lam, V[:, -p:], (lam[p] - lam[p - 1]) if p < H.shape[0] else np.inf
 
 
+def _reversed_plaquette(U, i, j, N, Nt):
+    return [U[i][j], U[i][(j + 1) % N], U[(i + 1) % Nt][(j + 1) % N], U[(i + 1) % Nt][j]]
+
+
 def _right_as_left_eigvecs_eigenphases(Wm):
     return np.sort(np.angle(np.linalg.eigvals(Wm.conj())))
 
@@ -85,6 +90,7 @@ MUTATIONS = {
     "unprojected_spin_operator": ("projected_spin_sector", _unprojected_spin),
     "highest_bands": ("occupied_states", _highest_bands),
     "conjugated_eigenphases": ("eigenphases", _right_as_left_eigvecs_eigenphases),
+    "reversed_plaquette": ("plaquette_corners", _reversed_plaquette),
 }
 
 

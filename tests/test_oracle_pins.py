@@ -397,3 +397,51 @@ def test_unitarise_option():
     Wu = O.wilson_matrix(U, unitarise=True)
     np.testing.assert_allclose(np.abs(np.linalg.eigvals(Wu)), 1.0, atol=1e-12)
     assert np.abs(np.abs(np.linalg.eigvals(O.wilson_matrix(U))) - 1).max() > 1e-3
+
+
+# ---------------------------------------------------------------- plaquette flux
+def test_plaquette_flux_chern_eq4():
+    """Sec. V coupling-matrix flux: Eq. 4 carries C = 1 (paper, Fig. 1), equal to the
+    WCC winding of the same grid and to the degree of d/|d|; m = 3.5 is trivial."""
+    model = I.chern_eq4(1.5)
+    flux, C = O.plaquette_flux(model, P(24, 24), 1)
+    assert abs(C - GOLDEN["chern_eq4_wcc_winding"]["value"]) < 1e-9
+    assert np.all(np.abs(flux) <= np.pi)
+    ph, _ = O.wilson_loop(model, P(24, 24), 1)
+    assert abs(C - O.winding(ph)) < 1e-9
+    d = lambda kx, ky: np.array([np.sin(kx), np.sin(ky), np.cos(kx) + np.cos(ky) + 1.5])
+    assert abs(abs(C) - abs(_skyrmion_degree(d, 48))) < 1e-9
+    _, C0 = O.plaquette_flux(I.chern_eq4(3.5), P(16, 16), 1)
+    assert abs(C0) < 1e-9
+
+
+def test_plaquette_flux_spin_sectors():
+    """Spin-Hall model: total flux 0, s_z-down sector -1, s_z-up sector +1 (Sec. IV);
+    the same with the independent product of normalised link determinants."""
+    wl = I.config_spin_hall()
+    plane = P(20, 20)
+    _, C = O.plaquette_flux(wl.model, plane, 2)
+    _, Cd = O.plaquette_flux(wl.model, plane, 2, wl.spin_op, -1)
+    _, Cu = O.plaquette_flux(wl.model, plane, 2, wl.spin_op, +1)
+    assert abs(C) < 1e-9 and abs(Cd + 1) < 1e-9 and abs(Cu - 1) < 1e-9
+    assert abs(C - _plaquette_chern(wl.model, 20, 2)) < 1e-9
+    assert abs(O.plaquette_flux(I.chern_eq4(1.5), P(16, 16), 1)[1]
+               - _plaquette_chern(I.chern_eq4(1.5), 16, 1)) < 1e-9
+
+
+def test_plaquette_flux_gauge_invariant():
+    """Each plaquette's flux is unchanged by a random unitary change of basis of the
+    states at every corner (gauge invariance of the closed loop)."""
+    rng = np.random.default_rng(9)
+    model = I.random_hermitian_model(5, 3)
+    f = O.plane_points(P(3, 3))
+    U = [[O.occupied_states(O.bloch_hamiltonian(model, f[i, j]), 2)[1] for j in range(3)]
+         for i in range(3)]
+    G = [[np.linalg.qr(rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2)))[0]
+          for _ in range(3)] for _ in range(3)]
+    Ug = [[U[i][j] @ G[i][j] for j in range(3)] for i in range(3)]
+    for i in range(3):
+        for j in range(3):
+            a = np.angle(np.linalg.det(O.plaquette_matrix(O.plaquette_corners(U, i, j, 3, 3))))
+            b = np.angle(np.linalg.det(O.plaquette_matrix(O.plaquette_corners(Ug, i, j, 3, 3))))
+            assert abs(np.angle(np.exp(1j * (a - b)))) < 1e-12
