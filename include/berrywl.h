@@ -189,6 +189,26 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
                                        double* phases, double* pso_evals,
                                        double* min_pso_gap, double* min_gap, void* stream);
 
+/* Plaquette Berry flux (the coupling-matrix method of BerryEasy's WSpinLine, used in
+ * the disordered-quadrupole example of Sec. V): the plane's grid is cut into N x N_t
+ * plaquettes; plaquette (j, i) has corners k(j, i), k(j+1, i), k(j+1, i+1), k(j, i+1)
+ * (both directions close cyclically, so trans_dir must be an integer vector) and its
+ * integrated Berry flux is the argument of the determinant of the Wilson loop of the
+ * occupied states around it, traversed k(j, i) -> k(j, i+1) -> k(j+1, i+1) ->
+ * k(j+1, i) -> k(j, i) with Eq. 2 overlaps; with this orientation the total flux / 2pi
+ * equals the Eq. 6 winding of the same states (the Chern number).  With spin_op
+ * (HOST, n x n, may be NULL) the states are the PSO sector of sign `sign` as in
+ * bw_spin_resolved_wilson_loop, and the total is the spin-Chern number C_down
+ * (sign -1) or C_up (+1).
+ * flux: DEVICE, N_t x N doubles in (-pi, pi] (row i, column j).  chern: DEVICE, one
+ * double, sum(flux) / 2pi (may be NULL).  min_gap, min_pso_gap: DEVICE, N_t doubles
+ * per transverse row (may be NULL; min_pso_gap only with spin_op).  p (p/2 with a
+ * spin operator) <= 64; with a spin operator and n > 32 also p <= 64. */
+bw_status bw_plaquette_flux(bw_ctx* ctx, const bw_model* model, const bw_plane* plane, int32_t p,
+                            const bw_c128* spin_op, int32_t sign, bw_precision prec,
+                            const bw_opts* opts, double* flux, double* chern, double* min_gap,
+                            double* min_pso_gap, void* stream);
+
 /* Winding of the hybrid Wannier centres over the transverse direction (Sec. II B,
  * Eq. 6: C = sum_n xbar_n(k_y = 2 pi) - sum_n xbar_n(k_y = 0), in units of the
  * lattice constant).  For the rows of `phases` (N_t x p, as written by the loop

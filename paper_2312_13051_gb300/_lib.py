@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                                    i32, vp, i32, i32, C.POINTER(bw_opts), vp,
                                                    vp, vp, vp, vp]),
             "bw_winding": (i32, [vp, vp, i32, i32, vp, vp, vp]),
+            "bw_plaquette_flux": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32, vp, i32,
+                                        i32, C.POINTER(bw_opts), vp, vp, vp, vp, vp]),
             "bw_wilson_loop_noalloc": (i32, [C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
                                              C.POINTER(bw_opts), vp, vp, vp, C.c_char_p,
                                              C.c_size_t]),
@@ -111,7 +113,7 @@ def exported_symbols():
     return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
             "bw_profile_read", "bw_build_hk",
             "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
-            "bw_spin_resolved_wilson_loop", "bw_winding", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
+            "bw_spin_resolved_wilson_loop", "bw_winding", "bw_plaquette_flux", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
             "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
             "bw_server_poll", "bw_server_wait", "bw_server_outstanding"]
 
@@ -331,6 +333,34 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     if check:
         ctx.status()
     return ph, pso, pg, gap
+
+
+def plaquette_flux(model, plane, p: int, spin_op=None, sign: int = -1, precision: str = "fp64",
+                   ctx: Context | None = None, check=True, **opts):
+    """Plaquette Berry flux: (flux[N_t, N], chern scalar, min_gap[N_t], min_pso_gap[N_t]
+    or None) as CUDA tensors; with ``spin_op`` the flux of the PSO sector ``sign``."""
+    import torch
+    ctx = ctx or context()
+    dev = _cuda_device(ctx)
+    hm = _HostModel(model)
+    pl = _plane(plane)
+    o = _opts(**opts)
+    S = None
+    if spin_op is not None:
+        S = np.ascontiguousarray(spin_op, dtype=np.complex128)
+        if S.shape != (model.n, model.n):
+            raise BWError(1, f"spin operator must be {model.n} x {model.n}")
+    flux = _empty((plane.N_t, plane.N), torch.float64, dev)
+    chern = _empty((), torch.float64, dev)
+    gap = _empty((plane.N_t,), torch.float64, dev)
+    pg = _empty((plane.N_t,), torch.float64, dev) if S is not None else None
+    ctx.check(ctx.lib.bw_plaquette_flux(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
+                                        S.ctypes.data if S is not None else None, int(sign),
+                                        PRECISION[precision], C.byref(o), _ptr(flux), _ptr(chern),
+                                        _ptr(gap), _ptr(pg), _stream_ptr()))
+    if check:
+        ctx.status()
+    return flux, chern, gap, pg
 
 
 def winding(phases, ctx: Context | None = None, check=True, want_sums=False):

@@ -219,6 +219,12 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);
 cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
                               cudaStream_t s);
 
+// Plaquette Berry flux of the states in a.U (K x n x p, p <= 64): link determinants
+// (Lx, Ly: K unit complex numbers each, scratch), flux (N_t x N) and chern = sum / 2pi
+// (device double); a.min_gap / a.min_pso_gap per transverse row from a.gap / a.pso_gap.
+cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux, double* chern,
+                              cudaStream_t s);
+
 // Winding of the summed Wannier centres over the transverse direction (Eq. 6).
 cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,
                            cudaStream_t s);

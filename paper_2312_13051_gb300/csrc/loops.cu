@@ -1020,6 +1020,133 @@ cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Plaquette Berry flux (the coupling-matrix method of the WSpinLine example): link
+// variables from the determinants of the overlaps between neighbouring k-points,
+//   Lx(j, i) = det U(j+1, i)^dag U(j, i),   Ly(j, i) = det U(j, i+1)^dag U(j, i),
+// kept as unit complex numbers (phase only); the plaquette at (j, i), traversed
+// k(j, i) -> k(j, i+1) -> k(j+1, i+1) -> k(j+1, i) -> k(j, i), has the Wilson loop
+// determinant Ly(j, i) Lx(j, i+1) conj(Ly(j+1, i)) conj(Lx(j, i)) and its flux is the
+// argument of that product, in (-pi, pi].  One CTA per k-point forms both overlaps in
+// shared memory and takes each determinant's phase by LU with partial pivoting.
+// ---------------------------------------------------------------------------
+__global__ void k_plaquette_links(const z64* U, int n, int p, int N, int Nt, z64* Lx, z64* Ly) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  z64* A = reinterpret_cast<z64*>(smem);
+  __shared__ int piv;
+  __shared__ z64 dsh;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long K = (long long)N * Nt;
+  for (long long k = blockIdx.x; k < K; k += gridDim.x) {
+    const int i = int(k / N), j = int(k - (long long)i * N);
+    const z64* Uk = U + k * (long long)n * p;
+    for (int dir = 0; dir < 2; ++dir) {
+      const long long kb = dir == 0 ? (long long)i * N + (j + 1 == N ? 0 : j + 1)
+                                    : (long long)(i + 1 == Nt ? 0 : i + 1) * N + j;
+      const z64* Ub = U + kb * (long long)n * p;
+      for (int e = tid; e < p * p; e += nt) {
+        const int r = e / p, c = e - r * p;
+        z64 acc(0.0, 0.0);
+        for (int q = 0; q < n; ++q) cfma_conj(acc, Ub[(long long)q * p + r], Uk[(long long)q * p + c]);
+        A[e] = acc;
+      }
+      if (tid == 0) dsh = z64(1.0, 0.0);
+      __syncthreads();
+      for (int c = 0; c < p; ++c) {
+        if (tid == 0) {
+          int best = c;
+          double bmax = abs2(A[c * p + c]);
+          for (int r = c + 1; r < p; ++r) {
+            const double v = abs2(A[r * p + c]);
+            if (v > bmax) {
+              bmax = v;
+              best = r;
+            }
+          }
+          piv = best;
+          const z64 pv = A[best * p + c];
+          const double a = sqrt(bmax);
+          z64 d = a > 0.0 ? dsh * z64(pv.re / a, pv.im / a) : z64(0.0, 0.0);
+          if (best != c) d = z64(-d.re, -d.im);
+          dsh = d;
+        }
+        __syncthreads();
+        const int r0 = piv;
+        if (r0 != c)
+          for (int cc = c + tid; cc < p; cc += nt) {
+            const z64 t = A[c * p + cc];
+            A[c * p + cc] = A[r0 * p + cc];
+            A[r0 * p + cc] = t;
+          }
+        __syncthreads();
+        const z64 pv = A[c * p + c];
+        const double pa = abs2(pv);
+        for (int r = c + 1 + tid; r < p; r += nt) {  // multipliers A[r][c] / A[c][c]
+          const z64 v = A[r * p + c];
+          A[r * p + c] = pa > 0.0 ? z64((v.re * pv.re + v.im * pv.im) / pa, (v.im * pv.re - v.re * pv.im) / pa)
+                                  : z64(0.0, 0.0);
+        }
+        __syncthreads();
+        const int w = p - c - 1;
+        for (int e = tid; e < w * w; e += nt) {
+          const int r = c + 1 + e / w, cc = c + 1 + e % w;
+          A[r * p + cc] = A[r * p + cc] - A[r * p + c] * A[c * p + cc];
+        }
+        __syncthreads();
+      }
+      if (tid == 0) (dir == 0 ? Lx : Ly)[k] = dsh;
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_plaquette_flux(const z64* Lx, const z64* Ly, int N, int Nt, double* flux) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (long long)N * Nt) return;
+  const int i = int(k / N), j = int(k - (long long)i * N);
+  const int j1 = j + 1 == N ? 0 : j + 1, i1 = i + 1 == Nt ? 0 : i + 1;
+  const z64 w = Ly[k] * Lx[(long long)i1 * N + j] * conj(Ly[(long long)i * N + j1]) * conj(Lx[k]);
+  flux[k] = atan2(w.im, w.re);
+}
+
+// Sum of the fluxes / 2pi in a fixed order (one CTA), and per transverse row the
+// minimum direct and PSO gaps.
+__global__ void k_plaquette_sum(const double* flux, const double* gap, const double* pso_gap, int N,
+                                int Nt, double* chern, double* min_gap, double* min_pso_gap) {
+  __shared__ double red[64];
+  const long long K = (long long)N * Nt;
+  double acc = 0.0;
+  for (long long k = threadIdx.x; k < K; k += blockDim.x) acc += flux[k];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0 && chern) *chern = acc / 6.283185307179586;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) {
+    double g = INFINITY, gp = INFINITY;
+    for (int j = 0; j < N; ++j) {
+      if (gap) g = fmin(g, gap[(long long)i * N + j]);
+      if (pso_gap) gp = fmin(gp, pso_gap[(long long)i * N + j]);
+    }
+    if (min_gap) min_gap[i] = g;
+    if (min_pso_gap) min_pso_gap[i] = gp;
+  }
+}
+
+cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux, double* chern,
+                              cudaStream_t s) {
+  const long long K = (long long)a.N * a.N_t;
+  if (K <= 0) return cudaSuccess;
+  const size_t sm = size_t(a.p) * a.p * sizeof(z64);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_plaquette_links, sm, cached);
+  if (e != cudaSuccess) return e;
+  const long long cap = 152LL * 16;
+  k_plaquette_links<<<int(K < cap ? K : cap), a.p <= 8 ? 32 : 128, sm, s>>>(a.U, a.n, a.p, a.N, a.N_t, Lx, Ly);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_plaquette_flux<<<int((K + 127) / 128), 128, 0, s>>>(Lx, Ly, a.N, a.N_t, flux);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_plaquette_sum<<<1, 256, 0, s>>>(flux, a.gap, a.pso_gap, a.N, a.N_t, chern, a.min_gap, a.min_pso_gap);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
   if (scan_nested_fit(a)) {

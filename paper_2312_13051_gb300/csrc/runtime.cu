@@ -653,16 +653,18 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
 }
 
 // Shared driver of the three loop entry points.
-enum class LoopKind { Plain, Nested, Spin };
+enum class LoopKind { Plain, Nested, Spin, Plaquette };
 
 bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_plane* plane,
                    int p, bw_precision prec, const bw_opts* opts, const bw_c128* spin_op,
                    int sign, double cut, int first, int m, double* phases, double* min_gap,
                    double* nested_out, double* min_wgap, double* pso_evals, double* min_pso_gap,
-                   cudaStream_t s) {
+                   cudaStream_t s, double* chern_out = nullptr) {
   if (!ctx) return BW_EINVAL;
   ctx->err.clear();
-  bw_status st = check_plane(ctx, plane, kind == LoopKind::Nested);
+  // the PSO split runs for the spin-resolved loop and for the flux of a spin sector
+  const bool spin = kind == LoopKind::Spin || (kind == LoopKind::Plaquette && spin_op != nullptr);
+  bw_status st = check_plane(ctx, plane, kind == LoopKind::Nested || kind == LoopKind::Plaquette);
   if (st) return st;
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
   if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
@@ -675,7 +677,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const bool large = n > bw::SMALL_N_MAX;
   int p_eff = p;
   HostOp op;
-  if (kind == LoopKind::Spin) {
+  if (spin) {
     if (p % 2) return fail(ctx, BW_EINVAL, "spin-resolved loop needs an even p (p = %d)", p);
     if (sign != -1 && sign != 1) return fail(ctx, BW_EINVAL, "sign must be -1 or +1");
     if ((st = make_op(ctx, spin_op, n, op))) return st;
@@ -690,6 +692,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   }
   if (kind == LoopKind::Nested && p_eff > bw::LOOP_P_MAX)
     return fail(ctx, BW_EINVAL, "nested loop supports p <= %d (p = %d)", bw::LOOP_P_MAX, p_eff);
+  if (kind == LoopKind::Plaquette && (p_eff > bw::LOOP_P_MAX || (spin && large && p > 64)))
+    return fail(ctx, BW_EINVAL, "plaquette flux supports p <= %d (and p <= 64 with a spin operator "
+                "for n > %d)", bw::LOOP_P_MAX, bw::SMALL_N_MAX);
   // many occupied bands: batched-GEMM loops (the spin-resolved one from p > 64 at
   // large n, where the split runs on the tridiagonal path)
   const bool big = (kind == LoopKind::Plain && p_eff > bw::LOOP_P_MAX) ||
@@ -699,7 +704,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const long long K = (long long)plane->N * plane->N_t;
   Blob blob;
   plan_to_blob(P, blob);
-  if (kind == LoopKind::Spin) {
+  if (spin) {
     op.o_row = blob.add(op.row);
     op.o_col = blob.add(op.col);
     op.o_val = blob.add(op.val);
@@ -729,8 +734,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     transport_only = bw::loops_transport_only(q);
   }
   const size_t bNu = transport_only ? al256(size_t(K) * p_eff * m * sizeof(z64)) : 0;
-  const size_t bPso = kind == LoopKind::Spin ? al256(size_t(K) * sizeof(double)) : 0;
-  size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bNu + bPso + 4096;
+  const size_t bPso = spin ? al256(size_t(K) * sizeof(double)) : 0;
+  const size_t bLink = kind == LoopKind::Plaquette ? al256(size_t(K) * sizeof(z64)) : 0;
+  size_t total = al256(blob.data.size()) + bU + bGap + bM + bW + bNu + bPso + 2 * bLink + 4096;
   // large n: per-k-point scratch of the tridiagonal solver, processed in waves
   const bool mx = prec == BW_MIXED;
   const size_t ts = mx ? sizeof(float) : sizeof(double);
@@ -744,7 +750,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
                sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
                sz_C = mx ? al256(size_t(n) * p * sizeof(bw::c32)) : 0,
                sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0,
-               sz_Uf = kind == LoopKind::Spin ? al256(size_t(n) * p * sizeof(z64)) : 0;
+               sz_Uf = spin ? al256(size_t(n) * p * sizeof(z64)) : 0;
   const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
                        sz_G + sz_Uf;
   long long Wv = 0;
@@ -763,6 +769,8 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   z64* w = bW ? reinterpret_cast<z64*>(carve(ctx, bW)) : nullptr;
   z64* nu_buf = bNu ? reinterpret_cast<z64*>(carve(ctx, bNu)) : nullptr;
   double* psog = bPso ? reinterpret_cast<double*>(carve(ctx, bPso)) : nullptr;
+  z64* Lx = bLink ? reinterpret_cast<z64*>(carve(ctx, bLink)) : nullptr;
+  z64* Ly = bLink ? reinterpret_cast<z64*>(carve(ctx, bLink)) : nullptr;
   if ((st = upload(ctx, blob, dblob, s))) return st;
 
   bw::StatesArgs sa;
@@ -777,7 +785,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   sa.max_sweeps = o.max_sweeps;
   sa.gap_tol = o.gap_tol;
   sa.op.nnz = 0;
-  if (kind == LoopKind::Spin) {
+  if (spin) {
     sa.op.nnz = int(op.val.size());
     sa.op.row = reinterpret_cast<const int*>(dblob + op.o_row);
     sa.op.col = reinterpret_cast<const int*>(dblob + op.o_col);
@@ -793,7 +801,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   // Mixed precision with four bands and the scan loop kernels: states, overlaps and
   // loop products in double-float on the FP32 pipe (U and w as complex double-float)
   bool use_df = false, fused = false;
-  if (!large && sa.mixed && kind != LoopKind::Spin) {
+  if (!large && sa.mixed && (kind == LoopKind::Plain || kind == LoopKind::Nested)) {
     bw::LoopArgs q;
     std::memset(&q, 0, sizeof(q));
     q.n = n;
@@ -849,9 +857,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
       lg.k0 = k0;
       lg.W = std::min(Wv, K - k0);
       // the wave's occupied blocks go straight to U, or through the spin split
-      lg.U = kind == LoopKind::Spin ? Ufull : U + k0 * (long long)n * p;
+      lg.U = spin ? Ufull : U + k0 * (long long)n * p;
       BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
-      if (kind == LoopKind::Spin) {
+      if (spin) {
         BW_CUDA(bw::launch_pso_global(sa, Ufull, k0, lg.W, s), "spin split kernel");
         prof_mark(ctx, s, "pso_split");
       }
@@ -876,6 +884,12 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.min_pso_gap = min_pso_gap;
   la.status = ctx->status;
   la.u_df = use_df ? 1 : 0;
+  if (kind == LoopKind::Plaquette) {
+    BW_CUDA(bw::launch_plaquettes(la, Lx, Ly, phases, chern_out, s), "plaquette kernels");
+    prof_mark(ctx, s, "plaquettes");
+    end_call(ctx, s);
+    return BW_OK;
+  }
   if (kind == LoopKind::Nested) {
     la.nested = 1;
     // the kernels measure phases from cut as (theta - cut) wrapped into [0, 2 pi)
@@ -1260,6 +1274,19 @@ bw_status bw_nested_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_pla
   return run_loop(ctx, LoopKind::Nested, model, plane, p, prec, opts, nullptr, 0, cut, first, m,
                   phases, min_gap, nested, min_wannier_gap, nullptr, nullptr,
                   static_cast<cudaStream_t>(stream));
+}
+
+bw_status bw_plaquette_flux(bw_ctx* ctx, const bw_model* model, const bw_plane* plane, int32_t p,
+                            const bw_c128* spin_op, int32_t sign, bw_precision prec,
+                            const bw_opts* opts, double* flux, double* chern, double* min_gap,
+                            double* min_pso_gap, void* stream) {
+  if (ctx && !flux) {
+    ctx->err.clear();
+    return fail(ctx, BW_EINVAL, "flux output is NULL");
+  }
+  return run_loop(ctx, LoopKind::Plaquette, model, plane, p, prec, opts, spin_op, sign, 0.0, 0, 0,
+                  flux, min_gap, nullptr, nullptr, nullptr, spin_op ? min_pso_gap : nullptr,
+                  static_cast<cudaStream_t>(stream), chern);
 }
 
 bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,

@@ -471,3 +471,59 @@ def test_spin_resolved_many_bands_status(lib, ctx):
     with pytest.raises(lib.BWError) as e:
         lib.spin_resolved_wilson_loop(model, P(4, 3), 72, S, -1, ctx=ctx)
     assert e.value.status == "EPSOGAP"
+
+
+# ---------------------------------------------------------------- plaquette flux
+PLAQ = {
+    "chern_eq4": (lambda: I.chern_eq4(1.5), None, P(16, 16), 1, -1),
+    "spin_hall_down": (lambda: I.spin_hall(1.0), I.SPIN_HALL_SZ, P(20, 20), 2, -1),
+    "spin_hall_up": (lambda: I.spin_hall(1.0), I.SPIN_HALL_SZ, P(20, 20), 2, 1),
+    "random6_p3": (lambda: I.random_hermitian_model(6, 2), None, P(7, 5), 3, -1),
+    "supercell_L4_down": (lambda: I.supercell(I.spin_hall(1.0), 4, W=1.5, seed=3),
+                          np.kron(np.eye(16), I.SPIN_HALL_SZ), P(5, 4), 32, -1),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(PLAQ))
+def test_plaquette_flux_parity(lib, ctx, case, precision):
+    """Flux of every plaquette against the oracle (circular distance) and the total."""
+    mk, S, plane, p, sign = PLAQ[case]
+    model = mk()
+    rflux, rC = oracle.plaquette_flux(model, plane, p, S, sign)
+    flux, C, gap, pg = lib.plaquette_flux(model, plane, p, S, sign, precision=precision, ctx=ctx)
+    d = np.abs(np.angle(np.exp(1j * (flux.cpu().numpy() - rflux))))
+    assert d.max() <= TOL[precision]
+    assert abs(C.item() - rC) <= 1e-8
+    assert np.all(np.isfinite(gap.cpu().numpy()))
+    if S is not None:
+        assert np.all(pg.cpu().numpy() > 0)
+
+
+def test_plaquette_flux_invariants(lib, ctx):
+    """Eq. 4 carries C = 1 (paper); the spin-Hall sectors -1 / +1, total 0."""
+    _, C, _, _ = lib.plaquette_flux(I.chern_eq4(1.5), P(24, 24), 1, ctx=ctx)
+    assert abs(C.item() - 1) < 1e-9
+    wl = I.config_spin_hall()
+    _, Ct, _, _ = lib.plaquette_flux(wl.model, wl.plane, 2, ctx=ctx)
+    _, Cd, _, _ = lib.plaquette_flux(wl.model, wl.plane, 2, wl.spin_op, -1, precision="mixed", ctx=ctx)
+    _, Cu, _, _ = lib.plaquette_flux(wl.model, wl.plane, 2, wl.spin_op, 1, precision="mixed", ctx=ctx)
+    assert abs(Ct.item()) < 1e-9 and abs(Cd.item() + 1) < 1e-9 and abs(Cu.item() - 1) < 1e-9
+
+
+def test_disordered_supercell_spin_chern(lib, ctx):
+    """Disordered spin-Hall supercell at full size (L = 10, n = 400, p = 200, W = 2,
+    16 x 16): the C_down / C_up windings are -1 / +1 (the clean model's values survive
+    this disorder), and one transverse row matches the oracle."""
+    wl = I.config_disordered(10, 5)
+    for sign in (-1, 1):
+        ph, _, pg, _ = lib.spin_resolved_wilson_loop(wl.model, wl.plane, wl.p, wl.spin_op, sign,
+                                                     precision="mixed", ctx=ctx, want_pso=False)
+        assert abs(lib.winding(ph, ctx=ctx).item() - sign) < 1e-6
+        assert pg.min().item() > 0.9
+    row = 7
+    plr = P(wl.plane.N, 1, origin=tuple(np.array(wl.plane.trans_dir) * row / wl.plane.N_t))
+    ref, _, _, _ = oracle.spin_resolved_wilson_loop(wl.model, plr, wl.p, wl.spin_op, -1)
+    ph, _, _, _ = lib.spin_resolved_wilson_loop(wl.model, wl.plane, wl.p, wl.spin_op, -1,
+                                                precision="mixed", ctx=ctx, want_pso=False)
+    assert circ_err_rows(ph.cpu().numpy()[row:row + 1], ref) <= TOL["mixed"]
