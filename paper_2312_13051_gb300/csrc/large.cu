@@ -533,6 +533,12 @@ __global__ void k_lg_bisect(LargeArgs a) {
 // pseudo-random start.  Eigenvalues closer than 1e-3 ||T'|| form a cluster, whose
 // vectors one thread computes in order, orthogonalising each against the earlier
 // ones of its cluster at every iteration.
+// Where only the span of the computed vectors matters (subspace_only: the PSO
+// sector), every vector iterates on its own thread at once instead, converging into
+// its cluster's invariant subspace from a distinct start, and a second kernel
+// orthonormalises each cluster's vectors by modified Gram-Schmidt applied twice,
+// one warp per cluster: a cluster of p/2 exactly degenerate PSO eigenvalues no
+// longer serialises on one thread.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double hash_unit(unsigned long long x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -636,6 +642,70 @@ __global__ void k_lg_invit(LargeArgs a) {
       for (int r = 0; r < n; ++r) W.at(5, r, t) *= s2;
     }
     for (int r = 0; r < n; ++r) Z[(long long)r * nv + j] = W.at(5, r, t);
+  }
+}
+
+template <typename T>
+__global__ void k_lg_invit_par(LargeArgs a) {
+  const long long NT = a.W * a.nvec;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NT) return;
+  const long long kw = t / a.nvec;
+  const int j = int(t - kw * a.nvec), n = a.n, nv = a.nvec;
+  const T* dg = reinterpret_cast<const T*>(a.dg) + kw * n;
+  const T* od = reinterpret_cast<const T*>(a.od) + kw * n;
+  const T* lam = reinterpret_cast<const T*>(a.lam) + kw * a.nval;
+  T lo, hi, tn;
+  gershgorin(dg, od, n, lo, hi, tn);
+  T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)nv * n;   // row-major n x nvec
+  const Strided<T> W{reinterpret_cast<T*>(a.work), NT, n};
+  const T tiny = fmax(lg_eps<T>() * tn, T(1e-30));
+  tri_factor(dg, od, n, lam[j], tiny, W, t);
+  for (int r = 0; r < n; ++r) W.at(5, r, t) = T(hash_unit((unsigned long long)j * 1000003ull + r));
+  for (int it = 0; it < 3; ++it) {
+    tri_solve(n, tiny, W, t);
+    T s2 = T(0);
+    for (int r = 0; r < n; ++r) s2 += W.at(5, r, t) * W.at(5, r, t);
+    s2 = T(1) / sqrt(s2);
+    for (int r = 0; r < n; ++r) W.at(5, r, t) *= s2;
+  }
+  for (int r = 0; r < n; ++r) Z[(long long)r * nv + j] = W.at(5, r, t);
+}
+
+// Orthonormalises the vectors of each cluster in place: one warp per eigenvalue index,
+// working only where the index starts a cluster of two or more.
+template <typename T>
+__global__ void k_lg_invit_orth(LargeArgs a) {
+  const long long NT = a.W * a.nvec;
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= NT) return;
+  const long long kw = t / a.nvec;
+  const int idx = int(t - kw * a.nvec), n = a.n, nv = a.nvec;
+  const T* dg = reinterpret_cast<const T*>(a.dg) + kw * n;
+  const T* od = reinterpret_cast<const T*>(a.od) + kw * n;
+  const T* lam = reinterpret_cast<const T*>(a.lam) + kw * a.nval;
+  T lo, hi, tn;
+  gershgorin(dg, od, n, lo, hi, tn);
+  const T tolc = T(1e-3) * tn;
+  if (idx > 0 && lam[idx] - lam[idx - 1] <= tolc) return;  // not the first of its cluster
+  int end = idx;
+  while (end + 1 < nv && lam[end + 1] - lam[end] <= tolc) ++end;
+  if (end == idx) return;
+  T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)nv * n;
+  for (int j = idx; j <= end; ++j) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = idx; q < j; ++q) {
+        T d = T(0);
+        for (int r = lane; r < n; r += 32) d += Z[(long long)r * nv + q] * Z[(long long)r * nv + j];
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        for (int r = lane; r < n; r += 32) Z[(long long)r * nv + j] -= d * Z[(long long)r * nv + q];
+      }
+    T s2 = T(0);
+    for (int r = lane; r < n; r += 32) s2 += Z[(long long)r * nv + j] * Z[(long long)r * nv + j];
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s2 = T(1) / sqrt(s2);
+    for (int r = lane; r < n; r += 32) Z[(long long)r * nv + j] *= s2;
   }
 }
 
@@ -906,7 +976,15 @@ cudaError_t lg_common(const LargeArgs& a, cudaStream_t s) {
   lg_mark(a, "lg_bisect");
   const long long ni = a.W * a.nvec;
   if (ni > 0) {
-    k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
+    if (a.subspace_only) {
+      k_lg_invit_par<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      const long long nw = ni * 32;
+      if (nw / 128 + 1 > 0x7fffffffLL) return cudaErrorInvalidValue;
+      k_lg_invit_orth<T><<<int((nw + 127) / 128), 128, 0, s>>>(a);
+    } else {
+      k_lg_invit<T><<<int((ni + 63) / 64), 64, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lg_mark(a, "lg_invit");
   }

@@ -140,6 +140,7 @@ struct LargeArgs {
   const long long* h_off;
   const int* idx;
   int no_refine;          // mixed path without a block to refine (p = 0)
+  int subspace_only;      // only the span of the nvec vectors matters (parallel clusters)
 };
 
 // Outputs of the batched eigensolve for one wave of the large path.
@@ -215,9 +216,6 @@ cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s);
 
 // Launches every stage of the large-n solver for one wave.
 cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);
-// Projected-spin split of global occupied blocks: U (K x n x p) -> Us (K x n x p/2).
-cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
-                              cudaStream_t s);
 
 // Plaquette Berry flux of the states in a.U (K x n x p, p <= 64): link determinants
 // (Lx, Ly: K unit complex numbers each, scratch), flux (N_t x N) and chern = sum / 2pi

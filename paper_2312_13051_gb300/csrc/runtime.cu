@@ -419,6 +419,116 @@ bw::DevPlane dev_plane(const bw_plane* pl) {
   return d;
 }
 
+// Projected-spin split of waves of occupied blocks (Sec. IV) for n > 32: the
+// occupied-space operator S = U^dagger (sigma s U) of every k-point of a wave by one
+// sparse application and one batched GEMM, its FP64 eigen-decomposition on the
+// tridiagonal path (sigma = +1 for the sector s < 0, -1 for s > 0, so the sector is
+// the lowest p/2 eigenvectors V of sigma S), the PSO gap check, and the sector
+// states U V by a second GEMM.  pso_split_bytes: scratch per wave slot.
+struct PsoSplit {
+  int n = 0, p = 0, pl = 0, pnval = 0;
+  double sigma = 1.0, tol = 0.0;
+  z64 *Yw = nullptr, *Sw = nullptr, *Vw = nullptr;
+  const int* rowp = nullptr;
+  const int* col = nullptr;
+  const z64* val = nullptr;
+  double* pso_evals = nullptr;
+  double* psog = nullptr;
+  bw::LargeArgs ps;
+};
+
+size_t pso_split_bytes(int n, int p, bool want_evals) {
+  const int pl = p / 2, pnval = want_evals ? p : pl + 1;
+  const size_t d8 = sizeof(double);
+  return al256(size_t(n) * p * sizeof(z64)) + 2 * al256(size_t(p) * p * sizeof(z64)) +
+         al256(size_t(p) * pl * sizeof(z64)) + 2 * al256(size_t(p) * d8) + al256(size_t(p) * 2 * d8) +
+         al256(size_t(pnval) * d8) + al256(size_t(pl) * p * d8) + al256(size_t(pl) * 6 * p * d8) +
+         sizeof(long long) + sizeof(int);
+}
+
+bw_status pso_split_setup(bw_ctx* ctx, PsoSplit& X, long long Wv, int n, int p, const HostOp& op,
+                          const char* dblob, int sign, double tol, double* pso_evals, double* psog,
+                          MarkHook* hook, cudaStream_t s) {
+  X.n = n;
+  X.p = p;
+  X.pl = p / 2;
+  X.pnval = pso_evals ? p : X.pl + 1;
+  X.sigma = sign < 0 ? 1.0 : -1.0;
+  X.tol = tol;
+  X.pso_evals = pso_evals;
+  X.psog = psog;
+  const size_t d8 = sizeof(double);
+  X.Yw = reinterpret_cast<z64*>(carve(ctx, Wv * al256(size_t(n) * p * sizeof(z64))));
+  X.Sw = reinterpret_cast<z64*>(carve(ctx, Wv * al256(size_t(p) * p * sizeof(z64))));
+  X.Vw = reinterpret_cast<z64*>(carve(ctx, Wv * al256(size_t(p) * X.pl * sizeof(z64))));
+  long long* h_off = reinterpret_cast<long long*>(carve(ctx, Wv * sizeof(long long)));
+  int* idx = reinterpret_cast<int*>(carve(ctx, Wv * sizeof(int)));
+  BW_CUDA(bw::launch_iota(h_off, idx, Wv, (long long)al256(size_t(p) * p * sizeof(z64)) / long(sizeof(z64)), s),
+          "index kernel");
+  bw::LargeArgs& ps = X.ps;
+  std::memset(&ps, 0, sizeof(ps));
+  ps.n = p;
+  ps.p = X.pl;
+  ps.nval = X.pnval;
+  ps.nvec = X.pl;
+  ps.nbt = X.pl;
+  ps.mixed = 0;
+  ps.gap = psog;
+  ps.status = ctx->status;
+  ps.A = carve(ctx, Wv * al256(size_t(p) * p * sizeof(z64)));
+  ps.dg = carve(ctx, Wv * al256(size_t(p) * d8));
+  ps.od = carve(ctx, Wv * al256(size_t(p) * d8));
+  ps.Dp = carve(ctx, Wv * al256(size_t(p) * 2 * d8));
+  ps.lam = carve(ctx, Wv * al256(size_t(X.pnval) * d8));
+  ps.Z = carve(ctx, Wv * al256(size_t(X.pl) * p * d8));
+  ps.work = carve(ctx, Wv * al256(size_t(X.pl) * 6 * p * d8));
+  ps.U = X.Vw;
+  ps.mark = mark_hook;
+  ps.mark_user = hook;
+  ps.subspace_only = 1;  // the sector's span is what the loop needs
+  ps.Hin = X.Sw;
+  ps.h_off = h_off;
+  ps.idx = idx;
+  X.rowp = reinterpret_cast<const int*>(dblob + op.o_rowp);
+  X.col = reinterpret_cast<const int*>(dblob + op.o_col);
+  X.val = reinterpret_cast<const z64*>(dblob + op.o_val);
+  return BW_OK;
+}
+
+// One wave: Uw holds Wn occupied blocks (n x p) of k-points k0 .. k0 + Wn - 1; the
+// sector states go to dst (n x p/2 per k-point).
+bw_status pso_split_wave(bw_ctx* ctx, PsoSplit& X, const z64* Uw, long long Wn, long long k0, z64* dst,
+                         cudaStream_t s) {
+  const int n = X.n, p = X.p, pl = X.pl;
+  // S slots at the stride of the eigensolver's matrix index; sigma s U as written by the
+  // spin kernel and V as written by the back-transform are packed
+  const long long sS = (long long)al256(size_t(p) * p * sizeof(z64)) / long(sizeof(z64));
+  const long long sY = (long long)n * p, sV = (long long)p * pl;
+  BW_CUDA(bw::launch_spin_apply(Uw, X.Yw, Wn, n, p, X.rowp, X.col, X.val, X.sigma, s), "spin operator kernel");
+  bw::GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = Uw; g.B = X.Yw; g.C = X.Sw;
+  g.m = p; g.n = p; g.k = n; g.opA = 1;
+  g.lda = p; g.ldb = p; g.ldc = p;
+  g.sA = (long long)n * p; g.sB = sY; g.sC = sS;
+  g.batch = Wn;
+  BW_CUDA(bw::launch_zgemm(g, s), "spin operator GEMM");
+  X.ps.k0 = 0;
+  X.ps.W = Wn;
+  BW_CUDA(bw::launch_states_large(X.ps, s), "spin operator eigensolve");
+  BW_CUDA(bw::launch_pso_post(reinterpret_cast<const double*>(X.ps.lam), X.pnval, Wn, k0, p, X.sigma, X.tol,
+                              X.pso_evals, X.psog, ctx->status, s),
+          "spin sector check");
+  std::memset(&g, 0, sizeof(g));
+  g.A = Uw; g.B = X.Vw; g.C = dst;
+  g.m = n; g.n = pl; g.k = p; g.opA = 0;
+  g.lda = p; g.ldb = pl; g.ldc = pl;
+  g.sA = (long long)n * p; g.sB = sV; g.sC = (long long)n * pl;
+  g.batch = Wn;
+  BW_CUDA(bw::launch_zgemm(g, s), "sector states GEMM");
+  return BW_OK;
+}
+
 // Wilson loop with many occupied bands (p > LOOP_P_MAX, n > SMALL_N_MAX).  The
 // Wilson matrix no longer fits in shared memory, so the loop runs as batched GEMMs:
 // for a block of nl loops (their k-points are contiguous, k = i N + j) the states are
@@ -439,7 +549,6 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
   const int n = P.n, N = plane->N, Nt = plane->N_t;
   const bool spin = op != nullptr;
   const int pl = spin ? p / 2 : p;  // columns the loop runs on
-  const double sigma = sign < 0 ? 1.0 : -1.0;
   const long long K = (long long)N * Nt;
   const size_t ts = mx ? sizeof(float) : sizeof(double);
   const int nval = mx ? n : std::min(n, p + 1), nvec = mx ? n : p;
@@ -452,20 +561,10 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
                sz_R = mx ? al256(size_t(n) * p * sizeof(z64)) : 0,
                sz_C = mx ? al256(size_t(n) * p * sizeof(bw::c32)) : 0,
                sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0;
-  // spin split, per wave slot: the occupied block, sigma s U, S, the sector vectors and
-  // the FP64 tridiagonal solver's scratch for the p x p problem
-  const int pnval = pso_evals ? p : pl + 1;
-  const size_t d8 = sizeof(double);
-  const size_t sp_U = spin ? al256(size_t(n) * p * sizeof(z64)) : 0,
-               sp_S = spin ? al256(size_t(p) * p * sizeof(z64)) : 0,
-               sp_V = spin ? al256(size_t(p) * pl * sizeof(z64)) : 0,
-               sp_v = spin ? al256(size_t(p) * d8) : 0, sp_D = spin ? al256(size_t(p) * 2 * d8) : 0,
-               sp_lam = spin ? al256(size_t(pnval) * d8) : 0,
-               sp_Z = spin ? al256(size_t(pl) * p * d8) : 0,
-               sp_wk = spin ? al256(size_t(pl) * 6 * p * d8) : 0;
+  // spin split, per wave slot: the occupied block and the split's scratch
+  const size_t sp_U = spin ? al256(size_t(n) * p * sizeof(z64)) : 0;
   const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
-                       sz_G + 2 * sp_U + 2 * sp_S + sp_V + 2 * sp_v + sp_D + sp_lam + sp_Z + sp_wk +
-                       (spin ? sizeof(long long) + sizeof(int) : 0);
+                       sz_G + sp_U + (spin ? pso_split_bytes(n, p, pso_evals != nullptr) : 0);
   const size_t bUk = size_t(n) * pl * sizeof(z64), bPk = size_t(pl) * pl * sizeof(z64);
   const size_t bEl = size_t(pl) * (2 * sizeof(z64) + sizeof(double) + sizeof(int));
   const size_t per_loop = size_t(N) * (bUk + bPk) + 2 * bPk + bEl;
@@ -523,45 +622,13 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
   MarkHook hook{ctx, s};
   lg.mark = mark_hook;
   lg.mark_user = &hook;
-  // spin split of a wave: U (wave), sigma s U, S and the FP64 eigensolve of S
-  z64 *Uw = nullptr, *Yw = nullptr, *Sw = nullptr, *Vw = nullptr;
-  bw::LargeArgs ps;
-  std::memset(&ps, 0, sizeof(ps));
-  const int* op_rowp = nullptr;
-  const int* op_col = nullptr;
-  const z64* op_val = nullptr;
+  // spin split of a wave: the wave's occupied blocks, then the sector states
+  z64* Uw = nullptr;
+  PsoSplit X;
   if (spin) {
     Uw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_U));
-    Yw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_U));
-    Sw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_S));
-    Vw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_V));
-    long long* h_off = reinterpret_cast<long long*>(carve(ctx, Wv * sizeof(long long)));
-    int* idx = reinterpret_cast<int*>(carve(ctx, Wv * sizeof(int)));
-    BW_CUDA(bw::launch_iota(h_off, idx, Wv, (long long)p * p, s), "index kernel");
-    ps.model = lg.model;
-    ps.plane = lg.plane;
-    ps.n = p;
-    ps.p = pl;
-    ps.nval = pnval;
-    ps.nvec = pl;
-    ps.nbt = pl;
-    ps.mixed = 0;
-    ps.gap = psog;
-    ps.status = ctx->status;
-    ps.A = carve(ctx, Wv * sp_S);
-    ps.dg = carve(ctx, Wv * sp_v);
-    ps.od = carve(ctx, Wv * sp_v);
-    ps.Dp = carve(ctx, Wv * sp_D);
-    ps.lam = carve(ctx, Wv * sp_lam);
-    ps.Z = carve(ctx, Wv * sp_Z);
-    ps.work = carve(ctx, Wv * sp_wk);
-    ps.U = Vw;
-    ps.Hin = Sw;
-    ps.h_off = h_off;
-    ps.idx = idx;
-    op_rowp = reinterpret_cast<const int*>(dblob + op->o_rowp);
-    op_col = reinterpret_cast<const int*>(dblob + op->o_col);
-    op_val = reinterpret_cast<const z64*>(dblob + op->o_val);
+    if ((st = pso_split_setup(ctx, X, Wv, n, p, *op, dblob, sign, o.pso_gap_tol, pso_evals, psog, &hook, s)))
+      return st;
   }
   prof_start(ctx, s);
   const long long sU = (long long)n * pl, sP = (long long)pl * pl;
@@ -575,29 +642,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
       lg.U = spin ? Uw : Ublk + w0 * sU;
       BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
       if (!spin) continue;
-      BW_CUDA(bw::launch_spin_apply(Uw, Yw, Wn, n, p, op_rowp, op_col, op_val, sigma, s),
-              "spin operator kernel");
-      bw::GemmArgs g;
-      std::memset(&g, 0, sizeof(g));
-      g.A = Uw; g.B = Yw; g.C = Sw;
-      g.m = p; g.n = p; g.k = n; g.opA = 1;
-      g.lda = p; g.ldb = p; g.ldc = p;
-      g.sA = (long long)n * p; g.sB = (long long)n * p; g.sC = (long long)p * p;
-      g.batch = Wn;
-      BW_CUDA(bw::launch_zgemm(g, s), "spin operator GEMM");
-      ps.k0 = 0;
-      ps.W = Wn;
-      BW_CUDA(bw::launch_states_large(ps, s), "spin operator eigensolve");
-      BW_CUDA(bw::launch_pso_post(reinterpret_cast<const double*>(ps.lam), pnval, Wn, kb + w0, p, sigma,
-                                  o.pso_gap_tol, pso_evals, psog, ctx->status, s),
-              "spin sector check");
-      std::memset(&g, 0, sizeof(g));
-      g.A = Uw; g.B = Vw; g.C = Ublk + w0 * sU;
-      g.m = n; g.n = pl; g.k = p; g.opA = 0;
-      g.lda = p; g.ldb = pl; g.ldc = pl;
-      g.sA = (long long)n * p; g.sB = (long long)p * pl; g.sC = sU;
-      g.batch = Wn;
-      BW_CUDA(bw::launch_zgemm(g, s), "sector states GEMM");
+      if ((st = pso_split_wave(ctx, X, Uw, Wn, kb + w0, Ublk + w0 * sU, s))) return st;
       prof_mark(ctx, s, "pso_split");
     }
     // every overlap of the block: batch b = l N + j, A = U(k_{j+1}) (closing on j = 0)
@@ -752,7 +797,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
                sz_G = mx ? al256(size_t(p) * p * sizeof(z64)) : 0,
                sz_Uf = spin ? al256(size_t(n) * p * sizeof(z64)) : 0;
   const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
-                       sz_G + sz_Uf;
+                       sz_G + sz_Uf + (spin && large ? pso_split_bytes(n, p, pso_evals != nullptr) : 0);
   long long Wv = 0;
   if (large) {
     const size_t avail = ctx->budget > total ? (ctx->budget - total) / 2 : 0;
@@ -850,9 +895,13 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
       lg.G64 = reinterpret_cast<z64*>(carve(ctx, Wv * sz_G));
     }
     z64* Ufull = reinterpret_cast<z64*>(carve(ctx, Wv * sz_Uf));
+    PsoSplit X;
     MarkHook hook{ctx, s};
     lg.mark = mark_hook;
     lg.mark_user = &hook;
+    if (spin && (st = pso_split_setup(ctx, X, Wv, n, p, op, dblob, sign, o.pso_gap_tol, pso_evals, psog,
+                                      &hook, s)))
+      return st;
     for (long long k0 = 0; k0 < K; k0 += Wv) {
       lg.k0 = k0;
       lg.W = std::min(Wv, K - k0);
@@ -860,7 +909,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
       lg.U = spin ? Ufull : U + k0 * (long long)n * p;
       BW_CUDA(bw::launch_states_large(lg, s), "large-n states kernels");
       if (spin) {
-        BW_CUDA(bw::launch_pso_global(sa, Ufull, k0, lg.W, s), "spin split kernel");
+        if ((st = pso_split_wave(ctx, X, Ufull, lg.W, k0, U + k0 * (long long)n * p_eff, s))) return st;
         prof_mark(ctx, s, "pso_split");
       }
     }

@@ -508,166 +508,4 @@ cudaError_t launch_eigh_small(const EighArgs& a, int n_max, cudaStream_t s) {
   return a.mixed ? eigh_impl<float>(a, n_max, s) : eigh_impl<double>(a, n_max, s);
 }
 
-// ---------------------------------------------------------------------------
-// Projected-spin split of occupied blocks already in global memory (large n):
-// U (n x p per k) -> a.U (n x p/2 per k).  One CTA per k-point.
-// FP64 path: pso_split (FP64 Jacobi of S = U^dag s U).
-// Mixed path: FP32 Jacobi of S (negated for the + sector, so the sector is always
-// the lower half), one FP64 Newton correction of the p/2-dimensional sector in the
-// FP32 eigenbasis (refine_mixed on S), and FP64 Rayleigh quotients as the
-// reported PSO eigenvalues.
-// ---------------------------------------------------------------------------
-__host__ __device__ inline size_t pso_mixed_smem(int p) {
-  const int h = p / 2;
-  size_t o = 0;
-  o = align16(o + size_t(p) * p * sizeof(z64));   // S64
-  o = align16(o + size_t(p) * p * sizeof(c32));   // A32, later the residual C (p x h z64)
-  o = align16(o + size_t(p) * p * sizeof(c32));   // V32
-  o = align16(o + size_t(p) * h * sizeof(z64));   // Q
-  o = align16(o + size_t(p) * h * sizeof(z64));   // HQ
-  o = align16(o + size_t(h) * h * sizeof(z64));   // G
-  o = align16(o + 3 * size_t(p) * sizeof(double)); // lam, rho, mu
-  o = align16(o + 2 * size_t(p) * sizeof(int));   // ord, ord2
-  o = align16(o + size_t(p / 2 + 2) * sizeof(JacRot<double>));
-  o = align16(o + 64 * sizeof(double));
-  return o;
-}
-
-__device__ void pso_split_mixed(const z64* U, const DevOp& op, int sign, int n, int p,
-                                unsigned char* smem, int max_sweeps, z64* out, double* pso_out,
-                                double* pso_gap_out, double pso_tol, DevStatus* st, long long k) {
-  const int tid = threadIdx.x, nt = blockDim.x, h = p / 2;
-  size_t o = 0;
-  z64* S = reinterpret_cast<z64*>(smem + o); o = align16(o + size_t(p) * p * sizeof(z64));
-  c32* A = reinterpret_cast<c32*>(smem + o); o = align16(o + size_t(p) * p * sizeof(c32));
-  c32* V = reinterpret_cast<c32*>(smem + o); o = align16(o + size_t(p) * p * sizeof(c32));
-  z64* Q = reinterpret_cast<z64*>(smem + o); o = align16(o + size_t(p) * h * sizeof(z64));
-  z64* HQ = reinterpret_cast<z64*>(smem + o); o = align16(o + size_t(p) * h * sizeof(z64));
-  z64* G = reinterpret_cast<z64*>(smem + o); o = align16(o + size_t(h) * h * sizeof(z64));
-  double* lam = reinterpret_cast<double*>(smem + o);
-  double* rho = lam + p;
-  double* mu = rho + p;
-  o = align16(o + 3 * size_t(p) * sizeof(double));
-  int* ord = reinterpret_cast<int*>(smem + o);
-  int* ord2 = ord + p;
-  o = align16(o + 2 * size_t(p) * sizeof(int));
-  JacRot<double>* rot64 = reinterpret_cast<JacRot<double>*>(smem + o);
-  JacRot<float>* rot32 = reinterpret_cast<JacRot<float>*>(smem + o);
-  o = align16(o + size_t(p / 2 + 2) * sizeof(JacRot<double>));
-  double* red = reinterpret_cast<double*>(smem + o);
-  int* flag = reinterpret_cast<int*>(red + 40);
-  const double sg = sign < 0 ? 1.0 : -1.0;
-  for (int e = tid; e < p * p; e += nt) {
-    const int x = e / p, y = e - x * p;
-    z64 acc(0.0, 0.0);
-    for (int q = 0; q < op.nnz; ++q) cfma_conj(acc, U[op.row[q] * p + x], op.val[q] * U[op.col[q] * p + y]);
-    S[e] = sg * acc;
-  }
-  __syncthreads();
-  for (int e = tid; e < p * p; e += nt) {
-    const int x = e / p, y = e - x * p;
-    z64 v = S[e];
-    if (x == y) v = z64(v.re, 0.0);
-    else v = 0.5 * (v + conj(S[y * p + x]));
-    A[e] = ccast<float>(v);
-  }
-  __syncthreads();
-  for (int e = tid; e < p * p; e += nt) {  // keep S exactly Hermitian in FP64 too
-    const int x = e / p, y = e - x * p;
-    if (x < y) {
-      const z64 v = 0.5 * (S[e] + conj(S[y * p + x]));
-      S[e] = v;
-      S[y * p + x] = conj(v);
-    } else if (x == y) {
-      S[e] = z64(S[e].re, 0.0);
-    }
-  }
-  __syncthreads();
-  const int sw = jacobi_eigh<float>(A, V, p, p, max_sweeps, rot32, red);
-  sort_diag<float>(A, p, p, ord);
-  for (int c = tid; c < p; c += nt) lam[c] = double(A[c * p + c].re);
-  for (int e = tid; e < p * h; e += nt) {
-    const int r = e / h, c = e - r * h;
-    Q[e] = ccast<double>(V[r * p + ord[c]]);
-  }
-  __syncthreads();
-  int ok = 1;
-  // A is free now: it holds the residual (p x h z64 fits in p x p c32)
-  refine_mixed(S, V, ord, lam, p, h, Q, HQ, reinterpret_cast<z64*>(A), G, G, rho, ord2, rot64, red,
-               max_sweeps, &ok, flag);
-  // PSO eigenvalues: FP64 Rayleigh quotients of the FP32 vectors (sign restored)
-  for (int c = tid; c < p; c += nt) {
-    const int col = ord[c];
-    double num = 0.0, den = 0.0;
-    for (int r = 0; r < p; ++r) {
-      z64 sv(0.0, 0.0);
-      for (int q = 0; q < p; ++q) cfma(sv, S[r * p + q], ccast<double>(V[q * p + col]));
-      const z64 v = ccast<double>(V[r * p + col]);
-      num += v.re * sv.re + v.im * sv.im;
-      den += abs2(v);
-    }
-    mu[c] = sg * num / den;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int neg = 0;
-    double g = INFINITY;
-    for (int c = 0; c < p; ++c) {
-      neg += mu[c] < 0.0;
-      g = fmin(g, fabs(mu[c]));
-    }
-    if (pso_out)  // ascending in the original sign
-      for (int c = 0; c < p; ++c) pso_out[c] = sign < 0 ? mu[c] : mu[p - 1 - c];
-    if (pso_gap_out) *pso_gap_out = g;
-    if (sw < 0 || !ok) report(st, ST_ENOCONV, k, 0.0);
-    if (neg != h || !(g > pso_tol)) report(st, ST_EPSOGAP, k, g);
-  }
-  for (int e = tid; e < n * h; e += nt) {
-    const int r = e / h, c = e - r * h;
-    z64 acc(0.0, 0.0);
-    for (int q = 0; q < p; ++q) cfma(acc, U[r * p + q], Q[q * h + c]);
-    out[e] = acc;
-  }
-  __syncthreads();
-}
-
-__global__ void k_pso_global(StatesArgs a, const z64* U, long long k0, long long W) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.model.n, p = a.p;
-  z64* S = reinterpret_cast<z64*>(smem);
-  z64* SV = S + p * p;
-  double* mu = reinterpret_cast<double*>(SV + p * p);
-  int* ord = reinterpret_cast<int*>(mu + p);
-  JacRot<double>* rot = reinterpret_cast<JacRot<double>*>(smem + align16(2 * size_t(p) * p * sizeof(z64) +
-                                                                          p * sizeof(double) + p * sizeof(int)));
-  double* red = reinterpret_cast<double*>(rot + (p / 2 + 2));
-  for (long long kw = blockIdx.x; kw < W; kw += gridDim.x) {
-    const long long k = k0 + kw;
-    const z64* Uk = U + kw * (long long)n * p;
-    z64* out = a.U + k * (long long)n * (p / 2);
-    double* po = a.pso_evals ? a.pso_evals + k * p : nullptr;
-    double* pg = a.pso_gap ? a.pso_gap + k : nullptr;
-    if (a.mixed)
-      pso_split_mixed(Uk, a.op, a.sign, n, p, smem, a.max_sweeps, out, po, pg, a.pso_gap_tol, a.status, k);
-    else
-      pso_split(Uk, a.op, a.sign, n, p, S, SV, ord, mu, rot, red, a.max_sweeps, out, po, pg,
-                a.pso_gap_tol, a.status, k);
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_pso_global(const StatesArgs& a, const z64* U, long long k0, long long W,
-                              cudaStream_t s) {
-  if (W <= 0) return cudaSuccess;
-  const int p = a.p;
-  size_t sm = align16(2 * size_t(p) * p * sizeof(z64) + p * sizeof(double) + p * sizeof(int)) +
-              (p / 2 + 2) * sizeof(JacRot<double>) + 64 * sizeof(double);
-  if (a.mixed && pso_mixed_smem(p) > sm) sm = pso_mixed_smem(p);
-  static size_t cached = 0;
-  cudaError_t e = set_smem_once(k_pso_global, sm, cached);
-  if (e != cudaSuccess) return e;
-  k_pso_global<<<grid_for(W), 512, sm, s>>>(a, U, k0, W);
-  return cudaGetLastError();
-}
-
 }  // namespace bw
