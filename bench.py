@@ -36,6 +36,9 @@ UNIT = "k-points/s"
 WORKLOAD = "bbh_quadrupole_60x60_nested (gamma=0.5, lambda=1, n=4, p=2, m=1, N=N_t=60)"
 FP64_PEAK_TFLOPS = 1.25       # GB300 nominal dense FP64 (152 SMs; see the design notes)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock: 80.5
+# DRAM bytes (read + write) of one launch of the fused mixed-precision loop kernel on
+# the BBH 60 x 60 nested workload, from the ncu capture summarised under profiles/
+FUSED_KERNEL_DRAM_BYTES = 161024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SIMT FMA lanes x 2 flops x max clock
 
 
@@ -441,7 +444,10 @@ def run_ours(args):
         "phase_err_rad": err.get("mixed"),
         "kernel_ms_per_step": {k: v / args.steps for k, v in pk.items()},
         "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": FUSED_KERNEL_DRAM_BYTES if dom == "loops" and "states" not in pk else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "launch (profiles/k_loops_fused_df_bbh60x60.md)",
                      "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s): the FP64-grade "
                                     "arithmetic the path delivers (computed in double-float on the "
                                     "FP32 pipe); latency-bound at 3600 k-points: 60 loops, one CTA "
