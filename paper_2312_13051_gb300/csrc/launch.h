@@ -87,6 +87,7 @@ struct LoopArgs {
   double* nested_out;    // N x m
   DevStatus* status;
   int u_df;              // U and w hold complex double-float (loops_accept_df() holds)
+  int df_overlaps;       // mixed request: overlaps from the FP64 states in double-float
 };
 
 // Raises a kernel's dynamic shared-memory limit only when a launch needs more than

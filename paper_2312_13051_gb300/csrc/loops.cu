@@ -111,6 +111,55 @@ __global__ void k_overlaps(LoopArgs a) {
   }
 }
 
+// Mixed precision, p > 4: the overlaps in double-float on the FP32 pipe.  One CTA per
+// k-point; the two FP64 state blocks pass through shared memory in chunks of
+// OVL_ROWS rows, converted to double-float once per element, and each thread
+// accumulates up to 16 entries of M; M is written back in FP64.
+constexpr int OVL_ROWS = 32, OVL_THREADS = 256;
+
+__global__ void __launch_bounds__(OVL_THREADS, 1) k_overlaps_df(LoopArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, pp = p * p;
+  const long long K = (long long)N * a.N_t;
+  cdf* Ah = reinterpret_cast<cdf*>(smem);        // OVL_ROWS x p, U(k_j)
+  cdf* An = Ah + OVL_ROWS * p;                   // OVL_ROWS x p, U(k_{j+1})
+  for (long long k = blockIdx.x; k < K; k += gridDim.x) {
+    const int i = int(k / N), j = int(k - (long long)i * N);
+    const long long kn = (long long)i * N + (j + 1 == N ? 0 : j + 1);
+    const z64* Uh = a.U + k * (long long)n * p;
+    const z64* Un = a.U + kn * (long long)n * p;
+    cdf acc[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc[s] = cdf_zero();
+    for (int r0 = 0; r0 < n; r0 += OVL_ROWS) {
+      const int rows = min(OVL_ROWS, n - r0);
+      for (int e = tid; e < rows * p; e += OVL_THREADS) {
+        Ah[e] = cdf_from(Uh[(long long)r0 * p + e]);
+        An[e] = cdf_from(Un[(long long)r0 * p + e]);
+      }
+      __syncthreads();
+      // the entries' chains interleave: independent accumulators for every q
+      for (int q = 0; q < rows; ++q) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+          const int e = tid + OVL_THREADS * s;
+          if (e < pp) {
+            const int r = e / p, c = e - r * p;
+            cfma_conj(acc[s], An[q * p + r], Ah[q * p + c]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    z64* M = a.M + k * (long long)pp;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int e = tid + OVL_THREADS * s;
+      if (e < pp) M[e] = cdf_to_z64(acc[s]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Per-loop product, eigenphases and (nested) Wannier states
 // ---------------------------------------------------------------------------
@@ -948,6 +997,15 @@ bool loops_accept_df(const LoopArgs& a) {
 cudaError_t launch_overlaps(const LoopArgs& a, cudaStream_t s) {
   const long long K = (long long)a.N * a.N_t;
   if (K <= 0 || loops_form_overlaps(a)) return cudaSuccess;
+  if (a.df_overlaps && !a.unitarise && a.p * a.p <= 16 * OVL_THREADS) {
+    const size_t sm = 2 * size_t(OVL_ROWS) * a.p * sizeof(cdf);
+    static size_t cached_df = 0;
+    cudaError_t e = set_smem_once(k_overlaps_df, sm, cached_df);
+    if (e != cudaSuccess) return e;
+    const long long cap = 152LL * 8;
+    k_overlaps_df<<<int(K < cap ? K : cap), OVL_THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+  }
   const size_t sm = a.unitarise ? (4 * size_t(a.p) * a.p * sizeof(z64) +
                                    (a.p / 2 + 2) * sizeof(JacRot<double>) + 64 * sizeof(double))
                                 : 0;

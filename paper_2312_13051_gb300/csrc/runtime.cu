@@ -933,6 +933,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.min_pso_gap = min_pso_gap;
   la.status = ctx->status;
   la.u_df = use_df ? 1 : 0;
+  la.df_overlaps = mx ? 1 : 0;
   if (kind == LoopKind::Plaquette) {
     BW_CUDA(bw::launch_plaquettes(la, Lx, Ly, phases, chern_out, s), "plaquette kernels");
     prof_mark(ctx, s, "plaquettes");

@@ -527,3 +527,21 @@ def test_disordered_supercell_spin_chern(lib, ctx):
     ph, _, _, _ = lib.spin_resolved_wilson_loop(wl.model, wl.plane, wl.p, wl.spin_op, -1,
                                                 precision="mixed", ctx=ctx, want_pso=False)
     assert circ_err_rows(ph.cpu().numpy()[row:row + 1], ref) <= TOL["mixed"]
+
+
+def test_mixed_four_band_launch_shapes(lib, ctx):
+    """The double-float path at the edges of its launch shapes: loops of exactly 64
+    points (256 threads, one CTA per loop), loops of 70 points (separate states and
+    loop kernels), and a nested loop over more loops than the GPU holds at once (no
+    cooperative launch: loop kernel, then the nested kernel)."""
+    model = I.bbh(0.5, 0.5)
+    for plane in (P(64, 5), P(70, 4, origin=(0.0, 0.1, 0.0))):
+        ref, rgap = oracle.wilson_loop(model, plane, 2)
+        ph, gap = lib.wilson_loop(model, plane, 2, precision="mixed", ctx=ctx)
+        assert circ_err_rows(ph.cpu().numpy(), ref) <= DF_TOL
+        assert np.abs(gap.cpu().numpy() - rgap).max() <= 1e-9 * np.abs(rgap).max()
+    plane = P(8, 2000)
+    ref_ph, ref_n, _, _ = oracle.nested_wilson_loop(model, plane, 2, m=1)
+    ph, nest, _, _ = lib.nested_wilson_loop(model, plane, 2, m=1, precision="mixed", ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= DF_TOL
+    assert circ_err_rows(nest.cpu().numpy(), ref_n) <= DF_TOL
