@@ -164,15 +164,17 @@ __global__ void __launch_bounds__(OVL_THREADS, 1) k_overlaps_df(LoopArgs a) {
 // Per-loop product, eigenphases and (nested) Wannier states
 // ---------------------------------------------------------------------------
 struct LoopSmem {
-  size_t X, Y, G, lam, vec, th, key, ord, sh, red, total;
+  size_t X, Y, Ms, G, lam, vec, th, key, ord, sh, red, total;
 };
 
-__host__ __device__ inline LoopSmem loop_layout(int p, int m) {
+// df: room for one overlap matrix in double-float (the mixed request's product)
+__host__ __device__ inline LoopSmem loop_layout(int p, int m, bool df = false) {
   auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
   LoopSmem L;
   size_t o = 0;
   L.X = o; o = al(o + size_t(p) * p * sizeof(z64));
   L.Y = o; o = al(o + size_t(p) * p * sizeof(z64));
+  L.Ms = o; o = al(o + (df ? size_t(p) * p * sizeof(cdf) : 0));
   L.G = o; o = al(o + size_t(m) * m * sizeof(z64));
   L.lam = o; o = al(o + size_t(p) * sizeof(z64));
   L.vec = o; o = al(o + size_t(p) * sizeof(z64));
@@ -189,7 +191,7 @@ __global__ void k_loops(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, p = a.p, N = a.N, tid = threadIdx.x, nt = blockDim.x;
   const int m = a.nested ? a.m : 1;
-  const LoopSmem L = loop_layout(p, m);
+  const LoopSmem L = loop_layout(p, m, a.df_overlaps != 0);
   z64* X = reinterpret_cast<z64*>(smem + L.X);
   z64* Y = reinterpret_cast<z64*>(smem + L.Y);
   z64* lam = reinterpret_cast<z64*>(smem + L.lam);
@@ -219,21 +221,66 @@ __global__ void k_loops(LoopArgs a) {
     // W = M_{N-1} ... M_0
     z64* W = X;
     z64* T = Y;
-    for (int e = tid; e < p * p; e += nt) {
-      const int r = e / p, c = e - r * p;
-      W[e] = z64(double(r == c), 0.0);
-    }
-    __syncthreads();
-    for (int j = 0; j < N; ++j) {
-      const z64* M = a.M + (k0 + j) * (long long)p * p;
+    if (a.df_overlaps) {
+      // mixed request: the product in double-float on the FP32 pipe; each M_j is
+      // staged in shared memory once, each thread advances four entries at a time
+      cdf* Wd = reinterpret_cast<cdf*>(X);
+      cdf* Td = reinterpret_cast<cdf*>(Y);
+      cdf* Md = reinterpret_cast<cdf*>(smem + L.Ms);
       for (int e = tid; e < p * p; e += nt) {
         const int r = e / p, c = e - r * p;
-        z64 acc(0.0, 0.0);
-        for (int q = 0; q < p; ++q) cfma(acc, M[r * p + q], W[q * p + c]);
-        T[e] = acc;
+        Wd[e] = cdf(df(r == c ? 1.f : 0.f), df(0.f));
+      }
+      for (int j = 0; j < N; ++j) {
+        const z64* M = a.M + (k0 + j) * (long long)p * p;
+        for (int e = tid; e < p * p; e += nt) Md[e] = cdf_from(M[e]);
+        __syncthreads();
+        for (int e0 = tid; e0 < p * p; e0 += 4 * nt) {
+          cdf acc[4];
+          int rr[4], cc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = min(e0 + u * nt, p * p - 1);
+            rr[u] = e / p;
+            cc[u] = e - rr[u] * p;
+            acc[u] = cdf_zero();
+          }
+          for (int q = 0; q < p; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cfma(acc[u], Md[rr[u] * p + q], Wd[q * p + cc[u]]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (e0 + u * nt < p * p) Td[e0 + u * nt] = acc[u];
+        }
+        __syncthreads();
+        cdf* t = Wd; Wd = Td; Td = t;
+      }
+      // back to FP64 in place for the eigen-decomposition
+      z64* Wz = reinterpret_cast<z64*>(Wd);
+      for (int e = tid; e < p * p; e += nt) {
+        const cdf v = Wd[e];
+        Wz[e] = cdf_to_z64(v);
       }
       __syncthreads();
-      z64* t = W; W = T; T = t;
+      W = Wz;
+      T = Wz == X ? Y : X;
+    } else {
+      for (int e = tid; e < p * p; e += nt) {
+        const int r = e / p, c = e - r * p;
+        W[e] = z64(double(r == c), 0.0);
+      }
+      __syncthreads();
+      for (int j = 0; j < N; ++j) {
+        const z64* M = a.M + (k0 + j) * (long long)p * p;
+        for (int e = tid; e < p * p; e += nt) {
+          const int r = e / p, c = e - r * p;
+          z64 acc(0.0, 0.0);
+          for (int q = 0; q < p; ++q) cfma(acc, M[r * p + q], W[q * p + c]);
+          T[e] = acc;
+        }
+        __syncthreads();
+        z64* t = W; W = T; T = t;
+      }
     }
     // eigen-decomposition (vectors for the nested loop); Z goes to T
     const int rc = geig(W, T, p, p, a.nested != 0, lam, vec, sh);
@@ -1035,11 +1082,16 @@ cudaError_t launch_loops(const LoopArgs& a, cudaStream_t s) {
     k_loops_scan<z64><<<a.N_t, 128, Z.total, s>>>(a);
     return cudaGetLastError();
   }
-  const LoopSmem L = loop_layout(a.p, a.nested ? a.m : 1);
+  // the double-float product stages one more p x p matrix; without room for it the
+  // product stays in FP64
+  LoopArgs b = a;
+  if (b.df_overlaps && loop_layout(b.p, b.nested ? b.m : 1, true).total > size_t(227) * 1024)
+    b.df_overlaps = 0;
+  const LoopSmem L = loop_layout(b.p, b.nested ? b.m : 1, b.df_overlaps != 0);
   static size_t cached = 0;
   cudaError_t e = set_smem_once(k_loops, L.total, cached);
   if (e != cudaSuccess) return e;
-  k_loops<<<a.N_t, loop_threads(a.p), L.total, s>>>(a);
+  k_loops<<<b.N_t, loop_threads(b.p), L.total, s>>>(b);
   return cudaGetLastError();
 }
 
