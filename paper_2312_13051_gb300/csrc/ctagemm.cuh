@@ -84,12 +84,16 @@ struct GemmGramComp {  // C = A^dag B (A passed unconjugated), compensated sums
 };
 
 constexpr int CG_TILE = 64, CG_K = 16;
+// Row length of the staged tiles: one element of padding, so that the staging stores
+// of an operand whose k index is contiguous in memory (consecutive threads, rows kk
+// apart) fall in different banks.
+constexpr int CG_LD = CG_TILE + 1;
 // Shared memory used by cta_gemm<Pol> (a 16 x 64 tile of each operand).
 template <class Pol>
 __host__ __device__ constexpr size_t cg_smem() {
-  return CG_K * CG_TILE * (sizeof(typename Pol::TA) + sizeof(typename Pol::TB));
+  return CG_K * CG_LD * (sizeof(typename Pol::TA) + sizeof(typename Pol::TB));
 }
-constexpr size_t CG_SMEM = CG_K * CG_TILE * (sizeof(SplitC) + sizeof(c32));  // the largest policy
+constexpr size_t CG_SMEM = CG_K * CG_LD * (sizeof(SplitC) + sizeof(c32));  // the largest policy
 
 // C(m, c) = sum_k A(m, k) B(k, c) (the policy's product and accumulator) for m < M,
 // c < Ncol, k < K, computed by all blockDim.x == 256 threads of the CTA in 64 x 64
@@ -102,8 +106,8 @@ template <class Pol, bool A_K_CONTIG, bool B_C_CONTIG, class LA, class LB, class
 __device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned char* sm) {
   using TA = typename Pol::TA;
   using TB = typename Pol::TB;
-  TA(*As)[CG_TILE] = reinterpret_cast<TA(*)[CG_TILE]>(sm);
-  TB(*Bs)[CG_TILE] = reinterpret_cast<TB(*)[CG_TILE]>(sm + CG_K * CG_TILE * sizeof(TA));
+  TA(*As)[CG_LD] = reinterpret_cast<TA(*)[CG_LD]>(sm);
+  TB(*Bs)[CG_LD] = reinterpret_cast<TB(*)[CG_LD]>(sm + CG_K * CG_LD * sizeof(TA));
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int m0 = 0; m0 < M; m0 += CG_TILE)
     for (int c0 = 0; c0 < Ncol; c0 += CG_TILE) {
