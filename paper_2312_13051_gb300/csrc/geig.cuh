@@ -23,23 +23,61 @@ struct GeigShared {
 
 __device__ __forceinline__ double zabs(z64 a) { return hypot(a.re, a.im); }
 
-// Givens G with G [x; y] = [r; 0], c real >= 0.
+// Givens G with G [x; y] = [r; 0], c real >= 0: c = |x| / r, s = (x / |x|) conj(y) / r,
+// r = sqrt(|x|^2 + |y|^2), from two reciprocal square roots (the entries of the
+// Wilson matrices are O(1), far from the range where the squares over- or
+// underflow; a square that underflows makes the rotation swap the two rows, still
+// unitary, and the entry it leaves behind is set to zero by the caller).
 __device__ __forceinline__ void givens(z64 x, z64 y, double& c, z64& s) {
-  const double ax = zabs(x), ay = zabs(y);
-  if (ay == 0.0) {
+  const double ax2 = abs2(x), ay2 = abs2(y);
+  if (ay2 == 0.0) {
     c = 1.0;
     s = z64(0.0, 0.0);
     return;
   }
-  if (ax == 0.0) {
+  if (ax2 == 0.0) {
     c = 0.0;
-    s = z64(y.re / ay, -y.im / ay);  // conj(y)/|y|
+    const double iy = rsqrt(ay2);
+    s = z64(y.re * iy, -y.im * iy);  // conj(y)/|y|
     return;
   }
-  const double r = hypot(ax, ay);
-  c = ax / r;
-  const z64 ux(x.re / ax, x.im / ax);
-  s = (1.0 / r) * (ux * conj(y));
+  const double ir = rsqrt(ax2 + ay2), iax = rsqrt(ax2);
+  c = ax2 * iax * ir;
+  const z64 ux(x.re * iax, x.im * iax);
+  s = ir * (ux * conj(y));
+}
+
+// Whether the subdiagonal entry H[l][l-1] is negligible: against the neighbouring
+// diagonal entries, or by the product test of Ahues and Tisseur (its product with
+// the superdiagonal small against the local separation of the diagonal entries).
+__device__ __forceinline__ bool geig_negligible(const z64* H, int ld, int l, double eps) {
+  const z64 h11 = H[(l - 1) * ld + l - 1], h12 = H[(l - 1) * ld + l];
+  const z64 h21 = H[l * ld + l - 1], h22 = H[l * ld + l];
+  const double sub = zabs(h21);
+  const double dia = zabs(h22) + zabs(h11);
+  bool small = sub <= eps * dia || sub < 1e-300;
+  if (!small && sub <= dia) {
+    const double x = zabs(h12);
+    const double ab = fmax(sub, x), ba = fmin(sub, x);
+    const double y = zabs(h11 - h22);
+    const double aa = fmax(zabs(h22), y), bb = fmin(zabs(h22), y);
+    const double sc = aa + ab;
+    small = ba * (ab / sc) <= fmax(1e-300, eps * (bb * (aa / sc)));
+  }
+  return small;
+}
+
+// Largest l in [1, hi] whose subdiagonal entry is negligible, or 0: the first warp
+// tests 32 subdiagonals at a time from hi down.  Every lane of the warp calls it.
+__device__ __forceinline__ int geig_split_point(const z64* H, int ld, int hi, double eps) {
+  const int lane = threadIdx.x & 31;
+  for (int base = hi; base >= 1; base -= 32) {
+    const int l = base - lane;
+    const bool f = l >= 1 && geig_negligible(H, ld, l, eps);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (m) return base - (__ffs(m) - 1);
+  }
+  return 0;
 }
 
 // Eigen-decomposition of H (p x p, leading dimension ld), destroyed on output.
@@ -120,44 +158,25 @@ __device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* la
   int iter = 0, total = 0;
   const int cap = 120 * p + 120;
   while (true) {
-    if (tid == 0) {
+    if (tid < 32) {  // the first warp finds the active block; its lane 0 sets the shift
       int hi = sh->hi;
-      sh->active = 0;
+      if (tid == 0) sh->active = 0;
       while (hi >= 0) {
         if (hi == 0) {
-          lam[0] = H[0];
+          if (tid == 0) lam[0] = H[0];
           hi = -1;
           break;
         }
-        int l = hi;
-        while (l > 0) {
-          const z64 h11 = H[(l - 1) * ld + l - 1], h12 = H[(l - 1) * ld + l];
-          const z64 h21 = H[l * ld + l - 1], h22 = H[l * ld + l];
-          const double sub = zabs(h21);
-          const double dia = zabs(h22) + zabs(h11);
-          bool small = sub <= eps * dia || sub < 1e-300;
-          if (!small && sub <= dia) {
-            // product test (Ahues and Tisseur): the subdiagonal is negligible when its
-            // product with the superdiagonal is small against the local separation
-            const double x = zabs(h12);
-            const double ab = fmax(sub, x), ba = fmin(sub, x);
-            const double y = zabs(h11 - h22);
-            const double aa = fmax(zabs(h22), y), bb = fmin(zabs(h22), y);
-            const double sc = aa + ab;
-            small = ba * (ab / sc) <= fmax(1e-300, eps * (bb * (aa / sc)));
-          }
-          if (small) {
-            H[l * ld + l - 1] = z64(0.0, 0.0);
-            break;
-          }
-          --l;
-        }
+        const int l = geig_split_point(H, ld, hi, eps);
+        __syncwarp();
+        if (tid == 0 && l > 0) H[l * ld + l - 1] = z64(0.0, 0.0);
         if (l == hi) {
-          lam[hi] = H[hi * ld + hi];
+          if (tid == 0) lam[hi] = H[hi * ld + hi];
           --hi;
           iter = 0;
           continue;
         }
+        if (tid != 0) break;
         // shift from the trailing 2x2 of the active window
         z64 mu;
         const z64 a = H[(hi - 1) * ld + hi - 1], b = H[(hi - 1) * ld + hi];
@@ -189,13 +208,15 @@ __device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* la
         sh->active = 1;
         break;
       }
-      sh->hi = hi;
-      ++iter;
-      ++total;
-      if (total > cap) {
-        sh->fail = 1;
-        sh->active = 0;
-        sh->hi = -1;
+      if (tid == 0) {
+        sh->hi = hi;
+        ++iter;
+        ++total;
+        if (total > cap) {
+          sh->fail = 1;
+          sh->active = 0;
+          sh->hi = -1;
+        }
       }
     }
     __syncthreads();
