@@ -23,6 +23,7 @@ import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -105,7 +106,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples go to BW_CLOCKS_DIR when set (kept for inspection), else to a
+        # temporary directory; the JSON line carries their summary either way
+        d = os.environ.get("BW_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"berrywl_clocks_rank{index}.csv")
 
     def start(self):
         try:
