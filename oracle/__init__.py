@@ -17,4 +17,5 @@ from .wilson import (  # noqa: F401
     projected_spin_sector, spin_resolved_wilson_loop, nested_wilson_loop,
     cyclic_wilson_matrix, winding, circular_match_error, eigh_batched,
     plaquette_flux, plaquette_corners, plaquette_matrix,
+    wcc_fractions, largest_gap_midpoint, z2_largest_gap,
 )

@@ -281,7 +281,7 @@ def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0
 # ----------------------------------------------------------------------------
 
 # ----------------------------------------------------------------------------
-# Plaquette Berry flux (Sec. V example, the WSpinLine coupling-matrix method): the
+# Plaquette Berry flux (Sec. IV A example, the WSpinLine coupling-matrix method): the
 # Brillouin zone is cut into a grid of plaquettes; the Wilson loop of the occupied
 # bands (or of a PSO sector) around each plaquette's closed path gives its
 # integrated Berry flux, the sum of its eigenphases = arg det of the loop matrix,
@@ -312,7 +312,7 @@ def _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol):
 
 def plaquette_flux(model, plane, p: int, S=None, sign: int = -1, gap_tol=None,
                    pso_gap_tol: float = 1e-6):
-    """Integrated Berry flux through every plaquette of the plane (Sec. V, WSpinLine).
+    """Integrated Berry flux through every plaquette of the plane (Sec. IV A, WSpinLine).
     Returns (flux[N_t, N] in (-pi, pi], Chern number = sum(flux) / 2pi).  With a spin
     operator S the states are the PSO sector of sign ``sign`` (Sec. IV)."""
     _check_plane(model, plane, p)
@@ -349,6 +349,68 @@ def winding(phases: np.ndarray) -> float:
     d = np.diff(np.append(s, s[0]))
     d = d - np.round(d)
     return float(d.sum())
+
+
+# ----------------------------------------------------------------------------
+# Z2 index from the connectivity of the hybrid Wannier centres (Sec. II B, after
+# Eq. 7: with T^2 = -1 the two members of each Kramers pair carry opposite Chern
+# numbers and nu = (C1 - C2)/2 mod 2; a non-trivial index shows as WCCs that
+# interpolate across the whole cell between the two time-reversal-invariant lines
+# t2 = 0 and t2 = 1/2, Sec. II C uses it for supercells with vacancies).  The paper
+# reads the connectivity off a plot; read automatically here by the largest-gap
+# construction of Soluyanov and Vanderbilt (Phys. Rev. B 83, 235401 (2011)): on
+# every row from t2 = 0 to t2 = 1/2 take the midpoint of the widest circular gap
+# between the WCCs x = theta / 2pi (mod 1); at each step count the WCCs of the next
+# row that lie strictly between the two midpoints.  nu is the total count mod 2
+# (for an even number of WCCs the count's parity does not depend on which of the
+# two arcs between the midpoints is taken).
+# Conventions fixed here (the GPU kernel follows them): x = theta / 2pi, plus 1 when
+# negative; gaps of the sorted x are x[m+1] - x[m] and, last, (x[0] + 1) - x[p-1];
+# the first widest gap wins a tie; its midpoint x[m] + gap / 2 is reduced by 1 when
+# it reaches 1.
+# ----------------------------------------------------------------------------
+
+def wcc_fractions(theta_row) -> np.ndarray:
+    """Sorted WCC positions in [0, 1) of one row of eigenphases (Eq. 3, x = theta / 2pi)."""
+    x = np.asarray(theta_row, np.float64) / TWO_PI
+    x = np.where(x < 0.0, x + 1.0, x)
+    return np.sort(x)
+
+
+def largest_gap_midpoint(x_sorted):
+    """(midpoint, width) of the widest circular gap between sorted positions in [0, 1)."""
+    x = np.asarray(x_sorted, np.float64)
+    p = x.size
+    gaps = np.empty(p)
+    gaps[: p - 1] = x[1:] - x[:-1]
+    gaps[p - 1] = (x[0] + 1.0) - x[p - 1]
+    m = int(np.argmax(gaps))
+    z = x[m] + 0.5 * gaps[m]
+    if z >= 1.0:
+        z -= 1.0
+    return float(z), float(gaps[m])
+
+
+def z2_largest_gap(phases):
+    """Z2 index of a time-reversal-symmetric plane from its WCC spectrum (reading above).
+
+    phases: N_t x p eigenphases of the Wilson loops at t2 = i / N_t (N_t even, so that
+    t2 = 1/2 is row N_t / 2).  Returns (nu, crossings[N_t / 2], midpoints[N_t / 2 + 1],
+    widest gaps[N_t / 2 + 1])."""
+    ph = np.asarray(phases, np.float64)
+    if ph.ndim != 2 or ph.shape[1] < 1 or ph.shape[0] < 2 or ph.shape[0] % 2:
+        raise OracleError("EINVAL", "need an N_t x p array with N_t even and p >= 1")
+    h = ph.shape[0] // 2
+    xs = [wcc_fractions(ph[i]) for i in range(h + 1)]
+    mids = np.empty(h + 1)
+    widths = np.empty(h + 1)
+    for i in range(h + 1):
+        mids[i], widths[i] = largest_gap_midpoint(xs[i])
+    crossings = np.zeros(h, dtype=np.int64)
+    for i in range(h):
+        lo, hi = min(mids[i], mids[i + 1]), max(mids[i], mids[i + 1])
+        crossings[i] = int(np.count_nonzero((xs[i + 1] > lo) & (xs[i + 1] < hi)))
+    return int(crossings.sum() % 2), crossings, mids, widths
 
 
 def circular_match_error(a, b) -> float:

@@ -221,6 +221,48 @@ def supercell(model: HoppingList, L: int, W: float = 0.0, seed: int | None = Non
                        + ("_flux" if flux else ""))
 
 
+def remove_orbitals(model: HoppingList, drop) -> HoppingList:
+    """The model with the orbitals in ``drop`` taken out (every hopping that touches one
+    is dropped) and the rest renumbered in their original order (Sec. II C: vacancies
+    through PyBinding's site-state modifier)."""
+    drop = np.unique(np.asarray(drop, np.int64))
+    keep = np.ones(model.n, bool)
+    keep[drop] = False
+    new_index = np.cumsum(keep) - 1
+    sel = keep[model.i] & keep[model.j]
+    return HoppingList(n=int(keep.sum()), R=model.R[sel], i=new_index[model.i[sel]],
+                       j=new_index[model.j[sel]], t=model.t[sel], dim=model.dim,
+                       name=f"{model.name}_minus{drop.size}")
+
+
+def vacancy_cells(L: int, r: float, Ly: int | None = None) -> np.ndarray:
+    """Cells (x, y) of an L x Ly supercell within distance r of the origin cell, distances
+    taken to the nearest periodic image (Sec. II C: sites removed inside a circle of
+    radius r centred at the origin; r = 0 removes the origin cell alone)."""
+    Ly = L if Ly is None else Ly
+    out = []
+    for x in range(L):
+        for y in range(Ly):
+            dx, dy = min(x, L - x), min(y, Ly - y)
+            if dx * dx + dy * dy <= r * r:
+                out.append((x, y))
+    return np.array(out, np.int64).reshape(-1, 2)
+
+
+def vacancy_supercell(model: HoppingList, L: int, r: float, Ly: int | None = None,
+                      W: float = 0.0, seed: int | None = None) -> HoppingList:
+    """L x Ly supercell of a 2D model with the cells within radius r of the origin removed
+    (every orbital of a removed cell, Sec. II C), optionally with Anderson disorder."""
+    Ly = L if Ly is None else Ly
+    sc = supercell(model, L, W=W, seed=seed, Ly=Ly)
+    nc = model.n
+    cells = vacancy_cells(L, r, Ly)
+    drop = ((cells[:, 0] * Ly + cells[:, 1])[:, None] * nc + np.arange(nc)[None, :]).ravel()
+    out = remove_orbitals(sc, drop)
+    out.name = f"{sc.name}_vac{cells.shape[0]}"
+    return out
+
+
 def manyband(norb: int = 128, seed: int = GLOBAL_SEED + 3, decay: float = 1.5,
              soc: float = 0.1, zeeman: float = 0.05, n_low: int | None = None,
              e_low: float = -4.0) -> HoppingList:
@@ -303,6 +345,15 @@ def config_disordered(L: int, seed: int, W: float = 2.0, nk: int = 16) -> Worklo
     model = supercell(spin_hall(1.0), L, W=W, seed=seed)
     sz = np.kron(np.eye(L * L), SPIN_HALL_SZ)
     return Workload(f"disordered_L{L}_s{seed}", model, Plane(nk, nk), model.n // 2, sz)
+
+
+def config_vacancy(L: int = 6, r: float = 1.0, nk: int = 16, m: float = 1.5) -> Workload:
+    """Eq. 7 insulator on an L x L supercell with the cells within radius r of the origin
+    removed (Sec. II C uses 21 x 21), half filling, loop along kx, S = s3 (x) t3."""
+    model = vacancy_supercell(bhz_eq7(m), L, r)
+    cells = model.n // 4
+    sz = np.kron(np.eye(cells), np.diag([1.0, -1.0, -1.0, 1.0])).astype(np.complex128)
+    return Workload(f"bhz_vacancy_L{L}_r{r:g}", model, Plane(nk, nk), model.n // 2, sz)
 
 
 def config_manyband(N: int = 101, norb: int = 128) -> Workload:

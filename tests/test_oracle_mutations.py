@@ -24,7 +24,8 @@ def _all_pins():
             pins.test_choti_eq9_paper_statements, pins.test_eigenphases_known_spectrum,
             pins.test_two_band_closed_form_eigenvectors,
             pins.test_eigh_against_independent_jacobi, pins.test_plaquette_flux_chern_eq4,
-            pins.test_plaquette_flux_spin_sectors]
+            pins.test_plaquette_flux_spin_sectors, pins.test_z2_synthetic_spectra,
+            pins.test_z2_paper_models]
     return out
 
 
@@ -80,6 +81,22 @@ def _right_as_left_eigvecs_eigenphases(Wm):
     return np.sort(np.angle(np.linalg.eigvals(Wm.conj())))
 
 
+def _smallest_gap_midpoint(x_sorted):
+    x = np.asarray(x_sorted, np.float64)
+    gaps = np.append(x[1:] - x[:-1], (x[0] + 1.0) - x[-1])
+    m = int(np.argmin(gaps))
+    return float((x[m] + 0.5 * gaps[m]) % 1.0), float(gaps[m])
+
+
+def _no_wrap_gap_midpoint(x_sorted):
+    x = np.asarray(x_sorted, np.float64)
+    if x.size < 2:
+        return float(x[0]), 0.0
+    gaps = x[1:] - x[:-1]
+    m = int(np.argmax(gaps))
+    return float(x[m] + 0.5 * gaps[m]), float(gaps[m])
+
+
 MUTATIONS = {
     "conjugated_overlap": ("overlap", lambda a, b: b.conj().T @ a),
     "transposed_overlap": ("overlap", lambda a, b: (a.conj().T @ b).T),
@@ -91,6 +108,8 @@ MUTATIONS = {
     "highest_bands": ("occupied_states", _highest_bands),
     "conjugated_eigenphases": ("eigenphases", _right_as_left_eigvecs_eigenphases),
     "reversed_plaquette": ("plaquette_corners", _reversed_plaquette),
+    "smallest_wcc_gap": ("largest_gap_midpoint", _smallest_gap_midpoint),
+    "no_circular_wcc_gap": ("largest_gap_midpoint", _no_wrap_gap_midpoint),
 }
 
 

@@ -401,7 +401,7 @@ def test_unitarise_option():
 
 # ---------------------------------------------------------------- plaquette flux
 def test_plaquette_flux_chern_eq4():
-    """Sec. V coupling-matrix flux: Eq. 4 carries C = 1 (paper, Fig. 1), equal to the
+    """Sec. IV A coupling-matrix flux: Eq. 4 carries C = 1 (paper, Fig. 1), equal to the
     WCC winding of the same grid and to the degree of d/|d|; m = 3.5 is trivial."""
     model = I.chern_eq4(1.5)
     flux, C = O.plaquette_flux(model, P(24, 24), 1)
@@ -445,3 +445,92 @@ def test_plaquette_flux_gauge_invariant():
             a = np.angle(np.linalg.det(O.plaquette_matrix(O.plaquette_corners(U, i, j, 3, 3))))
             b = np.angle(np.linalg.det(O.plaquette_matrix(O.plaquette_corners(Ug, i, j, 3, 3))))
             assert abs(np.angle(np.exp(1j * (a - b)))) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Z2 index from WCC connectivity (largest-gap reading; Sec. II B, II C, III)
+# ----------------------------------------------------------------------------
+
+def _lines_to_phases(lines, Nt):
+    """Eigenphases of hand-drawn WCC lines x_a(t2) (t2 = i / Nt, rows 0 .. Nt - 1)."""
+    t = np.arange(Nt) / Nt
+    x = np.stack([f(t) for f in lines], axis=1)
+    th = 2 * np.pi * (np.mod(x + 0.5, 1.0) - 0.5)
+    return np.sort(th, axis=1)
+
+
+def test_z2_synthetic_spectra():
+    """Drawn spectra whose partner switching is known: one Kramers pair that switches
+    partners between t2 = 0 and 1/2 gives 1, a pair that returns gives 0, two switching
+    pairs give 0; a rigid shift, a mirror x -> -x and the order inside a row change
+    nothing."""
+    Nt = 400
+    switch = [lambda t: t, lambda t: -t]                                   # 0 -> 1/2 and 0 -> -1/2
+    stay = [lambda t: 0.2 + 0.05 * np.sin(2 * np.pi * t), lambda t: 0.2 - 0.05 * np.sin(2 * np.pi * t)]
+    second = [lambda t: 0.3 + t, lambda t: 0.3 - t]
+    cases = [(switch, 1), (stay, 0), (switch + second, 0), (switch + stay, 1), (stay + second, 1)]
+    for lines, nu in cases:
+        ph = _lines_to_phases(lines, Nt)
+        assert O.z2_largest_gap(ph)[0] == nu
+        shifted = _lines_to_phases([(lambda f: (lambda t: f(t) + 0.137))(f) for f in lines], Nt)
+        assert O.z2_largest_gap(shifted)[0] == nu
+        assert O.z2_largest_gap(np.sort(-ph, axis=1))[0] == nu
+        rng = np.random.default_rng(5)
+        assert O.z2_largest_gap(rng.permuted(ph, axis=1))[0] == nu
+    # the widest gap of a single pair at the Kramers-degenerate row t2 = 0 is the whole cell
+    nu, _, mids, widths = O.z2_largest_gap(_lines_to_phases(switch, 8))
+    assert widths[0] == 1.0 and abs(mids[0] - 0.5) < 1e-15
+
+
+def test_z2_paper_models():
+    """Eq. 7 (m = 1.5): nu = 1 (paper); m = 3.5 (no band inversion): 0.  For the
+    s_z-conserving spin-Hall model nu equals |C_down| mod 2 from the spin-resolved
+    winding (the paper's nu = (C1 - C2) / 2 mod 2 with C1 = -C2), a second route."""
+    ph, _ = O.wilson_loop(I.bhz_eq7(1.5), P(24, 32), 2)
+    assert O.z2_largest_gap(ph)[0] == GOLDEN["bhz_eq7_z2"]["value"]
+    ph, _ = O.wilson_loop(I.bhz_eq7(3.5), P(24, 32), 2)
+    assert O.z2_largest_gap(ph)[0] == 0
+    for m in (1.0, 3.0):
+        wl = I.config_spin_hall()
+        model = I.spin_hall(m)
+        ph, _ = O.wilson_loop(model, P(24, 16), 2)
+        dn, _, _, _ = O.spin_resolved_wilson_loop(model, P(24, 16), 2, wl.spin_op, -1)
+        assert O.z2_largest_gap(ph)[0] == int(round(abs(O.winding(dn)))) % 2
+        assert O.z2_largest_gap(ph)[0] == (1 if m == 1.0 else 0)
+
+
+def test_z2_vacancy_supercells():
+    """Sec. II C: removing the cells near the origin of an Eq. 7 supercell leaves the
+    spectrum gapless and nu = 1 (Fig. 5); the conserved s3 (x) t3 sector winds -1."""
+    for L, r in ((5, 0.0), (6, 1.0)):
+        wl = I.config_vacancy(L, r, 12)
+        removed = I.vacancy_cells(L, r).shape[0]
+        assert removed == (1 if r == 0 else 5) and wl.model.n == 4 * (L * L - removed)
+        ph, _ = O.wilson_loop(wl.model, P(12, 16), wl.p)
+        assert O.z2_largest_gap(ph)[0] == GOLDEN["bhz_vacancy_z2"]["value"]
+        dn, _, _, _ = O.spin_resolved_wilson_loop(wl.model, P(12, 16), wl.p, wl.spin_op, -1)
+        assert abs(O.winding(dn) + 1) < 1e-9
+
+
+def test_z2_strong_index_eq9():
+    """Eq. 9 with Delta0 = 0 (strong topological insulator, Sec. III): nu = 1 on the
+    kz = 0 plane and 0 on kz = pi, so the strong index nu0 = 1 and the weak indices
+    vanish; the kx planes agree (nu0 is the same from every direction)."""
+    assert GOLDEN["choti_eq9_delta0_zero"]["value"] == "strong"
+    model = I.choti_eq9(0.0)
+    z = {}
+    for axis, (ld, td) in {2: ((1, 0, 0), (0, 1, 0)), 0: ((0, 1, 0), (0, 0, 1))}.items():
+        for v in (0.0, 0.5):
+            origin = [0.0, 0.0, 0.0]
+            origin[axis] = v
+            ph, _ = O.wilson_loop(model, P(24, 16, origin=tuple(origin), loop_dir=ld, trans_dir=td), 2)
+            z[(axis, v)] = O.z2_largest_gap(ph)[0]
+    assert (z[(2, 0.0)] + z[(2, 0.5)]) % 2 == 1 and z[(2, 0.5)] == 0
+    assert (z[(0, 0.0)] + z[(0, 0.5)]) % 2 == 1 and z[(0, 0.5)] == 0
+
+
+def test_z2_input_checks():
+    with pytest.raises(O.OracleError):
+        O.z2_largest_gap(np.zeros((7, 2)))
+    with pytest.raises(O.OracleError):
+        O.z2_largest_gap(np.zeros((8, 0)))
