@@ -91,6 +91,21 @@ typedef struct {
   int32_t N_t;            /* transverse points, >= 1                                */
 } bw_plane;
 
+/* A stack of N_s parallel planes (Sec. III: the nested loop as a function of k_z;
+ * Sec. II B: the weak and strong Z2 indices of a 3D crystal from the planes k_a = 0 and
+ * k_a = 1/2): plane s, 0 <= s < N_s, is `plane` with its origin moved by
+ * (s / N_s) sweep_dir,
+ *   f(j, i, s) = origin + (j / N) loop_dir + (i / N_t) trans_dir + (s / N_s) sweep_dir.
+ * sweep_dir is an integer reciprocal vector (N_s planes over one period; N_s = 2 with
+ * sweep_dir = e_z gives k_z = 0 and k_z = 1/2).  Every plane's loops run in the same
+ * launches.  Outputs are plane-major: row s N_t + i of a per-row output belongs to
+ * transverse point i of plane s; k-point index k = (s N_t + i) N + j. */
+typedef struct {
+  bw_plane plane;         /* plane s = 0; N_t transverse points per plane              */
+  int32_t sweep_dir[3];
+  int32_t N_s;            /* planes, >= 1                                             */
+} bw_plane_stack;
+
 /* Options.  A negative tolerance selects the default. */
 typedef struct {
   double gap_tol;         /* direct gap; default 1e-6 * max(1, max|t|)              */
@@ -189,8 +204,29 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
                                        double* phases, double* pso_evals,
                                        double* min_pso_gap, double* min_gap, void* stream);
 
+/* The three loop entry points over a stack of planes (bw_plane_stack): the results of
+ * the single-plane calls for every plane, in one pass.  phases: DEVICE, N_s N_t x p
+ * (N_s N_t x p/2 for the spin-resolved loop); min_gap, min_wannier_gap, min_pso_gap:
+ * DEVICE, N_s N_t (may be NULL); nested: DEVICE, N_s N x m (row s N + j: base point j of
+ * plane s; each nested loop closes within its plane); pso_evals: DEVICE, N_s N_t N x p
+ * (may be NULL).  Limits and statuses as for the single-plane calls; the device status
+ * reports k-point indices k = (s N_t + i) N + j and nested base points s N + j. */
+bw_status bw_wilson_loop_stack(bw_ctx* ctx, const bw_model* model, const bw_plane_stack* stack,
+                               int32_t p, bw_precision prec, const bw_opts* opts, double* phases,
+                               double* min_gap, void* stream);
+bw_status bw_nested_wilson_loop_stack(bw_ctx* ctx, const bw_model* model, const bw_plane_stack* stack,
+                                      int32_t p, double cut, int32_t first, int32_t m,
+                                      bw_precision prec, const bw_opts* opts, double* phases,
+                                      double* nested, double* min_wannier_gap, double* min_gap,
+                                      void* stream);
+bw_status bw_spin_resolved_wilson_loop_stack(bw_ctx* ctx, const bw_model* model,
+                                             const bw_plane_stack* stack, int32_t p,
+                                             const bw_c128* spin_op, int32_t sign, bw_precision prec,
+                                             const bw_opts* opts, double* phases, double* pso_evals,
+                                             double* min_pso_gap, double* min_gap, void* stream);
+
 /* Plaquette Berry flux (the coupling-matrix method of BerryEasy's WSpinLine, used in
- * the disordered-quadrupole example of Sec. V): the plane's grid is cut into N x N_t
+ * the disordered-quadrupole example of Sec. IV A): the plane's grid is cut into N x N_t
  * plaquettes; plaquette (j, i) has corners k(j, i), k(j+1, i), k(j+1, i+1), k(j, i+1)
  * (both directions close cyclically, so trans_dir must be an integer vector) and its
  * integrated Berry flux is the argument of the determinant of the Wilson loop of the
@@ -221,6 +257,31 @@ bw_status bw_plaquette_flux(bw_ctx* ctx, const bw_model* model, const bw_plane* 
  * DEVICE, one double.  Asynchronous on `stream`; no scratch memory. */
 bw_status bw_winding(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, double* sums,
                      double* winding, void* stream);
+
+/* Z2 index of a time-reversal-symmetric plane from the connectivity of its hybrid
+ * Wannier centres (Sec. II B after Eq. 7: the WCCs of a non-trivial plane run across
+ * the whole cell between the time-reversal-invariant lines t2 = 0 and t2 = 1/2;
+ * Sec. II C reads it for supercells with vacancies; the weak and strong indices of a
+ * 3D crystal are those of its high-symmetry planes).  The connectivity is read by the
+ * largest-gap construction of Soluyanov and Vanderbilt (Phys. Rev. B 83, 235401
+ * (2011)):
+ *   x = theta / 2pi, plus 1 when negative;
+ *   for rows i = 0 .. N_t/2 the widest circular gap between the sorted x (gaps
+ *   x[q+1] - x[q], then (x[0] + 1) - x[p-1]; the first widest wins a tie) and its
+ *   midpoint z_i = x[q] + gap/2 (minus 1 when it reaches 1), in FP64;
+ *   crossings[i] = the number of x of row i + 1 strictly between z_i and z_{i+1};
+ *   nu = sum of crossings mod 2.
+ * The reading is a heuristic on a finite grid: it needs the midpoint to move less than
+ * the WCCs around it between rows (refine N_t when `width` gets small).
+ * phases: DEVICE, N_t x p as the loop entry points write them (row i at t2 = i / N_t,
+ * each row ascending in [-pi, pi]); N_t even, p >= 1; rows 0 .. N_t/2 are read.
+ * nu: DEVICE, one int32: 0 or 1, or -1 when a row is not ascending in [-pi, pi] (then
+ * the device status is BW_EINVAL with the row index; bw_get_status reports it).
+ * crossings: DEVICE, N_t/2 int32 (may be NULL).  mid, width: DEVICE, N_t/2 + 1
+ * doubles, the midpoint and the width of each row's widest gap (may be NULL; NULL
+ * outputs take scratch from the context).  Asynchronous on `stream`. */
+bw_status bw_z2_largest_gap(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, int32_t* nu,
+                            int32_t* crossings, double* mid, double* width, void* stream);
 
 /* Allocation-free Wilson loop (no counterpart in the paper: it serves callers).
  * Some callers cannot let a library allocate device memory: programs that give all

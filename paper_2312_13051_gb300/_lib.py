@@ -41,6 +41,10 @@ class bw_plane(C.Structure):
                 ("trans_dir", C.c_double * 3), ("N", C.c_int32), ("N_t", C.c_int32)]
 
 
+class bw_plane_stack(C.Structure):
+    _fields_ = [("plane", bw_plane), ("sweep_dir", C.c_int32 * 3), ("N_s", C.c_int32)]
+
+
 class bw_opts(C.Structure):
     _fields_ = [("gap_tol", C.c_double), ("pso_gap_tol", C.c_double),
                 ("wannier_gap_tol", C.c_double), ("unitarise", C.c_int32),
@@ -84,7 +88,17 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_spin_resolved_wilson_loop": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane),
                                                    i32, vp, i32, i32, C.POINTER(bw_opts), vp,
                                                    vp, vp, vp, vp]),
+            "bw_wilson_loop_stack": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane_stack), i32,
+                                           i32, C.POINTER(bw_opts), vp, vp, vp]),
+            "bw_nested_wilson_loop_stack": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane_stack),
+                                                  i32, dbl, i32, i32, i32, C.POINTER(bw_opts), vp,
+                                                  vp, vp, vp, vp]),
+            "bw_spin_resolved_wilson_loop_stack": (i32, [vp, C.POINTER(bw_model),
+                                                         C.POINTER(bw_plane_stack), i32, vp, i32,
+                                                         i32, C.POINTER(bw_opts), vp, vp, vp, vp,
+                                                         vp]),
             "bw_winding": (i32, [vp, vp, i32, i32, vp, vp, vp]),
+            "bw_z2_largest_gap": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, vp]),
             "bw_plaquette_flux": (i32, [vp, C.POINTER(bw_model), C.POINTER(bw_plane), i32, vp, i32,
                                         i32, C.POINTER(bw_opts), vp, vp, vp, vp, vp]),
             "bw_wilson_loop_noalloc": (i32, [C.POINTER(bw_model), C.POINTER(bw_plane), i32, i32,
@@ -113,7 +127,8 @@ def exported_symbols():
     return ["bw_create", "bw_destroy", "bw_last_error", "bw_get_status", "bw_set_profiling",
             "bw_profile_read", "bw_build_hk",
             "bw_eigh_batched", "bw_wilson_loop", "bw_nested_wilson_loop",
-            "bw_spin_resolved_wilson_loop", "bw_winding", "bw_plaquette_flux", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
+            "bw_spin_resolved_wilson_loop", "bw_wilson_loop_stack", "bw_nested_wilson_loop_stack",
+            "bw_spin_resolved_wilson_loop_stack", "bw_winding", "bw_z2_largest_gap", "bw_plaquette_flux", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
             "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
             "bw_server_poll", "bw_server_wait", "bw_server_outstanding"]
 
@@ -210,6 +225,18 @@ def _plane(plane) -> bw_plane:
                     (C.c_double * 3)(*map(float, plane.trans_dir)), int(plane.N), int(plane.N_t))
 
 
+def _plane_arg(plane):
+    """(ctypes struct, entry-point suffix, leading output shape, the single plane) for a
+    plane or a stack of planes (any object with ``plane, sweep_dir, N_s``)."""
+    if hasattr(plane, "sweep_dir"):
+        sw = [int(round(x)) for x in plane.sweep_dir]
+        if any(abs(float(x) - round(float(x))) > 0 for x in plane.sweep_dir):
+            raise BWError(1, "sweep_dir must be an integer vector")
+        st = bw_plane_stack(_plane(plane.plane), (C.c_int32 * 3)(*sw), int(plane.N_s))
+        return st, "_stack", (int(plane.N_s),), plane.plane
+    return _plane(plane), "", (), plane
+
+
 def _opts(gap_tol=-1.0, pso_gap_tol=-1.0, wannier_gap_tol=-1.0, unitarise=False, max_sweeps=0):
     return bw_opts(float(gap_tol), float(pso_gap_tol), float(wannier_gap_tol), int(unitarise),
                    int(max_sweeps))
@@ -265,19 +292,22 @@ def eigh_batched(H, n_per, n_vec: int, precision: str = "fp64", ctx: Context | N
 
 def wilson_loop(model, plane, p: int, precision: str = "fp64", ctx: Context | None = None,
                 check=True, out=None, **opts):
-    """Hybrid Wannier centres: (phases[N_t, p], min_gap[N_t]) as CUDA float64 tensors."""
+    """Hybrid Wannier centres: (phases[N_t, p], min_gap[N_t]) as CUDA float64 tensors.
+    ``plane`` may be a stack of planes (``inputs.PlaneStack``): then every output has a
+    leading plane axis, phases[N_s, N_t, p] and min_gap[N_s, N_t]."""
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
     hm = _HostModel(model)
-    pl = _plane(plane)
+    pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
-        out = (_empty((plane.N_t, p), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+        out = (_empty(lead + (plane.N_t, p), torch.float64, dev),
+               _empty(lead + (plane.N_t,), torch.float64, dev))
     ph, gap = out
-    ctx.check(ctx.lib.bw_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
-                                     PRECISION[precision], C.byref(o), _ptr(ph), _ptr(gap),
-                                     _stream_ptr()))
+    ctx.check(getattr(ctx.lib, "bw_wilson_loop" + sfx)(
+        ctx.h, C.byref(hm.s), C.byref(pl), int(p), PRECISION[precision], C.byref(o), _ptr(ph),
+        _ptr(gap), _stream_ptr()))
     if check:
         ctx.status()
     return ph, gap
@@ -286,22 +316,24 @@ def wilson_loop(model, plane, p: int, precision: str = "fp64", ctx: Context | No
 def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0,
                        m: int | None = None, precision: str = "fp64",
                        ctx: Context | None = None, check=True, out=None, **opts):
-    """Nested loop: (phases[N_t, p], nested[N, m], min_wannier_gap[N_t], min_gap[N_t])."""
+    """Nested loop: (phases[N_t, p], nested[N, m], min_wannier_gap[N_t], min_gap[N_t]);
+    for a stack of planes each output has a leading plane axis (nested[N_s, N, m])."""
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
     m = p // 2 if m is None else int(m)
     hm = _HostModel(model)
-    pl = _plane(plane)
+    pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
-        out = (_empty((plane.N_t, p), torch.float64, dev), _empty((plane.N, m), torch.float64, dev),
-               _empty((plane.N_t,), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+        out = (_empty(lead + (plane.N_t, p), torch.float64, dev),
+               _empty(lead + (plane.N, m), torch.float64, dev),
+               _empty(lead + (plane.N_t,), torch.float64, dev),
+               _empty(lead + (plane.N_t,), torch.float64, dev))
     ph, nest, wg, gap = out
-    ctx.check(ctx.lib.bw_nested_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
-                                            float(cut), int(first), int(m), PRECISION[precision],
-                                            C.byref(o), _ptr(ph), _ptr(nest), _ptr(wg), _ptr(gap),
-                                            _stream_ptr()))
+    ctx.check(getattr(ctx.lib, "bw_nested_wilson_loop" + sfx)(
+        ctx.h, C.byref(hm.s), C.byref(pl), int(p), float(cut), int(first), int(m),
+        PRECISION[precision], C.byref(o), _ptr(ph), _ptr(nest), _ptr(wg), _ptr(gap), _stream_ptr()))
     if check:
         ctx.status()
     return ph, nest, wg, gap
@@ -311,28 +343,53 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
                               precision: str = "fp64", ctx: Context | None = None, check=True,
                               want_pso=True, out=None, **opts):
     """Spin-resolved loop: (phases[N_t, p/2], pso_evals[N_t, N, p] or None,
-    min_pso_gap[N_t], min_gap[N_t])."""
+    min_pso_gap[N_t], min_gap[N_t]); for a stack of planes each output has a leading
+    plane axis."""
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
     hm = _HostModel(model)
-    pl = _plane(plane)
+    pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     S = np.ascontiguousarray(spin_op, dtype=np.complex128)
     if S.shape != (model.n, model.n):
         raise BWError(1, f"spin operator must be {model.n} x {model.n}")
     if out is None:
-        out = (_empty((plane.N_t, p // 2), torch.float64, dev),
-               _empty((plane.N_t, plane.N, p), torch.float64, dev) if want_pso else None,
-               _empty((plane.N_t,), torch.float64, dev), _empty((plane.N_t,), torch.float64, dev))
+        out = (_empty(lead + (plane.N_t, p // 2), torch.float64, dev),
+               _empty(lead + (plane.N_t, plane.N, p), torch.float64, dev) if want_pso else None,
+               _empty(lead + (plane.N_t,), torch.float64, dev),
+               _empty(lead + (plane.N_t,), torch.float64, dev))
     ph, pso, pg, gap = out
-    ctx.check(ctx.lib.bw_spin_resolved_wilson_loop(ctx.h, C.byref(hm.s), C.byref(pl), int(p),
-                                                   S.ctypes.data, int(sign), PRECISION[precision],
-                                                   C.byref(o), _ptr(ph), _ptr(pso), _ptr(pg),
-                                                   _ptr(gap), _stream_ptr()))
+    ctx.check(getattr(ctx.lib, "bw_spin_resolved_wilson_loop" + sfx)(
+        ctx.h, C.byref(hm.s), C.byref(pl), int(p), S.ctypes.data, int(sign), PRECISION[precision],
+        C.byref(o), _ptr(ph), _ptr(pso), _ptr(pg), _ptr(gap), _stream_ptr()))
     if check:
         ctx.status()
     return ph, pso, pg, gap
+
+
+def _need_stack(stack):
+    if not hasattr(stack, "sweep_dir"):
+        raise BWError(1, "expected a stack of planes (plane, sweep_dir, N_s)")
+
+
+def wilson_loop_stack(model, stack, p: int, **kw):
+    """``bw_wilson_loop_stack``: :func:`wilson_loop` over a stack of planes."""
+    _need_stack(stack)
+    return wilson_loop(model, stack, p, **kw)
+
+
+def nested_wilson_loop_stack(model, stack, p: int, **kw):
+    """``bw_nested_wilson_loop_stack``: :func:`nested_wilson_loop` over a stack of planes."""
+    _need_stack(stack)
+    return nested_wilson_loop(model, stack, p, **kw)
+
+
+def spin_resolved_wilson_loop_stack(model, stack, p: int, spin_op, sign: int = -1, **kw):
+    """``bw_spin_resolved_wilson_loop_stack``: :func:`spin_resolved_wilson_loop` over a
+    stack of planes."""
+    _need_stack(stack)
+    return spin_resolved_wilson_loop(model, stack, p, spin_op, sign, **kw)
 
 
 def plaquette_flux(model, plane, p: int, spin_op=None, sign: int = -1, precision: str = "fp64",
@@ -380,6 +437,29 @@ def winding(phases, ctx: Context | None = None, check=True, want_sums=False):
     if check:
         ctx.status()
     return (w, sums) if want_sums else w
+
+
+def z2_largest_gap(phases, ctx: Context | None = None, check=True, want_detail=False):
+    """Z2 index of a time-reversal-symmetric plane from its WCC spectrum ``phases`` (CUDA
+    float64 N_t x p, rows ascending, N_t even) by the largest-gap construction.  Returns
+    a CUDA int32 scalar tensor (0, 1, or -1 for a rejected row), or (nu, crossings[N_t/2],
+    midpoints[N_t/2 + 1], widest gaps[N_t/2 + 1]) with ``want_detail``."""
+    import torch
+    ctx = ctx or context()
+    if not (phases.is_cuda and phases.dtype == torch.float64 and phases.is_contiguous()
+            and phases.dim() == 2):
+        raise BWError(1, "phases must be a contiguous CUDA float64 tensor of shape (N_t, p)")
+    Nt, p = phases.shape
+    dev = phases.device
+    nu = _empty((), torch.int32, dev)
+    h = Nt // 2
+    detail = ((_empty((h,), torch.int32, dev), _empty((h + 1,), torch.float64, dev),
+               _empty((h + 1,), torch.float64, dev)) if want_detail else (None, None, None))
+    ctx.check(ctx.lib.bw_z2_largest_gap(ctx.h, _ptr(phases), int(Nt), int(p), _ptr(nu),
+                                        *(_ptr(d) for d in detail), _stream_ptr()))
+    if check:
+        ctx.status()
+    return (nu, *detail) if want_detail else nu
 
 
 def wilson_loop_noalloc(model, plane, p: int, precision: str = "fp64", out=None, **opts):

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libberrywl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["states.cu", "tiny.cu", "large.cu", "loops.cu", "bigloop.cu", "runtime.cu", "server.cu"]
+SOURCES = ["states.cu", "tiny.cu", "large.cu", "loops.cu", "bigloop.cu", "wcc.cu", "runtime.cu", "server.cu"]
 
 
 def nvcc() -> str:

@@ -108,16 +108,38 @@ struct DevOp {
 };
 
 // Plane parameters passed by value.
+// A stack of N_s parallel planes: row i (0 <= i < N_t = N_s N_tp) is transverse point
+// it = i mod N_tp of plane s = i / N_tp, whose origin is moved by (s / N_s) sweep
+// (an integer reciprocal vector).  One plane: N_s = 1, N_tp = N_t, sweep = 0.
 struct DevPlane {
   double origin[3];
   double loop_dir[3];
   double trans_dir[3];
   int N, N_t;
+  int N_s, N_tp;
+  int sweep[3];
 };
 
 __device__ __forceinline__ void plane_f(const DevPlane& pl, int i, int j, double f[3]) {
-  const double a = double(j) / double(pl.N), b = double(i) / double(pl.N_t);
+  const double a = double(j) / double(pl.N);
+  if (pl.N_s > 1) {
+    const int s = i / pl.N_tp, it = i - s * pl.N_tp;
+    const double b = double(it) / double(pl.N_tp), c = double(s) / double(pl.N_s);
+    for (int d = 0; d < 3; ++d)
+      f[d] = pl.origin[d] + a * pl.loop_dir[d] + b * pl.trans_dir[d] + c * double(pl.sweep[d]);
+    return;
+  }
+  const double b = double(i) / double(pl.N_t);
   for (int d = 0; d < 3; ++d) f[d] = pl.origin[d] + a * pl.loop_dir[d] + b * pl.trans_dir[d];
+}
+
+// Index m of exp(i 2pi m / N_t) for the transverse and sweep part of the Bloch phase of
+// a translation at row i (integer trans_dir and sweep): tq = trans_dir . R, sq =
+// sweep . R; (it tq / N_tp + s sq / N_s) = (it tq N_s + s sq N_tp) / N_t.
+__host__ __device__ __forceinline__ long long plane_row_index(const DevPlane& pl, int i, int tq, int sq) {
+  if (pl.N_s <= 1) return (long long)i * tq;
+  const int s = i / pl.N_tp, it = i - s * pl.N_tp;
+  return (long long)it * tq * pl.N_s + (long long)s * sq * pl.N_tp;
 }
 
 // exp(i 2 pi f . R), argument reduced exactly by sincospi.

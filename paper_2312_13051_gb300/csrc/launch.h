@@ -84,8 +84,9 @@ struct LoopArgs {
   z64* w;                // N x N_t x n x m
   z64* nu_buf;           // N x N_t x p x m transported sector bases (sequential loop path), or NULL
   double* min_wannier_gap;  // N_t (optional)
-  double* nested_out;    // N x m
+  double* nested_out;    // N_s x N x m
   DevStatus* status;
+  int N_s;               // planes stacked along the rows (N_t = N_s x rows per plane; 0 or 1: one)
   int u_df;              // U and w hold complex double-float (loops_accept_df() holds)
   int df_overlaps;       // mixed request: overlaps from the FP64 states in double-float
 };
@@ -227,6 +228,13 @@ cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux,
 // Winding of the summed Wannier centres over the transverse direction (Eq. 6).
 cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,
                            cudaStream_t s);
+
+// Z2 index of a plane from its WCC spectrum (wcc.cu): rows 0 .. Nt / 2 of phases
+// (Nt x p, each row ascending in [-pi, pi]); mid / width (Nt / 2 + 1) and crossings
+// (Nt / 2) are written; *nu = total crossings mod 2, or -1 when a row was rejected
+// (also reported as ST_EINVAL with the row index).
+cudaError_t launch_z2(const double* phases, int Nt, int p, double* mid, double* width, int* crossings,
+                      int* nu, DevStatus* status, cudaStream_t s);
 
 cudaError_t launch_build_hk(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_states_small(const StatesArgs& a, int p_out, cudaStream_t s);

@@ -29,6 +29,10 @@ namespace bw {
 
 __device__ __forceinline__ double phase_of(z64 z) { return atan2(z.im, z.re); }
 
+// Planes stacked along the rows: the nested loop of base point b (of N_s N) runs over
+// the rows of plane s = b / N and closes within it.
+__host__ __device__ __forceinline__ int n_planes(const LoopArgs& a) { return a.N_s > 1 ? a.N_s : 1; }
+
 // Ranks th[0..p) ascending (stable) into ord.
 __device__ void rank_sort(const double* th, int p, int* ord) {
   for (int a = threadIdx.x; a < p; a += blockDim.x) {
@@ -436,7 +440,7 @@ cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 __global__ void k_nested(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n, m = a.m, Nt = a.N_t, tid = threadIdx.x, nt = blockDim.x;
+  const int n = a.n, m = a.m, Ns = n_planes(a), Nt = a.N_t / Ns, tid = threadIdx.x, nt = blockDim.x;
   const LoopSmem L = loop_layout(m, 1);
   z64* W = reinterpret_cast<z64*>(smem + L.X);
   z64* T = reinterpret_cast<z64*>(smem + L.Y);
@@ -446,13 +450,14 @@ __global__ void k_nested(LoopArgs a) {
   int* ord = reinterpret_cast<int*>(smem + L.ord);
   GeigShared* sh = reinterpret_cast<GeigShared*>(smem + L.sh);
   z64* Mt = reinterpret_cast<z64*>(smem + L.total);  // m x m after the layout
-  for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
+  for (int b = blockIdx.x; b < a.N * Ns; b += gridDim.x) {
+    const int sp = b / a.N, j = b - sp * a.N;
     for (int e = tid; e < m * m; e += nt) {
       const int r = e / m, c = e - r * m;
       W[e] = z64(double(r == c), 0.0);
     }
     __syncthreads();
-    const z64* wj = a.w + (long long)j * Nt * n * m;
+    const z64* wj = a.w + ((long long)j * a.N_t + (long long)sp * Nt) * n * m;
     for (int i = 0; i < Nt; ++i) {
       const z64* wa = wj + (long long)i * n * m;
       const z64* wb = wj + (long long)(i + 1 == Nt ? 0 : i + 1) * n * m;
@@ -473,11 +478,11 @@ __global__ void k_nested(LoopArgs a) {
       z64* t = W; W = T; T = t;
     }
     const int rc = geig(W, T, m, m, false, lam, vec, sh);
-    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, j, 0.0);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, b, 0.0);
     for (int c = tid; c < m; c += nt) th[c] = phase_of(lam[c]);
     __syncthreads();
     rank_sort(th, m, ord);
-    for (int c = tid; c < m; c += nt) a.nested_out[(long long)j * m + c] = th[ord[c]];
+    for (int c = tid; c < m; c += nt) a.nested_out[(long long)b * m + c] = th[ord[c]];
     __syncthreads();
   }
 }
@@ -768,11 +773,12 @@ __global__ void k_loops_scan(LoopArgs a) {
 // of the scalar overlaps w(i+1)^dagger w(i) (any order), taken by the CTA's first
 // warp straight from global memory; the other threads return at once.
 template <typename E>
-__device__ void nested_base_m1(const LoopArgs& a, int j) {
+__device__ void nested_base_m1(const LoopArgs& a, int b) {
   using A = Arith<E>;
-  const int n = a.n, Nt = a.N_t, tid = threadIdx.x;
+  const int n = a.n, Nt = a.N_t / n_planes(a), tid = threadIdx.x;
   if (tid >= 32) return;
-  const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * n;
+  const int sp = b / a.N, j = b - sp * a.N;
+  const E* wj = reinterpret_cast<const E*>(a.w) + ((long long)j * a.N_t + (long long)sp * Nt) * n;
   E prod = A::one();
   for (int i = tid; i < Nt; i += 32) {
     const E* wa = wj + (size_t)i * n;
@@ -782,7 +788,7 @@ __device__ void nested_base_m1(const LoopArgs& a, int j) {
     prod = prod * acc;
   }
   for (int o = 16; o > 0; o >>= 1) prod = prod * A::shfl_xor(prod, o);
-  if (tid == 0) a.nested_out[j] = phase_of(A::to64(prod));
+  if (tid == 0) a.nested_out[b] = phase_of(A::to64(prod));
 }
 
 // ---------------------------------------------------------------------------
@@ -864,13 +870,14 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
     for (int r = tid - rbase; r >= 0 && r < nR; r += nt) {
       const int* Rv = md.Rv + 3 * r;
       double x = 0.0;
-      int lq = 0, tq = 0;
+      int lq = 0, tq = 0, sq = 0;
       for (int dd = 0; dd < 3; ++dd) {
         x += sa.plane.origin[dd] * double(Rv[dd]);
         lq += int(sa.plane.loop_dir[dd]) * Rv[dd];
         tq += int(sa.plane.trans_dir[dd]) * Rv[dd];
+        sq += sa.plane.sweep[dd] * Rv[dd];
       }
-      x += double(pmod((long long)i * tq, Nt)) / double(Nt);
+      x += double(pmod(plane_row_index(sa.plane, i, tq, sq), Nt)) / double(Nt);
       double sn, cs;
       sincospi(2.0 * x, &sn, &cs);
       rowf[r] = cdf_from(z64(cs, sn));
@@ -916,7 +923,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
     // has passed this barrier; then the nested loops of one Wannier band
     __threadfence();
     cooperative_groups::this_grid().sync();
-    for (int j = blockIdx.x; j < a.N; j += gridDim.x) nested_base_m1<cdf>(a, j);
+    for (int b = blockIdx.x; b < a.N * n_planes(a); b += gridDim.x) nested_base_m1<cdf>(a, b);
   }
 }
 
@@ -974,7 +981,7 @@ template <typename E>
 __global__ void k_nested_scan(LoopArgs a) {
   using A = Arith<E>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n, m = a.m, Nt = a.N_t, tid = threadIdx.x, nt = blockDim.x;
+  const int n = a.n, m = a.m, Nt = a.N_t / n_planes(a), tid = threadIdx.x, nt = blockDim.x;
   const ScanSmem Z = scan_layout(Nt, m, Nt * n * m);
   E* S = reinterpret_cast<E*>(smem + Z.S);
   E* T = reinterpret_cast<E*>(smem + Z.T);
@@ -987,10 +994,11 @@ __global__ void k_nested_scan(LoopArgs a) {
   int* ord = reinterpret_cast<int*>(smem + Z.ord);
   GeigShared* sh = reinterpret_cast<GeigShared*>(smem + Z.sh);
   const int mm2 = m * m, nm = n * m;
-  for (int j = blockIdx.x; j < a.N; j += gridDim.x) {
-    const E* wj = reinterpret_cast<const E*>(a.w) + (long long)j * Nt * nm;
+  for (int b = blockIdx.x; b < a.N * n_planes(a); b += gridDim.x) {
+    const int sp = b / a.N, j = b - sp * a.N;
+    const E* wj = reinterpret_cast<const E*>(a.w) + ((long long)j * a.N_t + (long long)sp * Nt) * nm;
     if (m == 1) {
-      nested_base_m1<E>(a, j);
+      nested_base_m1<E>(a, b);
       continue;
     }
     for (int e = tid; e < Nt * nm; e += nt) Wn[e] = wj[e];
@@ -1009,11 +1017,11 @@ __global__ void k_nested_scan(LoopArgs a) {
     for (int e = tid; e < mm2; e += nt) X[e] = A::to64(Pf[(Nt - 1) * mm2 + e]);
     __syncthreads();
     const int rc = geig(X, Y, m, m, false, lam, vec, sh);
-    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, j, 0.0);
+    if (rc != 0 && tid == 0) report(a.status, ST_ENOCONV, b, 0.0);
     for (int c = tid; c < m; c += nt) th[c] = phase_of(lam[c]);
     __syncthreads();
     rank_sort(th, m, ord);
-    for (int c = tid; c < m; c += nt) a.nested_out[(long long)j * m + c] = th[ord[c]];
+    for (int c = tid; c < m; c += nt) a.nested_out[(long long)b * m + c] = th[ord[c]];
     __syncthreads();
   }
 }
@@ -1025,7 +1033,8 @@ static bool scan_loops_fit(const LoopArgs& a) {
 }
 
 static bool scan_nested_fit(const LoopArgs& a) {
-  return a.m <= SCAN_P_MAX && scan_layout(a.N_t, a.m, a.N_t * a.n * a.m).total <= SCAN_SMEM_MAX;
+  const int Nt = a.N_t / n_planes(a);
+  return a.m <= SCAN_P_MAX && scan_layout(Nt, a.m, Nt * a.n * a.m).total <= SCAN_SMEM_MAX;
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,19 +1268,22 @@ cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux,
 
 cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
+  const long long bases = (long long)a.N * n_planes(a);
+  const int grid = int(bases < 152LL * 64 ? bases : 152LL * 64);
   if (scan_nested_fit(a)) {
-    const ScanSmem Z = scan_layout(a.N_t, a.m, a.N_t * a.n * a.m);
+    const int Nt = a.N_t / n_planes(a);
+    const ScanSmem Z = scan_layout(Nt, a.m, Nt * a.n * a.m);
     if (a.u_df) {
       static size_t cached_df = 0;
       cudaError_t e = set_smem_once(k_nested_scan<cdf>, Z.total, cached_df);
       if (e != cudaSuccess) return e;
-      k_nested_scan<cdf><<<a.N, 128, Z.total, s>>>(a);
+      k_nested_scan<cdf><<<grid, 128, Z.total, s>>>(a);
       return cudaGetLastError();
     }
     static size_t cached_scan = 0;
     cudaError_t e = set_smem_once(k_nested_scan<z64>, Z.total, cached_scan);
     if (e != cudaSuccess) return e;
-    k_nested_scan<z64><<<a.N, 128, Z.total, s>>>(a);
+    k_nested_scan<z64><<<grid, 128, Z.total, s>>>(a);
     return cudaGetLastError();
   }
   const LoopSmem L = loop_layout(a.m, 1);
@@ -1279,7 +1291,7 @@ cudaError_t launch_nested(const LoopArgs& a, cudaStream_t s) {
   static size_t cached = 0;
   cudaError_t e = set_smem_once(k_nested, sm, cached);
   if (e != cudaSuccess) return e;
-  k_nested<<<a.N, loop_threads(a.m), sm, s>>>(a);
+  k_nested<<<grid, loop_threads(a.m), sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -407,15 +407,41 @@ bw_status check_plane(bw_ctx* ctx, const bw_plane* pl, bool nested) {
   return BW_OK;
 }
 
-bw::DevPlane dev_plane(const bw_plane* pl) {
+// One plane, or a stack of N_s parallel planes flattened into N_s N_t rows: `flat` is
+// the plane with N_t = all rows, which sizes every buffer; the kernels take plane and
+// transverse point from the row (bw::DevPlane).
+struct PlaneX {
+  bw_plane flat;
+  int N_s = 1, N_tp = 0;
+  int sweep[3] = {0, 0, 0};
+};
+
+bw_status stack_planes(bw_ctx* ctx, const bw_plane* pl, const int32_t* sweep, int N_s, PlaneX& X) {
+  if (N_s < 1) return fail(ctx, BW_EINVAL, "need N_s >= 1 planes (N_s = %d)", N_s);
+  if (int64_t(pl->N_t) * N_s > (int64_t(1) << 30) ||
+      int64_t(pl->N) * pl->N_t * N_s > (int64_t(1) << 31))
+    return fail(ctx, BW_EINVAL, "plane stack has too many k-points");
+  X.flat = *pl;
+  X.flat.N_t = pl->N_t * N_s;
+  X.N_s = N_s;
+  X.N_tp = pl->N_t;
+  for (int d = 0; d < 3; ++d) X.sweep[d] = (sweep && N_s > 1) ? sweep[d] : 0;
+  return BW_OK;
+}
+
+bw::DevPlane dev_plane(const PlaneX& X) {
+  const bw_plane* pl = &X.flat;
   bw::DevPlane d;
   for (int k = 0; k < 3; ++k) {
     d.origin[k] = pl->origin[k];
     d.loop_dir[k] = double(pl->loop_dir[k]);
     d.trans_dir[k] = pl->trans_dir[k];
+    d.sweep[k] = X.sweep[k];
   }
   d.N = pl->N;
   d.N_t = pl->N_t;
+  d.N_s = X.N_s;
+  d.N_tp = X.N_tp;
   return d;
 }
 
@@ -542,10 +568,11 @@ bw_status pso_split_wave(bw_ctx* ctx, PsoSplit& X, const z64* Uw, long long Wn, 
 // path (sigma = +1 for the sector s < 0, -1 for s > 0: the sector is the lowest p/2
 // eigenvectors V of sigma S), checks the PSO gap, and keeps the sector states U V;
 // the loop then runs on those p/2 columns.
-bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const bw_plane* plane,
+bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const PlaneX& PX,
                        int p, bool mx, const Opts& o, double* phases, double* min_gap,
                        cudaStream_t s, const HostOp* op = nullptr, int sign = -1,
                        double* pso_evals = nullptr, double* min_pso_gap = nullptr) {
+  const bw_plane* plane = &PX.flat;
   const int n = P.n, N = plane->N, Nt = plane->N_t;
   const bool spin = op != nullptr;
   const int pl = spin ? p / 2 : p;  // columns the loop runs on
@@ -594,7 +621,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
   bw::LargeArgs lg;
   std::memset(&lg, 0, sizeof(lg));
   lg.model = dev_model(P, dblob);
-  lg.plane = dev_plane(plane);
+  lg.plane = dev_plane(PX);
   lg.n = n;
   lg.p = p;
   lg.nval = nval;
@@ -700,17 +727,22 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const b
 // Shared driver of the three loop entry points.
 enum class LoopKind { Plain, Nested, Spin, Plaquette };
 
-bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_plane* plane,
+bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_plane* user_plane,
                    int p, bw_precision prec, const bw_opts* opts, const bw_c128* spin_op,
                    int sign, double cut, int first, int m, double* phases, double* min_gap,
                    double* nested_out, double* min_wgap, double* pso_evals, double* min_pso_gap,
-                   cudaStream_t s, double* chern_out = nullptr) {
+                   cudaStream_t s, double* chern_out = nullptr, const int32_t* sweep = nullptr,
+                   int N_s = 1) {
   if (!ctx) return BW_EINVAL;
   ctx->err.clear();
   // the PSO split runs for the spin-resolved loop and for the flux of a spin sector
   const bool spin = kind == LoopKind::Spin || (kind == LoopKind::Plaquette && spin_op != nullptr);
-  bw_status st = check_plane(ctx, plane, kind == LoopKind::Nested || kind == LoopKind::Plaquette);
+  bw_status st = check_plane(ctx, user_plane, kind == LoopKind::Nested || kind == LoopKind::Plaquette);
   if (st) return st;
+  PlaneX PX;
+  if ((st = stack_planes(ctx, user_plane, sweep, N_s, PX))) return st;
+  if (kind == LoopKind::Plaquette && PX.N_s > 1) return fail(ctx, BW_EINVAL, "plaquette flux takes one plane");
+  const bw_plane* plane = &PX.flat;
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
   if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
   HostPlan P;
@@ -758,9 +790,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   if (big) {
     begin_call(ctx, s);
     if (kind == LoopKind::Spin)
-      return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s, &op, sign,
+      return run_big_loop(ctx, P, blob, PX, p, prec == BW_MIXED, o, phases, min_gap, s, &op, sign,
                           pso_evals, min_pso_gap);
-    return run_big_loop(ctx, P, blob, plane, p, prec == BW_MIXED, o, phases, min_gap, s);
+    return run_big_loop(ctx, P, blob, PX, p, prec == BW_MIXED, o, phases, min_gap, s);
   }
   const size_t bU = al256(size_t(K) * n * p_eff * sizeof(z64));
   const size_t bGap = al256(size_t(K) * sizeof(double));
@@ -774,6 +806,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     q.p = p_eff;
     q.N = plane->N;
     q.N_t = plane->N_t;
+    q.N_s = PX.N_s;
     q.nested = 1;
     q.m = m;
     transport_only = bw::loops_transport_only(q);
@@ -822,7 +855,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   std::memset(&sa, 0, sizeof(sa));
   sa.model = dev_model(P, dblob);
   sa.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
-  sa.plane = dev_plane(plane);
+  sa.plane = dev_plane(PX);
   sa.f = nullptr;
   sa.K = K;
   sa.p = p;
@@ -853,6 +886,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     q.p = p_eff;
     q.N = plane->N;
     q.N_t = plane->N_t;
+    q.N_s = PX.N_s;
     q.unitarise = o.unitarise;
     q.nested = kind == LoopKind::Nested;
     q.m = m;
@@ -924,6 +958,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.p = p_eff;
   la.N = plane->N;
   la.N_t = plane->N_t;
+  la.N_s = PX.N_s;
   la.unitarise = o.unitarise;
   la.max_sweeps = o.max_sweeps;
   la.gap = gap;
@@ -1124,6 +1159,33 @@ bw_status bw_winding(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, 
   prof_start(ctx, s);
   BW_CUDA(bw::launch_winding(phases, N_t, p, sums, winding, s), "winding kernel");
   prof_mark(ctx, s, "winding");
+  end_call(ctx, s);
+  return BW_OK;
+}
+
+bw_status bw_z2_largest_gap(bw_ctx* ctx, const double* phases, int32_t N_t, int32_t p, int32_t* nu,
+                            int32_t* crossings, double* mid, double* width, void* stream) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  if (N_t < 2 || N_t % 2 || p < 1)
+    return fail(ctx, BW_EINVAL, "need an even N_t >= 2 and p >= 1 (N_t = %d, p = %d)", N_t, p);
+  if (!phases || !nu) return fail(ctx, BW_EINVAL, "phases or nu is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t h = size_t(N_t / 2);
+  const size_t need = (crossings ? 0 : al256(h * sizeof(int32_t))) +
+                      (mid ? 0 : al256((h + 1) * sizeof(double))) +
+                      (width ? 0 : al256((h + 1) * sizeof(double)));
+  begin_call(ctx, s);
+  if (need) {
+    bw_status st = reserve(ctx, need, s);
+    if (st) return st;
+    if (!crossings) crossings = reinterpret_cast<int32_t*>(carve(ctx, h * sizeof(int32_t)));
+    if (!mid) mid = reinterpret_cast<double*>(carve(ctx, (h + 1) * sizeof(double)));
+    if (!width) width = reinterpret_cast<double*>(carve(ctx, (h + 1) * sizeof(double)));
+  }
+  prof_start(ctx, s);
+  BW_CUDA(bw::launch_z2(phases, N_t, p, mid, width, crossings, nu, ctx->status, s), "z2 kernels");
+  prof_mark(ctx, s, "z2");
   end_call(ctx, s);
   return BW_OK;
 }
@@ -1339,6 +1401,49 @@ bw_status bw_plaquette_flux(bw_ctx* ctx, const bw_model* model, const bw_plane* 
                   static_cast<cudaStream_t>(stream), chern);
 }
 
+bw_status bw_wilson_loop_stack(bw_ctx* ctx, const bw_model* model, const bw_plane_stack* stack,
+                               int32_t p, bw_precision prec, const bw_opts* opts, double* phases,
+                               double* min_gap, void* stream) {
+  if (ctx && !stack) {
+    ctx->err.clear();
+    return fail(ctx, BW_EINVAL, "plane stack is NULL");
+  }
+  return run_loop(ctx, LoopKind::Plain, model, stack ? &stack->plane : nullptr, p, prec, opts, nullptr, 0,
+                  0.0, 0, 0, phases, min_gap, nullptr, nullptr, nullptr, nullptr,
+                  static_cast<cudaStream_t>(stream), nullptr, stack ? stack->sweep_dir : nullptr,
+                  stack ? stack->N_s : 1);
+}
+
+bw_status bw_nested_wilson_loop_stack(bw_ctx* ctx, const bw_model* model, const bw_plane_stack* stack,
+                                      int32_t p, double cut, int32_t first, int32_t m,
+                                      bw_precision prec, const bw_opts* opts, double* phases,
+                                      double* nested, double* min_wannier_gap, double* min_gap,
+                                      void* stream) {
+  if (ctx && !stack) {
+    ctx->err.clear();
+    return fail(ctx, BW_EINVAL, "plane stack is NULL");
+  }
+  return run_loop(ctx, LoopKind::Nested, model, stack ? &stack->plane : nullptr, p, prec, opts, nullptr, 0,
+                  cut, first, m, phases, min_gap, nested, min_wannier_gap, nullptr, nullptr,
+                  static_cast<cudaStream_t>(stream), nullptr, stack ? stack->sweep_dir : nullptr,
+                  stack ? stack->N_s : 1);
+}
+
+bw_status bw_spin_resolved_wilson_loop_stack(bw_ctx* ctx, const bw_model* model,
+                                             const bw_plane_stack* stack, int32_t p,
+                                             const bw_c128* spin_op, int32_t sign, bw_precision prec,
+                                             const bw_opts* opts, double* phases, double* pso_evals,
+                                             double* min_pso_gap, double* min_gap, void* stream) {
+  if (ctx && !stack) {
+    ctx->err.clear();
+    return fail(ctx, BW_EINVAL, "plane stack is NULL");
+  }
+  return run_loop(ctx, LoopKind::Spin, model, stack ? &stack->plane : nullptr, p, prec, opts, spin_op, sign,
+                  0.0, 0, 0, phases, min_gap, nullptr, nullptr, pso_evals, min_pso_gap,
+                  static_cast<cudaStream_t>(stream), nullptr, stack ? stack->sweep_dir : nullptr,
+                  stack ? stack->N_s : 1);
+}
+
 bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
                                        int32_t p, const bw_c128* spin_op, int32_t sign,
                                        bw_precision prec, const bw_opts* opts, double* phases,
@@ -1399,6 +1504,8 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
                       cudaStream_t s) {
   bw_status st = check_plane(ctx, plane, false);
   if (st) return st;
+  PlaneX PX;
+  if ((st = stack_planes(ctx, plane, nullptr, 1, PX))) return st;
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
   if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
   HostPlan P;
@@ -1441,7 +1548,7 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
   std::memset(&sa, 0, sizeof(sa));
   sa.model = dev_model(P, dblob);
   sa.row_ptr = reinterpret_cast<const int*>(dblob + P.o_rowptr);
-  sa.plane = dev_plane(plane);
+  sa.plane = dev_plane(PX);
   sa.K = K;
   sa.p = p;
   sa.mixed = prec == BW_MIXED;

@@ -148,23 +148,26 @@ k_states_tiny(StatesArgs a, int use_tab) {
   z64* oph = tabNt + (use_tab ? tT.B + tT.H : 0);          // nR
   int* lR = reinterpret_cast<int*>(oph + (use_tab ? nR : 0));
   int* tR = lR + (use_tab ? nR : 0);
+  int* sR = tR + (use_tab ? nR : 0);
   if (use_tab) {
     fill_tab(tabN, tabN + tN.B, N, tN);
     fill_tab(tabNt, tabNt + tT.B, Nt, tT);
     for (int r = tid; r < nR; r += bd) {
       const int* R = md.Rv + 3 * r;
       double x = 0.0;
-      int l = 0, t = 0;
+      int l = 0, t = 0, sw = 0;
       for (int d = 0; d < 3; ++d) {
         x += a.plane.origin[d] * double(R[d]);
         l += int(a.plane.loop_dir[d]) * R[d];
         t += int(a.plane.trans_dir[d]) * R[d];
+        sw += a.plane.sweep[d] * R[d];
       }
       double sn, cs;
       sincospi(2.0 * x, &sn, &cs);
       oph[r] = z64(cs, sn);
       lR[r] = l;
       tR[r] = t;
+      sR[r] = sw;
     }
     __syncthreads();
   }
@@ -174,7 +177,7 @@ k_states_tiny(StatesArgs a, int use_tab) {
   // Bloch phases of the distinct translations at this k-point
   if (use_tab) {
     for (int r = 0; r < nR; ++r) {
-      const int mN = pmod((long long)j * lR[r], N), mT = pmod((long long)i * tR[r], Nt);
+      const int mN = pmod((long long)j * lR[r], N), mT = pmod(plane_row_index(a.plane, i, tR[r], sR[r]), Nt);
       cache[r * bd + tid] = oph[r] * tab_at(tabN, tabN + tN.B, tN, mN) * tab_at(tabNt, tabNt + tT.B, tT, mT);
     }
   } else {
@@ -330,22 +333,25 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
   z64* oph = tabNt + tT.B + tT.H;
   int* lR = reinterpret_cast<int*>(oph + nR);
   int* tR = lR + nR;
+  int* sR = tR + nR;
   fill_tab(tabN, tabN + tN.B, N, tN);
   fill_tab(tabNt, tabNt + tT.B, Nt, tT);
   for (int r = tid; r < nR; r += blockDim.x) {
     const int* Rv = md.Rv + 3 * r;
     double x = 0.0;
-    int lq = 0, tq = 0;
+    int lq = 0, tq = 0, sq = 0;
     for (int dd = 0; dd < 3; ++dd) {
       x += a.plane.origin[dd] * double(Rv[dd]);
       lq += int(a.plane.loop_dir[dd]) * Rv[dd];
       tq += int(a.plane.trans_dir[dd]) * Rv[dd];
+      sq += a.plane.sweep[dd] * Rv[dd];
     }
     double sn, cs;
     sincospi(2.0 * x, &sn, &cs);
     oph[r] = z64(cs, sn);
     lR[r] = lq;
     tR[r] = tq;
+    sR[r] = sq;
   }
   __syncthreads();
   const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
   const long long k = active ? kraw : a.K - 1;  // idle groups recompute the last k-point
   const int i = int(k / N), j = int(k - (long long)i * N);
   for (int r = l; r < nR; r += 4) {
-    const int mN = pmod((long long)j * lR[r], N), mT = pmod((long long)i * tR[r], Nt);
+    const int mN = pmod((long long)j * lR[r], N), mT = pmod(plane_row_index(a.plane, i, tR[r], sR[r]), Nt);
     cache[r * KPB + kl] = oph[r] * tab_at(tabN, tabN + tN.B, tN, mN) * tab_at(tabNt, tabNt + tT.B, tT, mT);
   }
   __syncwarp();
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad(StatesArgs a) {
 size_t quad_df_smem(int nR, int N, int Nt) {
   const TabShape tN = tab_shape_split(N), tT = tab_shape_split(Nt);
   return (size_t(nR) * (QUAD_THREADS / 4) + tN.B + tN.H + tT.B + tT.H + nR) * sizeof(cdf) +
-         2 * size_t(nR) * sizeof(int);
+         3 * size_t(nR) * sizeof(int);
 }
 
 template <int PP>
@@ -450,22 +456,25 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad_df(StatesArgs a) {
   cdf* oph = tabNt + tT.B + tT.H;
   int* lR = reinterpret_cast<int*>(oph + nR);
   int* tR = lR + nR;
+  int* sR = tR + nR;
   fill_tab_df(tabN, tabN + tN.B, N, tN);
   fill_tab_df(tabNt, tabNt + tT.B, Nt, tT);
   for (int r = tid; r < nR; r += blockDim.x) {
     const int* Rv = md.Rv + 3 * r;
     double x = 0.0;
-    int lq = 0, tq = 0;
+    int lq = 0, tq = 0, sq = 0;
     for (int dd = 0; dd < 3; ++dd) {
       x += a.plane.origin[dd] * double(Rv[dd]);
       lq += int(a.plane.loop_dir[dd]) * Rv[dd];
       tq += int(a.plane.trans_dir[dd]) * Rv[dd];
+      sq += a.plane.sweep[dd] * Rv[dd];
     }
     double sn, cs;
     sincospi(2.0 * x, &sn, &cs);
     oph[r] = cdf_from(z64(cs, sn));
     lR[r] = lq;
     tR[r] = tq;
+    sR[r] = sq;
   }
   __syncthreads();
   const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(QUAD_THREADS) k_states_quad_df(StatesArgs a) {
   const long long k = active ? kraw : a.K - 1;  // idle groups recompute the last k-point
   const int i = int(k / N), j = int(k - (long long)i * N);
   for (int r = l; r < nR; r += 4) {
-    const int mN = pmod((long long)j * lR[r], N), mT = pmod((long long)i * tR[r], Nt);
+    const int mN = pmod((long long)j * lR[r], N), mT = pmod(plane_row_index(a.plane, i, tR[r], sR[r]), Nt);
     cache[r * KPB + kl] = oph[r] * tab_at_df(tabN, tabN + tN.B, tN, mN) *
                           tab_at_df(tabNt, tabNt + tT.B, tT, mT);
   }
@@ -566,7 +575,7 @@ cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, b
   const size_t tab = size_t(tN.B) + tN.H + tT.B + tT.H;
   const bool use_tab = integer_plane && tab <= 4096;
   size_t smem = size_t(a.model.n_R) * TINY_THREADS * sizeof(z64);
-  if (use_tab) smem += (tab + a.model.n_R) * sizeof(z64) + 2 * a.model.n_R * sizeof(int);
+  if (use_tab) smem += (tab + a.model.n_R) * sizeof(z64) + 3 * a.model.n_R * sizeof(int);
   *handled = true;
   if (a.want_df)  // the caller checked states_df_eligible()
     return quad_df_launch<2>(a, quad_df_smem(a.model.n_R, N, Nt), s);
@@ -576,7 +585,7 @@ cudaError_t launch_states_tiny(const StatesArgs& a, int p_out, cudaStream_t s, b
   // total work.
   if (n == 4 && a.op.nnz == 0 && use_tab && a.row_ptr && a.K <= 8192) {
     const size_t qs = size_t(a.model.n_R) * (QUAD_THREADS / 4) * sizeof(z64) +
-                      (tab + a.model.n_R) * sizeof(z64) + 2 * a.model.n_R * sizeof(int);
+                      (tab + a.model.n_R) * sizeof(z64) + 3 * a.model.n_R * sizeof(int);
     switch (p) {
       case 1: return quad_launch<1>(a, qs, s);
       case 2: return quad_launch<2>(a, qs, s);

@@ -319,6 +319,32 @@ class Plane:
 
 
 @dataclass
+class PlaneStack:
+    """N_s parallel planes (Sec. III: the nested loop against k_z; Sec. II B: weak and
+    strong Z2 from the planes k_a = 0 and 1/2): plane s is ``plane`` with its origin
+    moved by (s / N_s) sweep_dir, sweep_dir an integer reciprocal vector."""
+    plane: Plane
+    sweep_dir: tuple = (0, 0, 1)
+    N_s: int = 2
+
+    @property
+    def N(self) -> int:
+        return self.plane.N
+
+    @property
+    def N_t(self) -> int:
+        return self.plane.N_t
+
+    def planes(self) -> list:
+        pl = self.plane
+        return [Plane(pl.N, pl.N_t,
+                      origin=tuple(float(o) + (s / self.N_s) * float(d)
+                                   for o, d in zip(pl.origin, self.sweep_dir)),
+                      loop_dir=pl.loop_dir, trans_dir=pl.trans_dir)
+                for s in range(self.N_s)]
+
+
+@dataclass
 class Workload:
     name: str
     model: HoppingList

@@ -545,3 +545,155 @@ def test_mixed_four_band_launch_shapes(lib, ctx):
     ph, nest, _, _ = lib.nested_wilson_loop(model, plane, 2, m=1, precision="mixed", ctx=ctx)
     assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= DF_TOL
     assert circ_err_rows(nest.cpu().numpy(), ref_n) <= DF_TOL
+
+
+# ---------------------------------------------------------------- Z2 from WCC connectivity
+def _z2_phase_tables():
+    """Seeded phase tables: oracle spectra of the paper's models and drawn spectra
+    with exact ties (Kramers-degenerate rows, repeated values), +-pi, one band, many
+    bands, and enough rows that the row and step kernels span several CTAs."""
+    rng = np.random.default_rng(17)
+    out = {}
+    out["eq7"] = oracle.wilson_loop(I.bhz_eq7(1.5), P(16, 32), 2)[0]
+    out["eq7_trivial"] = oracle.wilson_loop(I.bhz_eq7(3.5), P(16, 32), 2)[0]
+    out["vacancy_L4"] = oracle.wilson_loop(I.config_vacancy(4, 0.0).model, P(10, 16), 30)[0]
+    t = np.arange(64) / 64
+    out["switch_pair"] = np.sort(np.stack([2 * np.pi * t, -2 * np.pi * t], 1), axis=1)
+    out["degenerate"] = np.sort(np.repeat(rng.uniform(-np.pi, np.pi, (40, 3)), 2, axis=1), axis=1)
+    edge = np.sort(rng.uniform(-np.pi, np.pi, (10, 5)), axis=1)
+    edge[:, 0], edge[:, -1] = -np.pi, np.pi
+    out["plus_minus_pi"] = edge
+    out["one_band"] = rng.uniform(-np.pi, np.pi, (18, 1))
+    out["many"] = np.sort(rng.uniform(-np.pi, np.pi, (300, 97)), axis=1)
+    out["quantised"] = np.sort(rng.integers(-8, 9, (50, 6)) * (np.pi / 8), axis=1)
+    return out
+
+
+def test_z2_largest_gap_parity(lib, ctx):
+    """Same phases in, bit-identical midpoints, widths, crossings and index out."""
+    torch = _torch()
+    for name, ph in _z2_phase_tables().items():
+        nu_r, c_r, mid_r, w_r = oracle.z2_largest_gap(ph)
+        nu, c, mid, w = lib.z2_largest_gap(torch.tensor(np.ascontiguousarray(ph), device="cuda"),
+                                           ctx=ctx, want_detail=True)
+        assert nu.item() == nu_r, name
+        assert np.array_equal(c.cpu().numpy(), c_r), name
+        assert np.array_equal(mid.cpu().numpy(), mid_r), name
+        assert np.array_equal(w.cpu().numpy(), w_r), name
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_z2_from_gpu_loops(lib, ctx, precision):
+    """The paper's statements end to end on the GPU: Eq. 7 nu = 1 (Sec. II B), nu = 0
+    past the band inversion, and nu = 1 for supercells with vacancies (Sec. II C,
+    p = 48 and p = 62); each equal to the oracle's index of the oracle's spectrum."""
+    cases = [(I.bhz_eq7(1.5), P(24, 32), 2, 1), (I.bhz_eq7(3.5), P(24, 32), 2, 0),
+             (I.config_vacancy(5, 0.0).model, P(12, 16), 48, 1),
+             (I.config_vacancy(6, 1.0).model, P(12, 16), 62, 1)]
+    for model, plane, p, expect in cases:
+        ph, _ = lib.wilson_loop(model, plane, p, precision=precision, ctx=ctx)
+        nu = lib.z2_largest_gap(ph, ctx=ctx).item()
+        ref = oracle.z2_largest_gap(oracle.wilson_loop(model, plane, p)[0])[0]
+        assert nu == ref == expect, model.name
+
+
+def test_z2_rejects_bad_input(lib, ctx):
+    """An unsorted row gives nu = -1 and BW_EINVAL from the device status (with the row);
+    an odd N_t is refused at the call."""
+    torch = _torch()
+    ph = np.sort(np.random.default_rng(3).uniform(-np.pi, np.pi, (8, 4)), axis=1)
+    bad = ph.copy()
+    bad[3] = bad[3][::-1]
+    nu = lib.z2_largest_gap(torch.tensor(bad, device="cuda"), ctx=ctx, check=False)
+    assert nu.item() == -1
+    with pytest.raises(lib.BWError) as e:
+        ctx.status()
+    assert e.value.code == 1 and e.value.k_index == 3
+    with pytest.raises(lib.BWError):
+        lib.z2_largest_gap(torch.tensor(ph[:7].copy(), device="cuda"), ctx=ctx)
+
+
+# ---------------------------------------------------------------- stacks of planes
+def _stack_ref(fn, stack, *args, **kw):
+    return [fn(*args[:1], pl, *args[1:], **kw) for pl in stack.planes()]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plane_stack_parity(lib, ctx, precision):
+    """Every plane of a stack against the oracle on that plane: Eq. 9 over k_z (3D, the
+    tabulated four-band kernels), a many-band model (n = 40, tridiagonal path), and one
+    plane (the single-plane call, bit for bit)."""
+    tol = TOL[precision]
+    model = I.choti_eq9(1.0)
+    st = I.PlaneStack(P(12, 10, origin=(0.0, 0.05, 0.0)), (0, 0, 1), 5)
+    ph, gap = lib.wilson_loop(model, st, 2, precision=precision, ctx=ctx)
+    assert ph.shape == (5, 10, 2) and gap.shape == (5, 10)
+    for s, pl in enumerate(st.planes()):
+        rph, rgap = oracle.wilson_loop(model, pl, 2)
+        assert circ_err_rows(ph[s].cpu().numpy(), rph) <= tol, s
+        assert np.abs(gap[s].cpu().numpy() - rgap).max() <= 1e-9 * max(1.0, rgap.max())
+    big = I.manyband(20)
+    st = I.PlaneStack(P(6, 4), (0, 0, 1), 3)        # a 2D model: identical planes
+    ph, _ = lib.wilson_loop(big, st, 10, precision=precision, ctx=ctx)
+    rph, _ = oracle.wilson_loop(big, P(6, 4), 10)
+    for s in range(3):
+        assert circ_err_rows(ph[s].cpu().numpy(), rph) <= tol
+        assert np.array_equal(ph[s].cpu().numpy(), ph[0].cpu().numpy())
+    one = I.PlaneStack(P(12, 10, origin=(0.0, 0.0, 0.25)), (0, 0, 1), 1)
+    a, _ = lib.wilson_loop(model, one, 2, precision=precision, ctx=ctx)
+    b, _ = lib.wilson_loop(model, one.plane, 2, precision=precision, ctx=ctx)
+    assert np.array_equal(a[0].cpu().numpy(), b.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nested_stack_over_kz(lib, ctx, precision):
+    """Sec. III, Fig. 4(b): the nested spectrum of Eq. 9 (Delta0 = 1) over a k_z stack,
+    every plane against the oracle; its phase winds once over k_z.  The 12 x 12 x 12
+    stack runs the mixed path's fused kernel (one cooperative launch for all planes)."""
+    model = I.choti_eq9(1.0)
+    st = I.PlaneStack(P(12, 12), (0, 0, 1), 12)
+    ph, nest, wg, gap = lib.nested_wilson_loop(model, st, 2, m=1, precision=precision, ctx=ctx)
+    assert nest.shape == (12, 12, 1) and wg.shape == (12, 12)
+    tol = TOL[precision]
+    for s, pl in enumerate(st.planes()):
+        rph, rnest, _, _ = oracle.nested_wilson_loop(model, pl, 2, m=1)
+        assert circ_err_rows(ph[s].cpu().numpy(), rph) <= tol, s
+        d = np.abs(np.angle(np.exp(1j * (nest[s].cpu().numpy() - rnest))))
+        assert d.max() <= 10 * tol, s
+    curve = nest[:, 0, :].cpu().numpy()
+    assert abs(abs(oracle.winding(curve)) - 1) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spin_resolved_stack(lib, ctx, precision):
+    """Spin-resolved loops of Eq. 9 on a k_z stack (s = s3 (x) t3) against the oracle."""
+    model = I.choti_eq9(1.0)
+    S = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+    st = I.PlaneStack(P(10, 8), (0, 0, 1), 4)
+    ph, pso, pg, _ = lib.spin_resolved_wilson_loop(model, st, 2, S, -1, precision=precision, ctx=ctx)
+    assert ph.shape == (4, 8, 1) and pso.shape == (4, 8, 10, 2)
+    for s, pl in enumerate(st.planes()):
+        rph, rpso, rpg, _ = oracle.spin_resolved_wilson_loop(model, pl, 2, S, -1)
+        assert circ_err_rows(ph[s].cpu().numpy(), rph) <= TOL[precision], s
+        assert np.abs(np.sort(pso[s].cpu().numpy(), -1) - np.sort(rpso, -1)).max() <= 1e-9
+
+
+def test_z2_weak_strong_from_planes(lib, ctx):
+    """Sec. II B / Sec. III: Eq. 9 with Delta0 = 0 is a strong topological insulator.
+    The stacks k_z in {0, 1/2} and k_x in {0, 1/2} give nu = (1, 0) each on the GPU,
+    so nu0 = 1 and the weak indices vanish (the oracle agrees plane by plane)."""
+    model = I.choti_eq9(0.0)
+    stacks = [I.PlaneStack(P(24, 16), (0, 0, 1), 2),
+              I.PlaneStack(P(24, 16, loop_dir=(0, 1, 0), trans_dir=(0, 0, 1)), (1, 0, 0), 2)]
+    for st in stacks:
+        ph, _ = lib.wilson_loop(model, st, 2, ctx=ctx)
+        z = [lib.z2_largest_gap(ph[s].contiguous(), ctx=ctx).item() for s in range(2)]
+        ref = [oracle.z2_largest_gap(oracle.wilson_loop(model, pl, 2)[0])[0] for pl in st.planes()]
+        assert z == ref == [1, 0]
+
+
+def test_plane_stack_rejections(lib, ctx):
+    """A stack with N_s < 1 is refused at the call."""
+    st = I.PlaneStack(P(6, 6), (0, 0, 1), 0)
+    with pytest.raises(lib.BWError):
+        lib.wilson_loop(I.choti_eq9(1.0), st, 2, ctx=ctx)
