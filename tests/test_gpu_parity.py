@@ -697,3 +697,21 @@ def test_plane_stack_rejections(lib, ctx):
     st = I.PlaneStack(P(6, 6), (0, 0, 1), 0)
     with pytest.raises(lib.BWError):
         lib.wilson_loop(I.choti_eq9(1.0), st, 2, ctx=ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vacancy_supercell_parity(lib, ctx, precision):
+    """Sec. II C: an Eq. 7 supercell with the cells within r = 1 of the origin removed
+    (6 x 6 cells less 5, n = 124, p = 62): Wannier centres and the s3 (x) t3 sector's
+    centres against the oracle; the sector winds -1."""
+    wl = I.config_vacancy(6, 1.0)
+    plane = P(10, 8)
+    ph, gap = lib.wilson_loop(wl.model, plane, wl.p, precision=precision, ctx=ctx)
+    rph, rgap = oracle.wilson_loop(wl.model, plane, wl.p)
+    assert circ_err_rows(ph.cpu().numpy(), rph) <= TOL[precision]
+    assert np.abs(gap.cpu().numpy() - rgap).max() <= 1e-9
+    dn, _, pg, _ = lib.spin_resolved_wilson_loop(wl.model, plane, wl.p, wl.spin_op, -1,
+                                                 precision=precision, ctx=ctx, want_pso=False)
+    rdn, _, _, _ = oracle.spin_resolved_wilson_loop(wl.model, plane, wl.p, wl.spin_op, -1)
+    assert circ_err_rows(dn.cpu().numpy(), rdn) <= TOL[precision]
+    assert abs(lib.winding(dn, ctx=ctx).item() + 1) < 1e-6
