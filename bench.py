@@ -276,18 +276,18 @@ def time_e2e(lib, ctx, wl, precision, steps, warmup, dev):
     """Public API on host inputs: upload of the hopping list inside the call, results
     copied back to pinned host memory, wall clock per step."""
     import torch
-    out = (torch.empty((wl.plane.N_t, wl.p), dtype=torch.float64, device=dev),
-           torch.empty((wl.plane.N, wl.nested_m), dtype=torch.float64, device=dev),
-           torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev),
-           torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev))
-    host = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in out]
+    # the four outputs are views of one device buffer, read back by one copy
+    shapes = ((wl.plane.N_t, wl.p), (wl.plane.N, wl.nested_m), (wl.plane.N_t,), (wl.plane.N_t,))
+    sizes = [int(np.prod(sh)) for sh in shapes]
+    dbuf = torch.empty(sum(sizes), dtype=torch.float64, device=dev)
+    out = tuple(v.view(sh) for v, sh in zip(torch.split(dbuf, sizes), shapes))
+    host = torch.empty(sum(sizes), dtype=torch.float64, pin_memory=True)
     s = torch.cuda.current_stream(dev)
 
     def step():
         lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m, precision=precision,
                                ctx=ctx, check=False, out=out)
-        for h, o in zip(host, out):
-            h.copy_(o, non_blocking=True)
+        host.copy_(dbuf, non_blocking=True)
         s.synchronize()
 
     for _ in range(max(warmup, 3)):
@@ -304,7 +304,7 @@ def time_e2e(lib, ctx, wl, precision, steps, warmup, dev):
     ctx.status()
     m = wl.model
     h2d = int(m.R.nbytes + m.i.nbytes + m.j.nbytes + m.t.nbytes)
-    d2h = int(sum(h.numel() * h.element_size() for h in host))
+    d2h = int(host.numel() * host.element_size())
     return sum(lat), lat, h2d, d2h
 
 

@@ -215,6 +215,33 @@ class _HostModel:
         self.t = np.ascontiguousarray(model.t, dtype=np.complex128)
         self.s = bw_model(int(model.n), int(self.t.shape[0]), self.R.ctypes.data,
                           self.i.ctypes.data, self.j.ctypes.data, self.t.ctypes.data)
+        # the struct points into the caller's own arrays (no copy was made), so a later
+        # call with the same arrays may reuse it; in-place edits stay visible
+        self.shared = all(isinstance(b, np.ndarray) and a.ctypes.data == b.ctypes.data
+                          for a, b in ((self.R, model.R), (self.i, model.i), (self.j, model.j),
+                                       (self.t, model.t)))
+
+
+_model_cache: dict = {}
+
+
+def _host_model(model) -> _HostModel:
+    """The marshalled model, reused while the model object holds the same arrays."""
+    key = (id(model), id(model.R), id(model.i), id(model.j), id(model.t), int(model.n))
+    hm = _model_cache.get(key)
+    if hm is not None and hm.owner() is model:
+        return hm
+    hm = _HostModel(model)
+    if hm.shared:
+        import weakref
+        try:
+            hm.owner = weakref.ref(model)
+        except TypeError:
+            return hm
+        if len(_model_cache) > 64:
+            _model_cache.clear()
+        _model_cache[key] = hm
+    return hm
 
 
 def _plane(plane) -> bw_plane:
@@ -259,7 +286,7 @@ def build_hk(model, f, complex64: bool = False, ctx: Context | None = None, chec
     if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.dim() == 2
             and f.shape[1] == 3):
         raise BWError(1, "f must be a contiguous CUDA float64 tensor of shape (K, 3)")
-    hm = _HostModel(model)
+    hm = _host_model(model)
     K = f.shape[0]
     H = _empty((K, model.n, model.n), torch.complex64 if complex64 else torch.complex128, f.device)
     ctx.check(ctx.lib.bw_build_hk(ctx.h, C.byref(hm.s), _ptr(f), K, int(complex64), _ptr(H),
@@ -298,7 +325,7 @@ def wilson_loop(model, plane, p: int, precision: str = "fp64", ctx: Context | No
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
@@ -322,7 +349,7 @@ def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0
     ctx = ctx or context()
     dev = _cuda_device(ctx)
     m = p // 2 if m is None else int(m)
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
@@ -348,7 +375,7 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     S = np.ascontiguousarray(spin_op, dtype=np.complex128)
@@ -399,7 +426,7 @@ def plaquette_flux(model, plane, p: int, spin_op=None, sign: int = -1, precision
     import torch
     ctx = ctx or context()
     dev = _cuda_device(ctx)
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl = _plane(plane)
     o = _opts(**opts)
     S = None
@@ -469,7 +496,7 @@ def wilson_loop_noalloc(model, plane, p: int, precision: str = "fp64", out=None,
     omitted they are allocated here, by the caller side, before the call."""
     import torch
     lib = load()
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl = _plane(plane)
     o = _opts(**opts)
     if out is None:
@@ -488,7 +515,7 @@ def wilson_loop_workspace(model, plane, p: int, precision: str = "fp64",
                           ctx: Context | None = None, **opts) -> int:
     """Device scratch bytes ``wilson_loop`` reserves for this problem on ``ctx``."""
     ctx = ctx or context()
-    hm = _HostModel(model)
+    hm = _host_model(model)
     pl = _plane(plane)
     o = _opts(**opts)
     nb = C.c_size_t(0)
@@ -527,7 +554,7 @@ class Server:
             pass
 
     def submit(self, model, plane, p: int, precision: str = "fp64", **opts) -> int:
-        hm = _HostModel(model)
+        hm = _host_model(model)
         pl = _plane(plane)
         o = _opts(**opts)
         ph = np.empty((plane.N_t, p), np.float64)

@@ -63,3 +63,22 @@ def test_no_device_fails_loudly(libpath):
     with pytest.raises(_lib.BWError) as e:
         _lib.Context(0)
     assert e.value.status == "ECUDA"
+
+
+def test_model_marshalling_cache():
+    """The binding reuses the marshalled hopping list only while the model object holds
+    the same arrays: reassigned arrays are marshalled again, in-place edits stay
+    visible (the struct points at the caller's memory), copies are never cached."""
+    import numpy as np
+    from paper_2312_13051_gb300 import _lib, inputs as I
+    m = I.bbh(0.5, 0.5)
+    a = _lib._host_model(m)
+    assert a.shared and _lib._host_model(m) is a and a.s.t == m.t.ctypes.data
+    m.t[0] = 7.0
+    assert _lib._host_model(m) is a
+    m.t = m.t * 2
+    b = _lib._host_model(m)
+    assert b is not a and b.s.t == m.t.ctypes.data
+    m.i = m.i.astype(np.int64)                 # needs a copy: marshalled every call
+    c = _lib._host_model(m)
+    assert not c.shared and _lib._host_model(m) is not c
