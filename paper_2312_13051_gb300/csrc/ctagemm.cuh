@@ -1,7 +1,8 @@
-// CTA-level building blocks of the large-n refinement: a tiled complex GEMM (plain
-// FP32, or with compensated sums for FP64-grade results) and the application of a
-// sequence of Householder reflectors to a column panel held in shared memory.  Both
-// keep operand reuse in shared memory instead of L2.
+// CTA-level building blocks of the large-n solver: a tiled complex GEMM (plain FP32 or
+// FP64, or with compensated sums for FP64-grade results) and the application of a
+// sequence of Householder reflectors, one at a time on column panels in shared memory
+// or in blocks (compact WY form) through that GEMM.  Both keep operand reuse in
+// shared memory instead of L2.
 #pragma once
 
 #include "common.cuh"
@@ -59,8 +60,19 @@ struct GemmPlain {  // C = A B in FP32
   using TA = c32;
   using TB = c32;
   using Acc = c32;
+  static constexpr bool kPrefetch = true;
   static __device__ __forceinline__ TA zero_a() { return c32(0.f, 0.f); }
   static __device__ __forceinline__ Acc zero() { return c32(0.f, 0.f); }
+  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
+};
+template <typename T>
+struct GemmPlainT {  // C = A B in the precision of T
+  using TA = cx<T>;
+  using TB = cx<T>;
+  using Acc = cx<T>;
+  static constexpr bool kPrefetch = true;
+  static __device__ __forceinline__ TA zero_a() { return TA(T(0), T(0)); }
+  static __device__ __forceinline__ Acc zero() { return Acc(T(0), T(0)); }
   static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
 };
 struct SplitC {  // an FP64 value as the float pair hi + lo
@@ -70,6 +82,7 @@ struct GemmSplitComp {  // C = A B, A an FP64 matrix as float pairs, compensated
   using TA = SplitC;
   using TB = c32;
   using Acc = CDF;
+  static constexpr bool kPrefetch = false;  // compute-bound; its accumulators fill the registers
   static __device__ __forceinline__ TA zero_a() { return SplitC{c32(0.f, 0.f), c32(0.f, 0.f)}; }
   static __device__ __forceinline__ Acc zero() { return CDF(); }
   static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { c.add_prod(a.hi, a.lo, b); }
@@ -78,6 +91,7 @@ struct GemmGramComp {  // C = A^dag B (A passed unconjugated), compensated sums
   using TA = c32;
   using TB = c32;
   using Acc = CDF;
+  static constexpr bool kPrefetch = false;
   static __device__ __forceinline__ TA zero_a() { return c32(0.f, 0.f); }
   static __device__ __forceinline__ Acc zero() { return CDF(); }
   static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { c.add_cprod(a, b); }
@@ -116,9 +130,17 @@ __device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned c
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = Pol::zero();
-      for (int k0 = 0; k0 < K; k0 += CG_K) {
-        for (int e = tid; e < CG_K * CG_TILE; e += 256) {
-          int kk, mm;
+      // each thread moves PER elements of each operand per k-step; with Pol::kPrefetch
+      // the next step's elements are loaded into registers before this step's products,
+      // so that their global-memory latency overlaps the arithmetic
+      constexpr int PER = CG_K * CG_TILE / 256;
+      TA ra[PER];
+      TB rb[PER];
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int s = 0; s < PER; ++s) {
+          const int e = tid + 256 * s;
+          int kk, mm, cc;
           if (A_K_CONTIG) {
             mm = e / CG_K;
             kk = e - mm * CG_K;
@@ -126,11 +148,7 @@ __device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned c
             kk = e / CG_TILE;
             mm = e - kk * CG_TILE;
           }
-          const int gm = m0 + mm, gk = k0 + kk;
-          As[kk][mm] = (gm < M && gk < K) ? la(gm, gk) : Pol::zero_a();
-        }
-        for (int e = tid; e < CG_K * CG_TILE; e += 256) {
-          int kk, cc;
+          ra[s] = (m0 + mm < M && k0 + kk < K) ? la(m0 + mm, k0 + kk) : Pol::zero_a();
           if (B_C_CONTIG) {
             kk = e / CG_TILE;
             cc = e - kk * CG_TILE;
@@ -138,10 +156,38 @@ __device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned c
             cc = e / CG_K;
             kk = e - cc * CG_K;
           }
-          const int gc = c0 + cc, gk = k0 + kk;
-          Bs[kk][cc] = (gc < Ncol && gk < K) ? lb(gk, gc) : c32(0.f, 0.f);
+          rb[s] = (c0 + cc < Ncol && k0 + kk < K) ? lb(k0 + kk, c0 + cc) : TB(0, 0);
         }
+      };
+      auto stage = [&]() {
+#pragma unroll
+        for (int s = 0; s < PER; ++s) {
+          const int e = tid + 256 * s;
+          int kk, mm, cc;
+          if (A_K_CONTIG) {
+            mm = e / CG_K;
+            kk = e - mm * CG_K;
+          } else {
+            kk = e / CG_TILE;
+            mm = e - kk * CG_TILE;
+          }
+          As[kk][mm] = ra[s];
+          if (B_C_CONTIG) {
+            kk = e / CG_TILE;
+            cc = e - kk * CG_TILE;
+          } else {
+            cc = e / CG_K;
+            kk = e - cc * CG_K;
+          }
+          Bs[kk][cc] = rb[s];
+        }
+      };
+      if (Pol::kPrefetch) fetch(0);
+      for (int k0 = 0; k0 < K; k0 += CG_K) {
+        if (!Pol::kPrefetch) fetch(k0);
+        stage();
         __syncthreads();
+        if (Pol::kPrefetch && k0 + CG_K < K) fetch(k0 + CG_K);
 #pragma unroll 2
         for (int kk = 0; kk < CG_K; ++kk) {
           TA av[4];
@@ -175,8 +221,10 @@ __device__ void cta_cgemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned 
 // Applies the reflectors P_c = I - 2 u_c u_c^dag, c = 0 .. n-3 (u_c in column c of
 // A below the diagonal, rows c+1..n-1), to X (n x ncol, leading dimension ldx, in
 // global memory): X <- P_{n-3} ... P_0 X (forward) or X <- P_0 ... P_{n-3} X
-// (reverse).  X is processed in panels of PW columns held in shared memory; each
-// reflector is read once per panel.  sm: reflect_smem<TX>(n, PW) bytes.
+// (reverse), one reflector at a time.  X is processed in panels of PW columns held in
+// shared memory; each reflector is read once per panel.  The FP64 back-transform
+// uses this form: it does two thirds of the flops of the blocked form below, and the
+// FP64 pipe, not latency, bounds it.  sm: reflect_smem<TX>(n, PW) bytes.
 template <class TX>
 __host__ __device__ inline size_t reflect_smem(int n, int PW) {
   return (size_t(n) * PW + n + 8 * size_t(PW)) * sizeof(cx<TX>);
@@ -247,6 +295,106 @@ __device__ void cta_reflect(const cx<TA>* A, int n, cx<TX>* X, int ncol, long lo
     case 4: cta_reflect_pw<4>(A, n, X, ncol, ldx, reverse, sm); break;
     case 2: cta_reflect_pw<2>(A, n, X, ncol, ldx, reverse, sm); break;
     default: cta_reflect_pw<1>(A, n, X, ncol, ldx, reverse, sm); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Applies the reflectors P_c = I - 2 u_c u_c^dag, c = 0 .. n-3 (u_c in column c of A
+// below the diagonal, rows c+1..n-1, unit norm) to X (n x ncol, leading dimension
+// ldx, in global memory), in blocks of RW_NB (compact WY form, Schreiber
+// and Van Loan, "A storage-efficient WY representation for products of Householder
+// transformations", SIAM J. Sci. Stat. Comput. 10 (1989)): the product of the
+// reflectors b .. b+nb-1,
+//   P_b P_{b+1} ... P_{b+nb-1} = I - V T V^dag,
+// V = [u_b ... u_{b+nb-1}] (n x nb, u_c zero above row c+1), T upper triangular with
+// T_ii = 2 and T[0:i, i] = -2 T[0:i, 0:i] (V^dag V)[0:i, i].  Reverse (X <- P_0 ...
+// P_{n-3} X) runs the blocks from last to first with X <- X - V (T (V^dag X)); forward
+// (X <- P_{n-3} ... P_0 X, the adjoint product) runs them first to last with T^dag.
+// Each block builds T once (a CTA GEMM and a triangular recurrence), then per chunk
+// of RW_CW columns of X two CTA GEMMs and a triangular product: a few barriers per
+// block instead of four per reflector.  Requires blockDim.x == 256.
+// ---------------------------------------------------------------------------
+constexpr int RW_NB = 32, RW_CW = 64;
+
+template <typename T>
+__host__ __device__ inline size_t reflect_wy_smem() {
+  return (size_t(RW_NB) * RW_NB + size_t(RW_NB) * RW_CW) * sizeof(cx<T>) + cg_smem<GemmPlainT<T>>();
+}
+
+template <typename T>
+__device__ void cta_reflect_wy(const cx<T>* A, int n, cx<T>* X, int ncol, long long ldx, bool reverse,
+                               unsigned char* sm) {
+  using C = cx<T>;
+  const int tid = threadIdx.x, lane = tid & 31;
+  C* Tm = reinterpret_cast<C*>(sm);                 // RW_NB x RW_NB: V^dag V, then T
+  C* W = Tm + RW_NB * RW_NB;                        // RW_NB x RW_CW
+  unsigned char* gsm = reinterpret_cast<unsigned char*>(W + RW_NB * RW_CW);
+  const int nrefl = n - 2;
+  if (nrefl <= 0) return;
+  const int nblk = (nrefl + RW_NB - 1) / RW_NB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = reverse ? nblk - 1 - bi : bi;
+    const int b0 = blk * RW_NB, bs = min(RW_NB, nrefl - b0);
+    const int r0 = b0 + 1, rows = n - r0;            // rows where the block's vectors live
+    // V[r][i] = u_{b0+i}[r] (zero for r <= b0 + i)
+    auto v = [&](int r, int i) -> C {
+      return r > b0 + i ? A[(long long)r * n + b0 + i] : C(T(0), T(0));
+    };
+    // Gram matrix V^dag V
+    cta_gemm<GemmPlainT<T>, false, true>(
+        bs, bs, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+        [&](int q, int i) { return v(r0 + q, i); },
+        [&](int i, int j, const C& g) { Tm[i * RW_NB + j] = g; }, gsm);
+    __syncthreads();
+    // T in place (one warp): column i from the columns before it
+    if (tid < 32) {
+      for (int i = 0; i < bs; ++i) {
+        C t(T(0), T(0));
+        if (lane < i)
+          for (int k = lane; k < i; ++k) cfma(t, Tm[lane * RW_NB + k], Tm[k * RW_NB + i]);
+        __syncwarp();
+        if (lane < i) Tm[lane * RW_NB + i] = T(-2) * t;
+        if (lane == 0) Tm[i * RW_NB + i] = C(T(2), T(0));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < ncol; c0 += RW_CW) {
+      const int cw = min(RW_CW, ncol - c0);
+      // W = V^dag X[:, c0 : c0 + cw]
+      cta_gemm<GemmPlainT<T>, false, true>(
+          bs, cw, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+          [&](int q, int c) { return X[(long long)(r0 + q) * ldx + c0 + c]; },
+          [&](int i, int c, const C& w) { W[i * RW_CW + c] = w; }, gsm);
+      __syncthreads();
+      // W <- T W (reverse) or T^dag W (forward), in place, one thread per column
+      for (int c = tid; c < cw; c += blockDim.x) {
+        if (reverse) {
+          for (int i = 0; i < bs; ++i) {
+            C acc(T(0), T(0));
+            for (int k = i; k < bs; ++k) cfma(acc, Tm[i * RW_NB + k], W[k * RW_CW + c]);
+            W[i * RW_CW + c] = acc;
+          }
+        } else {
+          for (int i = bs - 1; i >= 0; --i) {
+            C acc(T(0), T(0));
+            for (int k = 0; k <= i; ++k) cfma(acc, conj(Tm[k * RW_NB + i]), W[k * RW_CW + c]);
+            W[i * RW_CW + c] = acc;
+          }
+        }
+      }
+      __syncthreads();
+      // X[:, chunk] <- X[:, chunk] - V W (rows r0 .. n-1)
+      cta_gemm<GemmPlainT<T>, true, true>(
+          rows, cw, bs, [&](int q, int i) { return v(r0 + q, i); },
+          [&](int i, int c) { return W[i * RW_CW + c]; },
+          [&](int q, int c, const C& y) {
+            C& x = X[(long long)(r0 + q) * ldx + c0 + c];
+            x = x - y;
+          },
+          gsm);
+      __syncthreads();
+    }
   }
 }
 

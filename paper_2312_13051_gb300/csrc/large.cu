@@ -14,6 +14,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ctagemm.cuh"
 #include "df32.cuh"
@@ -711,11 +712,14 @@ __global__ void k_lg_invit_orth(LargeArgs a) {
 
 // ---------------------------------------------------------------------------
 // Stage 5: back-transform x = Q D z for the first ncol eigenvectors, Q = P_0 ... P_{n-3}:
-// X = D Z, then X <- P_c X for c = n-3 down to 0 (P_c = I - 2 u_c u_c^dagger).
+// X = D Z, then X <- P_c X for c = n-3 down to 0 (P_c = I - 2 u_c u_c^dagger): one
+// reflector at a time in FP64, in blocks of 32 reflectors (compact WY form) in FP32.
 // Output X[r][col] with leading dimension ncol, precision To.
 // ---------------------------------------------------------------------------
 template <typename T, typename To>
-__global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_stride, int ncol, int pw) {
+__global__ void __launch_bounds__(256, 2) k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_stride,
+                                                             int ncol, int pw) {
+  static_assert(std::is_same<T, To>::value, "the back-transform keeps the solver's precision");
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
@@ -731,7 +735,10 @@ __global__ void k_lg_backtransform(LargeArgs a, cx<To>* out, long long out_strid
       }
     }
     __syncthreads();
-    cta_reflect<T, To>(A, n, X, ncol, ncol, true, smem, pw);
+    if constexpr (std::is_same<T, double>::value)
+      cta_reflect<T, To>(A, n, X, ncol, ncol, true, smem, pw);   // FP64-pipe bound: fewest flops
+    else
+      cta_reflect_wy<T>(A, n, X, ncol, ncol, true, smem);        // latency bound: blocked
   }
 }
 
@@ -763,14 +770,16 @@ __host__ __device__ inline size_t refine_work_offset(int p) {
 //   and p-th FP32 vectors.  The off-diagonal part of Q^dag H Q is of the order of
 //   the FP32 error; its projection on the complement enters at second order.
 // ---------------------------------------------------------------------------
-__global__ void k_lg_refine(LargeArgs a, int pw) {
+// Two CTAs per SM: the compensated GEMM tiles hold 64 accumulator registers per
+// thread, and without the bound the kernel takes 136 registers (one CTA per SM).
+__global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, p = a.p, nbt = a.nbt, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const DevModel& md = a.model;
   double* rho = reinterpret_cast<double*>(smem);     // p + 2
   double* red = rho + p + 2;                         // 64
-  unsigned char* work = smem + refine_work_offset(p);  // reflector panels / GEMM tiles
+  unsigned char* work = smem + refine_work_offset(p);  // block reflectors / GEMM tiles
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
     const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     const c32* A = reinterpret_cast<const c32*>(a.A) + kw * (long long)n * n;
@@ -828,7 +837,7 @@ __global__ void k_lg_refine(LargeArgs a, int pw) {
       }
     __syncthreads();
     // C <- D^dag Q_h^dag C
-    cta_reflect<float, float>(A, n, C, p, p, false, work, pw);
+    cta_reflect_wy<float>(A, n, C, p, p, false, work);
     for (int r = warp; r < n; r += nwarp) {
       const c32 d = conj(Dp[r]);
       for (int c = lane; c < p; c += 32) C[(long long)r * p + c] = d * C[(long long)r * p + c];
@@ -853,7 +862,7 @@ __global__ void k_lg_refine(LargeArgs a, int pw) {
         [&](int ua, int c) { return coef[(long long)ua * p + c]; },
         [&](int r, int c, c32 v) { C[(long long)r * p + c] = Dp[r] * v; }, work);
     __syncthreads();
-    cta_reflect<float, float>(A, n, C, p, p, true, work, pw);
+    cta_reflect_wy<float>(A, n, C, p, p, true, work);
     // E = Q^dag Q - I with Q = Q32 + C: Q32^dag Q32 - I compensated (the FP32 basis is
     // orthonormal to ~1e-7, so the difference needs the extra precision), then the
     // small terms Q32^dag C + C^dag (Q32 + C) in FP32 as one GEMM over 2 n rows
@@ -888,30 +897,35 @@ __global__ void k_lg_refine(LargeArgs a, int pw) {
         },
         work);
     __syncthreads();
-    // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p
+    // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p: rho[p-1] is
+    // already q^dag H q of vector p-1; H x_p by one warp per row (lanes along the row,
+    // coalesced), in FP64
     if (p < n) {
-      double rq[2];
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int col = p - 1 + s2;
-        double num = 0.0, den = 0.0;
-        for (int r = tid; r < n; r += nt) {
-          z64 hv(0.0, 0.0);
-          const int q0 = dense ? r * n : a.row_ptr[r], q1 = dense ? (r + 1) * n : a.row_ptr[r + 1];
-          for (int q = q0; q < q1; ++q) {
-            const c32* hp = reinterpret_cast<const c32*>(He + q);
-            const z64 h(double(hp[0].re) + double(hp[1].re), double(hp[0].im) + double(hp[1].im));
-            cfma(hv, h, ccast<double>(X[(long long)(dense ? q - q0 : md.ent_col[q]) * nbt + col]));
-          }
-          const z64 v = ccast<double>(X[(long long)r * nbt + col]);
+      double num = 0.0, den = 0.0, den1 = 0.0;
+      for (int r = warp; r < n; r += nwarp) {
+        z64 hv(0.0, 0.0);
+        const int q0 = dense ? r * n : a.row_ptr[r], q1 = dense ? (r + 1) * n : a.row_ptr[r + 1];
+        for (int q = q0 + lane; q < q1; q += 32) {
+          const c32* hp = reinterpret_cast<const c32*>(He + q);
+          const z64 h(double(hp[0].re) + double(hp[1].re), double(hp[0].im) + double(hp[1].im));
+          cfma(hv, h, ccast<double>(X[(long long)(dense ? q - q0 : md.ent_col[q]) * nbt + p]));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          hv.re += __shfl_xor_sync(0xffffffffu, hv.re, o);
+          hv.im += __shfl_xor_sync(0xffffffffu, hv.im, o);
+        }
+        if (lane == 0) {
+          const z64 v = ccast<double>(X[(long long)r * nbt + p]);
           num += v.re * hv.re + v.im * hv.im;
           den += abs2(v);
+          den1 += abs2(ccast<double>(X[(long long)r * nbt + p - 1]));
         }
-        num = block_sum(num, red);
-        den = block_sum(den, red);
-        rq[s2] = num / den;
       }
+      num = block_sum(num, red);
+      den = block_sum(den, red);
+      den1 = block_sum(den1, red);
       if (tid == 0) {
-        const double g = rq[1] - rq[0];
+        const double g = num / den - rho[p - 1] / den1;
         a.gap[k] = g;
         if (!(g > a.gap_tol)) report(a.status, ST_EGAP, k, g);
       }
@@ -927,8 +941,6 @@ __global__ void k_lg_refine(LargeArgs a, int pw) {
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int LG_THREADS = 256;
-// shared memory for a reflector panel (the panel width adapts to n)
-constexpr size_t kReflectSmem = size_t(200) << 10;
 
 int lg_grid(long long units) {
   const long long cap = 152LL * 4;
@@ -998,7 +1010,7 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   if (!a.mixed) {
     if ((e = lg_common<double>(a, s)) != cudaSuccess) return e;
     if (a.p == 0) return cudaSuccess;  // values only
-    const int pw = reflect_pw<double>(a.n, kReflectSmem);
+    const int pw = reflect_pw<double>(a.n, size_t(200) << 10);
     if (pw == 0) return cudaErrorInvalidValue;
     const size_t sm = reflect_smem<double>(a.n, pw);
     static size_t cached = 0;
@@ -1015,19 +1027,17 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   }
   if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
   if (a.no_refine) return cudaSuccess;
-  const int pw = reflect_pw<float>(a.n, kReflectSmem - refine_work_offset(a.p));
-  if (pw == 0) return cudaErrorInvalidValue;
-  const size_t sm = reflect_smem<float>(a.n, pw);
+  const size_t sm = reflect_wy_smem<float>();
   static size_t cached = 0;
   if ((e = set_smem_once(k_lg_backtransform<float, float>, sm, cached)) != cudaSuccess) return e;
   k_lg_backtransform<float, float><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
-      a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt, pw);
+      a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_backtransform");
-  const size_t smr = refine_work_offset(a.p) + std::max(reflect_smem<float>(a.n, pw), CG_SMEM);
+  const size_t smr = refine_work_offset(a.p) + std::max(reflect_wy_smem<float>(), CG_SMEM);
   static size_t cached_r = 0;
   if ((e = set_smem_once(k_lg_refine, smr, cached_r)) != cudaSuccess) return e;
-  k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a, pw);
+  k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_refine");
   return cudaSuccess;

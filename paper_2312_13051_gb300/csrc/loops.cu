@@ -118,7 +118,8 @@ __global__ void k_overlaps(LoopArgs a) {
 // Mixed precision, p > 4: the overlaps in double-float on the FP32 pipe.  One CTA per
 // k-point; the two FP64 state blocks pass through shared memory in chunks of
 // OVL_ROWS rows, converted to double-float once per element, and each thread
-// accumulates up to 16 entries of M; M is written back in FP64.
+// accumulates a 4 x 4 tile of M (four values of each block per row q feed sixteen
+// products); M is written back in FP64.
 constexpr int OVL_ROWS = 32, OVL_THREADS = 256;
 
 __global__ void __launch_bounds__(OVL_THREADS, 1) k_overlaps_df(LoopArgs a) {
@@ -127,14 +128,18 @@ __global__ void __launch_bounds__(OVL_THREADS, 1) k_overlaps_df(LoopArgs a) {
   const long long K = (long long)N * a.N_t;
   cdf* Ah = reinterpret_cast<cdf*>(smem);        // OVL_ROWS x p, U(k_j)
   cdf* An = Ah + OVL_ROWS * p;                   // OVL_ROWS x p, U(k_{j+1})
+  // thread (ty, tx) of a 16 x 16 grid owns rows ty + 16 u and columns tx + 16 v of M
+  const int tx = tid & 15, ty = tid >> 4;
   for (long long k = blockIdx.x; k < K; k += gridDim.x) {
     const int i = int(k / N), j = int(k - (long long)i * N);
     const long long kn = (long long)i * N + (j + 1 == N ? 0 : j + 1);
     const z64* Uh = a.U + k * (long long)n * p;
     const z64* Un = a.U + kn * (long long)n * p;
-    cdf acc[16];
+    cdf acc[4][4];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) acc[s] = cdf_zero();
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = cdf_zero();
     for (int r0 = 0; r0 < n; r0 += OVL_ROWS) {
       const int rows = min(OVL_ROWS, n - r0);
       for (int e = tid; e < rows * p; e += OVL_THREADS) {
@@ -142,25 +147,29 @@ __global__ void __launch_bounds__(OVL_THREADS, 1) k_overlaps_df(LoopArgs a) {
         An[e] = cdf_from(Un[(long long)r0 * p + e]);
       }
       __syncthreads();
-      // the entries' chains interleave: independent accumulators for every q
       for (int q = 0; q < rows; ++q) {
+        cdf an[4], ah[4];
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-          const int e = tid + OVL_THREADS * s;
-          if (e < pp) {
-            const int r = e / p, c = e - r * p;
-            cfma_conj(acc[s], An[q * p + r], Ah[q * p + c]);
-          }
+        for (int u = 0; u < 4; ++u) {
+          const int r = ty + 16 * u, c = tx + 16 * u;
+          an[u] = r < p ? An[q * p + r] : cdf_zero();
+          ah[u] = c < p ? Ah[q * p + c] : cdf_zero();
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) cfma_conj(acc[u][v], an[u], ah[v]);
       }
       __syncthreads();
     }
     z64* M = a.M + k * (long long)pp;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int e = tid + OVL_THREADS * s;
-      if (e < pp) M[e] = cdf_to_z64(acc[s]);
-    }
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = ty + 16 * u, c = tx + 16 * v;
+        if (r < p && c < p) M[r * p + c] = cdf_to_z64(acc[u][v]);
+      }
   }
 }
 
