@@ -82,3 +82,53 @@ def test_model_marshalling_cache():
     m.i = m.i.astype(np.int64)                 # needs a copy: marshalled every call
     c = _lib._host_model(m)
     assert not c.shared and _lib._host_model(m) is not c
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the C compiler's size and field offsets for
+    every struct the header defines (a layout slip would pass garbage silently)."""
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    from paper_2312_13051_gb300 import _lib
+    structs = [_lib.bw_model, _lib.bw_plane, _lib.bw_plane_stack, _lib.bw_opts, _lib.bw_request_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "berrywl.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert got[(name, f[0])] == getattr(st, f[0]).offset, (name, f[0])
+
+
+def test_plane_stack_marshalling():
+    """A stack of planes: plane s at origin + (s / N_s) sweep_dir; the binding passes the
+    first plane, the integer sweep and N_s, refuses a fractional sweep, and gives its
+    outputs a leading plane axis."""
+    from paper_2312_13051_gb300 import _lib, inputs as I
+    st = I.PlaneStack(I.Plane(8, 6, origin=(0.1, 0.0, 0.25)), (0, 0, 1), 4)
+    origins = [pl.origin for pl in st.planes()]
+    assert origins == [(0.1, 0.0, 0.25), (0.1, 0.0, 0.5), (0.1, 0.0, 0.75), (0.1, 0.0, 1.0)]
+    assert all(pl.N == 8 and pl.N_t == 6 for pl in st.planes())
+    s, sfx, lead, base = _lib._plane_arg(st)
+    assert sfx == "_stack" and lead == (4,) and base is st.plane
+    assert list(s.sweep_dir) == [0, 0, 1] and s.N_s == 4 and s.plane.N_t == 6
+    assert list(s.plane.origin) == [0.1, 0.0, 0.25]
+    s1, sfx1, lead1, _ = _lib._plane_arg(st.plane)
+    assert sfx1 == "" and lead1 == () and s1.N == 8
+    with pytest.raises(_lib.BWError):
+        _lib._plane_arg(I.PlaneStack(st.plane, (0, 0, 0.5), 2))
