@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 1.25       # GB300 nominal dense FP64 (152 SMs; see the desig
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock: 80.5
 # DRAM bytes (read + write) of one launch of the fused mixed-precision loop kernel on
 # the BBH 60 x 60 nested workload, from the ncu capture summarised under profiles/
-FUSED_KERNEL_DRAM_BYTES = 161024
+FUSED_KERNEL_DRAM_BYTES = 161280
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SIMT FMA lanes x 2 flops x max clock
 
 
