@@ -209,8 +209,9 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model,
  * (N_s N_t x p/2 for the spin-resolved loop); min_gap, min_wannier_gap, min_pso_gap:
  * DEVICE, N_s N_t (may be NULL); nested: DEVICE, N_s N x m (row s N + j: base point j of
  * plane s; each nested loop closes within its plane); pso_evals: DEVICE, N_s N_t N x p
- * (may be NULL).  Limits and statuses as for the single-plane calls; the device status
- * reports k-point indices k = (s N_t + i) N + j and nested base points s N + j. */
+ * (may be NULL).  Limits and statuses as for the single-plane calls; a NULL stack or
+ * N_s < 1 is BW_EINVAL; the device status reports k-point indices k = (s N_t + i) N + j
+ * and nested base points s N + j. */
 bw_status bw_wilson_loop_stack(bw_ctx* ctx, const bw_model* model, const bw_plane_stack* stack,
                                int32_t p, bw_precision prec, const bw_opts* opts, double* phases,
                                double* min_gap, void* stream);
