@@ -145,6 +145,22 @@ def choti_eq9(delta0: float = 1.0, m: float = -1.5) -> HoppingList:
     return from_bloch_terms(4, m * kron(3, 0), cos_terms, sin_terms, dim=3, name="choti_eq9")
 
 
+def quadrupolar_eq10(delta: float = 0.5) -> HoppingList:
+    """Eq. 10 (spinful quadrupolar insulator, Sec. IV A), kron(sigma, tau):
+    sin kx s1t3 + sin ky s2t3 + (cos kx + cos ky + 1) s3t3 + delta (cos kx - cos ky) s0t1,
+    delta = 0.5.  The last term is printed with s0t0, which commutes with the chiral
+    operator S = s0t2 the text names; s0t1 is the reading that makes S^-1 H S = -H hold
+    and keeps the spectrum gapped (the other anticommuting choice, s0t3, closes the gap
+    at (pi, 0))."""
+    return from_bloch_terms(4, kron(3, 3),
+                            {0: kron(3, 3) + delta * kron(0, 1), 1: kron(3, 3) - delta * kron(0, 1)},
+                            {0: kron(1, 3), 1: kron(2, 3)}, dim=2, name="quadrupolar_eq10")
+
+
+EQ10_SPIN = np.diag([1.0, -1.0, 1.0, -1.0]).astype(np.complex128)   # s0 (x) t3 (Sec. IV A)
+EQ10_CHIRAL = np.kron(PAULI[0], PAULI[2])                            # S = s0 (x) t2
+
+
 def spin_hall(m: float = 1.0) -> HoppingList:
     """4-band spin-Hall model, kron(tau, s) (orbital-major, spin-minor):
     sin kx tx(x)sz + sin ky ty(x)s0 + (m - cos kx - cos ky) tz(x)s0."""
@@ -173,13 +189,14 @@ def square_lattice(t: float = 1.0) -> HoppingList:
 
 
 def supercell(model: HoppingList, L: int, W: float = 0.0, seed: int | None = None,
-              flux: bool = False, Ly: int | None = None) -> HoppingList:
+              flux: bool = False, Ly: int | None = None, onsite=None) -> HoppingList:
     """L x Ly supercell of a 2D model (Sec. II A, twisted boundary conditions with theta = 0).
 
     Supercell orbital index = ((x * Ly) + y) * n_cell + orbital.  A primitive hopping
     t_R from cell X to X + R becomes a supercell hopping with translation
     floor((x + R) / L).  ``W`` adds on-site Anderson disorder w ~ U[-W/2, W/2], one
-    value per primitive cell times the identity on its orbitals.  ``flux`` threads one
+    value per primitive cell times the identity on its orbitals, or times the matrix
+    ``onsite`` (n_cell x n_cell; Eq. 10's chiral-preserving disorder is s0 (x) t3).  ``flux`` threads one
     flux quantum per supercell (2 pi / (L Ly) per plaquette) in a torus-periodic
     Landau gauge: a +y bond starting at column x gets phase exp(i 2 pi x / (L Ly)),
     an x bond crossing the supercell seam gets exp(-i 2 pi s y / Ly) for s seam
@@ -211,10 +228,12 @@ def supercell(model: HoppingList, L: int, W: float = 0.0, seed: int | None = Non
             J_out.append(tcell + model.j)
             T_out.append(t)
             if W:
-                R_out.append(np.zeros((nc, 3), np.int64))
-                I_out.append(cell + np.arange(nc))
-                J_out.append(cell + np.arange(nc))
-                T_out.append(np.full(nc, wdis[x, y], np.complex128))
+                Md = np.eye(nc) if onsite is None else np.asarray(onsite, np.complex128)
+                ii, jj = np.nonzero(Md)
+                R_out.append(np.zeros((ii.size, 3), np.int64))
+                I_out.append(cell + ii)
+                J_out.append(cell + jj)
+                T_out.append(wdis[x, y] * Md[ii, jj].astype(np.complex128))
     return HoppingList(n=n, R=np.concatenate(R_out), i=np.concatenate(I_out),
                        j=np.concatenate(J_out), t=np.concatenate(T_out), dim=2,
                        name=f"{model.name}_sc{L}x{Ly}" + (f"_W{W}" if W else "")
@@ -380,6 +399,15 @@ def config_vacancy(L: int = 6, r: float = 1.0, nk: int = 16, m: float = 1.5) -> 
     cells = model.n // 4
     sz = np.kron(np.eye(cells), np.diag([1.0, -1.0, -1.0, 1.0])).astype(np.complex128)
     return Workload(f"bhz_vacancy_L{L}_r{r:g}", model, Plane(nk, nk), model.n // 2, sz)
+
+
+def config_quadrupolar(L: int, W: float, seed: int, nk: int = 6) -> Workload:
+    """Eq. 10 on an L x L supercell with the chiral-preserving disorder w s0 (x) t3 per
+    cell, w ~ U[-W/2, W/2] (Sec. IV A: 21 x 21, W from 0 to 9), half filling,
+    S = I (x) s0 (x) t3."""
+    model = supercell(quadrupolar_eq10(), L, W=W, seed=seed, onsite=EQ10_SPIN)
+    sz = np.kron(np.eye(L * L), EQ10_SPIN)
+    return Workload(f"quadrupolar_L{L}_W{W:g}_s{seed}", model, Plane(nk, nk), model.n // 2, sz)
 
 
 def config_manyband(N: int = 101, norb: int = 128) -> Workload:

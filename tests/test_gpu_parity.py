@@ -481,6 +481,10 @@ PLAQ = {
     "random6_p3": (lambda: I.random_hermitian_model(6, 2), None, P(7, 5), 3, -1),
     "supercell_L4_down": (lambda: I.supercell(I.spin_hall(1.0), 4, W=1.5, seed=3),
                           np.kron(np.eye(16), I.SPIN_HALL_SZ), P(5, 4), 32, -1),
+    # Eq. 10 (Sec. IV A): clean, and a 4 x 4 supercell with chiral disorder at W = 1
+    "quadrupolar_eq10": (lambda: I.quadrupolar_eq10(), I.EQ10_SPIN, P(16, 16), 2, -1),
+    "quadrupolar_L4_W1": (lambda: I.config_quadrupolar(4, 1.0, 1).model,
+                          np.kron(np.eye(16), I.EQ10_SPIN), P(6, 6), 32, -1),
 }
 
 

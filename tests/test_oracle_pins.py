@@ -43,12 +43,17 @@ def printed_forms():
         "bbh": (I.bbh(0.5, 0.5, 1.0, 1.0), lambda kx, ky, kz:
                 (0.5 + np.cos(kx)) * k(s1, s0) + np.sin(kx) * (-k(s2, s3))
                 + (0.5 + np.cos(ky)) * (-k(s2, s2)) + np.sin(ky) * (-k(s2, s1))),
+        # Eq. 10 with the printed s0 (x) t0 term read as s0 (x) t1 (chiral symmetry)
+        "eq10": (I.quadrupolar_eq10(0.5), lambda kx, ky, kz:
+                 np.sin(kx) * k(s1, s3) + np.sin(ky) * k(s2, s3)
+                 + (np.cos(kx) + np.cos(ky) + 1.0) * k(s3, s3)
+                 + 0.5 * (np.cos(kx) - np.cos(ky)) * k(s0, np.array([[0, 1], [1, 0]], dtype=complex))),
         "ssh": (I.ssh(0.7, 1.3), lambda kx, ky, kz:
                 np.array([[0, 0.7 + 1.3 * np.exp(-1j * kx)], [0.7 + 1.3 * np.exp(1j * kx), 0]])),
     }
 
 
-@pytest.mark.parametrize("name", ["eq4", "eq7", "eq9", "spin_hall", "bbh", "ssh"])
+@pytest.mark.parametrize("name", ["eq4", "eq7", "eq9", "eq10", "spin_hall", "bbh", "ssh"])
 def test_bloch_sum_matches_printed_form(name):
     """Step 1 (Bloch sum over the hopping list) equals the printed H(k), k = 2 pi f."""
     model, Hk = printed_forms()[name]
@@ -534,3 +539,51 @@ def test_z2_input_checks():
         O.z2_largest_gap(np.zeros((7, 2)))
     with pytest.raises(O.OracleError):
         O.z2_largest_gap(np.zeros((8, 0)))
+
+
+# ----------------------------------------------------------------------------
+# Eq. 10, the disordered quadrupolar insulator (Sec. IV A)
+# ----------------------------------------------------------------------------
+
+def test_quadrupolar_eq10_paper_statements():
+    """Eq. 10 (last term read as s0 (x) t1): chiral symmetry S^-1 H S = -H with
+    S = s0 (x) t2 (stated in Sec. IV A), also for the disorder w s0 (x) t3; the
+    spin-Chern number of the s = s0 (x) t3 sectors is 1 in magnitude (Fig. 6(b) at weak
+    disorder), equal from the spin-resolved winding and the plaquette flux."""
+    m = I.quadrupolar_eq10()
+    assert GOLDEN["quadrupolar_eq10_chiral_operator"]["value"] == "sigma0 (x) tau2"
+    Sc = I.EQ10_CHIRAL
+    assert np.array_equal(Sc, np.kron(s0, s2))
+    rng = np.random.default_rng(4)
+    for f in rng.uniform(-1, 1, size=(5, 3)):
+        H = O.bloch_hamiltonian(m, f)
+        assert np.abs(np.linalg.inv(Sc) @ H @ Sc + H).max() < 1e-13
+        lam = np.linalg.eigvalsh(H)
+        assert lam[1] < 0 < lam[2]                      # insulating at half filling
+    assert np.abs(np.linalg.inv(Sc) @ I.EQ10_SPIN @ Sc + I.EQ10_SPIN).max() == 0
+    S = I.EQ10_SPIN
+    dn, _, pg, _ = O.spin_resolved_wilson_loop(m, P(30, 30), 2, S, -1)
+    up, _, _, _ = O.spin_resolved_wilson_loop(m, P(30, 30), 2, S, +1)
+    expect = GOLDEN["quadrupolar_eq10_abs_spin_chern"]["value"]
+    assert abs(abs(O.winding(dn)) - expect) < 1e-9 and abs(O.winding(dn) + O.winding(up)) < 1e-9
+    _, C = O.plaquette_flux(m, P(20, 20), 2, S, -1)
+    assert abs(C - O.winding(dn)) < 1e-9
+    assert pg > 0.5
+
+
+def test_quadrupolar_eq10_disordered_supercells():
+    """Sec. IV A, Fig. 6(c): with the chiral-preserving disorder w s0 (x) t3 per cell at
+    W = 1 (below the gap closing near W = 5) the coupling-matrix flux of a supercell
+    keeps |C_s| = 1.  At W = 9 the half-filled states of these small supercells no longer
+    split evenly between the two s-sectors, so the fixed-size sector the method requires
+    does not exist and the oracle reports EPSOGAP (the paper's C_s = 0 is not a number
+    this reading produces)."""
+    for L, seed in ((4, 1), (4, 2), (5, 1)):
+        wl = I.config_quadrupolar(L, 1.0, seed)
+        assert wl.model.n == 4 * L * L and wl.p == 2 * L * L
+        _, C = O.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1)
+        assert abs(abs(C) - GOLDEN["quadrupolar_eq10_abs_spin_chern"]["value"]) < 1e-9
+    with pytest.raises(O.OracleError) as e:
+        wl = I.config_quadrupolar(4, 9.0, 1)
+        O.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1)
+    assert e.value.status == "EPSOGAP"
