@@ -719,3 +719,36 @@ def test_vacancy_supercell_parity(lib, ctx, precision):
     rdn, _, _, _ = oracle.spin_resolved_wilson_loop(wl.model, plane, wl.p, wl.spin_op, -1)
     assert circ_err_rows(dn.cpu().numpy(), rdn) <= TOL[precision]
     assert abs(lib.winding(dn, ctx=ctx).item() + 1) < 1e-6
+
+
+def test_eigh_batched_n256_n1024(lib, ctx):
+    """The FP64 tridiagonal solver at n = 256 and 1024 in one batch, with a degenerate
+    spectrum (each eigenvalue of a 128 x 128 block repeated four times at n = 512):
+    eigenvalues against LAPACK, residual |A V - V lam| and orthonormality of the lowest
+    eight vectors (a degenerate block's vectors only span the right subspace).  The
+    lowest eight eigenvalues of the degenerate matrix are two clusters of four with a
+    gap of 0.16 above them."""
+    torch = _torch()
+    rng = np.random.default_rng(23)
+    mats = I.random_hermitian_batch([256, 1024], seed=29)
+    B = I.random_hermitian_batch([128], seed=31)[0]
+    Q, _ = np.linalg.qr(rng.standard_normal((512, 512)) + 1j * rng.standard_normal((512, 512)))
+    D = Q @ np.kron(np.eye(4), B) @ Q.conj().T
+    mats.append(0.5 * (D + D.conj().T))
+    sizes = [m.shape[0] for m in mats]
+    n_vec = 8
+    H = torch.tensor(np.concatenate([m.reshape(-1) for m in mats]), device="cuda")
+    ev, vec = lib.eigh_batched(H, sizes, n_vec, precision="fp64", ctx=ctx)
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy()
+    eo = vo = 0
+    for A, n in zip(mats, sizes):
+        ref = np.linalg.eigvalsh(A)
+        got = ev[eo:eo + n]
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 1e-12 * scale, n
+        assert np.abs(got[:n_vec] - ref[:n_vec]).max() <= 1e-11 * scale, n
+        V = vec[vo:vo + n * n_vec].reshape(n, n_vec)
+        assert np.abs(A @ V - V * got[:n_vec]).max() <= 1e-10 * scale, n
+        assert np.abs(V.conj().T @ V - np.eye(n_vec)).max() <= 1e-11, n
+        eo += n
+        vo += n * n_vec
