@@ -15,6 +15,8 @@ from .wilson import (  # noqa: F401
     OracleError, STATUS, bloch_hamiltonian, plane_points, occupied_states,
     overlap, polar_factor, wilson_matrix, eigenphases, wilson_loop,
     projected_spin_sector, spin_resolved_wilson_loop, nested_wilson_loop,
+    wannier_sector, wannier_states, wannier_row, nested_phases,
+    translation_blocks, bloch_hamiltonian_grouped,
     cyclic_wilson_matrix, winding, circular_match_error, eigh_batched,
     plaquette_flux, plaquette_corners, plaquette_matrix,
     wcc_fractions, largest_gap_midpoint, z2_largest_gap,

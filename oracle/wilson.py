@@ -2,9 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Each function names the passage of arXiv 2312.13051 it follows.  The readings
-taken where the paper is silent or garbled are listed in the design notes and
-repeated next to the code that uses them.
+Each function names the passage of arXiv 2312.13051 it follows.  Where the paper
+is silent or garbled, the reading taken is stated next to the code that uses it.
 """
 from __future__ import annotations
 
@@ -38,6 +37,24 @@ def bloch_hamiltonian(model, f) -> np.ndarray:
     scale = max(np.abs(H).max(), np.abs(model.t).max(initial=0.0), 1e-300)
     if np.abs(H - H.conj().T).max() > 1e-12 * scale:
         raise OracleError("EINVAL", "hopping list is not Hermitian")
+    return 0.5 * (H + H.conj().T)
+
+
+def translation_blocks(model):
+    """The same sum grouped by translation: H(f) = sum_R exp(i 2pi f.R) T_R with T_R the
+    dense n x n matrix of the hoppings of translation R.  Returns (R list, T stack)."""
+    Rs, inv = np.unique(model.R, axis=0, return_inverse=True)
+    T = np.zeros((len(Rs), model.n, model.n), dtype=np.complex128)
+    np.add.at(T, (inv.ravel(), model.i, model.j), model.t)
+    return Rs, T
+
+
+def bloch_hamiltonian_grouped(blocks, f) -> np.ndarray:
+    """H(f) from ``translation_blocks`` (for models with many hoppings); equal to
+    ``bloch_hamiltonian`` term by term."""
+    Rs, T = blocks
+    phase = np.exp(1j * TWO_PI * (Rs.astype(np.float64) @ np.asarray(f, np.float64)))
+    H = np.tensordot(phase, T, axes=1)
     return 0.5 * (H + H.conj().T)
 
 
@@ -238,10 +255,89 @@ def _circ_gap(sel_phases, rest_phases):
     return float(d.min())
 
 
+def wannier_sector(theta, cut: float, first: int, m: int):
+    """The nested loop's sector (reading: ``WNWL`` has no sector argument): order the
+    eigenphases by their distance from ``cut`` going up, (theta - cut) mod 2pi, and take
+    positions [first, first + m).  Returns (selected indices, the other indices)."""
+    order = np.argsort(np.mod(np.asarray(theta) - cut, TWO_PI), kind="stable")
+    return order[first:first + m], np.concatenate([order[:first], order[first + m:]])
+
+
+def wannier_states(Uk: np.ndarray, nu: np.ndarray) -> np.ndarray:
+    """Wannier states of the sector at one k (Eq. 8): w = U(k) nu, with orthonormal
+    columns spanning the same space (QR; the right eigenvectors nu of a non-unitary W
+    are not orthogonal)."""
+    w, _ = np.linalg.qr(Uk @ nu)
+    return w
+
+
+def wannier_row(U_row, bases, cut, first, m, wannier_gap_tol, unitarise=False, row=0):
+    """One transverse row: for each base point j in ``bases`` the loop started at k_j,
+    its right eigenvectors, the sector and the Wannier states at k_j.  Returns (list of
+    w per base point, min Wannier gap of the row)."""
+    ws, gmin = [], np.inf
+    for j in bases:
+        W = cyclic_wilson_matrix(U_row, j, unitarise)
+        vals, vecs = np.linalg.eig(W)
+        th = np.angle(vals)
+        sel, rest = wannier_sector(th, cut, first, m)
+        g = _circ_gap(th[sel], th[rest])
+        gmin = min(gmin, g)
+        if not g > wannier_gap_tol:
+            raise OracleError("EWANGAP", f"Wannier gap {g:.3e}", (row, j))
+        ws.append(wannier_states(U_row[j], vecs[:, sel]))
+    return ws, gmin
+
+
+def nested_phases(w_column) -> np.ndarray:
+    """Wilson loop of the Wannier states along the transverse direction, closed on the
+    first point (Eq. 8 with the Eq. 2 overlaps), and its eigenphases."""
+    Nt = len(w_column)
+    Wn = np.eye(w_column[0].shape[1], dtype=np.complex128)
+    for i in range(Nt):
+        Wn = overlap(w_column[(i + 1) % Nt], w_column[i]) @ Wn
+    return eigenphases(Wn)
+
+
+def _row_points(plane, i) -> np.ndarray:
+    """Row i of ``plane_points(plane)``, by the same expression."""
+    o = np.asarray(plane.origin, np.float64)
+    a = np.asarray(plane.loop_dir, np.float64)
+    b = np.asarray(plane.trans_dir, np.float64)
+    return np.stack([o + (j / plane.N) * a + (i / plane.N_t) * b for j in range(plane.N)])
+
+
+def _row_states(model, plane, i, p, gap_tol, blocks=None):
+    """Occupied blocks of transverse row i and the row's minimum direct gap."""
+    f = _row_points(plane, i)
+    row, gmin = [], np.inf
+    for j in range(plane.N):
+        H = (bloch_hamiltonian(model, f[j]) if blocks is None
+             else bloch_hamiltonian_grouped(blocks, f[j]))
+        _, Uk, gap = occupied_states(H, p)
+        _check_gap(gap, gap_tol, (i, j))
+        gmin = min(gmin, gap)
+        row.append(Uk)
+    return row, gmin
+
+
+def _nested_row_task(args):
+    """Everything the nested loop needs from one transverse row (a picklable task, so a
+    caller may spread rows over processes)."""
+    model, plane, i, p, gap_tol, bases, cut, first, m, wtol, unitarise, blocks = args
+    U_row, gmin = _row_states(model, plane, i, p, gap_tol, blocks)
+    ph = eigenphases(wilson_matrix(U_row, unitarise))
+    ws, wg = wannier_row(U_row, bases, cut, first, m, wtol, unitarise, row=i)
+    return ph, gmin, ws, wg
+
+
 def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0,
                        m: int | None = None, gap_tol=None, wannier_gap_tol: float = 1e-6,
-                       unitarise=False):
-    """``WNWL``.  Returns (phases[N_t, p], nested[N, m], min_wannier_gap, min_gap[N_t])."""
+                       unitarise=False, bases=None, row_map=map, grouped=False):
+    """``WNWL``.  Returns (phases[N_t, p], nested[len(bases), m], min_wannier_gap,
+    min_gap[N_t]); ``bases`` (default: every base point j < N) selects base points,
+    ``row_map`` maps the per-row task over the rows (e.g. a process pool's map) and
+    ``grouped`` builds H(f) from ``translation_blocks``."""
     _check_plane(model, plane, p)
     m = p // 2 if m is None else m
     if not (1 <= m <= p) or not (0 <= first <= p - m):
@@ -249,29 +345,16 @@ def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0
     if np.any(np.asarray(plane.trans_dir) != np.round(plane.trans_dir)):
         raise OracleError("EINVAL", "trans_dir must be an integer vector for the nested loop")
     gap_tol = _default_gap_tol(model) if gap_tol is None else gap_tol
-    U, min_gap = _states_on_plane(model, plane, p, gap_tol)
-    N, Nt = plane.N, plane.N_t
-    phases = np.stack([eigenphases(wilson_matrix(U[i], unitarise)) for i in range(Nt)])
-    nested = np.empty((N, m))
-    min_wgap = np.inf
-    for j in range(N):
-        w = []
-        for i in range(Nt):
-            W = cyclic_wilson_matrix(U[i], j, unitarise)
-            vals, vecs = np.linalg.eig(W)
-            th = np.angle(vals)
-            order = np.argsort(np.mod(th - cut, TWO_PI), kind="stable")
-            sel, rest = order[first:first + m], np.concatenate([order[:first], order[first + m:]])
-            g = _circ_gap(th[sel], th[rest])
-            min_wgap = min(min_wgap, g)
-            if not g > wannier_gap_tol:
-                raise OracleError("EWANGAP", f"Wannier gap {g:.3e}", (i, j))
-            wv, _ = np.linalg.qr(U[i][j] @ vecs[:, sel])
-            w.append(wv)
-        Wn = np.eye(m, dtype=np.complex128)
-        for i in range(Nt):
-            Wn = overlap(w[(i + 1) % Nt], w[i]) @ Wn
-        nested[j] = eigenphases(Wn)
+    bases = list(range(plane.N)) if bases is None else list(bases)
+    blocks = translation_blocks(model) if grouped else None
+    tasks = [(model, plane, i, p, gap_tol, bases, cut, first, m, wannier_gap_tol, unitarise, blocks)
+             for i in range(plane.N_t)]
+    rows = list(row_map(_nested_row_task, tasks))
+    phases = np.stack([r[0] for r in rows])
+    min_gap = np.array([r[1] for r in rows])
+    min_wgap = min(r[3] for r in rows)
+    nested = np.stack([nested_phases([rows[i][2][b] for i in range(plane.N_t)])
+                       for b in range(len(bases))]) if bases else np.empty((0, m))
     return phases, nested, min_wgap, min_gap
 
 

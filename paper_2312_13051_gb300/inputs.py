@@ -181,6 +181,57 @@ def bbh(gx: float = 0.5, gy: float = 0.5, lx: float = 1.0, ly: float = 1.0) -> H
                             {0: lx * G3, 1: ly * G1}, dim=2, name=f"bbh({gx},{gy})")
 
 
+def cone_ssh_product(alpha: float, v: float, w: float) -> HoppingList:
+    """Four-band product model h_x(kx) (x) 1 + 1 (x) h_y(ky), kron(x-part, y-part):
+    h_x = sin(alpha) (cos kx s1 + sin kx s2) + cos(alpha) s3 (a unit vector on a cone of
+    opening alpha, so the Berry phase of its lower band along kx is known in closed form)
+    and h_y = (v + w cos ky) s1 + w sin ky s2 (the SSH chain of ``ssh`` along ky, Berry
+    phase pi for v < w and 0 for v > w).  Its lowest band is the product of the two
+    lower bands, so the two directions decouple."""
+    s = PAULI
+    hx_c, hx_s = np.sin(alpha) * np.kron(s[1], s[0]), np.sin(alpha) * np.kron(s[2], s[0])
+    const = np.cos(alpha) * np.kron(s[3], s[0]) + v * np.kron(s[0], s[1])
+    return from_bloch_terms(4, const, {0: hx_c, 1: w * np.kron(s[0], s[1])},
+                            {0: hx_s, 1: w * np.kron(s[0], s[2])}, dim=2,
+                            name=f"cone_ssh({alpha:.4f},{v},{w})")
+
+
+def direct_sum(models, name: str = "") -> HoppingList:
+    """Block-diagonal model: the orbitals of model b follow those of models 0 .. b-1 and
+    no hopping couples two blocks."""
+    off, R, I, J, T = 0, [], [], [], []
+    for m in models:
+        R.append(m.R)
+        I.append(m.i + off)
+        J.append(m.j + off)
+        T.append(m.t)
+        off += m.n
+    return HoppingList(n=off, R=np.concatenate(R), i=np.concatenate(I), j=np.concatenate(J),
+                       t=np.concatenate(T), dim=max(m.dim for m in models),
+                       name=name or "+".join(m.name for m in models))
+
+
+# Wannier ladder: three decoupled cone (x) SSH blocks.  The Wilson loop along kx has one
+# Wannier centre per block, at a different position for each block and the same at
+# every ky; the nested loop of a block's Wannier band along ky has the phase of that
+# block's SSH chain.  Targets xbar = theta / 2pi: about -0.45, -0.2, +0.3; nested
+# phases pi, 0, 0.
+LADDER_XBAR = (-0.45, -0.2, 0.3)
+LADDER_SSH = ((0.4, 1.0), (1.0, 0.5), (1.0, 0.6))
+
+
+def ladder_alpha(xbar: float) -> float:
+    """Cone opening whose lower band has Wannier centre close to xbar (-cos^2(alpha/2),
+    the continuum value, taken mod 1)."""
+    c2 = -xbar % 1.0
+    return float(2.0 * np.arccos(np.sqrt(c2)))
+
+
+def wannier_ladder() -> HoppingList:
+    return direct_sum([cone_ssh_product(ladder_alpha(x), v, w)
+                       for x, (v, w) in zip(LADDER_XBAR, LADDER_SSH)], name="wannier_ladder")
+
+
 def square_lattice(t: float = 1.0) -> HoppingList:
     """One orbital per cell, nearest-neighbour hopping -t (used for flux pins)."""
     T = np.array([[-t]], np.complex128)

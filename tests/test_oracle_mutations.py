@@ -2,7 +2,9 @@
 
 This shows that the pins in ``test_oracle_pins`` are strong enough: a dropped
 closure, a conjugated or transposed overlap, a reversed product, a flipped
-Fourier sign, an unprojected spin operator or the wrong bands all get caught.
+Fourier sign, an unprojected spin operator, the wrong bands, the wrong nested
+sector (taken from the other end, or from a shifted cut) or Wannier states that
+are not orthonormalised all get caught.
 """
 import functools
 
@@ -25,7 +27,11 @@ def _all_pins():
             pins.test_two_band_closed_form_eigenvectors,
             pins.test_eigh_against_independent_jacobi, pins.test_plaquette_flux_chern_eq4,
             pins.test_plaquette_flux_spin_sectors, pins.test_z2_synthetic_spectra,
-            pins.test_z2_paper_models]
+            pins.test_z2_paper_models, pins.test_ladder_first_loop_closed_form,
+            functools.partial(pins.test_cone_berry_phase_closed_form, 1.1, 24)]
+    out += [functools.partial(pins.test_nested_sector_choice, *case)
+            for case in pins.LADDER_CASES]
+    out += [functools.partial(pins.test_nested_full_sector_is_transverse_loop, 6, 3, 11)]
     return out
 
 
@@ -97,6 +103,27 @@ def _no_wrap_gap_midpoint(x_sorted):
     return float(x[m] + 0.5 * gaps[m]), float(gaps[m])
 
 
+def _sector_other_end(theta, cut, first, m):
+    order = np.argsort(np.mod(np.asarray(theta) - cut, 2 * np.pi), kind="stable")
+    p = len(order)
+    lo = p - m - first
+    return order[lo:lo + m], np.concatenate([order[:lo], order[lo + m:]])
+
+
+def _sector_cut_shifted(theta, cut, first, m):
+    order = np.argsort(np.mod(np.asarray(theta) - (cut + 1.0), 2 * np.pi), kind="stable")
+    return order[first:first + m], np.concatenate([order[:first], order[first + m:]])
+
+
+def _wannier_not_orthonormalised(Uk, nu):
+    return Uk @ nu
+
+
+def _wannier_columns_normalised(Uk, nu):
+    w = Uk @ nu
+    return w / np.linalg.norm(w, axis=0)
+
+
 MUTATIONS = {
     "conjugated_overlap": ("overlap", lambda a, b: b.conj().T @ a),
     "transposed_overlap": ("overlap", lambda a, b: (a.conj().T @ b).T),
@@ -110,6 +137,10 @@ MUTATIONS = {
     "reversed_plaquette": ("plaquette_corners", _reversed_plaquette),
     "smallest_wcc_gap": ("largest_gap_midpoint", _smallest_gap_midpoint),
     "no_circular_wcc_gap": ("largest_gap_midpoint", _no_wrap_gap_midpoint),
+    "nested_sector_other_end": ("wannier_sector", _sector_other_end),
+    "nested_cut_shifted": ("wannier_sector", _sector_cut_shifted),
+    "nested_no_orthonormalisation": ("wannier_states", _wannier_not_orthonormalised),
+    "nested_columns_only_normalised": ("wannier_states", _wannier_columns_normalised),
 }
 
 

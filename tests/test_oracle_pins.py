@@ -213,6 +213,100 @@ def test_bbh_nested_polarisation(gamma, expected):
     assert wgap > 0.1
 
 
+def _cone_phase(alpha, N):
+    """Closed-form discrete Berry phase of the lower band of h_x = sin(alpha)(cos k s1 +
+    sin k s2) + cos(alpha) s3 on N points.  Its lower eigenvector in the periodic gauge
+    is u(k) = (sin(alpha/2), -e^{ik} cos(alpha/2)); every Eq. 2 overlap
+    <u(k + 2pi/N)|u(k)> equals sin^2(alpha/2) + cos^2(alpha/2) e^{-2 pi i / N}, so the
+    loop is that number to the power N."""
+    z = np.sin(alpha / 2) ** 2 + np.cos(alpha / 2) ** 2 * np.exp(-2j * np.pi / N)
+    return float(np.angle(z ** N))
+
+
+@pytest.mark.parametrize("alpha,N", [(0.3, 7), (1.1, 24), (2.0, 24), (2.9, 40)])
+def test_cone_berry_phase_closed_form(alpha, N):
+    """A non-quantised Wilson-loop phase fixed in closed form (sign-sensitive, unlike the
+    0 / pi of SSH): the cone (x) SSH product block along kx, at several ky."""
+    model = I.cone_ssh_product(alpha, 1.0, 0.5)
+    ph, _ = O.wilson_loop(model, P(N, 5), 1)
+    d = np.angle(np.exp(1j * (ph[:, 0] - _cone_phase(alpha, N))))
+    assert np.abs(d).max() < 1e-12
+
+
+# Wannier ladder (three decoupled blocks A, B, C; inputs.wannier_ladder): Wannier centres
+# xbar ~ -0.45 (A), -0.2 (B), +0.3 (C) at every ky; nested phase of each block's band
+# along ky: pi (A, SSH v < w), 0 (B and C, v > w).  The sector picked by (cut, first, m)
+# is listed by hand from those positions: from cut = -pi the order is A, B, C; from 0
+# it is C, A, B; from -pi + 1 (past A at -0.45 * 2pi = -2.83) it is B, C, A.
+LADDER_NESTED = {"A": np.pi, "B": 0.0, "C": 0.0}
+LADDER_CASES = [(-np.pi, 0, 1, "A"), (-np.pi, 1, 1, "B"), (-np.pi, 2, 1, "C"),
+                (-np.pi, 0, 2, "AB"), (-np.pi, 1, 2, "BC"), (0.0, 0, 1, "C"), (0.0, 1, 1, "A"),
+                (0.0, 2, 1, "B"), (0.0, 0, 2, "CA"), (-np.pi + 1.0, 0, 1, "B"),
+                (-np.pi + 1.0, 2, 1, "A"), (-np.pi + 1.0, 1, 2, "CA")]
+
+
+def _ladder_thetas(N):
+    return {b: _cone_phase(I.ladder_alpha(x), N) for b, x in zip("ABC", I.LADDER_XBAR)}
+
+
+@pytest.mark.parametrize("cut,first,m,blocks", LADDER_CASES)
+def test_nested_sector_choice(cut, first, m, blocks):
+    """Eq. 8 on the Wannier ladder: the nested phases are those of the blocks in the
+    chosen sector (at every base point), and the Wannier gap is the closed-form
+    distance between the sector's centres and the others'."""
+    N, Nt = 24, 20
+    _, nest, wgap, _ = O.nested_wilson_loop(I.wannier_ladder(), P(N, Nt), 3, cut=cut,
+                                            first=first, m=m)
+    want = np.sort([LADDER_NESTED[b] for b in blocks])
+    for j in range(N):
+        assert O.circular_match_error(nest[j], want) < 1e-10
+    th = _ladder_thetas(N)
+    gaps = [abs(np.angle(np.exp(1j * (th[a] - th[b])))) for a in blocks for b in "ABC"
+            if b not in blocks]
+    assert abs(wgap - min(gaps)) < 1e-12
+
+
+def test_ladder_first_loop_closed_form():
+    """The first loop of the ladder: the three closed-form cone phases at every row."""
+    N = 24
+    ph, gap = O.wilson_loop(I.wannier_ladder(), P(N, 10), 3)
+    want = np.sort(list(_ladder_thetas(N).values()))
+    for r in range(10):
+        assert O.circular_match_error(ph[r], want) < 1e-12
+    # At ky = pi the SSH parts have |d_y| = |v - w| = 0.6, 0.5, 0.4; a block's levels are
+    # +-1 +-|d_y|, so the three occupied ones are -1.6, -1.5, -1.4 and the next is
+    # -|1 - 0.4| = -0.6: direct gap 0.8 on row 5 (t2 = 1/2).
+    assert abs(gap[5] - 0.8) < 1e-12
+
+
+@pytest.mark.parametrize("n,p,seed", [(6, 3, 11), (8, 4, 5)])
+def test_nested_full_sector_is_transverse_loop(n, p, seed):
+    """With the whole occupied space as the sector (m = p) the Wannier states span U(k),
+    so the nested loop at base point t1 is the ordinary Wilson loop along the transverse
+    direction at that t1 (the nested construction adds nothing).  Random models make
+    the Wilson matrix non-normal, so its eigenvectors are not orthogonal and the
+    orthonormalisation of the sector basis matters."""
+    model = I.random_hermitian_model(n, seed)
+    plane = P(9, 7)
+    _, nest, _, _ = O.nested_wilson_loop(model, plane, p, m=p)
+    for j in range(plane.N):
+        row = P(plane.N_t, 1, origin=(j / plane.N, 0.0, 0.0), loop_dir=(0, 1, 0),
+                trans_dir=(1.0, 0.0, 0.0))
+        ref, _ = O.wilson_loop(model, row, p)
+        assert O.circular_match_error(nest[j], ref[0]) < 1e-12
+
+
+def test_grouped_bloch_sum():
+    """H(f) summed per translation block equals the direct sum over the hopping list."""
+    rng = np.random.default_rng(4)
+    for model in (I.manyband(16), I.choti_eq9(), I.supercell(I.spin_hall(1.0), 3, W=1.0, seed=2)):
+        blocks = O.translation_blocks(model)
+        for _ in range(3):
+            f = rng.uniform(-1, 1, 3)
+            np.testing.assert_allclose(O.bloch_hamiltonian_grouped(blocks, f),
+                                       O.bloch_hamiltonian(model, f), atol=1e-13)
+
+
 def test_gauge_invariance():
     """Eigenphases are unchanged by a random unitary gauge U(k) -> U(k) G(k)."""
     model = I.random_hermitian_model(6, seed=3)
