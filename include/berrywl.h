@@ -51,7 +51,8 @@ typedef enum {
   BW_EWANGAP = 5,   /* Wannier (phase) gap around the nested sector <= tol         */
   BW_ENOCONV = 6,   /* an iterative eigensolver hit its iteration cap              */
   BW_ETIMEOUT = 7,  /* a bounded device-side wait gave up                          */
-  BW_ECUDA = 8      /* CUDA runtime error                                          */
+  BW_ECUDA = 8,     /* CUDA runtime error                                          */
+  BW_ECANCELED = 9  /* request withdrawn before it ran (bw_server_cancel)          */
 } bw_status;
 
 typedef enum {
@@ -288,21 +289,29 @@ bw_status bw_z2_largest_gap(bw_ctx* ctx, const double* phases, int32_t N_t, int3
  * Some callers cannot let a library allocate device memory: programs that give all
  * device memory to their own pool under a hard cap, plugins running inside another
  * program's CUDA context, or latency-critical loops where cudaMalloc / cudaFree
- * would block on or synchronise the device.  This entry point computes exactly
- * what bw_wilson_loop computes (same arguments and outputs, no context) without
- * allocating: all scratch lives in one fixed 8 MiB device array inside the
- * library, which every GPU that loads the library holds until the process exits.
- * The problem must fit in it: 16 K n p + 16 K p^2 + 8 K bytes (K = N * N_t) plus
- * the hopping-list plan; larger problems return BW_ENOMEM with a message, before
- * anything runs.  n <= 32 and p <= 64 as for bw_wilson_loop.
- *  - Runs on the current CUDA device.  The first call on a device looks up the
- *    array's device address (cudaGetSymbolAddress); make that first call before
- *    any stream capture on that device.
+ * would block on or synchronise the device.  This entry point computes the Wilson
+ * loop of bw_wilson_loop (same arguments and outputs, no context) without
+ * allocating: all scratch lives in one fixed 8 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *  - BW_FP64 runs the kernels bw_wilson_loop runs and gives the same results bit for
+ *    bit.  BW_MIXED runs the FP32 solve with FP64 refinement and FP64 overlaps (not
+ *    the double-float kernels bw_wilson_loop uses where they apply), so mixed results
+ *    agree with bw_wilson_loop within the mixed-precision tolerance (both within
+ *    1e-6 rad of the FP64 result), not bit for bit.
+ *  - The problem must fit in the array: 16 K n p + 8 K bytes (K = N * N_t) plus the
+ *    hopping-list plan, plus 16 K p^2 bytes for the overlaps when the loop kernel
+ *    does not form them itself (unitarise set, or p > 4 or a loop too long for the
+ *    scan kernel); larger problems return BW_ENOMEM with a message, before anything
+ *    runs.  n <= 32 and p <= 64.
+ *  - Runs on the current CUDA device, in the context current on the calling thread.
+ *    The first call in each context (normally once per device) looks up the array's
+ *    device address there (cudaGetSymbolAddress); make that first call before any
+ *    stream capture on that device.
  *  - Every call uses the same array and finds the previous call's data in it; the
  *    call clears its status word itself.  Calls whose work overlaps on the GPU
  *    (other host threads, other streams) race on the array: serialise them.
- *  - The call synchronises `stream` before returning and returns the device
- *    status of its own work (BW_EGAP etc.) as well as argument errors.
+ *  - The call waits for `stream` before returning and returns the device status of
+ *    its own work (BW_EGAP etc.) as well as argument errors.
  *  - err (may be NULL) receives a NUL-terminated message of at most err_len bytes.
  * phases, min_gap: DEVICE, caller-owned, as for bw_wilson_loop. */
 bw_status bw_wilson_loop_noalloc(const bw_model* model, const bw_plane* plane, int32_t p,
@@ -364,6 +373,12 @@ int bw_server_poll(bw_server* server, bw_request_info* done, int max);
 bw_status bw_server_wait(bw_server* server, int64_t id, double timeout_s, bw_request_info* info);
 /* Requests queued or running. */
 int64_t bw_server_outstanding(bw_server* server);
+/* Withdraws a request that is still queued (not yet admitted): it completes at once
+ * with status BW_ECANCELED and is collected like any other (bw_server_poll /
+ * bw_server_wait); its host buffers are not written.  A request already admitted
+ * runs to completion (kernels are not interrupted): BW_EINVAL, as for an unknown or
+ * already finished id. */
+bw_status bw_server_cancel(bw_server* server, int64_t id);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ import numpy as np
 TWO_PI = 2.0 * np.pi
 
 STATUS = {"OK": 0, "EINVAL": 1, "ENOMEM": 2, "EGAP": 3, "EPSOGAP": 4, "EWANGAP": 5,
-          "ENOCONV": 6, "ETIMEOUT": 7, "ECUDA": 8}
+          "ENOCONV": 6, "ETIMEOUT": 7, "ECUDA": 8, "ECANCELED": 9}
 
 
 class OracleError(Exception):

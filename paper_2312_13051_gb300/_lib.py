@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libberrywl.so")
 
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP", "ENOCONV", "ETIMEOUT",
-                "ECUDA"]
+                "ECUDA", "ECANCELED"]
 PRECISION = {"fp64": 0, "mixed": 1}
 
 
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_server_poll": (C.c_int, [vp, C.POINTER(bw_request_info), C.c_int]),
             "bw_server_wait": (i32, [vp, i64, dbl, C.POINTER(bw_request_info)]),
             "bw_server_outstanding": (i64, [vp]),
+            "bw_server_cancel": (i32, [vp, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -130,7 +131,7 @@ def exported_symbols():
             "bw_spin_resolved_wilson_loop", "bw_wilson_loop_stack", "bw_nested_wilson_loop_stack",
             "bw_spin_resolved_wilson_loop_stack", "bw_winding", "bw_z2_largest_gap", "bw_plaquette_flux", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
             "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
-            "bw_server_poll", "bw_server_wait", "bw_server_outstanding"]
+            "bw_server_poll", "bw_server_wait", "bw_server_outstanding", "bw_server_cancel"]
 
 
 class Context:
@@ -598,3 +599,10 @@ class Server:
 
     def outstanding(self) -> int:
         return int(self.lib.bw_server_outstanding(self.h))
+
+    def cancel(self, rid: int) -> None:
+        """Withdraws a queued request (it completes with status ECANCELED); raises
+        BWError(EINVAL) for a request already running, finished or unknown."""
+        rc = self.lib.bw_server_cancel(self.h, int(rid))
+        if rc != 0:
+            raise BWError(rc, self.lib.bw_server_last_error(self.h).decode())

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/berrywl.h"
 #include "launch.h"
 
@@ -1111,8 +1113,8 @@ bw_status bw_get_status(bw_ctx* ctx, void* stream, int64_t* k_index) {
   if (k_index) *k_index = h.code ? h.k_index : -1;
   if (h.code) {
     static const char* names[] = {"OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP",
-                                  "ENOCONV", "ETIMEOUT", "ECUDA"};
-    const char* nm = (h.code >= 0 && h.code <= 8) ? names[h.code] : "?";
+                                  "ENOCONV", "ETIMEOUT", "ECUDA", "ECANCELED"};
+    const char* nm = (h.code >= 0 && h.code <= 9) ? names[h.code] : "?";
     fail(ctx, bw_status(h.code), "device status %s at k index %lld (value %.6e)", nm, h.k_index, h.value);
     BW_CUDA(cudaMemset(ctx->status, 0, sizeof(bw::DevStatus)), "cudaMemset status");
   }
@@ -1463,39 +1465,87 @@ bw_status bw_spin_resolved_wilson_loop(bw_ctx* ctx, const bw_model* model, const
 // hands all device memory to its own pool under a hard cap, a plugin that runs
 // inside another program's CUDA context, or a latency-critical loop where
 // cudaMalloc / cudaFree would block on (or implicitly synchronise) the device.
-// For them bw_wilson_loop_noalloc runs the same kernels as bw_wilson_loop with
-// all of its scratch (the hopping-list plan, the occupied states, the overlaps,
-// the gaps and the status word) in one fixed file-scope device array.  The array
-// is part of the library image: every device that loads the library holds it
-// until the process exits.
+// For them bw_wilson_loop_noalloc runs the kernels of bw_wilson_loop with all of
+// its scratch (the hopping-list plan, the occupied states, the overlaps when the
+// loop kernel does not form them itself, the gaps and the status word) in one
+// fixed file-scope device array.  The array is part of the library image: every
+// device that loads the library holds it until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
-constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocMaxContexts = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_noalloc_mu;
-char* g_noalloc_base[kNoAllocMaxDevices] = {};
+// A __device__ array has one instance in every CUDA context that loads the library
+// (a device's primary context, or a context the caller created with the driver
+// API), each at its own address.  The address is looked up once per context, with
+// that context current, and kept under the context's unique id (cuCtxGetId; ids are
+// never reused within a process, unlike context handles).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the fixed array on the current device.  The host-side name
-// g_noalloc_scratch is only a stand-in for the symbol and must never reach a
-// kernel; the address comes from cudaGetSymbolAddress, once per device, with that
-// device current.
+struct NoAllocSlot {
+  unsigned long long ctx_id;
+  char* base;
+};
+
+std::mutex g_noalloc_mu;
+NoAllocSlot g_noalloc_slot[kNoAllocMaxContexts];
+int g_noalloc_slots = 0;
+CtxGetCurrentFn g_cu_ctx_get_current = nullptr;
+CtxGetIdFn g_cu_ctx_get_id = nullptr;
+
+// Driver-API functions through the runtime's entry-point query (no link against the
+// driver library).  Called with g_noalloc_mu held.
+bw_status noalloc_driver_entry_points(bw_ctx* ctx) {
+  if (g_cu_ctx_get_current && g_cu_ctx_get_id) return BW_OK;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+  BW_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1),
+          "cudaGetDriverEntryPointByVersion(cuCtxGetCurrent)");
+  BW_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2),
+          "cudaGetDriverEntryPointByVersion(cuCtxGetId)");
+  if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+    return fail(ctx, BW_ECUDA, "the CUDA driver does not provide cuCtxGetCurrent / cuCtxGetId");
+  g_cu_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_cu_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return BW_OK;
+}
+
+// Id of the context current on this thread; 0 when none is current yet.
+bw_status noalloc_context_id(bw_ctx* ctx, unsigned long long* id) {
+  *id = 0;
+  CUcontext c = nullptr;
+  if (g_cu_ctx_get_current(&c) != CUDA_SUCCESS)
+    return fail(ctx, BW_ECUDA, "cuCtxGetCurrent failed");
+  if (c && g_cu_ctx_get_id(c, id) != CUDA_SUCCESS) return fail(ctx, BW_ECUDA, "cuCtxGetId failed");
+  return BW_OK;
+}
+
+// Device address of the fixed array in the context current on this thread.  The
+// host-side name g_noalloc_scratch is only a stand-in for the symbol and must never
+// reach a kernel; the address comes from cudaGetSymbolAddress, looked up the first
+// time each context calls (with no context current yet, the runtime makes the
+// current device's primary context current during the lookup).
 bw_status noalloc_base(bw_ctx* ctx, char** out) {
-  int dev = -1;
-  BW_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
-  if (dev < 0 || dev >= kNoAllocMaxDevices)
-    return fail(ctx, BW_EINVAL, "device %d outside the %d devices the fixed scratch supports", dev,
-                kNoAllocMaxDevices);
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_base[dev]) {
-    void* p = nullptr;
-    BW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-    g_noalloc_base[dev] = static_cast<char*>(p);
-  }
-  *out = g_noalloc_base[dev];
+  bw_status st = noalloc_driver_entry_points(ctx);
+  if (st) return st;
+  unsigned long long id = 0;
+  if ((st = noalloc_context_id(ctx, &id))) return st;
+  for (int i = 0; id && i < g_noalloc_slots; ++i)
+    if (g_noalloc_slot[i].ctx_id == id) {
+      *out = g_noalloc_slot[i].base;
+      return BW_OK;
+    }
+  void* p = nullptr;
+  BW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+  if (!id && (st = noalloc_context_id(ctx, &id))) return st;
+  if (id && g_noalloc_slots < kNoAllocMaxContexts) g_noalloc_slot[g_noalloc_slots++] = {id, static_cast<char*>(p)};
+  *out = static_cast<char*>(p);
   return BW_OK;
 }
 
@@ -1520,17 +1570,28 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
   const long long K = (long long)plane->N * plane->N_t;
   Blob blob;
   plan_to_blob(P, blob);
+  bw::LoopArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.n = n;
+  la.p = p;
+  la.N = plane->N;
+  la.N_t = plane->N_t;
+  la.unitarise = o.unitarise;
+  la.max_sweeps = o.max_sweeps;
+  // the scan loop kernel forms the overlaps itself: no overlap buffer then
+  const bool need_M = !bw::loops_form_overlaps(la);
   const size_t bStat = al256(sizeof(bw::DevStatus));
   const size_t bBlob = al256(blob.data.size());
   const size_t bU = al256(size_t(K) * n * p * sizeof(z64));
   const size_t bGap = al256(size_t(K) * sizeof(double));
-  const size_t bM = al256(size_t(K) * p * p * sizeof(z64));
+  const size_t bM = need_M ? al256(size_t(K) * p * p * sizeof(z64)) : 0;
   const size_t total = bStat + bBlob + bU + bGap + bM;
   if (total > kNoAllocScratchBytes)
     return fail(ctx, BW_ENOMEM,
                 "this problem needs %zu bytes of scratch; the fixed scratch of "
-                "bw_wilson_loop_noalloc holds %zu bytes (K * n * p * 16 + K * p * p * 16 + "
-                "K * 8 + the hopping-list plan must fit)",
+                "bw_wilson_loop_noalloc holds %zu bytes (K * n * p * 16 + K * 8 + the "
+                "hopping-list plan, plus K * p * p * 16 when the loop kernel does not form the "
+                "overlaps itself, must fit)",
                 total, kNoAllocScratchBytes);
   char* base = nullptr;
   if ((st = noalloc_base(ctx, &base))) return st;
@@ -1538,7 +1599,7 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
   char* dblob = base + bStat;
   z64* U = reinterpret_cast<z64*>(dblob + bBlob);
   double* gap = reinterpret_cast<double*>(reinterpret_cast<char*>(U) + bU);
-  z64* M = reinterpret_cast<z64*>(reinterpret_cast<char*>(gap) + bGap);
+  z64* M = need_M ? reinterpret_cast<z64*>(reinterpret_cast<char*>(gap) + bGap) : nullptr;
   // The array keeps the previous call's contents: the status word must start at zero.
   BW_CUDA(cudaMemsetAsync(status, 0, sizeof(bw::DevStatus), s), "cudaMemsetAsync");
   BW_CUDA(cudaMemcpyAsync(dblob, blob.data.data(), blob.data.size(), cudaMemcpyHostToDevice, s),
@@ -1558,31 +1619,23 @@ bw_status noalloc_run(bw_ctx* ctx, const bw_model* model, const bw_plane* plane,
   sa.gap = gap;
   sa.status = status;
   BW_CUDA(bw::launch_states_small(sa, p, s), "states kernel");
-  bw::LoopArgs la;
-  std::memset(&la, 0, sizeof(la));
   la.U = U;
   la.M = M;
-  la.n = n;
-  la.p = p;
-  la.N = plane->N;
-  la.N_t = plane->N_t;
-  la.unitarise = o.unitarise;
-  la.max_sweeps = o.max_sweeps;
   la.gap = gap;
   la.phases = phases;
   la.min_gap = min_gap;
   la.status = status;
   BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
   BW_CUDA(bw::launch_loops(la, s), "loop kernel");
-  // Wait for the kernels (and for the copy out of the caller's host list), then
-  // report the device status of this call.
-  BW_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  // Read the status word behind the kernels on the caller's stream, then wait for that
+  // stream alone (the copy of the host list above is complete by then as well).
   bw::DevStatus h;
-  BW_CUDA(cudaMemcpy(&h, status, sizeof(h), cudaMemcpyDeviceToHost), "cudaMemcpy status");
+  BW_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync status");
+  BW_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   if (h.code) {
     static const char* names[] = {"OK", "EINVAL", "ENOMEM", "EGAP", "EPSOGAP", "EWANGAP",
-                                  "ENOCONV", "ETIMEOUT", "ECUDA"};
-    const char* nm = (h.code >= 0 && h.code <= 8) ? names[h.code] : "?";
+                                  "ENOCONV", "ETIMEOUT", "ECUDA", "ECANCELED"};
+    const char* nm = (h.code >= 0 && h.code <= 9) ? names[h.code] : "?";
     return fail(ctx, bw_status(h.code), "device status %s at k index %lld (value %.6e)", nm,
                 h.k_index, h.value);
   }

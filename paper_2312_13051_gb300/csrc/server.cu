@@ -418,6 +418,33 @@ bw_status bw_server_wait(bw_server* sv, int64_t id, double timeout_s, bw_request
   return BW_OK;
 }
 
+bw_status bw_server_cancel(bw_server* sv, int64_t id) {
+  if (!sv) return BW_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request* r = nullptr;
+    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it)
+      if ((*it)->id == id) {
+        r = *it;
+        sv->queue.erase(it);
+        break;
+      }
+    if (!r) {
+      for (auto& sl : sv->slots)
+        if (sl.req && sl.req->id == id)
+          return server_fail(sv, BW_EINVAL, "request is already running on the GPU; it runs to completion");
+      return server_fail(sv, BW_EINVAL, "unknown request id (finished, collected or never submitted)");
+    }
+    r->t_admit = r->t_done = Clock::now();
+    r->status = BW_ECANCELED;
+    r->err = "cancelled before admission";
+    sv->done[r->id] = r;
+    sv->done_order.push_back(r->id);
+  }
+  sv->cv_done.notify_all();
+  return BW_OK;
+}
+
 int64_t bw_server_outstanding(bw_server* sv) {
   if (!sv) return -1;
   std::lock_guard<std::mutex> lk(sv->mu);

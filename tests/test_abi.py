@@ -48,7 +48,8 @@ def test_binding_names_match_header(libpath):
     for s in declared_symbols():
         if s in ("bw_set_profiling", "bw_profile_read"):
             assert hasattr(_lib.Context, s[3:]), s
-        elif s in ("bw_server_submit", "bw_server_poll", "bw_server_wait", "bw_server_outstanding"):
+        elif s in ("bw_server_submit", "bw_server_poll", "bw_server_wait", "bw_server_outstanding",
+                   "bw_server_cancel"):
             assert hasattr(_lib.Server, s[len("bw_server_"):]), s
         elif s not in ("bw_create", "bw_destroy", "bw_last_error", "bw_get_status",
                        "bw_server_create", "bw_server_destroy", "bw_server_last_error"):

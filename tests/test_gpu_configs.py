@@ -60,13 +60,53 @@ def test_disordered_supercell_L10_full_plane(lib, ctx):
         assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
 
 
-def test_disordered_supercell_L20_sampled_row(lib, ctx):
+_L20 = {}
+
+
+def _l20_reference(wl, i):
+    if i not in _L20:
+        _L20[i] = oracle.wilson_loop(wl.model, _row_plane(wl.plane, i), wl.p)[0][0]
+    return _L20[i]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_disordered_supercell_L20_sampled_row(lib, ctx, precision):
     """Config 2 at L = 20 (n = 1600, p = 800): whole plane on the GPU, one row checked."""
     wl = I.config_disordered(20, seed=20231213 + 5)
-    ph, _ = lib.wilson_loop(wl.model, wl.plane, wl.p, precision="mixed", ctx=ctx)
+    ph, _ = lib.wilson_loop(wl.model, wl.plane, wl.p, precision=precision, ctx=ctx)
     i = 5
-    ref, _ = oracle.wilson_loop(wl.model, _row_plane(wl.plane, i), wl.p)
-    assert oracle.circular_match_error(ph.cpu().numpy()[i], ref[0]) <= TOL["mixed"]
+    assert oracle.circular_match_error(ph.cpu().numpy()[i], _l20_reference(wl, i)) <= TOL[precision]
+
+
+_MB_NESTED = {}
+
+
+def _manyband_nested_reference(wl, bases):
+    key = tuple(bases)
+    if key not in _MB_NESTED:
+        from tests import oracle_pool
+        _MB_NESTED[key] = oracle_pool.nested_wilson_loop(wl.model, wl.plane, wl.p, -np.pi, 0,
+                                                         wl.nested_m, bases)
+    return _MB_NESTED[key]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_manyband_full_size_nested_sampled_bases(lib, ctx, precision):
+    """Config 3's nested loop at full size (n = 256, p = 64, lower half m = 32 of the
+    Wannier bands, 101 x 101): the GPU runs the whole plane in one call; the oracle
+    (rows spread over host processes) gives the first-loop phases of every row and the
+    nested phases of three base points."""
+    wl = I.config_manyband()
+    bases = (0, 37, 88)
+    ph, nest, wgap, _ = lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m,
+                                               precision=precision, ctx=ctx)
+    ref_ph, ref_nest, ref_wgap, _ = _manyband_nested_reference(wl, bases)
+    assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= TOL[precision]
+    nest = nest.cpu().numpy()
+    for b, j in enumerate(bases):
+        assert oracle.circular_match_error(nest[j], ref_nest[b]) <= TOL[precision], j
+    # the GPU reports the gap per row over every base point; the oracle over three
+    assert float(wgap.min()) <= ref_wgap + 1e-9
 
 
 def test_serving_requests_sampled(lib):

@@ -752,3 +752,46 @@ def test_eigh_batched_n256_n1024(lib, ctx):
         assert np.abs(V.conj().T @ V - np.eye(n_vec)).max() <= 1e-11, n
         eo += n
         vo += n * n_vec
+
+
+@pytest.mark.parametrize("n,n_vec", [(256, 8), (256, 64), (1024, 8), (1024, 64)])
+def test_eigh_batched_mixed_refined_block(lib, ctx, n, n_vec):
+    """The mixed solver at n = 256 and 1024: FP32 tridiagonal solve, then the lowest
+    n_vec vectors refined to FP64 grade.  A gap of 0.5 is opened above the refined block
+    (its eigenvalues are shifted down), as the refinement needs.  The refined block must
+    meet FP64-grade bounds (eigenvalues against LAPACK, residual |A V - V lam|,
+    orthonormality); the other eigenvalues are FP32-accurate."""
+    torch = _torch()
+    A = I.random_hermitian_batch([n], seed=41 + n + n_vec)[0]
+    lam, V = np.linalg.eigh(A)
+    A = A - 0.5 * (V[:, :n_vec] @ V[:, :n_vec].conj().T)
+    A = 0.5 * (A + A.conj().T)
+    H = torch.tensor(A.reshape(-1), device="cuda")
+    ev, vec = lib.eigh_batched(H, [n], n_vec, precision="mixed", ctx=ctx)
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy().reshape(n, n_vec)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(ev[:n_vec] - ref[:n_vec]).max() <= 1e-11 * scale
+    assert np.abs(A @ vec - vec * ev[:n_vec]).max() <= 1e-10 * scale
+    assert np.abs(vec.conj().T @ vec - np.eye(n_vec)).max() <= 1e-11
+    assert np.abs(ev[n_vec:] - ref[n_vec:]).max() <= 1e-5 * scale
+
+
+LADDER_GPU = [(-np.pi, 0, 1), (-np.pi, 1, 1), (-np.pi, 2, 1), (-np.pi, 0, 2), (0.0, 1, 1),
+              (0.0, 0, 2), (-np.pi + 1.0, 0, 1), (-np.pi + 1.0, 1, 2), (-np.pi, 0, 3)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("cut,first,m", LADDER_GPU)
+def test_nested_sector_choice_ladder(lib, ctx, precision, cut, first, m):
+    """The nested sector (cut, first, m) on the three-block Wannier ladder, whose nested
+    phases identify the sector (pinned in closed form on the oracle): GPU against the
+    oracle, nested phases and Wannier gap."""
+    model, plane = I.wannier_ladder(), P(24, 20)
+    ref_ph, ref_n, ref_g, _ = oracle.nested_wilson_loop(model, plane, 3, cut=cut, first=first, m=m)
+    ph, nest, wg, _ = lib.nested_wilson_loop(model, plane, 3, cut=cut, first=first, m=m,
+                                             precision=precision, ctx=ctx)
+    assert circ_err_rows(ph.cpu().numpy(), ref_ph) <= TOL[precision]
+    assert circ_err_rows(nest.cpu().numpy(), ref_n) <= TOL[precision]
+    if np.isfinite(ref_g):
+        assert abs(float(wg.min()) - ref_g) <= TOL[precision]
