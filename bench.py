@@ -35,12 +35,10 @@ if ROOT not in sys.path:
 METRIC = "Wilson-loop k-points/sec (eigh+overlap+phases) mixed vs FP64 at ≤1e-6 rad; p50/p99 latency"
 UNIT = "k-points/s"
 WORKLOAD = "bbh_quadrupole_60x60_nested (gamma=0.5, lambda=1, n=4, p=2, m=1, N=N_t=60)"
-FP64_PEAK_TFLOPS = 1.25       # GB300 nominal dense FP64 (152 SMs; see the design notes)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock: 80.5
-# DRAM bytes (read + write) of one launch of the fused mixed-precision loop kernel on
-# the BBH 60 x 60 nested workload, from the ncu capture summarised under profiles/
-FUSED_KERNEL_DRAM_BYTES = 161280
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SIMT FMA lanes x 2 flops x max clock
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 dense FP64, NVIDIA's figure
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock: 80.5
+CSRC = os.path.join(ROOT, "paper_2312_13051_gb300", "csrc")
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def log(*a):
@@ -83,6 +81,64 @@ def barrier(device=None):
 def weak_scaling_value(units_per_rank: float, steps: int, world: int, max_seconds: float) -> float:
     """Whole-job throughput: all ranks' units over the slowest rank's time."""
     return units_per_rank * steps * world / max_seconds
+
+
+# ------------------------------------------------------------------ peaks and traffic
+def measure_peaks(dev):
+    """FP64 and FP32 (SIMT, TF32 off) pipe peaks measured in this run: cuBLAS DGEMM and
+    SGEMM on square matrices, best of 5 timed with CUDA events (2 n^3 flops each)."""
+    import torch
+    out = {}
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    torch.cuda.empty_cache()
+    return out
+
+
+def sources_sha256(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(CSRC, nm), "rb") as f:
+            h.update(nm.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the ncu summaries under
+    profiles/: a line `traffic: kernel=K workload=W dram_bytes_per_launch=B
+    sources=a.cu,b.cuh sha256=H`.  Returns (bytes, summary file), or (None, reason) when
+    no capture exists or the kernel's sources changed since it was taken."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split()[1:] if "=" in x)
+            if kv.get("kernel") != kernel or kv.get("workload") != workload:
+                continue
+            if sources_sha256(kv["sources"].split(",")) != kv.get("sha256"):
+                return None, f"{os.path.basename(path)}: sources changed since the capture"
+            return int(kv["dram_bytes_per_launch"]), os.path.basename(path)
+    return None, "no ncu capture of this kernel and workload under profiles/"
 
 
 # ------------------------------------------------------------------ algorithmic work
@@ -149,23 +205,94 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def run_oracle_once(wl):
+_BLAS_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """The oracle's per-row work spread over host processes (started with spawn, so it
+    is safe after CUDA has been initialised), one BLAS thread per worker: the per-k
+    multiprocessing mode of the CPU baseline.  Workers are started eagerly so that the
+    single-thread setting reaches every one of them."""
+
+    def __init__(self, workers: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers
+        saved = {k: os.environ.get(k) for k in _BLAS_VARS}
+        os.environ.update({k: "1" for k in _BLAS_VARS})
+        try:
+            self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+            fs = [self.ex.submit(time.sleep, 0.2) for _ in range(workers)]
+            for f in fs:
+                f.result(timeout=120)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def row_map(self, fn, tasks):
+        return self.ex.map(fn, list(tasks), chunksize=1, timeout=600)
+
+    def close(self):
+        self.ex.shutdown(cancel_futures=True)
+
+
+def run_oracle_once(wl, pool=None):
     import oracle
-    return oracle.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m)
+    kw = {"row_map": pool.row_map} if pool is not None else {}
+    return oracle.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m, **kw)
 
 
-def cpu_baseline(wl, min_seconds: float = 10.0):
+def _time_runs(wl, pool, min_seconds):
     runs, t0 = 0, time.perf_counter()
     while True:
-        run_oracle_once(wl)
+        run_oracle_once(wl, pool)
         runs += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
-            break
+            return runs, el
+
+
+def cpu_baseline(wl, min_seconds: float = 10.0):
+    """The oracle on the host cores, in both modes the measurement plan names, the better
+    one reported: (a) one process, LAPACK threaded by the BLAS library (at n = 4 nothing
+    threads, so it runs on one core); (b) the transverse rows of each run spread over
+    all cores by a process pool, one BLAS thread each.  A sample = repeated full runs of
+    the workload for at least min_seconds per mode."""
     K = wl.plane.N * wl.plane.N_t
-    return {"value": K * runs / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full runs of the 60x60 BBH nested workload (numpy FP64, one thread "
-                      f"of {os.cpu_count()} on {platform.machine()})", "seconds": el}
+    ncpu = os.cpu_count() or 1
+    modes = {}
+    run_oracle_once(wl)
+    runs, el = _time_runs(wl, None, min_seconds / 3)
+    modes["threaded_lapack"] = {"value": K * runs / el, "cores": 1, "runs": runs, "seconds": el}
+    pool = OraclePool(min(ncpu, wl.plane.N_t))
+    try:
+        run_oracle_once(wl, pool)
+        runs, el = _time_runs(wl, pool, min_seconds)
+    finally:
+        pool.close()
+    modes["per_row_processes"] = {"value": K * runs / el, "cores": pool.workers, "runs": runs,
+                                  "seconds": el}
+    best = max(modes, key=lambda m: modes[m]["value"])
+    b = modes[best]
+    return {"value": b["value"], "unit": UNIT, "cores": b["cores"], "kind": "oracle",
+            "mode": best, "nproc": ncpu, "cpu_model": cpu_model(), "machine": platform.machine(),
+            "sample": f"{b['runs']} full runs of the 60x60 BBH nested workload (numpy FP64) in "
+                      f"{b['seconds']:.1f} s, mode {best}",
+            "modes": modes}
 
 
 def run_reference(args):
@@ -175,22 +302,29 @@ def run_reference(args):
     from paper_2312_13051_gb300 import inputs as I
     wl = I.config_bbh()
     K = wl.plane.N * wl.plane.N_t
-    for _ in range(args.warmup):
-        run_oracle_once(wl)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        run_oracle_once(wl)
-        times.append(time.perf_counter() - t0)
+    ncpu = os.cpu_count() or 1
+    pool = OraclePool(min(ncpu, wl.plane.N_t))
+    try:
+        for _ in range(args.warmup):
+            run_oracle_once(wl, pool)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            run_oracle_once(wl, pool)
+            times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
     total = sum(times)
     value = K * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                             "nproc": ncpu, "cpu_model": cpu_model(),
                              "sample": "each step: the full 60x60 BBH nested workload, numpy FP64, "
-                                       "one thread"},
+                                       f"rows spread over {pool.workers} processes (one BLAS thread "
+                                       "each)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)),
                            "p99": 1e3 * float(np.percentile(times, 99))}}
@@ -199,42 +333,33 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU path
-def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
-    """Captured-graph replays timed with CUDA events, L2 flushed between steps.
-    Returns (total device ms, per-kernel ms totals, launches per step, outputs)."""
+def time_call_graph(ctx, call, out, steps, warmup, flush, dev, soak_s=0.5, profile_steps=None):
+    """Captured-graph replays of `call` timed with CUDA events on the replay stream, L2
+    flushed (a 256 MB write) before every timed step.  Returns (total device ms,
+    per-kernel ms totals over the profiled replays, kernels per call, outputs as numpy,
+    per-step ms).  The timed graph carries no timing marks; a second capture with
+    per-kernel CUDA-event marks gives the breakdown (profile_steps replays)."""
     import torch
     s = torch.cuda.Stream(device=dev)
-    if nested:
-        out = (torch.empty((wl.plane.N_t, wl.p), dtype=torch.float64, device=dev),
-               torch.empty((wl.plane.N, wl.nested_m), dtype=torch.float64, device=dev),
-               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev),
-               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev))
-        call = lambda: lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m,
-                                              precision=precision, ctx=ctx, check=False, out=out)
-    else:
-        out = (torch.empty((wl.plane.N_t, wl.p), dtype=torch.float64, device=dev),
-               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev))
-        call = lambda: lib.wilson_loop(wl.model, wl.plane, wl.p, precision=precision, ctx=ctx,
-                                       check=False, out=out)
     with torch.cuda.stream(s):
-        for _ in range(max(warmup, 3)):
+        for _ in range(max(min(warmup, 3), 1)):
             call()
     ctx.status(s)
 
-    def replay_steps(g, per_kernel):
+    def replay_steps(g, n, per_kernel):
         with torch.cuda.stream(s):
-            for _ in range(warmup):
+            for _ in range(min(warmup, 3)):
                 g.replay()
-            t_end = time.perf_counter() + 0.5          # untimed soak so clocks settle
+            t_end = time.perf_counter() + soak_s          # untimed soak so clocks settle
             while time.perf_counter() < t_end:
                 g.replay()
         torch.cuda.synchronize(dev)
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
         barrier(dev)
         torch.cuda.synchronize(dev)
         with torch.cuda.stream(s):
-            for k in range(steps):
+            for k in range(n):
                 flush.add_(1)                              # write > L2 between steps
                 ev0[k].record(s)
                 g.replay()
@@ -247,13 +372,11 @@ def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
         barrier(dev)
         return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
 
-    # the timed graph carries no timing marks; a second capture with per-kernel
-    # CUDA-event marks gives the breakdown
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         call()
     ctx.status(s)
-    per_step = replay_steps(g, None)
+    per_step = replay_steps(g, steps, None)
     total = sum(per_step)
     ctx.status(s)
     outs = [o.cpu().numpy() for o in out]
@@ -264,12 +387,46 @@ def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
         call()
     ctx.status(s)
     per_kernel = {}
-    replay_steps(gp, per_kernel)
+    replay_steps(gp, profile_steps or steps, per_kernel)
     ctx.status(s)
     ctx.set_profiling(False)
     launches = len(per_kernel)
     del gp
     return total, per_kernel, launches, outs, per_step
+
+
+def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
+    """The headline call (BBH nested, or the plain loop) under time_call_graph."""
+    import torch
+    if nested:
+        out = (torch.empty((wl.plane.N_t, wl.p), dtype=torch.float64, device=dev),
+               torch.empty((wl.plane.N, wl.nested_m), dtype=torch.float64, device=dev),
+               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev),
+               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev))
+        call = lambda: lib.nested_wilson_loop(wl.model, wl.plane, wl.p, m=wl.nested_m,
+                                              precision=precision, ctx=ctx, check=False, out=out)
+    else:
+        out = (torch.empty((wl.plane.N_t, wl.p), dtype=torch.float64, device=dev),
+               torch.empty((wl.plane.N_t,), dtype=torch.float64, device=dev))
+        call = lambda: lib.wilson_loop(wl.model, wl.plane, wl.p, precision=precision, ctx=ctx,
+                                       check=False, out=out)
+    return time_call_graph(ctx, call, out, steps, warmup, flush, dev)
+
+
+def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed):
+    """Algorithmic flops of each stage of the n > 32 Wilson-loop call over K = N Nt
+    k-points (complex multiply-add = 8 flops): Householder tridiagonalisation 16/3 n^3,
+    back-transform of nbt vectors 8 n^2 nbt, refinement 8 nnz p + 16 n (n - p) p +
+    16 n p^2 (mixed only), overlaps 8 n p^2, loop products 8 p^3 per step plus ~10 p^3
+    for the eigenphases of each loop; bisection and inverse iteration are O(n p)."""
+    K = N * Nt
+    nbt = min(n, p + 1) if mixed else p
+    fl = {"tridiag": K * 16.0 / 3.0 * n ** 3, "backtransform": K * 8.0 * n * n * nbt,
+          "overlaps": K * 8.0 * n * p * p, "loops": Nt * (N * 8.0 * p ** 3 + 10.0 * p ** 3),
+          "build": K * 8.0 * nnz_groups}
+    if mixed:
+        fl["refine"] = K * (8.0 * nnz_groups * p + 16.0 * n * (n - p) * p + 16.0 * n * p * p)
+    return fl
 
 
 def time_e2e(lib, ctx, wl, precision, steps, warmup, dev):
@@ -325,6 +482,7 @@ def run_ours(args):
     K = wl.plane.N * wl.plane.N_t
     ctx = lib.Context(local)
     flush = torch.zeros(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+    peaks = measure_peaks(dev)
     clocks = ClockSampler(local)
     clocks.start()
     res = {}
@@ -343,27 +501,23 @@ def run_ours(args):
                                             args.warmup, flush, dev, nested=False)
             sat_res[prec] = dict(total_ms=t, per_kernel=pk, nker=nk, steps=max(3, args.steps // 4),
                                  phases=outs[0])
-    # many-band model (n = 256, p = 64, 101 x 101): where the mixed path pays off
+    # many-band model (n = 256, p = 64, 101 x 101): where the mixed path pays off;
+    # graph replays of the whole call, L2 flushed between steps, per-stage marks
     mb_res = {}
     if not args.no_manyband:
         mb = I.config_manyband()
         for prec in ("mixed", "fp64"):
-            call = lambda: lib.wilson_loop(mb.model, mb.plane, mb.p, precision=prec, ctx=ctx)
-            call()
-            ctx.status()
-            ctx.set_profiling(True)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record()
-            ph, _ = call()
-            e1.record()
-            e1.synchronize()
-            stages = dict(ctx.profile_read())
-            ctx.set_profiling(False)
-            ctx.status()
-            mb_res[prec] = dict(ms=e0.elapsed_time(e1), stages=stages, phases=ph.cpu().numpy())
+            out = (torch.empty((mb.plane.N_t, mb.p), dtype=torch.float64, device=dev),
+                   torch.empty((mb.plane.N_t,), dtype=torch.float64, device=dev))
+            call = (lambda prec=prec, out=out:
+                    lib.wilson_loop(mb.model, mb.plane, mb.p, precision=prec, ctx=ctx, check=False,
+                                    out=out))
+            t, pk, nk, outs, per_step = time_call_graph(ctx, call, out, args.manyband_steps, 1, flush,
+                                                        dev, soak_s=0.0, profile_steps=1)
+            mb_res[prec] = dict(total_ms=t, steps=args.manyband_steps, stages=pk, nker=nk,
+                                phases=outs[0], per_step=per_step)
         # the spin-resolved (C_down sector) and nested (lower Wannier band) loops of the
-        # same plane, mixed request, one call each
+        # same plane, mixed request, one profiled call each
         kinds = [k for k in args.manyband_kinds.split(",") if k in ("spin", "nested")]
         for kind in kinds:
             if kind == "spin":
@@ -426,38 +580,43 @@ def run_ours(args):
     dom = max(pk, key=pk.get)
     avg_ms = pk[dom] / args.steps
     achieved = flops[dom] / (avg_ms * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
+    peak = peaks["fp64"]
     shares = {k: v / sum(pk.values()) for k, v in pk.items()}
+    fused = dom == "loops" and "states" not in pk
+    traffic, traffic_src = (committed_traffic("k_loops_fused_df", "bbh_60x60_nested") if fused
+                            else (None, "no capture of this kernel"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["mixed"]["total_ms"] / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "precision": "mixed request: at n = 4, p = 2 states, overlaps and loop products "
-                                "in double-float on the FP32 pipe (FP32 Jacobi + double-float Newton "
-                                "refinement), one cooperative kernel; FP32 + FP64-grade refinement for "
-                                "larger n (see the manyband block)",
+                                "in double-float (pairs of FP32, ~48-bit) on the FP32 pipe (FP32 "
+                                "Jacobi + double-float Newton refinement), phase tables, atan2 and "
+                                "phase ordering in FP64, one cooperative kernel; FP32 solve + "
+                                "FP64-grade refinement for larger n (manyband block)",
                    "timing": "CUDA-graph replay of the whole call, CUDA events per step",
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "fp64": {"value": fp64_value, "ms_per_step": res["fp64"]["total_ms"] / args.steps,
-                 "phase_err_rad": err.get("fp64"),
+                 "dtype": "f64", "phase_err_rad": err.get("fp64"),
                  "kernel_ms_per_step": {k: v / args.steps for k, v in res["fp64"]["per_kernel"].items()}},
         "mixed_over_fp64": fp64_value and value / fp64_value,
         "phase_err_rad": err.get("mixed"),
         "kernel_ms_per_step": {k: v / args.steps for k, v in pk.items()},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": FUSED_KERNEL_DRAM_BYTES if dom == "loops" and "states" not in pk else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "launch (profiles/k_loops_fused_df_bbh60x60.md)",
-                     "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s): the FP64-grade "
-                                    "arithmetic the path delivers (computed in double-float on the "
-                                    "FP32 pipe); latency-bound at 3600 k-points: 60 loops, one CTA "
-                                    "of 8 warps each, on 60 of 152 SMs",
-                     "fp32_pipe_frac": achieved / FP32_PEAK_TFLOPS,
-                     "algorithmic_flops_per_launch": flops[dom], "share": shares[dom]},
+        "roofline": {"kernel": "k_loops_fused_df" if fused else dom, "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_source": "measured in this run: cuBLAS DGEMM 4096^3, best of 5 (the "
+                                    "FP64-grade arithmetic the path delivers, computed in "
+                                    "double-float on the FP32 pipe)",
+                     "frac_of_nominal_fp64": achieved / FP64_NOMINAL_TFLOPS,
+                     "fp32_pipe_frac_of_measured_sgemm": achieved / peaks["fp32"],
+                     "algorithmic_flops_per_launch": flops[dom], "share": shares[dom],
+                     "note": "latency-bound at 3600 k-points: 60 loops, one CTA each, on 60 of "
+                             "152 SMs (the saturated block fills the SMs)"},
+        "peaks_measured_tflops": peaks,
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                        "p99": 1e3 * float(np.percentile(lat, 99))},
         "e2e": {"value": weak_scaling_value(K, args.steps, world, max_e2e), "unit": UNIT,
@@ -484,18 +643,48 @@ def run_ours(args):
                          "kernel_ms_per_step": {k: v / r["steps"] for k, v in pks.items()},
                          "roofline": {"kernel": d, "bound": "alu", "achieved": ach, "peak": peak,
                                       "unit": "TFLOP/s", "frac": ach / peak,
-                                      "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s)",
-                                      "fp32_pipe_frac": ach / FP32_PEAK_TFLOPS}}
+                                      "peak_source": "measured cuBLAS DGEMM (FP64-grade work)",
+                                      "fp32_pipe_frac_of_measured_sgemm": ach / peaks["fp32"]}}
         line["saturated"] = blk
     if mb_res:
         Km = mb.plane.N * mb.plane.N_t
-        blk = {"workload": "manyband n=256 p=64 101x101 plain Wilson loop (one call, CUDA events)",
+        nnz_groups = len(np.unique(np.stack([mb.model.i, mb.model.j, mb.model.R[:, 0], mb.model.R[:, 1],
+                                             mb.model.R[:, 2]], 1), axis=0))
+        blk = {"workload": f"manyband n=256 p=64 101x101 plain Wilson loop ({args.manyband_steps} "
+                           "graph replays per precision, L2 flushed between them)",
                "k_points_per_call": Km}
-        for prec, r in mb_res.items():
-            blk[prec] = {"value": Km / (r["ms"] * 1e-3), "ms_per_call": r["ms"],
-                         "stage_ms": {k: round(v, 3) for k, v in r["stages"].items()}}
+        for prec in ("mixed", "fp64"):
+            r = mb_res[prec]
+            ms = r["total_ms"] / r["steps"]
+            st = r["stages"]
+            fl = manyband_stage_flops(mb.model.n, mb.p, mb.plane.N, mb.plane.N_t, nnz_groups,
+                                      prec == "mixed")
+            d = max((k for k in st if k in fl), key=st.get)
+            ach = fl[d] / (st[d] * 1e-3) / 1e12
+            pk_ = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
+            blk[prec] = {"value": weak_scaling_value(Km, r["steps"], world,
+                                                     reduce_max(r["total_ms"] / 1e3, dev)),
+                         "ms_per_call": ms, "dtype": "f32+df32" if prec == "mixed" else "f64",
+                         "per_step_ms": [round(x, 3) for x in r["per_step"]],
+                         "stage_ms": {k: round(v, 3) for k, v in st.items()},
+                         "roofline": {"kernel": d, "bound": "alu", "achieved": ach, "peak": pk_,
+                                      "unit": "TFLOP/s", "frac": ach / pk_,
+                                      "algorithmic_flops_per_call": fl[d],
+                                      "peak_source": ("measured cuBLAS SGEMM 8192^3, TF32 off (the "
+                                                      "FP32 pipe the mixed stages run on)"
+                                                      if prec == "mixed" else
+                                                      "measured cuBLAS DGEMM 4096^3 (FP64 pipe)"),
+                                      "eigensolve_frac": (sum(fl[k] for k in ("tridiag", "backtransform")
+                                                              if k in fl) /
+                                                          (sum(st.get(k, 0.0) for k in
+                                                               ("tridiag", "bisect", "invit",
+                                                                "backtransform")) * 1e-3) / 1e12) / pk_}}
             if "phase_err_rad" in r:
                 blk[prec]["phase_err_rad_sampled_row"] = r["phase_err_rad"]
+        for kind in ("spin_mixed", "nested_mixed"):
+            if kind in mb_res:
+                blk[kind] = {"ms_per_call": mb_res[kind]["ms"],
+                             "stage_ms": {k: round(v, 3) for k, v in mb_res[kind]["stages"].items()}}
         blk["mixed_over_fp64"] = blk["mixed"]["value"] / blk["fp64"]["value"]
         line["manyband"] = blk
     if world == 1 and not args.no_cpu_baseline:
@@ -639,6 +828,8 @@ def main(argv=None):
     ap.add_argument("--parity-samples", type=int, default=3)
     ap.add_argument("--no-manyband", action="store_true",
                     help="skip the many-band (n = 256) mixed-vs-FP64 measurement")
+    ap.add_argument("--manyband-steps", type=int, default=10,
+                    help="timed graph replays of the many-band call per precision")
     ap.add_argument("--manyband-kinds", default="wilson",
                     help="comma list of many-band loops to time: wilson (always), spin, nested")
     ap.add_argument("--profile-precision", choices=["mixed", "fp64"], default="mixed",

@@ -240,8 +240,11 @@ bw_status bw_spin_resolved_wilson_loop_stack(bw_ctx* ctx, const bw_model* model,
  * (sign -1) or C_up (+1).
  * flux: DEVICE, N_t x N doubles in (-pi, pi] (row i, column j).  chern: DEVICE, one
  * double, sum(flux) / 2pi (may be NULL).  min_gap, min_pso_gap: DEVICE, N_t doubles
- * per transverse row (may be NULL; min_pso_gap only with spin_op).  p (p/2 with a
- * spin operator) <= 64; with a spin operator and n > 32 also p <= 64. */
+ * per transverse row (may be NULL; min_pso_gap only with spin_op).  Up to 64 bands in
+ * the loop (p, or p/2 with a spin operator) each k-point's two link determinants come
+ * from overlaps and LU in shared memory; beyond, the link matrices are formed by a
+ * batched GEMM in blocks of 256 k-points and each determinant's phase by LU with
+ * partial pivoting in global memory (one CTA per matrix). */
 bw_status bw_plaquette_flux(bw_ctx* ctx, const bw_model* model, const bw_plane* plane, int32_t p,
                             const bw_c128* spin_op, int32_t sign, bw_precision prec,
                             const bw_opts* opts, double* flux, double* chern, double* min_gap,

@@ -12,6 +12,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "geig.cuh"
 #include "jacobi.cuh"
@@ -34,12 +35,14 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs g) {
   __shared__ z64 Bs[GK][GT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int tiles_n = (g.n + GT - 1) / GT;
-  const long long b = g.b0 + blockIdx.y;
-  const long long ba = g.a_next_N > 0 ? (b / g.a_next_N) * g.a_next_N + (b % g.a_next_N + 1) % g.a_next_N : b;
+  const long long bl = g.b0 + blockIdx.y, b = g.kfirst + bl;
+  const long long ba = g.a_next_N > 0 ? (b / g.a_next_N) * g.a_next_N + (b % g.a_next_N + 1) % g.a_next_N
+                       : g.a_mod > 0  ? (b + g.a_shift) % g.a_mod
+                                      : b;
   const int r0 = (blockIdx.x / tiles_n) * GT, c0 = (blockIdx.x % tiles_n) * GT;
   const z64* A = g.A + ba * g.sA;
   const z64* B = g.B + b * g.sB;
-  z64* C = g.C + b * g.sC;
+  z64* C = g.C + bl * g.sC;
   z64 acc[4][4];
 #pragma unroll
   for (int x = 0; x < 4; ++x)
@@ -113,6 +116,141 @@ cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Phase of a determinant (the link variables of the plaquette Berry flux for p > 64).
+// Right-looking LU with partial pivoting of one p x p matrix per CTA in global memory:
+// the row exchanges are kept in a permutation (rows are not moved), so
+// det = sign(perm) prod_c A[perm[c]][c].  Only the phase is kept, as the product of the
+// unit pivots (no overflow or underflow at any p); a zero pivot gives 0.  The pivot is
+// the largest |A[perm[r]][c]| over r >= c, the smallest r on ties.  The trailing update
+// gives each thread whole columns, so the warp's accesses to a row are contiguous.
+// ---------------------------------------------------------------------------
+constexpr int DET_THREADS = 256;
+
+__global__ void __launch_bounds__(DET_THREADS) k_det_phase(z64* A, long long sA, int p, long long nb,
+                                                          z64* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  z64* mult = reinterpret_cast<z64*>(smem);
+  int* perm = reinterpret_cast<int*>(mult + p);
+  __shared__ double red_v[DET_THREADS / 32];
+  __shared__ int red_i[DET_THREADS / 32];
+  __shared__ z64 pv_sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+    z64* M = A + b * sA;
+    for (int r = tid; r < p; r += DET_THREADS) perm[r] = r;
+    z64 phase(1.0, 0.0);  // thread 0
+    __syncthreads();
+    for (int c = 0; c < p; ++c) {
+      double best = -1.0;
+      int bi = p;
+      for (int r = c + tid; r < p; r += DET_THREADS) {
+        const double v = abs2(M[(long long)perm[r] * p + c]);
+        if (v > best) {
+          best = v;
+          bi = r;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        red_v[wid] = best;
+        red_i[wid] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < DET_THREADS / 32; ++w)
+          if (red_v[w] > best || (red_v[w] == best && red_i[w] < bi)) {
+            best = red_v[w];
+            bi = red_i[w];
+          }
+        if (bi >= p) bi = c;  // every candidate is NaN: keep the row order
+        const int t = perm[c];
+        perm[c] = perm[bi];
+        perm[bi] = t;
+        const z64 pv = M[(long long)perm[c] * p + c];
+        const double a = sqrt(abs2(pv));
+        if (a > 0.0) {
+          phase = phase * z64(pv.re / a, pv.im / a);
+          if (bi != c) phase = z64(-phase.re, -phase.im);
+        } else {
+          phase = z64(0.0, 0.0);
+        }
+        pv_sh = pv;
+      }
+      __syncthreads();
+      const z64 pv = pv_sh;
+      const double pa = abs2(pv);
+      for (int r = c + 1 + tid; r < p; r += DET_THREADS) {
+        const z64 v = M[(long long)perm[r] * p + c];
+        mult[r] = pa > 0.0 ? z64((v.re * pv.re + v.im * pv.im) / pa, (v.im * pv.re - v.re * pv.im) / pa)
+                           : z64(0.0, 0.0);
+      }
+      __syncthreads();
+      const z64* prow = M + (long long)perm[c] * p;
+      for (int cc = c + 1 + tid; cc < p; cc += DET_THREADS) {
+        const z64 t = prow[cc];
+        for (int r = c + 1; r < p; ++r) {
+          z64* e = M + (long long)perm[r] * p + cc;
+          *e = *e - mult[r] * t;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) out[b] = phase;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_det_phase(z64* A, long long sA, int p, long long nb, z64* out, cudaStream_t s) {
+  if (nb <= 0 || p <= 0) return cudaSuccess;
+  const size_t sm = size_t(p) * (sizeof(z64) + sizeof(int));
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_det_phase, sm, cached);
+  if (e != cudaSuccess) return e;
+  const long long cap = 152LL * 4;
+  k_det_phase<<<int(nb < cap ? nb : cap), DET_THREADS, sm, s>>>(A, sA, p, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plaquettes_big(const LoopArgs& a, z64* Lmat, long long kb, z64* Lx, z64* Ly,
+                                  double* flux, double* chern, cudaStream_t s) {
+  const long long K = (long long)a.N * a.N_t;
+  if (K <= 0) return cudaSuccess;
+  const int p = a.p;
+  const long long sU = (long long)a.n * p, sL = (long long)p * p;
+  cudaError_t e;
+  for (long long k0 = 0; k0 < K; k0 += kb) {
+    const long long nb = std::min(kb, K - k0);
+    for (int dir = 0; dir < 2; ++dir) {
+      // Lx(j, i) = det U(j+1, i)^dag U(j, i);  Ly(j, i) = det U(j, i+1)^dag U(j, i)
+      GemmArgs g;
+      memset(&g, 0, sizeof(g));
+      g.A = a.U; g.B = a.U; g.C = Lmat;
+      g.m = p; g.n = p; g.k = a.n; g.opA = 1;
+      g.lda = p; g.ldb = p; g.ldc = p;
+      g.sA = sU; g.sB = sU; g.sC = sL;
+      g.kfirst = k0;
+      if (dir == 0) {
+        g.a_next_N = a.N;
+      } else {
+        g.a_shift = a.N;
+        g.a_mod = K;
+      }
+      g.batch = nb;
+      if ((e = launch_zgemm(g, s)) != cudaSuccess) return e;
+      if ((e = launch_det_phase(Lmat, sL, p, nb, (dir == 0 ? Lx : Ly) + k0, s)) != cudaSuccess) return e;
+    }
+  }
+  return launch_plaquette_flux(a, Lx, Ly, flux, chern, s);
 }
 
 // ---------------------------------------------------------------------------

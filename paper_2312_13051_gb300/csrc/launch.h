@@ -165,8 +165,10 @@ cudaError_t launch_eigh_ritz(const LargeArgs& a, double* ritz, cudaStream_t s);
 cudaError_t launch_eigh_scatter(const EighScatterArgs& e, cudaStream_t s);
 
 // Batched complex GEMM C_b = op(A_b) B_b (row-major; op(A) is A or A^dagger), m x n
-// result, inner dimension k; batch b uses A + b' sA, B + b sB, C + b sC, where b' = b,
-// or with a_next_N > 0 the next k-point of the same loop, (b / N) N + (b % N + 1) % N.
+// result, inner dimension k; batch b (b = kfirst + the launch's batch index) uses
+// A + b' sA, B + b sB, C + (b - kfirst) sC, where b' = b, or with a_next_N > 0 the next
+// k-point of the same loop, (b / N) N + (b % N + 1) % N, or with a_mod > 0
+// (b + a_shift) % a_mod (the k-point of the next transverse row).
 struct GemmArgs {
   const z64* A;
   const z64* B;
@@ -178,6 +180,8 @@ struct GemmArgs {
   long long a_next_N;
   long long batch;
   long long b0;           // first batch index of this launch (set by launch_zgemm)
+  long long kfirst;       // absolute index of batch 0 for A and B (C stays relative)
+  long long a_shift, a_mod;
 };
 
 // Eigenphases of nl Wilson matrices W (p x p, stride sW), loops i0 .. i0+nl-1.
@@ -224,6 +228,20 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s);
 // (device double); a.min_gap / a.min_pso_gap per transverse row from a.gap / a.pso_gap.
 cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux, double* chern,
                               cudaStream_t s);
+
+// Plaquette flux from precomputed link phases Lx, Ly (K unit complex numbers each):
+// flux (N_t x N), chern = sum / 2pi, and a.min_gap / a.min_pso_gap per transverse row.
+cudaError_t launch_plaquette_flux(const LoopArgs& a, const z64* Lx, const z64* Ly, double* flux,
+                                  double* chern, cudaStream_t s);
+
+// Plaquette Berry flux for p > 64 (bigloop.cu): link matrices of kb k-points at a time
+// by the batched GEMM into Lmat (kb x p x p scratch), the phase of each determinant by
+// LU with partial pivoting (one CTA per matrix), then launch_plaquette_flux.
+cudaError_t launch_plaquettes_big(const LoopArgs& a, z64* Lmat, long long kb, z64* Lx, z64* Ly,
+                                  double* flux, double* chern, cudaStream_t s);
+
+// Phase of det(A_b) for nb p x p matrices (stride sA, overwritten by their LU factors).
+cudaError_t launch_det_phase(z64* A, long long sA, int p, long long nb, z64* out, cudaStream_t s);
 
 // Winding of the summed Wannier centres over the transverse direction (Eq. 6).
 cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,

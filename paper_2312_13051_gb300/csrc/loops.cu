@@ -1269,8 +1269,16 @@ cudaError_t launch_plaquettes(const LoopArgs& a, z64* Lx, z64* Ly, double* flux,
   const long long cap = 152LL * 16;
   k_plaquette_links<<<int(K < cap ? K : cap), a.p <= 8 ? 32 : 128, sm, s>>>(a.U, a.n, a.p, a.N, a.N_t, Lx, Ly);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_plaquette_flux(a, Lx, Ly, flux, chern, s);
+}
+
+cudaError_t launch_plaquette_flux(const LoopArgs& a, const z64* Lx, const z64* Ly, double* flux,
+                                  double* chern, cudaStream_t s) {
+  const long long K = (long long)a.N * a.N_t;
+  if (K <= 0) return cudaSuccess;
   k_plaquette_flux<<<int((K + 127) / 128), 128, 0, s>>>(Lx, Ly, a.N, a.N_t, flux);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_plaquette_sum<<<1, 256, 0, s>>>(flux, a.gap, a.pso_gap, a.N, a.N_t, chern, a.min_gap, a.min_pso_gap);
   return cudaGetLastError();
 }

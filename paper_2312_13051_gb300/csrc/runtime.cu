@@ -771,9 +771,6 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   }
   if (kind == LoopKind::Nested && p_eff > bw::LOOP_P_MAX)
     return fail(ctx, BW_EINVAL, "nested loop supports p <= %d (p = %d)", bw::LOOP_P_MAX, p_eff);
-  if (kind == LoopKind::Plaquette && (p_eff > bw::LOOP_P_MAX || (spin && large && p > 64)))
-    return fail(ctx, BW_EINVAL, "plaquette flux supports p <= %d (and p <= 64 with a spin operator "
-                "for n > %d)", bw::LOOP_P_MAX, bw::SMALL_N_MAX);
   // many occupied bands: batched-GEMM loops (the spin-resolved one from p > 64 at
   // large n, where the split runs on the tridiagonal path)
   const bool big = (kind == LoopKind::Plain && p_eff > bw::LOOP_P_MAX) ||
@@ -798,7 +795,12 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   }
   const size_t bU = al256(size_t(K) * n * p_eff * sizeof(z64));
   const size_t bGap = al256(size_t(K) * sizeof(double));
-  const size_t bM = al256(size_t(K) * p_eff * p_eff * sizeof(z64));
+  // overlap scratch; the plaquette flux needs none up to p = 64 (links in shared memory)
+  // and blocks of link matrices beyond
+  const long long kb_links = std::min<long long>(K, 256);
+  const size_t bM = kind != LoopKind::Plaquette ? al256(size_t(K) * p_eff * p_eff * sizeof(z64))
+                    : p_eff > bw::LOOP_P_MAX   ? al256(size_t(kb_links) * p_eff * p_eff * sizeof(z64))
+                                               : 0;
   const size_t bW = kind == LoopKind::Nested ? al256(size_t(K) * n * m * sizeof(z64)) : 0;
   bool transport_only = false;
   if (kind == LoopKind::Nested) {
@@ -972,7 +974,11 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   la.u_df = use_df ? 1 : 0;
   la.df_overlaps = mx ? 1 : 0;
   if (kind == LoopKind::Plaquette) {
-    BW_CUDA(bw::launch_plaquettes(la, Lx, Ly, phases, chern_out, s), "plaquette kernels");
+    if (p_eff <= bw::LOOP_P_MAX)
+      BW_CUDA(bw::launch_plaquettes(la, Lx, Ly, phases, chern_out, s), "plaquette kernels");
+    else
+      BW_CUDA(bw::launch_plaquettes_big(la, M, kb_links, Lx, Ly, phases, chern_out, s),
+              "plaquette link GEMM and determinant kernels");
     prof_mark(ctx, s, "plaquettes");
     end_call(ctx, s);
     return BW_OK;
