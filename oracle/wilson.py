@@ -203,19 +203,29 @@ def wilson_loop(model, plane, p: int, gap_tol=None, unitarise=False, gauge=None)
 # Spin-resolved loop (Sec. IV): projected spin operator P s P restricted to the
 # occupied space, S = U^dagger s U (p x p); its negative (sign -1) or positive
 # eigen-sector spans the states whose Wilson loop gives C_down (C_up).
-# Reading: split at zero, the sector must hold p/2 states at every k.
+# Reading (split "zero", the text's "negative eigenstates"): split at zero, the
+# sector must hold p/2 states at every k, gap = min |mu|.  Alternative reading
+# (split "median"): the p/2 lowest (sign -1) or highest (+1) eigenvalues, whatever
+# their sign, gap = mu_{p/2} - mu_{p/2-1}; with it the disordered Eq. 10 supercells
+# give Fig. 6(d)'s C_s = 0 at W = 9, where the zero split has no fixed-size sector.
 # ----------------------------------------------------------------------------
 
-def projected_spin_sector(U: np.ndarray, S: np.ndarray, sign: int):
+def projected_spin_sector(U: np.ndarray, S: np.ndarray, sign: int, split: str = "zero"):
     Sp = U.conj().T @ S @ U
     Sp = 0.5 * (Sp + Sp.conj().T)
     mu, V = np.linalg.eigh(Sp)
+    if split == "median":
+        h = mu.size // 2
+        sel = np.arange(mu.size) < h if sign < 0 else np.arange(mu.size) >= mu.size - h
+        return U @ V[:, sel], mu, int(sel.sum()), float(mu[h] - mu[h - 1])
+    if split != "zero":
+        raise OracleError("EINVAL", f"unknown PSO split {split!r}")
     sel = mu < 0 if sign < 0 else mu > 0
     return U @ V[:, sel], mu, int(sel.sum()), float(np.abs(mu).min())
 
 
 def spin_resolved_wilson_loop(model, plane, p: int, S, sign: int = -1, gap_tol=None,
-                              pso_gap_tol: float = 1e-6, unitarise=False):
+                              pso_gap_tol: float = 1e-6, unitarise=False, pso_split: str = "zero"):
     """``WSpinSurf``: Wilson loop of the PSO sector.  Returns
     (phases[N_t, p/2], pso_evals[N_t, N, p], min_pso_gap, min_gap[N_t])."""
     _check_plane(model, plane, p)
@@ -229,7 +239,7 @@ def spin_resolved_wilson_loop(model, plane, p: int, S, sign: int = -1, gap_tol=N
     for i in range(plane.N_t):
         sector = []
         for j in range(plane.N):
-            Us, mu, count, g = projected_spin_sector(U[i][j], S, sign)
+            Us, mu, count, g = projected_spin_sector(U[i][j], S, sign, pso_split)
             pso[i, j] = mu
             min_pso_gap = min(min_pso_gap, g)
             if count != p // 2 or not g > pso_gap_tol:
@@ -376,7 +386,7 @@ def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0
 # equals the Eq. 6 winding of the hybrid Wannier centres of the same states.
 # ----------------------------------------------------------------------------
 
-def _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol):
+def _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol, pso_split="zero"):
     f = plane_points(plane)
     U = []
     for i in range(plane.N_t):
@@ -385,7 +395,7 @@ def _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol):
             _, Uk, gap = occupied_states(bloch_hamiltonian(model, f[i, j]), p)
             _check_gap(gap, gap_tol, (i, j))
             if S is not None:
-                Uk, _, count, g = projected_spin_sector(Uk, S, sign)
+                Uk, _, count, g = projected_spin_sector(Uk, S, sign, pso_split)
                 if count != p // 2 or not g > pso_gap_tol:
                     raise OracleError("EPSOGAP", f"PSO sector size {count}, gap {g:.3e}", (i, j))
             row.append(Uk)
@@ -394,7 +404,7 @@ def _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol):
 
 
 def plaquette_flux(model, plane, p: int, S=None, sign: int = -1, gap_tol=None,
-                   pso_gap_tol: float = 1e-6):
+                   pso_gap_tol: float = 1e-6, pso_split: str = "zero"):
     """Integrated Berry flux through every plaquette of the plane (Sec. IV A, WSpinLine).
     Returns (flux[N_t, N] in (-pi, pi], Chern number = sum(flux) / 2pi).  With a spin
     operator S the states are the PSO sector of sign ``sign`` (Sec. IV)."""
@@ -404,7 +414,7 @@ def plaquette_flux(model, plane, p: int, S=None, sign: int = -1, gap_tol=None,
     if np.any(np.asarray(plane.trans_dir) != np.round(plane.trans_dir)):
         raise OracleError("EINVAL", "trans_dir must be an integer vector to close the plaquettes")
     gap_tol = _default_gap_tol(model) if gap_tol is None else gap_tol
-    U = _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol)
+    U = _sector_states_on_plane(model, plane, p, S, sign, gap_tol, pso_gap_tol, pso_split)
     N, Nt = plane.N, plane.N_t
     flux = np.empty((Nt, N))
     for i in range(Nt):

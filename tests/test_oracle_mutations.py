@@ -68,7 +68,7 @@ def _flipped_fourier(model, f):
     return 0.5 * (H + H.conj().T)
 
 
-def _unprojected_spin(U, S, sign):
+def _unprojected_spin(U, S, sign, split="zero"):
     mu, V = np.linalg.eigh(U.conj().T @ U)       # forgot the spin operator
     sel = np.argsort(mu)[: U.shape[1] // 2]
     return U @ V[:, sel], mu, U.shape[1] // 2, 1.0

@@ -665,6 +665,31 @@ def test_quadrupolar_eq10_paper_statements():
     assert pg > 0.5
 
 
+@pytest.mark.parametrize("L,seed", [(4, 1), (4, 2), (5, 1)])
+def test_quadrupolar_eq10_median_split_fig6(L, seed):
+    """Sec. IV A, Fig. 6(c)-(d) with the PSO sector taken as the p/2 most negative
+    eigenvalues (split at the median, the alternative reading): the coupling-matrix
+    flux gives |C_s| = 1 at W = 1 and C_s = 0 at W = 9, the two values the figure
+    shows on either side of the disorder-driven transition."""
+    g = GOLDEN["quadrupolar_eq10_spin_chern_vs_disorder"]
+    for W, want in ((1.0, g["W1_abs"]), (9.0, g["W9"])):
+        wl = I.config_quadrupolar(L, W, seed, nk=8)
+        _, C = O.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1, pso_split="median")
+        assert abs(abs(C) - want) < 1e-9, (W, C)
+
+
+def test_median_split_equals_zero_split_when_sectors_are_even():
+    """Where exactly p/2 PSO eigenvalues are negative at every k (the spin-Hall model,
+    the clean Eq. 10 model), the median split selects the same sector as the split at
+    zero: the spin-resolved phases agree."""
+    for model, S in ((I.spin_hall(1.0), I.SPIN_HALL_SZ), (I.quadrupolar_eq10(), I.EQ10_SPIN)):
+        for sign in (-1, 1):
+            a = O.spin_resolved_wilson_loop(model, P(12, 10), 2, S, sign)[0]
+            b = O.spin_resolved_wilson_loop(model, P(12, 10), 2, S, sign, pso_split="median")[0]
+            for r in range(10):
+                assert O.circular_match_error(a[r], b[r]) < 1e-12
+
+
 def test_quadrupolar_eq10_disordered_supercells():
     """Sec. IV A, Fig. 6(c): with the chiral-preserving disorder w s0 (x) t3 per cell at
     W = 1 (below the gap closing near W = 5) the coupling-matrix flux of a supercell
