@@ -114,6 +114,10 @@ typedef struct {
   double wannier_gap_tol; /* phase gap around the nested sector; default 1e-6 rad   */
   int32_t unitarise;      /* 1: replace each overlap by its unitary polar factor    */
   int32_t max_sweeps;     /* Jacobi sweep cap; 0 = default (30)                     */
+  int32_t pso_split;      /* PSO sector (Sec. IV): 0 = the eigenvalues of sign `sign`
+                             (split at zero, p/2 of them required; gap min |mu|);
+                             1 = the p/2 lowest (sign -1) or highest (+1) eigenvalues
+                             (split at the median; gap mu_{p/2} - mu_{p/2-1})      */
 } bw_opts;
 
 /* Context: binds device `device`, allocates nothing yet.  mem_budget_bytes bounds

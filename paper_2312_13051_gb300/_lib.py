@@ -48,7 +48,7 @@ class bw_plane_stack(C.Structure):
 class bw_opts(C.Structure):
     _fields_ = [("gap_tol", C.c_double), ("pso_gap_tol", C.c_double),
                 ("wannier_gap_tol", C.c_double), ("unitarise", C.c_int32),
-                ("max_sweeps", C.c_int32)]
+                ("max_sweeps", C.c_int32), ("pso_split", C.c_int32)]
 
 
 class bw_request_info(C.Structure):
@@ -265,9 +265,15 @@ def _plane_arg(plane):
     return _plane(plane), "", (), plane
 
 
-def _opts(gap_tol=-1.0, pso_gap_tol=-1.0, wannier_gap_tol=-1.0, unitarise=False, max_sweeps=0):
+PSO_SPLIT = {"zero": 0, "median": 1}
+
+
+def _opts(gap_tol=-1.0, pso_gap_tol=-1.0, wannier_gap_tol=-1.0, unitarise=False, max_sweeps=0,
+          pso_split="zero"):
+    if pso_split not in PSO_SPLIT:
+        raise BWError(1, f"pso_split must be one of {sorted(PSO_SPLIT)}")
     return bw_opts(float(gap_tol), float(pso_gap_tol), float(wannier_gap_tol), int(unitarise),
-                   int(max_sweeps))
+                   int(max_sweeps), PSO_SPLIT[pso_split])
 
 
 def _empty(shape, dtype, device):

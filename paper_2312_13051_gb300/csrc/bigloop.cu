@@ -330,7 +330,7 @@ cudaError_t launch_spin_apply(const z64* U, z64* Y, long long W, int n, int p, c
 }
 
 __global__ void k_pso_post(const double* nu, int nval, long long W, long long k0, int p,
-                           double sigma, double tol, double* pso_evals, double* pso_gap,
+                           double sigma, double tol, int median, double* pso_evals, double* pso_gap,
                            DevStatus* status) {
   const long long kw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (kw >= W) return;
@@ -338,19 +338,19 @@ __global__ void k_pso_post(const double* nu, int nval, long long W, long long k0
   const int h = p / 2;
   const long long k = k0 + kw;
   const double lo = v[h - 1], hi = v[h];
-  const double g = fmin(fabs(lo), fabs(hi));
+  const double g = median ? hi - lo : fmin(fabs(lo), fabs(hi));
   if (pso_gap) pso_gap[k] = g;
   if (pso_evals)
     for (int c = 0; c < p; ++c) pso_evals[k * p + c] = sigma > 0.0 ? v[c] : -v[p - 1 - c];
-  if (!(lo < 0.0 && hi > 0.0 && g > tol)) report(status, ST_EPSOGAP, k, g);
+  if (!((median || (lo < 0.0 && hi > 0.0)) && g > tol)) report(status, ST_EPSOGAP, k, g);
 }
 
 cudaError_t launch_pso_post(const double* nu, int nval, long long W, long long k0, int p,
-                            double sigma, double tol, double* pso_evals, double* pso_gap,
+                            double sigma, double tol, int median, double* pso_evals, double* pso_gap,
                             DevStatus* status, cudaStream_t s) {
   if (W <= 0) return cudaSuccess;
-  k_pso_post<<<unsigned((W + 127) / 128), 128, 0, s>>>(nu, nval, W, k0, p, sigma, tol, pso_evals,
-                                                       pso_gap, status);
+  k_pso_post<<<unsigned((W + 127) / 128), 128, 0, s>>>(nu, nval, W, k0, p, sigma, tol, median,
+                                                       pso_evals, pso_gap, status);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct StatesArgs {
   DevOp op;             // op.nnz == 0: no spin split
   int sign;
   double pso_gap_tol;
+  int pso_median;       // sector = the p/2 lowest / highest PSO eigenvalues (split at the median)
   // outputs
   z64* U;               // K x n x p_out
   double* gap;          // K
@@ -208,10 +209,11 @@ cudaError_t launch_spin_apply(const z64* U, z64* Y, long long W, int n, int p, c
                               const int* col, const z64* val, double sigma, cudaStream_t s);
 // From the ascending eigenvalues nu (W x nval) of sigma S_occ per wave slot: the PSO
 // eigenvalues mu = sigma nu ascending into pso_evals (K x p, optional, needs nval = p),
-// min |mu| around the split into pso_gap[k] and BW_EPSOGAP unless nu_{h-1} < 0 < nu_h
-// with min |nu| > tol (h = p / 2).
+// the PSO gap into pso_gap[k] and BW_EPSOGAP unless it exceeds tol (h = p / 2): split
+// at zero, gap min |nu_{h-1}|, |nu_h| and nu_{h-1} < 0 < nu_h required; split at the
+// median (median != 0), gap nu_h - nu_{h-1}.
 cudaError_t launch_pso_post(const double* nu, int nval, long long W, long long k0, int p,
-                            double sigma, double tol, double* pso_evals, double* pso_gap,
+                            double sigma, double tol, int median, double* pso_evals, double* pso_gap,
                             DevStatus* status, cudaStream_t s);
 
 // off[t] = t stride, idx[t] = t for t < W (wave slot -> explicit matrix).

@@ -382,6 +382,7 @@ bw_status upload(bw_ctx* ctx, const Blob& b, char* dst, cudaStream_t s) {
 struct Opts {
   double gap_tol, pso_gap_tol, wannier_gap_tol;
   int unitarise, max_sweeps;
+  int pso_median;  // bw_opts.pso_split (0 or 1; anything else is rejected by the callers)
 };
 
 Opts resolve_opts(const bw_opts* o, double tmax) {
@@ -391,6 +392,7 @@ Opts resolve_opts(const bw_opts* o, double tmax) {
   r.wannier_gap_tol = (o && o->wannier_gap_tol >= 0.0) ? o->wannier_gap_tol : 1e-6;
   r.unitarise = o ? o->unitarise : 0;
   r.max_sweeps = (o && o->max_sweeps > 0) ? o->max_sweeps : 30;
+  r.pso_median = o ? o->pso_split : 0;
   return r;
 }
 
@@ -456,6 +458,7 @@ bw::DevPlane dev_plane(const PlaneX& X) {
 struct PsoSplit {
   int n = 0, p = 0, pl = 0, pnval = 0;
   double sigma = 1.0, tol = 0.0;
+  int median = 0;
   z64 *Yw = nullptr, *Sw = nullptr, *Vw = nullptr;
   const int* rowp = nullptr;
   const int* col = nullptr;
@@ -545,7 +548,7 @@ bw_status pso_split_wave(bw_ctx* ctx, PsoSplit& X, const z64* Uw, long long Wn, 
   X.ps.W = Wn;
   BW_CUDA(bw::launch_states_large(X.ps, s), "spin operator eigensolve");
   BW_CUDA(bw::launch_pso_post(reinterpret_cast<const double*>(X.ps.lam), X.pnval, Wn, k0, p, X.sigma, X.tol,
-                              X.pso_evals, X.psog, ctx->status, s),
+                              X.median, X.pso_evals, X.psog, ctx->status, s),
           "spin sector check");
   std::memset(&g, 0, sizeof(g));
   g.A = Uw; g.B = X.Vw; g.C = dst;
@@ -658,6 +661,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
     Uw = reinterpret_cast<z64*>(carve(ctx, Wv * sp_U));
     if ((st = pso_split_setup(ctx, X, Wv, n, p, *op, dblob, sign, o.pso_gap_tol, pso_evals, psog, &hook, s)))
       return st;
+    X.median = o.pso_median;
   }
   prof_start(ctx, s);
   const long long sU = (long long)n * pl, sP = (long long)pl * pl;
@@ -777,6 +781,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
                    (kind == LoopKind::Spin && large && p > 64);
   const Opts o = resolve_opts(opts, P.tmax);
   if (o.unitarise && p_eff > 32) return fail(ctx, BW_EINVAL, "unitarise supports p <= 32");
+  if (o.pso_median != 0 && o.pso_median != 1)
+    return fail(ctx, BW_EINVAL, "pso_split must be 0 (split at zero) or 1 (at the median), got %d",
+                o.pso_median);
   const long long K = (long long)plane->N * plane->N_t;
   Blob blob;
   plan_to_blob(P, blob);
@@ -874,6 +881,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     sa.op.val = reinterpret_cast<const z64*>(dblob + op.o_val);
     sa.sign = sign;
     sa.pso_gap_tol = o.pso_gap_tol;
+    sa.pso_median = o.pso_median;
     sa.pso_evals = pso_evals;
     sa.pso_gap = psog;
   }
@@ -940,6 +948,7 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     if (spin && (st = pso_split_setup(ctx, X, Wv, n, p, op, dblob, sign, o.pso_gap_tol, pso_evals, psog,
                                       &hook, s)))
       return st;
+    X.median = o.pso_median;
     for (long long k0 = 0; k0 < K; k0 += Wv) {
       lg.k0 = k0;
       lg.W = std::min(Wv, K - k0);

@@ -246,8 +246,9 @@ __device__ double refine_mixed(const z64* H, const c32* V, const int* ord, const
 }
 
 // Projected spin operator sector (Sec. IV): S = U^dagger s U (p x p), eigh, keep the
-// eigenvectors with eigenvalue sign `sign`; Us = U V_s written to `out` (n x p/2).
-__device__ void pso_split(const z64* U, const DevOp& op, int sign, int n, int p, z64* S,
+// eigenvectors with eigenvalue sign `sign` (split at zero), or the p/2 lowest / highest
+// (median); Us = U V_s written to `out` (n x p/2).
+__device__ void pso_split(const z64* U, const DevOp& op, int sign, int median, int n, int p, z64* S,
                           z64* SV, int* ord, double* mu, JacRot<double>* rot, double* red,
                           int max_sweeps, z64* out, double* pso_out, double* pso_gap_out,
                           double pso_tol, DevStatus* st, long long k) {
@@ -284,6 +285,10 @@ __device__ void pso_split(const z64* U, const DevOp& op, int sign, int n, int p,
     for (int c = 0; c < p; ++c) {
       neg += mu[c] < 0.0;
       g = fmin(g, fabs(mu[c]));
+    }
+    if (median) {
+      neg = h;
+      g = mu[h] - mu[h - 1];
     }
     if (pso_out)
       for (int c = 0; c < p; ++c) pso_out[c] = mu[c];
@@ -379,7 +384,7 @@ __global__ void k_states_small(StatesArgs a, int p_out) {
     }
     z64* out = a.U + k * (long long)n * p_out;
     if (a.op.nnz > 0) {
-      pso_split(Q, a.op, a.sign, n, p, G, Zg, ord2, rho, rot64, red, a.max_sweeps, out,
+      pso_split(Q, a.op, a.sign, a.pso_median, n, p, G, Zg, ord2, rho, rot64, red, a.max_sweeps, out,
                 a.pso_evals ? a.pso_evals + k * p : nullptr, a.pso_gap ? a.pso_gap + k : nullptr,
                 a.pso_gap_tol, a.status, k);
     } else {

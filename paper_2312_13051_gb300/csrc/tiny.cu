@@ -280,6 +280,10 @@ k_states_tiny(StatesArgs a, int use_tab) {
         g = fmin(g, fabs(mu[c]));
         if (a.pso_evals) a.pso_evals[k * PP + c] = mu[c];
       }
+      if (a.pso_median) {
+        neg = PP / 2;
+        g = mu[PP / 2] - mu[PP / 2 - 1];
+      }
       if (a.pso_gap) a.pso_gap[k] = g;
       if (!okp) report(a.status, ST_ENOCONV, k, 0.0);
       if (neg != PP / 2 || !(g > a.pso_gap_tol)) report(a.status, ST_EPSOGAP, k, g);

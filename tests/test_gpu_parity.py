@@ -840,3 +840,45 @@ def test_row_blocks_match_whole_plane(lib, ctx, case):
             ph, gap = compute(model, shard.row_block(plane, i0, i1), p)
             assert circ_err_rows(ph, full[i0:i1]) <= 1e-12
             np.testing.assert_allclose(gap, gfull[i0:i1], atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pso_median_split_fig6(lib, ctx, precision):
+    """The PSO sector split at the median (bw_opts.pso_split = 1) on the Eq. 10
+    supercells: flux of every plaquette against the oracle's median-split reading, and
+    Fig. 6(c)-(d)'s spin-Chern numbers, |C_s| = 1 at W = 1 and C_s = 0 at W = 9 (where the
+    split at zero reports EPSOGAP)."""
+    for W, want in ((1.0, 1.0), (9.0, 0.0)):
+        wl = I.config_quadrupolar(4, W, 1, nk=6)
+        rflux, rC = oracle.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1, pso_split="median")
+        flux, C, _, pg = lib.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1, precision=precision,
+                                            ctx=ctx, pso_split="median")
+        d = np.abs(np.angle(np.exp(1j * (flux.cpu().numpy() - rflux))))
+        assert d.max() <= TOL[precision]
+        assert abs(abs(C.item()) - want) < 1e-8 and abs(C.item() - rC) < 1e-8
+        assert pg.min().item() > 0
+    wl = I.config_quadrupolar(4, 9.0, 1, nk=6)
+    with pytest.raises(lib.BWError) as e:
+        lib.plaquette_flux(wl.model, wl.plane, wl.p, wl.spin_op, -1, precision=precision, ctx=ctx)
+    assert e.value.status == "EPSOGAP"
+
+
+@pytest.mark.parametrize("case", ["eq10_clean_n4", "eq10_L2_n16", "eq10_L4_n64"])
+def test_pso_median_split_spin_resolved_parity(lib, ctx, case):
+    """Spin-resolved phases with the median split against the oracle, on the one-thread
+    (n = 4), shared-memory (n = 16) and tridiagonal (n = 64) paths, both signs."""
+    if case == "eq10_clean_n4":
+        model, S, plane, p = I.quadrupolar_eq10(), I.EQ10_SPIN, P(12, 10), 2
+    elif case == "eq10_L2_n16":
+        wl = I.config_quadrupolar(2, 9.0, 3, nk=6)
+        model, S, plane, p = wl.model, wl.spin_op, P(8, 6), wl.p
+    else:
+        wl = I.config_quadrupolar(4, 9.0, 2, nk=6)
+        model, S, plane, p = wl.model, wl.spin_op, P(6, 5), wl.p
+    for sign in (-1, 1):
+        ref, rpso, _, _ = oracle.spin_resolved_wilson_loop(model, plane, p, S, sign, pso_split="median")
+        for precision in ("fp64", "mixed"):
+            ph, pso, pg, _ = lib.spin_resolved_wilson_loop(model, plane, p, S, sign, precision=precision,
+                                                           ctx=ctx, pso_split="median")
+            assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
+            assert np.abs(pso.cpu().numpy().reshape(rpso.shape) - rpso).max() <= 1e-7
