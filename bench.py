@@ -413,6 +413,16 @@ def time_graph(lib, ctx, wl, precision, steps, warmup, flush, dev, nested=True):
     return time_call_graph(ctx, call, out, steps, warmup, flush, dev)
 
 
+def _eig_frac(fl, st, peak):
+    """Algorithmic eigensolve flops (16/3 n^3 + 8 n^2 nbt per k-point) over the time of
+    the eigensolve stages (tridiagonalisation, bisection, inverse iteration,
+    back-transform), as a fraction of `peak` TFLOP/s."""
+    ms = sum(st.get(k, 0.0) for k in ("lg_tridiag", "lg_bisect", "lg_invit", "lg_backtransform"))
+    if ms <= 0.0:
+        return None
+    return (fl["lg_tridiag"] + fl["lg_backtransform"]) / (ms * 1e-3) / 1e12 / peak
+
+
 def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed):
     """Algorithmic flops of each stage of the n > 32 Wilson-loop call over K = N Nt
     k-points (complex multiply-add = 8 flops): Householder tridiagonalisation 16/3 n^3,
@@ -421,11 +431,12 @@ def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed):
     for the eigenphases of each loop; bisection and inverse iteration are O(n p)."""
     K = N * Nt
     nbt = min(n, p + 1) if mixed else p
-    fl = {"tridiag": K * 16.0 / 3.0 * n ** 3, "backtransform": K * 8.0 * n * n * nbt,
+    # keys: the stage names the library's per-kernel timing marks carry
+    fl = {"lg_tridiag": K * 16.0 / 3.0 * n ** 3, "lg_backtransform": K * 8.0 * n * n * nbt,
           "overlaps": K * 8.0 * n * p * p, "loops": Nt * (N * 8.0 * p ** 3 + 10.0 * p ** 3),
-          "build": K * 8.0 * nnz_groups}
+          "lg_build": K * 8.0 * nnz_groups}
     if mixed:
-        fl["refine"] = K * (8.0 * nnz_groups * p + 16.0 * n * (n - p) * p + 16.0 * n * p * p)
+        fl["lg_refine"] = K * (8.0 * nnz_groups * p + 16.0 * n * (n - p) * p + 16.0 * n * p * p)
     return fl
 
 
@@ -674,11 +685,7 @@ def run_ours(args):
                                                       "FP32 pipe the mixed stages run on)"
                                                       if prec == "mixed" else
                                                       "measured cuBLAS DGEMM 4096^3 (FP64 pipe)"),
-                                      "eigensolve_frac": (sum(fl[k] for k in ("tridiag", "backtransform")
-                                                              if k in fl) /
-                                                          (sum(st.get(k, 0.0) for k in
-                                                               ("tridiag", "bisect", "invit",
-                                                                "backtransform")) * 1e-3) / 1e12) / pk_}}
+                                      "eigensolve_frac": _eig_frac(fl, st, pk_)}}
             if "phase_err_rad" in r:
                 blk[prec]["phase_err_rad_sampled_row"] = r["phase_err_rad"]
         for kind in ("spin_mixed", "nested_mixed"):

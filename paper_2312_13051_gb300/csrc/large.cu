@@ -533,7 +533,12 @@ __global__ void k_lg_bisect(LargeArgs a) {
 // partial pivoting (U has two superdiagonals); three solves from a fixed
 // pseudo-random start.  Eigenvalues closer than 1e-3 ||T'|| form a cluster, whose
 // vectors one thread computes in order, orthogonalising each against the earlier
-// ones of its cluster at every iteration.
+// ones of its cluster at every iteration.  Above INVIT_WINDOW_N, where the spectrum
+// of a supercell is so dense that the chained clusters span most of it, a vector is
+// orthogonalised only against the earlier ones within 1e-3 ||T'|| of its eigenvalue:
+// two vectors further apart are orthogonal to ~eps ||T'|| / (1e-3 ||T'||) already, the
+// bound the cluster rule accepts between clusters, and the cost per vector is O(n)
+// instead of O(n x cluster size).
 // Where only the span of the computed vectors matters (subspace_only: the PSO
 // sector), every vector iterates on its own thread at once instead, converging into
 // its cluster's invariant subspace from a distinct start, and a second kernel
@@ -608,6 +613,8 @@ __device__ void tri_solve(int n, T tiny, const Strided<T>& W, long long t) {
   }
 }
 
+constexpr int INVIT_WINDOW_N = 512;
+
 template <typename T>
 __global__ void k_lg_invit(LargeArgs a) {
   const long long NT = a.W * a.nvec;
@@ -627,12 +634,16 @@ __global__ void k_lg_invit(LargeArgs a) {
   T* Z = reinterpret_cast<T*>(a.Z) + kw * (long long)nv * n;   // row-major n x nvec
   const Strided<T> W{reinterpret_cast<T*>(a.work), NT, n};
   const T tiny = fmax(lg_eps<T>() * tn, T(1e-30));
+  const bool windowed = n > INVIT_WINDOW_N;
+  int q0 = idx;  // first earlier vector of the cluster to orthogonalise against
   for (int j = idx; j <= end; ++j) {
+    if (windowed)
+      while (lam[j] - lam[q0] > tolc) ++q0;
     tri_factor(dg, od, n, lam[j], tiny, W, t);
     for (int r = 0; r < n; ++r) W.at(5, r, t) = T(hash_unit((unsigned long long)j * 1000003ull + r));
     for (int it = 0; it < 3; ++it) {
       tri_solve(n, tiny, W, t);
-      for (int q = idx; q < j; ++q) {  // orthogonalise within the cluster
+      for (int q = q0; q < j; ++q) {  // orthogonalise within the cluster (or its window)
         T d = T(0);
         for (int r = 0; r < n; ++r) d += Z[(long long)r * nv + q] * W.at(5, r, t);
         for (int r = 0; r < n; ++r) W.at(5, r, t) -= d * Z[(long long)r * nv + q];
