@@ -423,12 +423,14 @@ def _eig_frac(fl, st, peak):
     return (fl["lg_tridiag"] + fl["lg_backtransform"]) / (ms * 1e-3) / 1e12 / peak
 
 
-def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed):
+def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed, n_ent=None):
     """Algorithmic flops of each stage of the n > 32 Wilson-loop call over K = N Nt
-    k-points (complex multiply-add = 8 flops): Householder tridiagonalisation 16/3 n^3,
-    back-transform of nbt vectors 8 n^2 nbt, refinement 8 nnz p + 16 n (n - p) p +
+    k-points (complex multiply-add = 8 flops): Bloch sum 8 per hopping group,
+    Householder tridiagonalisation 16/3 n^3, back-transform of nbt vectors 8 n^2 nbt,
+    refinement 8 n_ent p (H Q from the n_ent assembled entries of H) + 16 n (n - p) p +
     16 n p^2 (mixed only), overlaps 8 n p^2, loop products 8 p^3 per step plus ~10 p^3
     for the eigenphases of each loop; bisection and inverse iteration are O(n p)."""
+    n_ent = n * n if n_ent is None else n_ent
     K = N * Nt
     nbt = min(n, p + 1) if mixed else p
     # keys: the stage names the library's per-kernel timing marks carry
@@ -436,7 +438,7 @@ def manyband_stage_flops(n, p, N, Nt, nnz_groups, mixed):
           "overlaps": K * 8.0 * n * p * p, "loops": Nt * (N * 8.0 * p ** 3 + 10.0 * p ** 3),
           "lg_build": K * 8.0 * nnz_groups}
     if mixed:
-        fl["lg_refine"] = K * (8.0 * nnz_groups * p + 16.0 * n * (n - p) * p + 16.0 * n * p * p)
+        fl["lg_refine"] = K * (8.0 * n_ent * p + 16.0 * n * (n - p) * p + 16.0 * n * p * p)
     return fl
 
 
@@ -661,6 +663,7 @@ def run_ours(args):
         Km = mb.plane.N * mb.plane.N_t
         nnz_groups = len(np.unique(np.stack([mb.model.i, mb.model.j, mb.model.R[:, 0], mb.model.R[:, 1],
                                              mb.model.R[:, 2]], 1), axis=0))
+        n_ent = len(np.unique(np.stack([mb.model.i, mb.model.j], 1), axis=0))
         blk = {"workload": f"manyband n=256 p=64 101x101 plain Wilson loop ({args.manyband_steps} "
                            "graph replays per precision, L2 flushed between them)",
                "k_points_per_call": Km}
@@ -669,7 +672,7 @@ def run_ours(args):
             ms = r["total_ms"] / r["steps"]
             st = r["stages"]
             fl = manyband_stage_flops(mb.model.n, mb.p, mb.plane.N, mb.plane.N_t, nnz_groups,
-                                      prec == "mixed")
+                                      prec == "mixed", n_ent)
             d = max((k for k in st if k in fl), key=st.get)
             ach = fl[d] / (st[d] * 1e-3) / 1e12
             pk_ = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
