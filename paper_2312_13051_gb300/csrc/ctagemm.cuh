@@ -1,11 +1,12 @@
-// CTA-level building blocks of the large-n solver: a tiled complex GEMM (plain FP32 or
-// FP64, or with compensated sums for FP64-grade results) and the application of a
-// sequence of Householder reflectors, one at a time on column panels in shared memory
-// or in blocks (compact WY form) through that GEMM.  Both keep operand reuse in
-// shared memory instead of L2.
+// CTA-level building blocks of the large-n solver: a tiled complex GEMM with compensated
+// sums for FP64-grade results (the plain FP32 products run on the tensor cores,
+// tcgen05.cuh) and the application of a sequence of Householder reflectors, one at a
+// time on column panels in shared memory (FP64) or in blocks (compact WY form) through
+// tensor-core GEMMs (FP32).  Both keep operand reuse in shared memory instead of L2.
 #pragma once
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace bw {
 
@@ -56,25 +57,6 @@ struct CDF {
 
 
 // Operand and accumulator policies of cta_gemm.
-struct GemmPlain {  // C = A B in FP32
-  using TA = c32;
-  using TB = c32;
-  using Acc = c32;
-  static constexpr bool kPrefetch = true;
-  static __device__ __forceinline__ TA zero_a() { return c32(0.f, 0.f); }
-  static __device__ __forceinline__ Acc zero() { return c32(0.f, 0.f); }
-  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
-};
-template <typename T>
-struct GemmPlainT {  // C = A B in the precision of T
-  using TA = cx<T>;
-  using TB = cx<T>;
-  using Acc = cx<T>;
-  static constexpr bool kPrefetch = true;
-  static __device__ __forceinline__ TA zero_a() { return TA(T(0), T(0)); }
-  static __device__ __forceinline__ Acc zero() { return Acc(T(0), T(0)); }
-  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
-};
 struct SplitC {  // an FP64 value as the float pair hi + lo
   c32 hi, lo;
 };
@@ -213,11 +195,6 @@ __device__ void cta_gemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned c
     }
 }
 
-template <bool A_K_CONTIG, bool B_C_CONTIG, class LA, class LB, class ST>
-__device__ void cta_cgemm(int M, int Ncol, int K, LA la, LB lb, ST st, unsigned char* sm) {
-  cta_gemm<GemmPlain, A_K_CONTIG, B_C_CONTIG>(M, Ncol, K, la, lb, st, sm);
-}
-
 // Applies the reflectors P_c = I - 2 u_c u_c^dag, c = 0 .. n-3 (u_c in column c of
 // A below the diagonal, rows c+1..n-1), to X (n x ncol, leading dimension ldx, in
 // global memory): X <- P_{n-3} ... P_0 X (forward) or X <- P_0 ... P_{n-3} X
@@ -312,25 +289,28 @@ __device__ void cta_reflect(const cx<TA>* A, int n, cx<TX>* X, int ncol, long lo
 // (X <- P_{n-3} ... P_0 X, the adjoint product) runs them first to last with T^dag.
 // Each block builds T once (a CTA GEMM and a triangular recurrence), then per chunk
 // of RW_CW columns of X two CTA GEMMs and a triangular product: a few barriers per
-// block instead of four per reflector.  Requires blockDim.x == 256.
+// block instead of four per reflector.  Requires blockDim.x == 256.  Applies
+// `ts`'s tensor memory (set up by the calling kernel, tcgen05.cuh).
 // ---------------------------------------------------------------------------
 constexpr int RW_NB = 32, RW_CW = 64;
 
-template <typename T>
+// Shared memory of cta_reflect_wy: T, one chunk of W, and the tensor-core GEMM tiles.
 __host__ __device__ inline size_t reflect_wy_smem() {
-  return (size_t(RW_NB) * RW_NB + size_t(RW_NB) * RW_CW) * sizeof(cx<T>) + cg_smem<GemmPlainT<T>>();
+  return (size_t(RW_NB) * RW_NB + size_t(RW_NB) * RW_CW) * sizeof(c32) + tc::SMEM;
 }
 
-template <typename T>
-__device__ void cta_reflect_wy(const cx<T>* A, int n, cx<T>* X, int ncol, long long ldx, bool reverse,
-                               unsigned char* sm) {
-  using C = cx<T>;
+// FP32 (the mixed solver's precision); the three products of each block (V^dag V,
+// V^dag X and X - V W) on the tensor cores.  Returns false when a tensor-core wait gave
+// up (X is then incomplete).
+__device__ inline bool cta_reflect_wy(const c32* A, int n, c32* X, int ncol, long long ldx, bool reverse,
+                                      unsigned char* sm, tc::State& ts) {
+  using C = c32;
   const int tid = threadIdx.x, lane = tid & 31;
   C* Tm = reinterpret_cast<C*>(sm);                 // RW_NB x RW_NB: V^dag V, then T
   C* W = Tm + RW_NB * RW_NB;                        // RW_NB x RW_CW
   unsigned char* gsm = reinterpret_cast<unsigned char*>(W + RW_NB * RW_CW);
   const int nrefl = n - 2;
-  if (nrefl <= 0) return;
+  if (nrefl <= 0) return true;
   const int nblk = (nrefl + RW_NB - 1) / RW_NB;
   for (int bi = 0; bi < nblk; ++bi) {
     const int blk = reverse ? nblk - 1 - bi : bi;
@@ -338,23 +318,24 @@ __device__ void cta_reflect_wy(const cx<T>* A, int n, cx<T>* X, int ncol, long l
     const int r0 = b0 + 1, rows = n - r0;            // rows where the block's vectors live
     // V[r][i] = u_{b0+i}[r] (zero for r <= b0 + i)
     auto v = [&](int r, int i) -> C {
-      return r > b0 + i ? A[(long long)r * n + b0 + i] : C(T(0), T(0));
+      return r > b0 + i ? A[(long long)r * n + b0 + i] : C(0.f, 0.f);
     };
     // Gram matrix V^dag V
-    cta_gemm<GemmPlainT<T>, false, true>(
-        bs, bs, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
-        [&](int q, int i) { return v(r0 + q, i); },
-        [&](int i, int j, const C& g) { Tm[i * RW_NB + j] = g; }, gsm);
+    if (!cta_cgemm_tc<false, true>(
+            bs, bs, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+            [&](int q, int i) { return v(r0 + q, i); },
+            [&](int i, int j, const C& g) { Tm[i * RW_NB + j] = g; }, gsm, ts))
+      return false;
     __syncthreads();
     // T in place (one warp): column i from the columns before it
     if (tid < 32) {
       for (int i = 0; i < bs; ++i) {
-        C t(T(0), T(0));
+        C t(0.f, 0.f);
         if (lane < i)
           for (int k = lane; k < i; ++k) cfma(t, Tm[lane * RW_NB + k], Tm[k * RW_NB + i]);
         __syncwarp();
-        if (lane < i) Tm[lane * RW_NB + i] = T(-2) * t;
-        if (lane == 0) Tm[i * RW_NB + i] = C(T(2), T(0));
+        if (lane < i) Tm[lane * RW_NB + i] = -2.f * t;
+        if (lane == 0) Tm[i * RW_NB + i] = C(2.f, 0.f);
         __syncwarp();
       }
     }
@@ -362,22 +343,23 @@ __device__ void cta_reflect_wy(const cx<T>* A, int n, cx<T>* X, int ncol, long l
     for (int c0 = 0; c0 < ncol; c0 += RW_CW) {
       const int cw = min(RW_CW, ncol - c0);
       // W = V^dag X[:, c0 : c0 + cw]
-      cta_gemm<GemmPlainT<T>, false, true>(
-          bs, cw, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
-          [&](int q, int c) { return X[(long long)(r0 + q) * ldx + c0 + c]; },
-          [&](int i, int c, const C& w) { W[i * RW_CW + c] = w; }, gsm);
+      if (!cta_cgemm_tc<false, true>(
+              bs, cw, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+              [&](int q, int c) { return X[(long long)(r0 + q) * ldx + c0 + c]; },
+              [&](int i, int c, const C& w) { W[i * RW_CW + c] = w; }, gsm, ts))
+        return false;
       __syncthreads();
       // W <- T W (reverse) or T^dag W (forward), in place, one thread per column
       for (int c = tid; c < cw; c += blockDim.x) {
         if (reverse) {
           for (int i = 0; i < bs; ++i) {
-            C acc(T(0), T(0));
+            C acc(0.f, 0.f);
             for (int k = i; k < bs; ++k) cfma(acc, Tm[i * RW_NB + k], W[k * RW_CW + c]);
             W[i * RW_CW + c] = acc;
           }
         } else {
           for (int i = bs - 1; i >= 0; --i) {
-            C acc(T(0), T(0));
+            C acc(0.f, 0.f);
             for (int k = 0; k <= i; ++k) cfma(acc, conj(Tm[k * RW_NB + i]), W[k * RW_CW + c]);
             W[i * RW_CW + c] = acc;
           }
@@ -385,17 +367,19 @@ __device__ void cta_reflect_wy(const cx<T>* A, int n, cx<T>* X, int ncol, long l
       }
       __syncthreads();
       // X[:, chunk] <- X[:, chunk] - V W (rows r0 .. n-1)
-      cta_gemm<GemmPlainT<T>, true, true>(
-          rows, cw, bs, [&](int q, int i) { return v(r0 + q, i); },
-          [&](int i, int c) { return W[i * RW_CW + c]; },
-          [&](int q, int c, const C& y) {
-            C& x = X[(long long)(r0 + q) * ldx + c0 + c];
-            x = x - y;
-          },
-          gsm);
+      if (!cta_cgemm_tc<true, true>(
+              rows, cw, bs, [&](int q, int i) { return v(r0 + q, i); },
+              [&](int i, int c) { return W[i * RW_CW + c]; },
+              [&](int q, int c, const C& y) {
+                C& x = X[(long long)(r0 + q) * ldx + c0 + c];
+                x = x - y;
+              },
+              gsm, ts))
+        return false;
       __syncthreads();
     }
   }
+  return true;
 }
 
 }  // namespace bw

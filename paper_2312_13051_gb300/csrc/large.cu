@@ -732,6 +732,11 @@ __global__ void __launch_bounds__(256, 2) k_lg_backtransform(LargeArgs a, cx<To>
                                                              int ncol, int pw) {
   static_assert(std::is_same<T, To>::value, "the back-transform keeps the solver's precision");
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr bool kTc = std::is_same<T, float>::value;  // FP32: compact WY on the tensor cores
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t tc_bar;
+  tc::State ts{};
+  if constexpr (kTc) ts = tc::setup(&tmem_slot, &tc_bar);
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
     const cx<T>* A = reinterpret_cast<const cx<T>*>(a.A) + kw * (long long)n * n;
@@ -746,11 +751,14 @@ __global__ void __launch_bounds__(256, 2) k_lg_backtransform(LargeArgs a, cx<To>
       }
     }
     __syncthreads();
-    if constexpr (std::is_same<T, double>::value)
+    if constexpr (!kTc) {
       cta_reflect<T, To>(A, n, X, ncol, ncol, true, smem, pw);   // FP64-pipe bound: fewest flops
-    else
-      cta_reflect_wy<T>(A, n, X, ncol, ncol, true, smem);        // latency bound: blocked
+    } else if (!ts.failed) {                                     // blocked, tensor-core GEMMs
+      if (!cta_reflect_wy(A, n, X, ncol, ncol, true, smem, ts) && tid == 0)
+        report(a.status, ST_ETIMEOUT, a.k0 + kw, 0.0);
+    }
   }
+  if constexpr (kTc) tc::teardown(ts);
 }
 
 // FP64 path: direct gap from the bisection eigenvalues.
@@ -791,6 +799,9 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
   double* rho = reinterpret_cast<double*>(smem);     // p + 2
   double* red = rho + p + 2;                         // 64
   unsigned char* work = smem + refine_work_offset(p);  // block reflectors / GEMM tiles
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t tc_bar;
+  tc::State ts = tc::setup(&tmem_slot, &tc_bar);      // plain FP32 products: tensor cores
   for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
     const long long k = a.k0 + kw * (a.kstride > 0 ? a.kstride : 1);
     const c32* A = reinterpret_cast<const c32*>(a.A) + kw * (long long)n * n;
@@ -848,7 +859,7 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
       }
     __syncthreads();
     // C <- D^dag Q_h^dag C
-    cta_reflect_wy<float>(A, n, C, p, p, false, work);
+    bool tc_ok = cta_reflect_wy(A, n, C, p, p, false, work, ts);
     for (int r = warp; r < n; r += nwarp) {
       const c32 d = conj(Dp[r]);
       for (int c = lane; c < p; c += 32) C[(long long)r * p + c] = d * C[(long long)r * p + c];
@@ -859,21 +870,21 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
     const int nu = n - p;
     const int nvec = a.nvec;
     // coef[ua][c] = (Z_u^T C)[ua][c] / (rho_c - lam_{p+ua})
-    cta_cgemm<false, true>(
+    tc_ok = tc_ok && cta_cgemm_tc<false, true>(
         nu, p, n, [&](int ua, int r) { return c32(Z[(long long)r * nvec + p + ua], 0.f); },
         [&](int r, int c) { return C[(long long)r * p + c]; },
         [&](int ua, int c, c32 v) {
           coef[(long long)ua * p + c] = float(1.0 / (rho[c] - double(lam[p + ua]))) * v;
         },
-        work);
+        work, ts);
     __syncthreads();
     // update = Q_h D Z_u coef
-    cta_cgemm<true, true>(
+    tc_ok = tc_ok && cta_cgemm_tc<true, true>(
         n, p, nu, [&](int r, int ua) { return c32(Z[(long long)r * nvec + p + ua], 0.f); },
         [&](int ua, int c) { return coef[(long long)ua * p + c]; },
-        [&](int r, int c, c32 v) { C[(long long)r * p + c] = Dp[r] * v; }, work);
+        [&](int r, int c, c32 v) { C[(long long)r * p + c] = Dp[r] * v; }, work, ts);
     __syncthreads();
-    cta_reflect_wy<float>(A, n, C, p, p, true, work);
+    tc_ok = tc_ok && cta_reflect_wy(A, n, C, p, p, true, work, ts);
     // E = Q^dag Q - I with Q = Q32 + C: Q32^dag Q32 - I compensated (the FP32 basis is
     // orthonormal to ~1e-7, so the difference needs the extra precision), then the
     // small terms Q32^dag C + C^dag (Q32 + C) in FP32 as one GEMM over 2 n rows
@@ -887,7 +898,7 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
         },
         work);
     __syncthreads();
-    cta_cgemm<false, true>(
+    tc_ok = tc_ok && cta_cgemm_tc<false, true>(
         p, p, 2 * n,
         [&](int x, int k) {
           return conj(k < n ? X[(long long)k * nbt + x] : C[(long long)(k - n) * p + x]);
@@ -895,10 +906,10 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
         [&](int k, int y) {
           return k < n ? C[(long long)k * p + y] : X[(long long)(k - n) * nbt + y] + C[(long long)(k - n) * p + y];
         },
-        [&](int x, int y, c32 v) { E[(long long)x * p + y] = E[(long long)x * p + y] + v; }, work);
+        [&](int x, int y, c32 v) { E[(long long)x * p + y] = E[(long long)x * p + y] + v; }, work, ts);
     __syncthreads();
     // Q = (Q32 + C) - (Q32 + C) E / 2, the correction in FP32
-    cta_cgemm<true, true>(
+    tc_ok = tc_ok && cta_cgemm_tc<true, true>(
         n, p, p, [&](int r, int q) { return X[(long long)r * nbt + q] + C[(long long)r * p + q]; },
         [&](int q, int c) { return E[(long long)q * p + c]; },
         [&](int r, int c, c32 v) {
@@ -906,8 +917,9 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
           Q[(long long)r * p + c] = z64(double(x32.re) + double(dc.re) - 0.5 * double(v.re),
                                         double(x32.im) + double(dc.im) - 0.5 * double(v.im));
         },
-        work);
+        work, ts);
     __syncthreads();
+    if (!tc_ok && tid == 0) report(a.status, ST_ETIMEOUT, k, 0.0);
     // gap from FP64 Rayleigh quotients of the FP32 vectors p-1 and p: rho[p-1] is
     // already q^dag H q of vector p-1; H x_p by one warp per row (lanes along the row,
     // coalesced), in FP64
@@ -945,6 +957,7 @@ __global__ void __launch_bounds__(256, 2) k_lg_refine(LargeArgs a) {
     }
     __syncthreads();
   }
+  tc::teardown(ts);
 }
 
 // ---------------------------------------------------------------------------
@@ -1038,14 +1051,14 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   }
   if ((e = lg_common<float>(a, s)) != cudaSuccess) return e;
   if (a.no_refine) return cudaSuccess;
-  const size_t sm = reflect_wy_smem<float>();
+  const size_t sm = reflect_wy_smem();
   static size_t cached = 0;
   if ((e = set_smem_once(k_lg_backtransform<float, float>, sm, cached)) != cudaSuccess) return e;
   k_lg_backtransform<float, float><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
       a, reinterpret_cast<c32*>(a.X), (long long)a.n * a.nbt, a.nbt, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lg_mark(a, "lg_backtransform");
-  const size_t smr = refine_work_offset(a.p) + std::max(reflect_wy_smem<float>(), CG_SMEM);
+  const size_t smr = refine_work_offset(a.p) + std::max(std::max(reflect_wy_smem(), tc::SMEM), CG_SMEM);
   static size_t cached_r = 0;
   if ((e = set_smem_once(k_lg_refine, smr, cached_r)) != cudaSuccess) return e;
   k_lg_refine<<<lg_grid(a.W), LG_THREADS, smr, s>>>(a);
