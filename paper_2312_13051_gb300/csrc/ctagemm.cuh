@@ -57,6 +57,16 @@ struct CDF {
 
 
 // Operand and accumulator policies of cta_gemm.
+template <typename T>
+struct GemmPlainT {  // C = A B in the precision of T
+  using TA = cx<T>;
+  using TB = cx<T>;
+  using Acc = cx<T>;
+  static constexpr bool kPrefetch = true;
+  static __device__ __forceinline__ TA zero_a() { return TA(T(0), T(0)); }
+  static __device__ __forceinline__ Acc zero() { return Acc(T(0), T(0)); }
+  static __device__ __forceinline__ void mac(Acc& c, const TA& a, const TB& b) { cfma(c, a, b); }
+};
 struct SplitC {  // an FP64 value as the float pair hi + lo
   c32 hi, lo;
 };
@@ -381,5 +391,92 @@ __device__ inline bool cta_reflect_wy(const c32* A, int n, c32* X, int ncol, lon
   }
   return true;
 }
+
+// The same compact-WY application with SIMT GEMMs in the precision of T: the FP64
+// back-transform of large n, where a shared-memory panel of the one-reflector form
+// would hold fewer than 16 columns and every panel would sweep all the reflectors.
+template <typename T>
+__host__ __device__ inline size_t reflect_wy_simt_smem() {
+  return (size_t(RW_NB) * RW_NB + size_t(RW_NB) * RW_CW) * sizeof(cx<T>) + cg_smem<GemmPlainT<T>>();
+}
+
+template <typename T>
+__device__ void cta_reflect_wy_simt(const cx<T>* A, int n, cx<T>* X, int ncol, long long ldx, bool reverse,
+                               unsigned char* sm) {
+  using C = cx<T>;
+  const int tid = threadIdx.x, lane = tid & 31;
+  C* Tm = reinterpret_cast<C*>(sm);                 // RW_NB x RW_NB: V^dag V, then T
+  C* W = Tm + RW_NB * RW_NB;                        // RW_NB x RW_CW
+  unsigned char* gsm = reinterpret_cast<unsigned char*>(W + RW_NB * RW_CW);
+  const int nrefl = n - 2;
+  if (nrefl <= 0) return;
+  const int nblk = (nrefl + RW_NB - 1) / RW_NB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = reverse ? nblk - 1 - bi : bi;
+    const int b0 = blk * RW_NB, bs = min(RW_NB, nrefl - b0);
+    const int r0 = b0 + 1, rows = n - r0;            // rows where the block's vectors live
+    // V[r][i] = u_{b0+i}[r] (zero for r <= b0 + i)
+    auto v = [&](int r, int i) -> C {
+      return r > b0 + i ? A[(long long)r * n + b0 + i] : C(T(0), T(0));
+    };
+    // Gram matrix V^dag V
+    cta_gemm<GemmPlainT<T>, false, true>(
+        bs, bs, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+        [&](int q, int i) { return v(r0 + q, i); },
+        [&](int i, int j, const C& g) { Tm[i * RW_NB + j] = g; }, gsm);
+    __syncthreads();
+    // T in place (one warp): column i from the columns before it
+    if (tid < 32) {
+      for (int i = 0; i < bs; ++i) {
+        C t(T(0), T(0));
+        if (lane < i)
+          for (int k = lane; k < i; ++k) cfma(t, Tm[lane * RW_NB + k], Tm[k * RW_NB + i]);
+        __syncwarp();
+        if (lane < i) Tm[lane * RW_NB + i] = T(-2) * t;
+        if (lane == 0) Tm[i * RW_NB + i] = C(T(2), T(0));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < ncol; c0 += RW_CW) {
+      const int cw = min(RW_CW, ncol - c0);
+      // W = V^dag X[:, c0 : c0 + cw]
+      cta_gemm<GemmPlainT<T>, false, true>(
+          bs, cw, rows, [&](int i, int q) { return conj(v(r0 + q, i)); },
+          [&](int q, int c) { return X[(long long)(r0 + q) * ldx + c0 + c]; },
+          [&](int i, int c, const C& w) { W[i * RW_CW + c] = w; }, gsm);
+      __syncthreads();
+      // W <- T W (reverse) or T^dag W (forward), in place, one thread per column
+      for (int c = tid; c < cw; c += blockDim.x) {
+        if (reverse) {
+          for (int i = 0; i < bs; ++i) {
+            C acc(T(0), T(0));
+            for (int k = i; k < bs; ++k) cfma(acc, Tm[i * RW_NB + k], W[k * RW_CW + c]);
+            W[i * RW_CW + c] = acc;
+          }
+        } else {
+          for (int i = bs - 1; i >= 0; --i) {
+            C acc(T(0), T(0));
+            for (int k = 0; k <= i; ++k) cfma(acc, conj(Tm[k * RW_NB + i]), W[k * RW_CW + c]);
+            W[i * RW_CW + c] = acc;
+          }
+        }
+      }
+      __syncthreads();
+      // X[:, chunk] <- X[:, chunk] - V W (rows r0 .. n-1)
+      cta_gemm<GemmPlainT<T>, true, true>(
+          rows, cw, bs, [&](int q, int i) { return v(r0 + q, i); },
+          [&](int i, int c) { return W[i * RW_CW + c]; },
+          [&](int q, int c, const C& y) {
+            C& x = X[(long long)(r0 + q) * ldx + c0 + c];
+            x = x - y;
+          },
+          gsm);
+      __syncthreads();
+    }
+  }
+}
+
+
 
 }  // namespace bw

@@ -761,6 +761,29 @@ __global__ void __launch_bounds__(256, 2) k_lg_backtransform(LargeArgs a, cx<To>
   if constexpr (kTc) tc::teardown(ts);
 }
 
+// FP64 back-transform for large n (a one-reflector panel would hold fewer than 16
+// columns): X = D Z, then the reflectors in compact-WY blocks through FP64 GEMMs.
+__global__ void __launch_bounds__(256, 2) k_lg_backtransform_wy64(LargeArgs a, z64* out, long long out_stride,
+                                                                  int ncol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  for (long long kw = blockIdx.x; kw < a.W; kw += gridDim.x) {
+    const z64* A = reinterpret_cast<const z64*>(a.A) + kw * (long long)n * n;
+    const z64* Dp = reinterpret_cast<const z64*>(a.Dp) + kw * n;
+    const double* Z = reinterpret_cast<const double*>(a.Z) + kw * (long long)a.nvec * n;
+    z64* X = out + kw * out_stride;
+    for (int r = tid >> 5; r < n; r += nt >> 5) {
+      const z64 d = Dp[r];
+      for (int col = tid & 31; col < ncol; col += 32) {
+        const double z = Z[(long long)r * a.nvec + col];
+        X[(long long)r * ncol + col] = z64(d.re * z, d.im * z);
+      }
+    }
+    __syncthreads();
+    cta_reflect_wy_simt<double>(A, n, X, ncol, ncol, true, smem);
+  }
+}
+
 // FP64 path: direct gap from the bisection eigenvalues.
 __global__ void k_lg_gap64(LargeArgs a) {
   const long long kw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1034,13 +1057,22 @@ cudaError_t launch_states_large(const LargeArgs& a, cudaStream_t s) {
   if (!a.mixed) {
     if ((e = lg_common<double>(a, s)) != cudaSuccess) return e;
     if (a.p == 0) return cudaSuccess;  // values only
+    // one-reflector panels while a panel holds at least 16 columns (n <= ~780); beyond,
+    // a panel of a few columns would sweep every reflector once per few columns, so
+    // the reflectors are applied in compact-WY blocks through FP64 GEMMs (pw = 0)
     const int pw = reflect_pw<double>(a.n, size_t(200) << 10);
-    if (pw == 0) return cudaErrorInvalidValue;
-    const size_t sm = reflect_smem<double>(a.n, pw);
-    static size_t cached = 0;
-    if ((e = set_smem_once(k_lg_backtransform<double, double>, sm, cached)) != cudaSuccess) return e;
-    k_lg_backtransform<double, double><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
-        a, a.U, (long long)a.n * a.p, a.p, pw);
+    if (pw >= 16) {
+      const size_t sm = reflect_smem<double>(a.n, pw);
+      static size_t cached = 0;
+      if ((e = set_smem_once(k_lg_backtransform<double, double>, sm, cached)) != cudaSuccess) return e;
+      k_lg_backtransform<double, double><<<lg_grid(a.W), LG_THREADS, sm, s>>>(
+          a, a.U, (long long)a.n * a.p, a.p, pw);
+    } else {
+      const size_t sm = reflect_wy_simt_smem<double>();
+      static size_t cached_wy = 0;
+      if ((e = set_smem_once(k_lg_backtransform_wy64, sm, cached_wy)) != cudaSuccess) return e;
+      k_lg_backtransform_wy64<<<lg_grid(a.W), LG_THREADS, sm, s>>>(a, a.U, (long long)a.n * a.p, a.p);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lg_mark(a, "lg_backtransform");
     if (a.Hin) return cudaSuccess;  // batched eigensolve: every eigenvalue is returned, no gap test
