@@ -813,6 +813,9 @@ def run_profile_case(args):
         elif case == "supercell":
             m10 = I.supercell(I.spin_hall(1.0), 10, W=2.0, seed=5)
             lib.wilson_loop(m10, I.Plane(16, 16), 200, precision=prec, ctx=ctx)
+        elif case == "plaquette":   # past 64 bands: link GEMMs and determinant LU
+            lib.plaquette_flux(I.supercell(I.chern_eq4(1.5), 9), I.Plane(6, 5), 81, precision=prec,
+                               ctx=ctx)
     torch.cuda.synchronize()
     ctx.status()
     print("profile case done:", case, flush=True)
@@ -846,7 +849,7 @@ def main(argv=None):
                     help="precision of the --profile-case calls")
     ap.add_argument("--no-saturated", action="store_true",
                     help="skip the saturated-batch measurement (230 400 k-points per call)")
-    ap.add_argument("--profile-case", choices=["bench", "saturated", "manyband", "supercell"],
+    ap.add_argument("--profile-case", choices=["bench", "saturated", "manyband", "supercell", "plaquette"],
                     help="run --warmup uncaptured calls of one workload and exit (for ncu)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

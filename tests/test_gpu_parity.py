@@ -795,7 +795,8 @@ def test_eigh_batched_mixed_refined_block(lib, ctx, n, n_vec):
     H = torch.tensor(A.reshape(-1), device="cuda")
     ev, vec = lib.eigh_batched(H, [n], n_vec, precision="mixed", ctx=ctx)
     ev, vec = ev.cpu().numpy(), vec.cpu().numpy().reshape(n, n_vec)
-    ref = np.linalg.eigvalsh(A)
+    ref = lam.copy()      # the shift moves the lowest n_vec eigenvalues by -0.5 exactly
+    ref[:n_vec] -= 0.5
     scale = max(1.0, np.abs(ref).max())
     assert np.abs(ev[:n_vec] - ref[:n_vec]).max() <= 1e-10 * scale
     assert np.abs(A @ vec - vec * ev[:n_vec]).max() <= 1e-9 * scale
@@ -882,3 +883,30 @@ def test_pso_median_split_spin_resolved_parity(lib, ctx, case):
                                                            ctx=ctx, pso_split="median")
             assert circ_err_rows(ph.cpu().numpy(), ref) <= TOL[precision]
             assert np.abs(pso.cpu().numpy().reshape(rpso.shape) - rpso).max() <= 1e-7
+
+
+def test_eigh_batched_maximum_size(lib, ctx):
+    """The largest matrix the solver takes, n = 4096 (mixed: FP32 tridiagonal solve,
+    lowest eight vectors refined; a gap of 0.5 opened above them): refined eigenvalues,
+    residual and orthonormality within the mixed bounds, every eigenvalue within FP32
+    accuracy of LAPACK; n = 4097 is refused on the host before any device work."""
+    torch = _torch()
+    n, n_vec = 4096, 8
+    A = I.random_hermitian_batch([n], seed=53)[0]
+    lam, V = np.linalg.eigh(A)
+    A = A - 0.5 * (V[:, :n_vec] @ V[:, :n_vec].conj().T)
+    A = 0.5 * (A + A.conj().T)
+    ev, vec = lib.eigh_batched(torch.tensor(A.reshape(-1), device="cuda"), [n], n_vec,
+                               precision="mixed", ctx=ctx)
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy().reshape(n, n_vec)
+    ref = lam.copy()      # the shift moves the lowest n_vec eigenvalues by -0.5 exactly
+    ref[:n_vec] -= 0.5
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(ev[:n_vec] - ref[:n_vec]).max() <= 1e-10 * scale
+    assert np.abs(A @ vec - vec * ev[:n_vec]).max() <= 1e-9 * scale
+    assert np.abs(vec.conj().T @ vec - np.eye(n_vec)).max() <= 1e-10
+    assert np.abs(ev[n_vec:] - ref[n_vec:]).max() <= 1e-5 * scale
+    big = torch.zeros(4097 * 4097, dtype=torch.complex128, device="cuda")
+    with pytest.raises(lib.BWError) as e:
+        lib.eigh_batched(big, [4097], 1, ctx=ctx)
+    assert e.value.status == "EINVAL"
