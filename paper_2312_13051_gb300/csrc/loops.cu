@@ -837,6 +837,114 @@ __host__ __device__ inline FusedSmem fused_layout(const ScanSmem& Z, int N, int 
   return F;
 }
 
+// The loop of the fused kernel at p = 2 (and, nested, one Wannier band): the same
+// steps as scan_one_loop with the sizes fixed and the work laid out on the states'
+// four-lane groups (group j = tid / 4 holds k-point j, lane l its row l; Q0, Q1 are
+// row l of U(k_j) in registers, Us the same states in shared memory).  Lane l of
+// group j owns entry (l / 2, l % 2) of the 2 x 2 matrices: the overlap M_j, then the
+// prefix product P_j = M_j ... M_0, formed by an inclusive scan over the eight groups
+// of each warp (shuffles) and one over the warp totals (one warp), two CTA barriers
+// in all.  Groups past N repeat the last k-point and write nothing; only the totals
+// of warps followed by k-points are kept (Tw: 8 (ceil(N / 8) - 1) < 4 N entries).
+__device__ void pair_loop_df(const LoopArgs& a, int i, const cdf* Us, const double* gs, cdf Q0,
+                             cdf Q1, unsigned char* smem) {
+  const int N = a.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int l = tid & 3, gw = lane >> 2, g4 = lane & ~3, r = l >> 1, c = l & 1;
+  const int j = tid >> 2;
+  const bool active = j < N;
+  const int jj = active ? j : N - 1;
+  const int nW = (N + 7) >> 3, eoff = 4 * (nW - 1);  // warps holding k-points
+  const ScanSmem Z = scan_layout(N, 2, a.nested ? N * 2 * a.m : 1);
+  cdf* Ps = reinterpret_cast<cdf*>(smem + Z.S);  // P_j entry e at Ps[4 j + e]
+  cdf* Tw = reinterpret_cast<cdf*>(smem + Z.T);  // warp totals, then exclusive products at eoff
+  cdf* Ye = reinterpret_cast<cdf*>(smem + Z.Y);
+  cdf* lamd = reinterpret_cast<cdf*>(smem + Z.vec);
+  z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
+  double* th = reinterpret_cast<double*>(smem + Z.th);
+  double* key = reinterpret_cast<double*>(smem + Z.key);
+  int* ord = reinterpret_cast<int*>(smem + Z.ord);
+  const long long k0 = (long long)i * N;
+  if (a.min_gap && tid < 32) {
+    double g = INFINITY;
+    for (int q = tid; q < N; q += 32) g = fmin(g, gs[q]);
+    for (int o = 16; o > 0; o >>= 1) g = fmin(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if (tid == 0) a.min_gap[i] = g;
+  }
+  if (a.min_pso_gap && tid == 0) a.min_pso_gap[i] = INFINITY;
+  // M_j[r][c] = sum_q conj(U(k_{j+1})[q][r]) U(k_j)[q][c], closing on j = 0
+  const int jn = jj + 1 == N ? 0 : jj + 1;
+  cdf x = cdf_zero();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) cfma_conj(x, Us[(jn * 4 + q) * 2 + r], Us[(jj * 4 + q) * 2 + c]);
+  // x <- x y over the groups of the warp: y from the group d earlier
+  auto step = [&](cdf& v, int src4, bool take) {
+    const cdf a0 = shfl_cdf(v, g4 + 2 * r), a1 = shfl_cdf(v, g4 + 2 * r + 1);
+    const cdf b0 = shfl_cdf(v, src4 + c), b1 = shfl_cdf(v, src4 + 2 + c);
+    if (take) {
+      cdf y = cdf_zero();
+      cfma(y, a0, b0);
+      cfma(y, a1, b1);
+      v = y;
+    }
+  };
+#pragma unroll 1
+  for (int d = 1; d < 8; d <<= 1) step(x, (g4 - 4 * d) & 31, gw >= d);
+  if (gw == 7 && warp < nW - 1) Tw[warp * 4 + l] = x;
+  __syncthreads();
+  if (warp == 0 && nW > 1) {  // lane = 4 v + e holds entry e of warp v's total
+    cdf t = gw < nW - 1 ? Tw[lane] : cdf_zero();
+#pragma unroll 1
+    for (int d = 1; d < 8; d <<= 1) step(t, (g4 - 4 * d) & 31, gw >= d);
+    if (gw < nW - 1) Tw[eoff + 4 * gw + l] = t;  // the product before warp gw + 1
+  }
+  __syncthreads();
+  if (warp > 0 && warp < nW) {  // P_j = (M_j ... M_{8 warp}) (M_{8 warp - 1} ... M_0)
+    const cdf a0 = shfl_cdf(x, g4 + 2 * r), a1 = shfl_cdf(x, g4 + 2 * r + 1);
+    const cdf* E = Tw + eoff + 4 * (warp - 1);
+    cdf y = cdf_zero();
+    cfma(y, a0, E[c]);
+    cfma(y, a1, E[2 + c]);
+    x = y;
+  }
+  if (active) Ps[4 * j + l] = x;
+  __syncthreads();
+  // eigenvalues of W = P_{N-1} on one thread; the two eigenvectors (warp 0) and the
+  // two phases (warp 1) in parallel
+  const cdf* Wl = Ps + 4 * (N - 1);
+  if (tid == 0) eig2_values_df(Wl, lamd);
+  __syncthreads();
+  if (tid < 2 && a.nested) eig2_vector_df(Wl, lamd[tid], tid, Ye);
+  if (tid >= 32 && tid < 34) {
+    lam[tid - 32] = cdf_to_z64(lamd[tid - 32]);
+    th[tid - 32] = phase_of(lam[tid - 32]);
+  }
+  __syncthreads();
+  rank_sort(th, 2, ord);
+  if (tid < 2) a.phases[(long long)i * 2 + tid] = th[ord[tid]];
+  __syncthreads();
+  if (!a.nested) return;
+  nested_sector(a, th, 2, 1, key, ord, i, k0);
+  // nu_j = P_{j-1} nu_0 (nu_0: column ord[first] of Ye), normalised; lanes l and
+  // l + 2 of a group both form entry l % 2
+  const int col = ord[a.first];
+  cdf nu = Ye[c * 2 + col];
+  if (jj > 0) {
+    nu = cdf_zero();
+    cfma(nu, Ps[4 * (jj - 1) + 2 * c], Ye[col]);
+    cfma(nu, Ps[4 * (jj - 1) + 2 * c + 1], Ye[2 + col]);
+  }
+  const cdf nu_o = shfl_cdf(nu, lane ^ 1);
+  const df s = c == 0 ? abs2(nu) + abs2(nu_o) : abs2(nu_o) + abs2(nu);
+  const df inv = df_rsqrt(s);
+  nu = inv * nu;
+  // Wannier state w(j, i) = U(k_j) nu_j, row l on lane l
+  const cdf n0 = shfl_cdf(nu, g4), n1 = shfl_cdf(nu, g4 + 1);
+  cdf wv = cdf_zero();
+  cfma(wv, Q0, n0);
+  cfma(wv, Q1, n1);
+  if (active) reinterpret_cast<cdf*>(a.w)[((long long)j * a.N_t + i) * 4 + l] = wv;
+}
+
 template <bool kNested1>
 __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa, LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -924,7 +1032,10 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
       }
     }
     __syncthreads();
-    scan_one_loop<cdf>(a, i, Us, gs, nullptr, smem);
+    if (!a.nested || a.m == 1)
+      pair_loop_df(a, i, Us, gs, Qf[0], Qf[1], smem);
+    else
+      scan_one_loop<cdf>(a, i, Us, gs, nullptr, smem);
     __syncthreads();
   }
   if constexpr (kNested1) {
