@@ -280,8 +280,16 @@ bool loops_accept_df(const LoopArgs& a);
 bool loops_fused_eligible(const LoopArgs& a, const DevModel& md);
 // *nested_done: the launch also ran the nested loops (one Wannier band, cooperative
 // launch with the whole grid resident), so launch_nested must not run.
+// plan_host (optional, at most FUSED_PLAN_BYTES): the hopping-list plan whose device
+// copy sa.model / sa.row_ptr point into at plan_dev; the launch then carries the plan
+// as a kernel parameter and nothing needs to be copied to plan_dev.
+constexpr int FUSED_PLAN_BYTES = 2048;
+struct alignas(16) FusedPlan {
+  unsigned char bytes[FUSED_PLAN_BYTES];
+};
 cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s,
-                                  bool* nested_done);
+                                  bool* nested_done, const void* plan_host = nullptr,
+                                  size_t plan_bytes = 0, const void* plan_dev = nullptr);
 // Orthonormalised Wannier states w from the transported bases in nu_buf (no-op without).
 cudaError_t launch_wannier(const LoopArgs& a, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 #include <float.h>
 
 #include <cooperative_groups.h>
+#include <cstring>
 #include <type_traits>
 
 #include "df32.cuh"
@@ -945,8 +946,16 @@ __device__ void pair_loop_df(const LoopArgs& a, int i, const cdf* Us, const doub
   if (active) reinterpret_cast<cdf*>(a.w)[((long long)j * a.N_t + i) * 4 + l] = wv;
 }
 
+// The plan arrays as the kernel reads them: in global memory, or (inl != NULL) in the
+// kernel's parameter copy of the plan, at the same offsets from dbase.
+template <typename T>
+__device__ __forceinline__ const T* plan_ptr(const T* p, const unsigned char* inl, const char* dbase) {
+  return inl ? reinterpret_cast<const T*>(inl + (reinterpret_cast<const char*>(p) - dbase)) : p;
+}
+
 template <bool kNested1>
-__global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa, LoopArgs a) {
+__device__ __forceinline__ void loops_fused_body(const StatesArgs& sa, const LoopArgs& a,
+                                                 const unsigned char* inl, const char* dbase) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevModel& md = sa.model;
   const int N = a.N, Nt = a.N_t, nR = md.n_R, tid = threadIdx.x, nt = blockDim.x;
@@ -959,13 +968,18 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
   int* s_col = reinterpret_cast<int*>(smem + F.col);
   int* s_hr = reinterpret_cast<int*>(smem + F.hr);
   float4* s_ht = reinterpret_cast<float4*>(smem + F.ht);
-  for (int e = tid; e < 5; e += nt) s_rowp[e] = sa.row_ptr[e];
-  for (int e = tid; e <= md.n_ent; e += nt) s_ent[e] = md.ent_start[e];
-  for (int e = tid; e < md.n_ent; e += nt) s_col[e] = md.ent_col[e];
+  const int* g_rowp = plan_ptr(sa.row_ptr, inl, dbase);
+  const int* g_ent = plan_ptr(md.ent_start, inl, dbase);
+  const int* g_col = plan_ptr(md.ent_col, inl, dbase);
+  const int* g_hr = plan_ptr(md.hop_r, inl, dbase);
+  const float* g_tdf = plan_ptr(md.hop_tdf, inl, dbase);
+  const int* g_Rv = plan_ptr(md.Rv, inl, dbase);
+  for (int e = tid; e < 5; e += nt) s_rowp[e] = g_rowp[e];
+  for (int e = tid; e <= md.n_ent; e += nt) s_ent[e] = g_ent[e];
+  for (int e = tid; e < md.n_ent; e += nt) s_col[e] = g_col[e];
   for (int h = tid; h < md.n_hop; h += nt) {
-    s_hr[h] = md.hop_r[h];
-    s_ht[h] = make_float4(md.hop_tdf[4 * h], md.hop_tdf[4 * h + 1], md.hop_tdf[4 * h + 2],
-                          md.hop_tdf[4 * h + 3]);
+    s_hr[h] = g_hr[h];
+    s_ht[h] = make_float4(g_tdf[4 * h], g_tdf[4 * h + 1], g_tdf[4 * h + 2], g_tdf[4 * h + 3]);
   }
   double* gs = reinterpret_cast<double*>(smem + F.g);
   cdf* cache = reinterpret_cast<cdf*>(smem + F.cache);
@@ -985,7 +999,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
   const int rbase = nt - 32 * ((nR + 31) / 32);
   for (int i = blockIdx.x; i < Nt; i += gridDim.x) {
     for (int r = tid - rbase; r >= 0 && r < nR; r += nt) {
-      const int* Rv = md.Rv + 3 * r;
+      const int* Rv = g_Rv + 3 * r;
       double x = 0.0;
       int lq = 0, tq = 0, sq = 0;
       for (int dd = 0; dd < 3; ++dd) {
@@ -1047,6 +1061,17 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa,
   }
 }
 
+template <bool kNested1>
+__global__ void __launch_bounds__(FUSED_THREADS) k_loops_fused_df(StatesArgs sa, LoopArgs a) {
+  loops_fused_body<kNested1>(sa, a, nullptr, nullptr);
+}
+
+template <bool kNested1>
+__global__ void __launch_bounds__(FUSED_THREADS)
+    k_loops_fused_df_inl(StatesArgs sa, LoopArgs a, const char* dbase, const __grid_constant__ FusedPlan plan) {
+  loops_fused_body<kNested1>(sa, a, plan.bytes, dbase);
+}
+
 bool loops_fused_eligible(const LoopArgs& a, const DevModel& md) {
   if (!(a.n == 4 && a.p == 2 && a.N >= 1 && 4 * a.N <= FUSED_THREADS && loops_accept_df(a)))
     return false;
@@ -1055,23 +1080,36 @@ bool loops_fused_eligible(const LoopArgs& a, const DevModel& md) {
 }
 
 cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaStream_t s,
-                                  bool* nested_done) {
+                                  bool* nested_done, const void* plan_host, size_t plan_bytes,
+                                  const void* plan_dev) {
   *nested_done = false;
   if (a.N_t <= 0) return cudaSuccess;
+  const bool inl = plan_host && plan_bytes <= sizeof(FusedPlan);
+  if (plan_host && !inl) return cudaErrorInvalidValue;
+  FusedPlan fp;  // the kernel parameter (copied at launch)
+  const char* dbase = static_cast<const char*>(plan_dev);
+  if (inl) {
+    std::memset(fp.bytes, 0, sizeof(fp.bytes));
+    std::memcpy(fp.bytes, plan_host, plan_bytes);
+  }
   const ScanSmem Z = scan_layout(a.N, 2, a.nested ? a.N * 2 * a.m : 1);
   const FusedSmem F = fused_layout(Z, a.N, sa.model.n_R, sa.model.n_ent, sa.model.n_hop);
   cudaError_t e;
   if (a.nested && a.m == 1) {
     // one cooperative launch for the loops and the nested loops when the whole grid
     // is resident at once (one CTA per loop)
-    static size_t cached_c = 0;
-    if ((e = set_smem_once(k_loops_fused_df<true>, F.total, cached_c)) != cudaSuccess) return e;
+    static size_t cached_c = 0, cached_ci = 0;
+    if ((e = inl ? set_smem_once(k_loops_fused_df_inl<true>, F.total, cached_ci)
+                 : set_smem_once(k_loops_fused_df<true>, F.total, cached_c)) != cudaSuccess)
+      return e;
     int dev = 0, sms = 0, coop = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df<true>, FUSED_THREADS,
-                                                           F.total)) != cudaSuccess)
+    if ((e = inl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df_inl<true>,
+                                                                  FUSED_THREADS, F.total)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df<true>,
+                                                                  FUSED_THREADS, F.total)) != cudaSuccess)
       return e;
     if (coop && (long long)per_sm * sms >= a.N_t) {
       cudaLaunchConfig_t cfg = {};
@@ -1084,10 +1122,18 @@ cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaS
       attr[0].val.cooperative = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if ((e = cudaLaunchKernelEx(&cfg, k_loops_fused_df<true>, sa, a)) != cudaSuccess) return e;
+      if ((e = inl ? cudaLaunchKernelEx(&cfg, k_loops_fused_df_inl<true>, sa, a, dbase, fp)
+                   : cudaLaunchKernelEx(&cfg, k_loops_fused_df<true>, sa, a)) != cudaSuccess)
+        return e;
       *nested_done = true;
       return cudaSuccess;
     }
+  }
+  if (inl) {
+    static size_t cached_i = 0;
+    if ((e = set_smem_once(k_loops_fused_df_inl<false>, F.total, cached_i)) != cudaSuccess) return e;
+    k_loops_fused_df_inl<false><<<a.N_t, FUSED_THREADS, F.total, s>>>(sa, a, dbase, fp);
+    return cudaGetLastError();
   }
   static size_t cached = 0;
   if ((e = set_smem_once(k_loops_fused_df<false>, F.total, cached)) != cudaSuccess) return e;

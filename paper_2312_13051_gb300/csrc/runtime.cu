@@ -860,7 +860,6 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   double* psog = bPso ? reinterpret_cast<double*>(carve(ctx, bPso)) : nullptr;
   z64* Lx = bLink ? reinterpret_cast<z64*>(carve(ctx, bLink)) : nullptr;
   z64* Ly = bLink ? reinterpret_cast<z64*>(carve(ctx, bLink)) : nullptr;
-  if ((st = upload(ctx, blob, dblob, s))) return st;
 
   bw::StatesArgs sa;
   std::memset(&sa, 0, sizeof(sa));
@@ -906,6 +905,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     fused = use_df && bw::loops_fused_eligible(q, sa.model);
   }
   sa.want_df = use_df ? 1 : 0;
+  // a small plan rides along as a parameter of the fused kernel (no copy to dblob)
+  const bool plan_inline = fused && blob.data.size() <= sizeof(bw::FusedPlan);
+  if (!plan_inline && (st = upload(ctx, blob, dblob, s))) return st;
   prof_start(ctx, s);
   if (fused) {
     // states are solved inside the loop kernel below
@@ -1008,7 +1010,9 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   }
   bool nested_done = false;
   if (fused) {
-    BW_CUDA(bw::launch_loops_fused_df(sa, la, s, &nested_done), "fused states and loop kernel");
+    BW_CUDA(bw::launch_loops_fused_df(sa, la, s, &nested_done, plan_inline ? blob.data.data() : nullptr,
+                                      blob.data.size(), dblob),
+            "fused states and loop kernel");
   } else {
     if (!bw::loops_form_overlaps(la)) {
       BW_CUDA(bw::launch_overlaps(la, s), "overlap kernel");
