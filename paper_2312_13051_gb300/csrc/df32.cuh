@@ -211,6 +211,110 @@ __device__ inline void eig2_vector_df(const cdf* H, cdf l, int k, cdf* Z) {
   Z[2 + k] = inv * v1;
 }
 
+// ---------------------------------------------------------------------------
+// Unit-circle points and phases in double-float (FP32 pipe; GB300's FP64 pipe runs
+// at 1/64 of the FP32 rate, so a transcendental on one thread of the latency-bound
+// loop kernel costs microseconds in FP64).  Written from the textbook construction:
+// reduction of the angle to |y| <= pi/4 plus a quarter turn, then the Taylor series of
+// sin and cos about 0 by Horner's rule (truncated below 1e-17 at |y| = pi/4), every
+// step with the accurate double-float sum and product; the phase of z refines a float
+// estimate theta0 by the angle of z e^{-i theta0}, which is below 1e-6 in size, so
+// its arctangent equals the ratio to 1e-20.  Errors ~5e-15 (sin, cos) and ~1e-14 rad
+// (phase), at the double-float resolution.  Out of line: one copy of the code serves
+// every caller, so a cold instruction cache fetches it once.
+// ---------------------------------------------------------------------------
+
+// A double constant as a double-float (used in constant expressions only).
+__host__ __device__ constexpr df dfk(double x) { return df(float(x), float(x - double(float(x)))); }
+
+// sin y and cos y, |y| <= pi/4 (a little beyond is harmless).
+static __device__ __noinline__ void df_sincos_small(df y, df& s, df& c) {
+  // sin y / y = sum_k (-1)^k z^k / (2k+1)!, k <= 8; cos y = sum_k (-1)^k z^k / (2k)!, k <= 9
+  constexpr df s8 = dfk(1.0 / 355687428096000.0), s7 = dfk(-1.0 / 1307674368000.0),
+               s6 = dfk(1.0 / 6227020800.0), s5 = dfk(-1.0 / 39916800.0), s4 = dfk(1.0 / 362880.0),
+               s3 = dfk(-1.0 / 5040.0), s2 = dfk(1.0 / 120.0), s1 = dfk(-1.0 / 6.0);
+  constexpr df c9 = dfk(-1.0 / 6402373705728000.0), c8 = dfk(1.0 / 20922789888000.0),
+               c7 = dfk(-1.0 / 87178291200.0), c6 = dfk(1.0 / 479001600.0),
+               c5 = dfk(-1.0 / 3628800.0), c4 = dfk(1.0 / 40320.0), c3 = dfk(-1.0 / 720.0),
+               c2 = dfk(1.0 / 24.0);
+  const df z = y * y;
+  df ps = s8;
+  ps = ps * z + s7;
+  ps = ps * z + s6;
+  ps = ps * z + s5;
+  ps = ps * z + s4;
+  ps = ps * z + s3;
+  ps = ps * z + s2;
+  ps = ps * z + s1;
+  ps = ps * z + df(1.f);
+  df pc = c9;
+  pc = pc * z + c8;
+  pc = pc * z + c7;
+  pc = pc * z + c6;
+  pc = pc * z + c5;
+  pc = pc * z + c4;
+  pc = pc * z + c3;
+  pc = pc * z + c2;
+  pc = pc * z + df(-0.5f);
+  pc = pc * z + df(1.f);
+  s = y * ps;
+  c = pc;
+}
+
+// e^{i (q pi/2 + y)} from sin y, cos y.
+__device__ __forceinline__ cdf df_cis_quarter(int q, df s, df c) {
+  switch (q & 3) {
+    case 0: return cdf(c, s);
+    case 1: return cdf(-s, c);
+    case 2: return cdf(-c, -s);
+    default: return cdf(s, -c);
+  }
+}
+
+// e^{i pi num / den}, den >= 1, |num| < 2^28 (exact reduction in integers).
+static __device__ __noinline__ cdf df_cispi_ratio(int num, int den) {
+  int k = num % (2 * den);
+  if (k < 0) k += 2 * den;
+  const int q = (4 * k + den) / (2 * den);  // nearest quarter turn
+  const int n = 2 * k - q * den;            // y = pi n / (2 den), |n| <= den / 2
+  constexpr df pi = dfk(3.141592653589793);
+  const df r = df_div(df(float(n)), df(float(2 * den)));
+  df sn, cs;
+  df_sincos_small(pi * r, sn, cs);
+  return df_cis_quarter(q, sn, cs);
+}
+
+// e^{i pi t} for a double t.
+static __device__ __noinline__ cdf df_cispi(double t) {
+  t -= 2.0 * rint(0.5 * t);  // exact: t in [-1, 1]
+  const double qd = rint(2.0 * t);
+  const double r = t - 0.5 * qd;  // exact, |r| <= 1/4
+  constexpr df pi = dfk(3.141592653589793);
+  df sn, cs;
+  df_sincos_small(pi * df_from_double(r), sn, cs);
+  return df_cis_quarter(int(qd), sn, cs);
+}
+
+// arg z in (-pi, pi] (as atan2), for z of modest dynamic range (both parts of the
+// float exponent range); z = 0 and NaN take the FP64 atan2 of the leading parts.
+static __device__ __noinline__ double df_phase(cdf z) {
+  const float t0 = atan2f(z.im.hi, z.re.hi);
+  if ((z.re.hi == 0.f && z.im.hi == 0.f) || !(t0 == t0)) return atan2(double(z.im.hi), double(z.re.hi));
+  const int q = __float2int_rn(t0 * 0.636619772f);  // nearest quarter turn
+  constexpr df hp = dfk(1.5707963267948966);
+  const df y = df(t0) - df(float(q) * hp.hi, float(q) * hp.lo);  // q hp exact (|q| <= 2)
+  df sn, cs;
+  df_sincos_small(y, sn, cs);
+  const cdf e = df_cis_quarter(q, sn, cs);  // e^{i t0}
+  // z e^{-i t0} = (x c + y s) + i (y c - x s)
+  const df xr = z.re * e.re + z.im * e.im;
+  const df yr = z.im * e.re - z.re * e.im;
+  double th = double(t0) + df_to_double(df_div(yr, xr));
+  if (th > 3.141592653589793) th -= 6.283185307179586;
+  if (th <= -3.141592653589793) th += 6.283185307179586;
+  return th;
+}
+
 // Warp shuffle of a complex double-float.
 __device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
   return cdf(df(__shfl_sync(0xffffffffu, v.re.hi, src), __shfl_sync(0xffffffffu, v.re.lo, src)),

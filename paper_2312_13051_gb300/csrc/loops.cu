@@ -29,6 +29,8 @@
 namespace bw {
 
 __device__ __forceinline__ double phase_of(z64 z) { return atan2(z.im, z.re); }
+__device__ __forceinline__ double phase_E(z64 z) { return phase_of(z); }
+__device__ __forceinline__ double phase_E(cdf z) { return df_phase(z); }
 
 // Planes stacked along the rows: the nested loop of base point b (of N_s N) runs over
 // the rows of plane s = b / N and closes within it.
@@ -798,7 +800,7 @@ __device__ void nested_base_m1(const LoopArgs& a, int b) {
     prod = prod * acc;
   }
   for (int o = 16; o > 0; o >>= 1) prod = prod * A::shfl_xor(prod, o);
-  if (tid == 0) a.nested_out[b] = phase_of(A::to64(prod));
+  if (tid == 0) a.nested_out[b] = phase_E(prod);
 }
 
 // ---------------------------------------------------------------------------
@@ -860,10 +862,7 @@ __device__ void pair_loop_df(const LoopArgs& a, int i, const cdf* Us, const doub
   cdf* Tw = reinterpret_cast<cdf*>(smem + Z.T);  // warp totals, then exclusive products at eoff
   cdf* Ye = reinterpret_cast<cdf*>(smem + Z.Y);
   cdf* lamd = reinterpret_cast<cdf*>(smem + Z.vec);
-  z64* lam = reinterpret_cast<z64*>(smem + Z.lam);
-  double* th = reinterpret_cast<double*>(smem + Z.th);
-  double* key = reinterpret_cast<double*>(smem + Z.key);
-  int* ord = reinterpret_cast<int*>(smem + Z.ord);
+  int* ord = reinterpret_cast<int*>(smem + Z.ord);  // ord[0]: the sector's eigenvector
   const long long k0 = (long long)i * N;
   if (a.min_gap && tid < 32) {
     double g = INFINITY;
@@ -915,19 +914,40 @@ __device__ void pair_loop_df(const LoopArgs& a, int i, const cdf* Us, const doub
   if (tid == 0) eig2_values_df(Wl, lamd);
   __syncthreads();
   if (tid < 2 && a.nested) eig2_vector_df(Wl, lamd[tid], tid, Ye);
-  if (tid >= 32 && tid < 34) {
-    lam[tid - 32] = cdf_to_z64(lamd[tid - 32]);
-    th[tid - 32] = phase_of(lam[tid - 32]);
+  if (tid >= 32 && tid < 64) {  // warp 1: the two phases, their order and the sector
+    double t = 0.0;
+    if (tid < 34) t = df_phase(lamd[tid - 32]);
+    const double t1 = __shfl_sync(0xffffffffu, t, 1);
+    if (tid == 32) {
+      const double t0 = t;
+      // ascending (stable, NaN last), as rank_sort orders p = 2 phases
+      const bool sw = rank_key(t1) < rank_key(t0);
+      a.phases[(long long)i * 2] = sw ? t1 : t0;
+      a.phases[(long long)i * 2 + 1] = sw ? t0 : t1;
+      if (a.nested) {
+        // sector: position `first` in the order of (theta - cut) mod 2pi (as
+        // nested_sector); its Wannier gap is the distance between the two phases
+        const double two_pi = 6.283185307179586;
+        double key0 = t0 - a.cut, key1 = t1 - a.cut;
+        if (key0 < 0.0) key0 += two_pi;
+        if (key0 < 0.0) key0 += two_pi;
+        if (key0 >= two_pi) key0 = 0.0;
+        if (key1 < 0.0) key1 += two_pi;
+        if (key1 < 0.0) key1 += two_pi;
+        if (key1 >= two_pi) key1 = 0.0;
+        const int lo = rank_key(key1) < rank_key(key0) ? 1 : 0;
+        ord[0] = a.first == 0 ? lo : 1 - lo;
+        const double dd = fabs(t0 - t1), wgap = fmin(dd, two_pi - dd);
+        if (a.min_wannier_gap) a.min_wannier_gap[i] = wgap;
+        if (!(wgap > a.wannier_gap_tol)) report(a.status, ST_EWANGAP, k0, wgap);
+      }
+    }
   }
   __syncthreads();
-  rank_sort(th, 2, ord);
-  if (tid < 2) a.phases[(long long)i * 2 + tid] = th[ord[tid]];
-  __syncthreads();
   if (!a.nested) return;
-  nested_sector(a, th, 2, 1, key, ord, i, k0);
-  // nu_j = P_{j-1} nu_0 (nu_0: column ord[first] of Ye), normalised; lanes l and
+  // nu_j = P_{j-1} nu_0 (nu_0: the sector's column of Ye), normalised; lanes l and
   // l + 2 of a group both form entry l % 2
-  const int col = ord[a.first];
+  const int col = ord[0];
   cdf nu = Ye[c * 2 + col];
   if (jj > 0) {
     nu = cdf_zero();
@@ -986,12 +1006,7 @@ __device__ __forceinline__ void loops_fused_body(const StatesArgs& sa, const Loo
   cdf* tab = reinterpret_cast<cdf*>(smem + F.tab);
   cdf* rowf = reinterpret_cast<cdf*>(smem + F.rowf);
   int* lR = reinterpret_cast<int*>(smem + F.lR);
-  const double inv_N = 2.0 / double(N);
-  for (int m = tid; m < N; m += nt) {
-    double sn, cs;
-    sincospi(double(m) * inv_N, &sn, &cs);
-    tab[m] = cdf_from(z64(cs, sn));
-  }
+  for (int m = tid; m < N; m += nt) tab[m] = df_cispi_ratio(2 * m, N);  // e^{2 pi i m / N}
   const int l = tid & 3, kl = tid >> 2, base = (tid & 31) & ~3;
   const bool active = kl < N;
   const int j = active ? kl : N - 1;  // idle groups recompute the last k-point
@@ -1009,9 +1024,7 @@ __device__ __forceinline__ void loops_fused_body(const StatesArgs& sa, const Loo
         sq += sa.plane.sweep[dd] * Rv[dd];
       }
       x += double(pmod(plane_row_index(sa.plane, i, tq, sq), Nt)) / double(Nt);
-      double sn, cs;
-      sincospi(2.0 * x, &sn, &cs);
-      rowf[r] = cdf_from(z64(cs, sn));
+      rowf[r] = df_cispi(2.0 * x);
       lR[r] = lq;
     }
     __syncthreads();
