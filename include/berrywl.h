@@ -139,6 +139,15 @@ bw_status bw_get_status(bw_ctx* ctx, void* stream, int64_t* k_index);
  * a captured graph are timed as well).  No paper counterpart: measurement only. */
 bw_status bw_set_profiling(bw_ctx* ctx, int enable);
 
+/* Self-test of the double-float unit-circle arithmetic that the mixed four-band loop
+ * kernel uses in place of FP64 transcendentals (phase tables e^{2 pi i m / N}, Bloch
+ * factors e^{i pi t}, eigenphases arg z): runs it on the device against the FP64
+ * sincospi / atan2 of the CUDA math library and writes three maximum absolute errors
+ * to max_err (host, 3 doubles): e^{2 pi i m / N} for 1 <= N <= 64, 0 <= m < N;
+ * e^{i pi t} on 8192 points of [-3, 3); arg z (circular distance, radians) on 4096
+ * angles x radii 0.5, 1, 2.  Synchronous.  No paper counterpart: verification only. */
+bw_status bw_selftest_unit_circle(bw_ctx* ctx, double* max_err);
+
 /* Waits for the last timing event of the most recent profiled call (or replay) and
  * writes up to `max` kernel names (32 bytes each, NUL-terminated; may be NULL) and
  * durations in milliseconds (may be NULL).  Returns the count, -1 on error. */

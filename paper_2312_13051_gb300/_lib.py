@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "bw_server_wait": (i32, [vp, i64, dbl, C.POINTER(bw_request_info)]),
             "bw_server_outstanding": (i64, [vp]),
             "bw_server_cancel": (i32, [vp, i64]),
+            "bw_selftest_unit_circle": (i32, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -131,7 +132,8 @@ def exported_symbols():
             "bw_spin_resolved_wilson_loop", "bw_wilson_loop_stack", "bw_nested_wilson_loop_stack",
             "bw_spin_resolved_wilson_loop_stack", "bw_winding", "bw_z2_largest_gap", "bw_plaquette_flux", "bw_wilson_loop_noalloc", "bw_wilson_loop_workspace",
             "bw_server_create", "bw_server_destroy", "bw_server_last_error", "bw_server_submit",
-            "bw_server_poll", "bw_server_wait", "bw_server_outstanding", "bw_server_cancel"]
+            "bw_server_poll", "bw_server_wait", "bw_server_outstanding", "bw_server_cancel",
+            "bw_selftest_unit_circle"]
 
 
 class Context:
@@ -175,6 +177,13 @@ class Context:
         if n < 0:
             raise BWError(8, "bw_profile_read failed")
         return [(names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), ms[i]) for i in range(n)]
+
+    def selftest_unit_circle(self):
+        """Maximum errors of the double-float e^{2 pi i m / N}, e^{i pi t} and arg z against
+        FP64 on the device (bw_selftest_unit_circle)."""
+        err = (C.c_double * 3)()
+        self.check(self.lib.bw_selftest_unit_circle(self.h, C.cast(err, C.c_void_p)))
+        return tuple(err)
 
     def status(self, stream=None) -> None:
         """Synchronises the stream and raises on a device-side numerical status."""

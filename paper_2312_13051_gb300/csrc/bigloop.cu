@@ -9,7 +9,10 @@
 //                memory (Householder-Hessenberg + shifted QR, the same solver as the
 //                shared-memory path), theta = arg(lambda) sorted ascending, and the
 //                loop's minimum direct gap.
+//  - k_geig_cluster: the same eigenphases on a cluster of CTAs per loop, for larger p.
 #include <float.h>
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cstring>
@@ -367,10 +370,322 @@ cudaError_t launch_iota(long long* off, int* idx, long long W, long long stride,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Eigenphases of large Wilson matrices on a cluster of GC_CTAS CTAs per loop: the
+// same arithmetic as k_geig_big (Householder-Hessenberg, single-shift QR with the
+// same shifts, rotations and deflation tests), organised so that one SM does not
+// wait on one thread:
+//  - Hessenberg: every CTA forms the Householder vector in its shared memory (same
+//    data, same order, same bits); the left update is split over the columns, the
+//    right update over the rows of the cluster; two cluster barriers per column.
+//  - QR sweep in chunks of GC_W rotations: the first warp of CTA 0 chases the bulge
+//    through the window rows [k0-1, kend+1] x columns [k0-1, kend] (kend = k0 + GC_W)
+//    in shared memory and publishes the rotations; then every thread of the cluster
+//    applies the chunk's row rotations to one column right of the window, or its
+//    column rotations to one row above it, in order.  Right of the window only the
+//    chunk's row rotations act and above it only its column rotations, so every
+//    entry receives its rotations in the sequential order.
+//  - The matrix lives in global memory and other SMs of the cluster write it: every
+//    read bypasses L1 (ld.global.cg); the cluster barriers order the accesses.
+// ---------------------------------------------------------------------------
+constexpr int GC_CTAS = 4, GC_W = 16, GC_THREADS = 256;
+constexpr int GC_WR = GC_W + 3, GC_WC = GC_W + 2;  // window rows, columns
+constexpr int GC_MIN_P = 128;                      // smaller p: k_geig_big
+
+struct GcCtl {
+  double mu_re, mu_im;
+  int active, l, hi, fail;
+};
+
+__device__ __forceinline__ z64 ldz(const z64* q) { return z64(__ldcg(&q->re), __ldcg(&q->im)); }
+
+// geig_split_point with L1-bypassing loads, for the first warp.
+__device__ __forceinline__ int gc_split_point(const z64* H, int p, int hi, double eps) {
+  const int lane = threadIdx.x & 31;
+  for (int base = hi; base >= 1; base -= 32) {
+    const int l = base - lane;
+    bool f = false;
+    if (l >= 1)
+      f = geig_negligible_v(ldz(H + (long long)(l - 1) * p + l - 1), ldz(H + (long long)(l - 1) * p + l),
+                            ldz(H + (long long)l * p + l - 1), ldz(H + (long long)l * p + l), eps);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (m) return base - (__ffs(m) - 1);
+  }
+  return 0;
+}
+
+// The bulge chase of rotations k0 .. kend-1 on the window (first warp of CTA 0).
+__device__ void gc_chase(z64* H, int p, int l, int hi, int k0, int kend, z64 mu, z64* win, z64* rot) {
+  const int lane = threadIdx.x & 31;
+  const int rlo = k0 > l ? k0 - 1 : l, rhi = min(kend + 1, hi), clo = rlo, chi = kend;
+  const int nr = rhi - rlo + 1, nc = chi - clo + 1;
+  for (int e = lane; e < nr * nc; e += 32) {
+    const int r = e / nc, c = e - r * nc;
+    win[r * GC_WC + c] = ldz(H + (long long)(rlo + r) * p + clo + c);
+  }
+  __syncwarp();
+#define GCW(r, c) win[((r) - rlo) * GC_WC + ((c) - clo)]
+  for (int k = k0; k < kend; ++k) {
+    const z64 x = k == l ? GCW(l, l) - mu : GCW(k, k - 1);
+    const z64 y = k == l ? GCW(l + 1, l) : GCW(k + 1, k - 1);
+    double c;
+    z64 sr;
+    givens(x, y, c, sr);  // every lane, same values
+    const int cb = k > l ? k - 1 : l;
+    for (int col = cb + lane; col <= chi; col += 32) {
+      const z64 xv = GCW(k, col), yv = GCW(k + 1, col);
+      GCW(k, col) = c * xv + sr * yv;
+      GCW(k + 1, col) = c * yv - conj(sr) * xv;
+    }
+    __syncwarp();
+    if (lane == 0 && k > l) GCW(k + 1, k - 1) = z64(0.0, 0.0);
+    __syncwarp();
+    const int re = min(k + 2, hi);
+    for (int row = rlo + lane; row <= re; row += 32) {
+      const z64 xv = GCW(row, k), yv = GCW(row, k + 1);
+      GCW(row, k) = c * xv + yv * conj(sr);
+      GCW(row, k + 1) = c * yv - xv * sr;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      rot[2 * (k - k0)] = z64(c, 0.0);
+      rot[2 * (k - k0) + 1] = sr;
+    }
+  }
+  for (int e = lane; e < nr * nc; e += 32) {
+    const int r = e / nc, c = e - r * nc;
+    H[(long long)(rlo + r) * p + clo + c] = win[r * GC_WC + c];
+  }
+#undef GCW
+}
+
+__global__ void __launch_bounds__(GC_THREADS) k_geig_cluster(BigEigArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int p = a.p, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  z64* vsh = reinterpret_cast<z64*>(gsm);  // p: Householder vector
+  z64* win = vsh + p;                      // GC_WR x GC_WC window (CTA 0)
+  z64* rsh = win + GC_WR * GC_WC;          // 2 GC_W: the chunk's rotations
+  __shared__ double red[32];
+  const int rank = int(cluster.block_rank());
+  const int lp = blockIdx.x / GC_CTAS;  // the cluster's loop: every CTA of it runs every
+                                        // cluster barrier below
+  const int gtid = rank * nt + tid, gnt = GC_CTAS * nt;
+  const int nwarp = nt >> 5, gwarp = rank * nwarp + warp, gnwarp = GC_CTAS * nwarp;
+  const double eps = 2.220446049250313e-16;
+  z64* H = a.W + (long long)lp * a.sW;
+  z64* lam = a.lam + (long long)lp * p;
+  z64* rot = a.vec + (long long)lp * p;
+  GcCtl* ctl = reinterpret_cast<GcCtl*>(a.ctl + 8LL * lp);
+  if (rank == 0 && tid == 0) ctl->fail = 0;  // read by CTA 0 alone, at the end
+  // --- Householder reduction to Hessenberg form
+  for (int c = 0; c + 2 < p; ++c) {
+    double nrm2 = 0.0;
+    for (int r = c + 1 + tid; r < p; r += nt) nrm2 += abs2(ldz(H + (long long)r * p + c));
+    nrm2 = block_sum(nrm2, red);
+    const z64 x0 = ldz(H + (long long)(c + 1) * p + c);
+    const double tail = nrm2 - abs2(x0);
+    // a column already reduced is skipped; the barriers below run regardless, so the
+    // CTAs of the cluster pass the same barriers whatever the data
+    const bool work = tail > 0.0;
+    const double nx = sqrt(nrm2), ax0 = zabs(x0);
+    const z64 ph = ax0 > 0.0 ? z64(x0.re / ax0, x0.im / ax0) : z64(1.0, 0.0);
+    const double v0m = ax0 + nx, nv = work ? 1.0 / sqrt(v0m * v0m + tail) : 0.0;
+    if (work)
+      for (int r = c + 1 + tid; r < p; r += nt)
+        vsh[r] = r == c + 1 ? z64(nv * v0m * ph.re, nv * v0m * ph.im) : nv * ldz(H + (long long)r * p + c);
+    __syncthreads();
+    // left: H <- (I - 2 v v^dagger) H on rows c+1.., the cluster's columns c+1..
+    for (int col = c + 1 + gtid; work && col < p; col += gnt) {
+      z64 w(0.0, 0.0);
+#pragma unroll 4
+      for (int r = c + 1; r < p; ++r) cfma_conj(w, vsh[r], ldz(H + (long long)r * p + col));
+#pragma unroll 4
+      for (int r = c + 1; r < p; ++r) {
+        z64* h = H + (long long)r * p + col;
+        *h = ldz(h) - 2.0 * (vsh[r] * w);
+      }
+    }
+    cluster.sync();
+    if (work && rank == 0)  // column c (every CTA has read it)
+      for (int r = c + 1 + tid; r < p; r += nt) H[(long long)r * p + c] = r == c + 1 ? -nx * ph : z64(0.0, 0.0);
+    // right: H <- H (I - 2 v v^dagger) on columns c+1.., one warp per row of the cluster
+    for (int row = gwarp; work && row < p; row += gnwarp) {
+      z64* hr = H + (long long)row * p;
+      z64 w(0.0, 0.0);
+      for (int k = c + 1 + lane; k < p; k += 32) cfma(w, ldz(hr + k), vsh[k]);
+      for (int o = 16; o > 0; o >>= 1) {
+        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+      }
+      for (int k = c + 1 + lane; k < p; k += 32) hr[k] = ldz(hr + k) - 2.0 * (w * conj(vsh[k]));
+    }
+    cluster.sync();
+  }
+  // --- shifted QR sweeps; the first warp of CTA 0 keeps the iteration state
+  int hi_s = p - 1, iter = 0, total = 0;
+  const int cap = 120 * p + 120;
+  while (true) {
+    if (rank == 0 && warp == 0) {
+      int hi = hi_s, l = 0, active = 0, fail = 0;
+      z64 mu(0.0, 0.0);
+      while (hi >= 0) {
+        if (hi == 0) {
+          if (lane == 0) lam[0] = ldz(H);
+          hi = -1;
+          break;
+        }
+        const int sl = gc_split_point(H, p, hi, eps);
+        if (lane == 0 && sl > 0) H[(long long)sl * p + sl - 1] = z64(0.0, 0.0);
+        __syncwarp();
+        if (sl == hi) {
+          if (lane == 0) lam[hi] = ldz(H + (long long)hi * p + hi);
+          --hi;
+          iter = 0;
+          continue;
+        }
+        mu = geig_shift(ldz(H + (long long)(hi - 1) * p + hi - 1), ldz(H + (long long)(hi - 1) * p + hi),
+                        ldz(H + (long long)hi * p + hi - 1), ldz(H + (long long)hi * p + hi), iter,
+                        hi >= 2 ? zabs(ldz(H + (long long)(hi - 1) * p + hi - 2)) : 0.0);
+        l = sl;
+        active = 1;
+        break;
+      }
+      ++iter;
+      ++total;
+      if (total > cap) {
+        fail = 1;
+        active = 0;
+        hi = -1;
+      }
+      hi_s = hi;
+      if (lane == 0) {
+        ctl->mu_re = mu.re;
+        ctl->mu_im = mu.im;
+        ctl->active = active;
+        ctl->l = l;
+        ctl->hi = hi;
+        if (fail) ctl->fail = 1;
+      }
+    }
+    cluster.sync();
+    const int active = __ldcg(&ctl->active);
+    if (!active) break;  // the same value in every CTA of the cluster
+    const int l = __ldcg(&ctl->l), hi = __ldcg(&ctl->hi);
+    const z64 mu(__ldcg(&ctl->mu_re), __ldcg(&ctl->mu_im));
+    for (int k0 = l; k0 < hi; k0 += GC_W) {
+      const int kend = min(k0 + GC_W, hi), nk = kend - k0;
+      const int rlo = k0 > l ? k0 - 1 : l, chi = kend;
+      if (rank == 0 && warp == 0) gc_chase(H, p, l, hi, k0, kend, mu, win, rot);
+      cluster.sync();
+      for (int e = tid; e < 2 * nk; e += nt) rsh[e] = ldz(rot + e);
+      __syncthreads();
+      // right of the window: rows k0 .. kend of columns chi+1 .. hi, row rotations in
+      // order; above it: columns k0 .. kend of rows l .. rlo-1, column rotations in order
+      const int nA = hi - chi, nB = rlo - l;
+      for (int t = gtid; t < nA + nB; t += gnt) {
+        if (t < nA) {
+          z64* hc = H + (long long)k0 * p + chi + 1 + t;
+          z64 v[GC_W + 1];
+#pragma unroll
+          for (int q = 0; q <= GC_W; ++q)
+            if (q <= nk) v[q] = ldz(hc + (long long)q * p);
+#pragma unroll
+          for (int q = 0; q < GC_W; ++q)
+            if (q < nk) {
+              const double c = rsh[2 * q].re;
+              const z64 sr = rsh[2 * q + 1];
+              const z64 x = v[q], y = v[q + 1];
+              v[q] = c * x + sr * y;
+              v[q + 1] = c * y - conj(sr) * x;
+            }
+#pragma unroll
+          for (int q = 0; q <= GC_W; ++q)
+            if (q <= nk) hc[(long long)q * p] = v[q];
+        } else {
+          z64* hr = H + (long long)(l + t - nA) * p + k0;
+          z64 v[GC_W + 1];
+#pragma unroll
+          for (int q = 0; q <= GC_W; ++q)
+            if (q <= nk) v[q] = ldz(hr + q);
+#pragma unroll
+          for (int q = 0; q < GC_W; ++q)
+            if (q < nk) {
+              const double c = rsh[2 * q].re;
+              const z64 sr = rsh[2 * q + 1];
+              const z64 x = v[q], y = v[q + 1];
+              v[q] = c * x + y * conj(sr);
+              v[q + 1] = c * y - x * sr;
+            }
+#pragma unroll
+          for (int q = 0; q <= GC_W; ++q)
+            if (q <= nk) hr[q] = v[q];
+        }
+      }
+      cluster.sync();
+    }
+  }
+  if (rank != 0) return;  // after the last cluster barrier
+  // --- CTA 0: gaps, phases in ascending order
+  const int i = a.i0 + lp;
+  const long long k0 = (long long)i * a.N;
+  if (a.min_gap) {
+    double g = INFINITY;
+    for (int j = tid; j < a.N; j += nt) g = fmin(g, a.gap[k0 + j]);
+    g = block_min(g, red);
+    if (tid == 0) a.min_gap[i] = g;
+  }
+  if (a.min_pso_gap && a.pso_gap) {
+    double g = INFINITY;
+    for (int j = tid; j < a.N; j += nt) g = fmin(g, a.pso_gap[k0 + j]);
+    g = block_min(g, red);
+    if (tid == 0) a.min_pso_gap[i] = g;
+  }
+  if (tid == 0 && __ldcg(&ctl->fail)) report(a.status, ST_ENOCONV, k0, 0.0);
+  double* th = a.th + (long long)lp * p;
+  int* ord = a.ord + (long long)lp * p;
+  for (int c = tid; c < p; c += nt) {
+    const z64 lc = ldz(lam + c);
+    th[c] = atan2(lc.im, lc.re);
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += nt) {
+    const double x = rank_key(th[c]);
+    int rnk = 0;
+    for (int d = 0; d < p; ++d) {
+      const double y = rank_key(th[d]);
+      rnk += (y < x) || (y == x && d < c);
+    }
+    ord[rnk] = c;
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += nt) a.phases[(long long)i * p + c] = th[ord[c]];
+}
+
 cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s) {
   if (a.nl <= 0) return cudaSuccess;
-  k_geig_big<<<a.nl, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.p < GC_MIN_P || !a.ctl) {
+    k_geig_big<<<a.nl, 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t(a.p) + GC_WR * GC_WC + 2 * GC_W) * sizeof(z64);
+  static size_t cached = 0;
+  cudaError_t e = set_smem_once(k_geig_cluster, smem, cached);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(GC_CTAS * a.nl));
+  cfg.blockDim = dim3(GC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = GC_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_geig_cluster, a);
 }
 
 }  // namespace bw

@@ -50,9 +50,7 @@ __device__ __forceinline__ void givens(z64 x, z64 y, double& c, z64& s) {
 // Whether the subdiagonal entry H[l][l-1] is negligible: against the neighbouring
 // diagonal entries, or by the product test of Ahues and Tisseur (its product with
 // the superdiagonal small against the local separation of the diagonal entries).
-__device__ __forceinline__ bool geig_negligible(const z64* H, int ld, int l, double eps) {
-  const z64 h11 = H[(l - 1) * ld + l - 1], h12 = H[(l - 1) * ld + l];
-  const z64 h21 = H[l * ld + l - 1], h22 = H[l * ld + l];
+__device__ __forceinline__ bool geig_negligible_v(z64 h11, z64 h12, z64 h21, z64 h22, double eps) {
   const double sub = zabs(h21);
   const double dia = zabs(h22) + zabs(h11);
   bool small = sub <= eps * dia || sub < 1e-300;
@@ -65,6 +63,34 @@ __device__ __forceinline__ bool geig_negligible(const z64* H, int ld, int l, dou
     small = ba * (ab / sc) <= fmax(1e-300, eps * (bb * (aa / sc)));
   }
   return small;
+}
+
+__device__ __forceinline__ bool geig_negligible(const z64* H, int ld, int l, double eps) {
+  return geig_negligible_v(H[(l - 1) * ld + l - 1], H[(l - 1) * ld + l], H[l * ld + l - 1],
+                           H[l * ld + l], eps);
+}
+
+// Shift of a QR sweep from the trailing 2 x 2 [[a, b], [c, d]] of the active window:
+// its eigenvalue closest to d (Wilkinson); every 12th sweep without a deflation the
+// exceptional shift d + 0.75 (|c| + sub2), sub2 = |H[hi-1][hi-2]| (0 when hi < 2).
+__device__ __forceinline__ z64 geig_shift(z64 a, z64 b, z64 c, z64 d, int iter, double sub2) {
+  if (iter > 0 && iter % 12 == 0) return d + z64(0.75 * (zabs(c) + sub2), 0.0);
+  const z64 half = 0.5 * (a - d);
+  const z64 disc = half * half + b * c;
+  // complex sqrt
+  const double r = zabs(disc);
+  const double sr = sqrt(0.5 * (r + fabs(disc.re)));
+  z64 sq;
+  if (sr == 0.0) {
+    sq = z64(0.0, 0.0);
+  } else if (disc.re >= 0.0) {
+    sq = z64(sr, disc.im / (2.0 * sr));
+  } else {
+    sq = z64(fabs(disc.im) / (2.0 * sr), disc.im >= 0.0 ? sr : -sr);
+  }
+  // mu = d + half -/+ sq, the one closer to d
+  const z64 m1 = d + half - sq, m2 = d + half + sq;
+  return (abs2(m1 - d) <= abs2(m2 - d)) ? m1 : m2;
 }
 
 // Largest l in [1, hi] whose subdiagonal entry is negligible, or 0: the first warp
@@ -178,31 +204,8 @@ __device__ inline int geig(z64* H, z64* Z, int p, int ld, bool want_vec, z64* la
         }
         if (tid != 0) break;
         // shift from the trailing 2x2 of the active window
-        z64 mu;
-        const z64 a = H[(hi - 1) * ld + hi - 1], b = H[(hi - 1) * ld + hi];
-        const z64 c = H[hi * ld + hi - 1], d = H[hi * ld + hi];
-        if (iter > 0 && iter % 12 == 0) {
-          const double ex = zabs(H[hi * ld + hi - 1]) + (hi >= 2 ? zabs(H[(hi - 1) * ld + hi - 2]) : 0.0);
-          mu = d + z64(0.75 * ex, 0.0);
-        } else {
-          // eigenvalue of [[a,b],[c,d]] closest to d
-          const z64 half = 0.5 * (a - d);
-          const z64 disc = half * half + b * c;
-          // complex sqrt
-          const double r = zabs(disc);
-          double sr = sqrt(0.5 * (r + fabs(disc.re)));
-          z64 sq;
-          if (sr == 0.0) {
-            sq = z64(0.0, 0.0);
-          } else if (disc.re >= 0.0) {
-            sq = z64(sr, disc.im / (2.0 * sr));
-          } else {
-            sq = z64(fabs(disc.im) / (2.0 * sr), disc.im >= 0.0 ? sr : -sr);
-          }
-          // mu = d + half -/+ sq, choose closer to d
-          const z64 m1 = d + half - sq, m2 = d + half + sq;
-          mu = (abs2(m1 - d) <= abs2(m2 - d)) ? m1 : m2;
-        }
+        const z64 mu = geig_shift(H[(hi - 1) * ld + hi - 1], H[(hi - 1) * ld + hi], H[hi * ld + hi - 1],
+                                  H[hi * ld + hi], iter, hi >= 2 ? zabs(H[(hi - 1) * ld + hi - 2]) : 0.0);
         sh->mu = mu;
         sh->l = l;
         sh->active = 1;

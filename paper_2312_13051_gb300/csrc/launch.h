@@ -199,6 +199,7 @@ struct BigEigArgs {
   z64* vec;               // nl x p scratch
   double* th;             // nl x p scratch
   int* ord;               // nl x p scratch
+  double* ctl;            // nl x 8 scratch (control block of the cluster solver)
   DevStatus* status;
 };
 
@@ -246,6 +247,9 @@ cudaError_t launch_plaquettes_big(const LoopArgs& a, z64* Lmat, long long kb, z6
 cudaError_t launch_det_phase(z64* A, long long sA, int p, long long nb, z64* out, cudaStream_t s);
 
 // Winding of the summed Wannier centres over the transverse direction (Eq. 6).
+// Maximum errors of the double-float unit-circle helpers against FP64 (err: 3 device
+// doubles, zeroed by the caller).
+cudaError_t launch_selftest_unit_circle(double* err, cudaStream_t s);
 cudaError_t launch_winding(const double* phases, int Nt, int p, double* sums, double* winding,
                            cudaStream_t s);
 

@@ -1154,6 +1154,48 @@ cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaS
   return cudaGetLastError();
 }
 
+// Self-test of the double-float unit-circle helpers (df_cispi_ratio, df_cispi,
+// df_phase) against the FP64 sincospi / atan2 of the CUDA math library; maxima by
+// atomicMax on the bit patterns of the non-negative errors.
+__device__ __forceinline__ void err_max(double* e, double v) {
+  if (!(v <= 1.0)) v = 1.0;  // NaN or a gross error
+  atomicMax(reinterpret_cast<unsigned long long*>(e), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+__global__ void k_selftest_unit_circle(double* err) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int e = tid; e < 64 * 64; e += nth) {  // (N, m)
+    const int N = e / 64 + 1, m = e % 64;
+    if (m >= N) continue;
+    const cdf z = df_cispi_ratio(2 * m, N);
+    double sn, cs;
+    sincospi(2.0 * double(m) / double(N), &sn, &cs);
+    err_max(err, fmax(fabs(df_to_double(z.re) - cs), fabs(df_to_double(z.im) - sn)));
+  }
+  for (int e = tid; e < 8192; e += nth) {
+    const double t = -3.0 + 6.0 * double(e) / 8192.0;
+    const cdf z = df_cispi(t);
+    double sn, cs;
+    sincospi(t, &sn, &cs);
+    err_max(err + 1, fmax(fabs(df_to_double(z.re) - cs), fabs(df_to_double(z.im) - sn)));
+  }
+  for (int e = tid; e < 3 * 4096; e += nth) {
+    const double rad = e < 4096 ? 0.5 : (e < 8192 ? 1.0 : 2.0);
+    const double t = -1.0 + 2.0 * double(e % 4096 + 1) / 4096.0;  // (-1, 1] half-turns
+    double sn, cs;
+    sincospi(t, &sn, &cs);
+    const cdf z(df_from_double(rad * cs), df_from_double(rad * sn));
+    const double ref = atan2(df_to_double(z.im), df_to_double(z.re));
+    const double d = fabs(df_phase(z) - ref);
+    err_max(err + 2, fmin(d, 6.283185307179586 - d));
+  }
+}
+
+cudaError_t launch_selftest_unit_circle(double* err, cudaStream_t s) {
+  k_selftest_unit_circle<<<48, 256, 0, s>>>(err);
+  return cudaGetLastError();
+}
+
 // Nested loop for small m: one CTA per base point, all Wannier states of the base
 // point in shared memory, overlaps in parallel, product by prefix scan.
 template <typename E>

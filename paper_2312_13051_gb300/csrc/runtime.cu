@@ -598,9 +598,9 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
   const size_t per_k = sz_A + 2 * sz_v + sz_D + sz_lam + sz_Z + sz_wk + sz_X + sz_He + sz_R + sz_C +
                        sz_G + sp_U + (spin ? pso_split_bytes(n, p, pso_evals != nullptr) : 0);
   const size_t bUk = size_t(n) * pl * sizeof(z64), bPk = size_t(pl) * pl * sizeof(z64);
-  const size_t bEl = size_t(pl) * (2 * sizeof(z64) + sizeof(double) + sizeof(int));
+  const size_t bEl = size_t(pl) * (2 * sizeof(z64) + sizeof(double) + sizeof(int)) + 8 * sizeof(double);
   const size_t per_loop = size_t(N) * (bUk + bPk) + 2 * bPk + bEl;
-  size_t total = al256(blob.data.size()) + (spin ? 2 : 1) * al256(size_t(K) * sizeof(double)) + 40 * 256;
+  size_t total = al256(blob.data.size()) + (spin ? 2 : 1) * al256(size_t(K) * sizeof(double)) + 48 * 256;
   const size_t avail = ctx->budget > total ? ctx->budget - total : 0;
   long long Wv = std::min<long long>(K, 2048);
   while (Wv > 1 && size_t(Wv) * per_k + per_loop > avail) Wv /= 2;
@@ -622,6 +622,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
   z64* e_vec = reinterpret_cast<z64*>(carve(ctx, nl_max * size_t(pl) * sizeof(z64)));
   double* e_th = reinterpret_cast<double*>(carve(ctx, nl_max * size_t(pl) * sizeof(double)));
   int* e_ord = reinterpret_cast<int*>(carve(ctx, nl_max * size_t(pl) * sizeof(int)));
+  double* e_ctl = reinterpret_cast<double*>(carve(ctx, nl_max * 8 * sizeof(double)));
 
   bw::LargeArgs lg;
   std::memset(&lg, 0, sizeof(lg));
@@ -722,6 +723,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
     e.vec = e_vec;
     e.th = e_th;
     e.ord = e_ord;
+    e.ctl = e_ctl;
     e.status = ctx->status;
     BW_CUDA(bw::launch_geig_big(e, s), "eigenphase kernel");
     prof_mark(ctx, s, "eigenphases");
@@ -1083,6 +1085,21 @@ const char* bw_last_error(const bw_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 bw_status bw_set_profiling(bw_ctx* ctx, int enable) {
   if (!ctx) return BW_EINVAL;
   ctx->prof = enable != 0;
+  return BW_OK;
+}
+
+bw_status bw_selftest_unit_circle(bw_ctx* ctx, double* max_err) {
+  if (!ctx) return BW_EINVAL;
+  ctx->err.clear();
+  if (!max_err) return fail(ctx, BW_EINVAL, "max_err is NULL");
+  BW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  double* d = nullptr;
+  BW_CUDA(cudaMalloc(&d, 3 * sizeof(double)), "cudaMalloc");
+  cudaError_t e = cudaMemset(d, 0, 3 * sizeof(double));
+  if (e == cudaSuccess) e = bw::launch_selftest_unit_circle(d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(max_err, d, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(ctx, BW_ECUDA, "self-test: %s", cudaGetErrorString(e));
   return BW_OK;
 }
 

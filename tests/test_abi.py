@@ -46,7 +46,7 @@ def test_binding_names_match_header(libpath):
     from paper_2312_13051_gb300 import _lib
     assert sorted(_lib.exported_symbols()) == declared_symbols()
     for s in declared_symbols():
-        if s in ("bw_set_profiling", "bw_profile_read"):
+        if s in ("bw_set_profiling", "bw_profile_read", "bw_selftest_unit_circle"):
             assert hasattr(_lib.Context, s[3:]), s
         elif s in ("bw_server_submit", "bw_server_poll", "bw_server_wait", "bw_server_outstanding",
                    "bw_server_cancel"):

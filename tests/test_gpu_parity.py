@@ -301,6 +301,11 @@ MANY = {
     "flux_L6": (lambda: I.supercell(I.spin_hall(1.0), 6, W=1.0, seed=11, flux=True), P(6, 4), 72),
     "random160_p80": (lambda: I.random_hermitian_model(160, 41), P(5, 3), 80),
     "disordered_L10": (lambda: I.supercell(I.spin_hall(1.0), 10, W=2.0, seed=5), P(4, 3), 200),
+    # either side of the switch to the cluster eigenphase solver (p >= 128), with sweeps
+    # whose rotation count is not a multiple of the 16-rotation chunk
+    "random254_p127": (lambda: I.random_hermitian_model(254, 43), P(4, 3), 127),
+    "random256_p128": (lambda: I.random_hermitian_model(256, 44), P(4, 3), 128),
+    "random300_p149": (lambda: I.random_hermitian_model(300, 45), P(3, 2), 149),
 }
 
 
@@ -910,3 +915,14 @@ def test_eigh_batched_maximum_size(lib, ctx):
     with pytest.raises(lib.BWError) as e:
         lib.eigh_batched(big, [4097], 1, ctx=ctx)
     assert e.value.status == "EINVAL"
+
+
+def test_unit_circle_double_float_against_fp64(lib, ctx):
+    """The double-float e^{2 pi i m / N}, e^{i pi t} and arg z of the four-band loop
+    kernel (Taylor series after quarter-turn reduction; refined float arctangent)
+    against the FP64 sincospi / atan2 of the CUDA math library: within a few units of
+    the double-float resolution 2^-48 = 3.6e-15."""
+    e_ratio, e_cis, e_phase = ctx.selftest_unit_circle()
+    assert e_ratio <= 1e-14, e_ratio
+    assert e_cis <= 1.5e-14, e_cis
+    assert e_phase <= 2e-14, e_phase
