@@ -552,6 +552,29 @@ def run_ours(args):
             ctx.set_profiling(False)
             ctx.status()
             mb_res[kind + "_mixed"] = dict(ms=e0.elapsed_time(e1), stages=stages)
+    # disordered spin-Hall supercells (L x L cells of the config-0 model, W = 2, 16 x 16
+    # supercell k-grid, half filling): seeded realisations, one graph replay of the whole
+    # call per realisation and precision, L2 flushed before it, per-stage marks
+    sc_res = {}
+    if not args.no_supercell:
+        for Ls in [int(x) for x in args.supercell_sides.split(",") if x]:
+            for prec in ("mixed", "fp64"):
+                acc = dict(total_ms=0.0, stages={}, phases=[], per_call=[])
+                for seed in range(args.supercell_realisations):
+                    msc = I.supercell(I.spin_hall(1.0), Ls, W=2.0, seed=seed)
+                    psc, plsc = msc.n // 2, I.Plane(16, 16)
+                    out = (torch.empty((plsc.N_t, psc), dtype=torch.float64, device=dev),
+                           torch.empty((plsc.N_t,), dtype=torch.float64, device=dev))
+                    call = (lambda m_=msc, pl_=plsc, p_=psc, prec=prec, out=out:
+                            lib.wilson_loop(m_, pl_, p_, precision=prec, ctx=ctx, check=False, out=out))
+                    t, pk, _, outs, _ = time_call_graph(ctx, call, out, 1, 1, flush, dev, soak_s=0.0,
+                                                        profile_steps=1)
+                    acc["total_ms"] += t
+                    acc["per_call"].append(t)
+                    for k, v in pk.items():
+                        acc["stages"][k] = acc["stages"].get(k, 0.0) + v
+                    acc["phases"].append(outs[0])
+                sc_res[(Ls, prec)] = acc
     clk = clocks.stop()
     e2e_s, lat, h2d, d2h = time_e2e(lib, ctx, wl, "mixed", args.steps, args.warmup, dev)
 
@@ -569,6 +592,17 @@ def run_ours(args):
             ref_mb, _ = oracle.wilson_loop(mb.model, plr, mb.p)
             for prec in ("mixed", "fp64"):
                 mb_res[prec]["phase_err_rad"] = oracle.circular_match_error(mb_res[prec]["phases"][row], ref_mb[0])
+        for Ls in sorted({k[0] for k in sc_res}):   # one transverse row of realisation 0
+            row = 5
+            msc = I.supercell(I.spin_hall(1.0), Ls, W=2.0, seed=0)
+            plr = I.Plane(16, 1, origin=(0.0, row / 16.0, 0.0))
+            t0 = time.perf_counter()
+            ref_sc, _ = oracle.wilson_loop(msc, plr, msc.n // 2)
+            t_row = time.perf_counter() - t0
+            for prec in ("mixed", "fp64"):
+                sc_res[(Ls, prec)]["phase_err_rad"] = oracle.circular_match_error(
+                    sc_res[(Ls, prec)]["phases"][0][row], ref_sc[0])
+            sc_res[(Ls, "cpu")] = dict(seconds=t_row, k_points=16)
         for prec in sat_res:   # rows 64 i of the fine grid are the k-points of row i
             ph = sat_res[prec]["phases"]
             sat_res[prec]["phase_err_rad"] = max(
@@ -606,8 +640,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD,
                    "precision": "mixed request: at n = 4, p = 2 states, overlaps and loop products "
                                 "in double-float (pairs of FP32, ~48-bit) on the FP32 pipe (FP32 "
-                                "Jacobi + double-float Newton refinement), phase tables, atan2 and "
-                                "phase ordering in FP64, one cooperative kernel; FP32 solve + "
+                                "Jacobi + double-float Newton refinement), phase tables, Bloch "
+                                "factors and eigenphases in double-float, one cooperative kernel "
+                                "with the plan in its parameters; FP32 solve + "
                                 "FP64-grade refinement for larger n (manyband block)",
                    "timing": "CUDA-graph replay of the whole call, CUDA events per step",
                    "l2": "flushed between steps (256 MB write)",
@@ -697,6 +732,49 @@ def run_ours(args):
                              "stage_ms": {k: round(v, 3) for k, v in mb_res[kind]["stages"].items()}}
         blk["mixed_over_fp64"] = blk["mixed"]["value"] / blk["fp64"]["value"]
         line["manyband"] = blk
+    if sc_res:
+        blk = {"workload": "disordered spin-Hall supercells (L x L cells of the 4-band model, n = 4 L^2, "
+                           "p = n/2), on-site disorder U[-W/2, W/2] with W = 2, 16 x 16 supercell "
+                           f"k-grid, {args.supercell_realisations} seeded realisations per L; plain "
+                           "Wilson loop, one CUDA-graph replay per realisation, L2 flushed before each"}
+        for Ls in sorted({k[0] for k in sc_res}):
+            msc = I.supercell(I.spin_hall(1.0), Ls, W=2.0, seed=0)
+            n_, p_ = msc.n, msc.n // 2
+            groups = len(np.unique(np.stack([msc.i, msc.j, msc.R[:, 0], msc.R[:, 1], msc.R[:, 2]], 1), axis=0))
+            n_ent = len(np.unique(np.stack([msc.i, msc.j], 1), axis=0))
+            Kc = 16 * 16
+            sub = {"n": n_, "p": p_, "k_points_per_call": Kc}
+            for prec in ("mixed", "fp64"):
+                r = sc_res[(Ls, prec)]
+                calls = len(r["per_call"])
+                st = {k: v / calls for k, v in r["stages"].items()}
+                fl = manyband_stage_flops(n_, p_, 16, 16, groups, prec == "mixed", n_ent)
+                fl["loops"] = 16 * 15 * 8.0 * p_ ** 3       # N - 1 products of p x p per loop
+                fl["eigenphases"] = 16 * 10.0 * p_ ** 3    # Hessenberg + QR per loop
+                d = max((k for k in st if k in fl), key=st.get)
+                ach = fl[d] / (st[d] * 1e-3) / 1e12
+                fp32_stage = prec == "mixed" and d.startswith("lg_")
+                pk_ = peaks["fp32"] if fp32_stage else peaks["fp64"]
+                sub[prec] = {"value": Kc * calls / (r["total_ms"] * 1e-3), "unit": UNIT,
+                             "ms_per_call": r["total_ms"] / calls,
+                             "per_call_ms": [round(x, 2) for x in r["per_call"]],
+                             "stage_ms_per_call": {k: round(v, 2) for k, v in st.items()},
+                             "phase_err_rad_sampled_row": r.get("phase_err_rad"),
+                             "roofline": {"kernel": d, "bound": "alu", "achieved": ach, "peak": pk_,
+                                          "unit": "TFLOP/s", "frac": ach / pk_,
+                                          "algorithmic_flops_per_call": fl[d],
+                                          "peak_source": ("measured cuBLAS SGEMM (FP32 pipe)" if fp32_stage
+                                                          else "measured cuBLAS DGEMM (FP64 pipe)")}}
+            cpu = sc_res.get((Ls, "cpu"))
+            if cpu:
+                sub["cpu_baseline"] = {"value": cpu["k_points"] / cpu["seconds"], "unit": UNIT,
+                                       "cores": os.cpu_count(), "kind": "oracle",
+                                       "sample": f"one transverse row (16 of 256 k-points) of realisation 0, "
+                                                 f"numpy FP64 with threaded LAPACK, {cpu['seconds']:.2f} s; "
+                                                 "the rate is extrapolated to the whole call"}
+            sub["mixed_over_fp64"] = sub["mixed"]["value"] / sub["fp64"]["value"]
+            blk[f"L{Ls}"] = sub
+        line["supercell"] = blk
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -847,6 +925,11 @@ def main(argv=None):
                     help="comma list of many-band loops to time: wilson (always), spin, nested")
     ap.add_argument("--profile-precision", choices=["mixed", "fp64"], default="mixed",
                     help="precision of the --profile-case calls")
+    ap.add_argument("--no-supercell", action="store_true",
+                    help="skip the disordered-supercell block (config 2)")
+    ap.add_argument("--supercell-sides", default="10",
+                    help="supercell sides L of the disordered-supercell block (n = 4 L^2)")
+    ap.add_argument("--supercell-realisations", type=int, default=4)
     ap.add_argument("--no-saturated", action="store_true",
                     help="skip the saturated-batch measurement (230 400 k-points per call)")
     ap.add_argument("--profile-case", choices=["bench", "saturated", "manyband", "supercell", "plaquette"],
