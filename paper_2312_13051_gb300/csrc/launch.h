@@ -200,8 +200,13 @@ struct BigEigArgs {
   double* th;             // nl x p scratch
   int* ord;               // nl x p scratch
   double* ctl;            // nl x 8 scratch (control block of the cluster solver)
+  int df;                 // W (and lam) hold complex double-float: the cluster solver in
+                          // double-float arithmetic (needs geig_df_eligible(p))
   DevStatus* status;
 };
+// True when the cluster eigenphase solver takes p (p >= 128); the double-float form
+// (BigEigArgs::df) needs it.
+bool geig_df_eligible(int p);
 
 // Spin-resolved loop with many occupied bands (bigloop.cu).
 // Y = sigma s U for a wave of W occupied blocks (n x p each), s a sparse operator in
@@ -220,7 +225,10 @@ cudaError_t launch_pso_post(const double* nu, int nval, long long W, long long k
 // off[t] = t stride, idx[t] = t for t < W (wave slot -> explicit matrix).
 cudaError_t launch_iota(long long* off, int* idx, long long W, long long stride, cudaStream_t s);
 
-cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s);
+// df: A, B and C hold complex double-float (cdf) instead of complex FP64.
+cudaError_t launch_zgemm(const GemmArgs& g, cudaStream_t s, bool df = false);
+// In place, count elements: complex FP64 -> complex double-float (to_cdf) or back.
+cudaError_t launch_convert_cdf(z64* x, long long count, bool to_cdf, cudaStream_t s);
 cudaError_t launch_geig_big(const BigEigArgs& a, cudaStream_t s);
 
 // Launches every stage of the large-n solver for one wave.

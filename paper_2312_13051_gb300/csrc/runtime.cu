@@ -561,7 +561,8 @@ bw_status pso_split_wave(bw_ctx* ctx, PsoSplit& X, const z64* Uw, long long Wn, 
 }
 
 // Wilson loop with many occupied bands (p > LOOP_P_MAX, n > SMALL_N_MAX).  The
-// Wilson matrix no longer fits in shared memory, so the loop runs as batched GEMMs:
+// Wilson matrix no longer fits in shared memory, so the loop runs as batched GEMMs
+// (FP64, or double-float on the FP32 pipe in the mixed request):
 // for a block of nl loops (their k-points are contiguous, k = i N + j) the states are
 // solved in waves of up to 2048 k-points, one GEMM forms every overlap
 // M_j = U(k_{j+1})^dagger U(k_j) of the block (closing on U(k_0), Eq. 2), N - 1 GEMMs
@@ -679,6 +680,9 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
       if ((st = pso_split_wave(ctx, X, Uw, Wn, kb + w0, Ublk + w0 * sU, s))) return st;
       prof_mark(ctx, s, "pso_split");
     }
+    // mixed request: the overlaps and loop products in complex double-float on the
+    // FP32 pipe (the states converted in place; W converted back for the eigenphases)
+    if (mx) BW_CUDA(bw::launch_convert_cdf(Ublk, Kb * sU, true, s), "state conversion");
     // every overlap of the block: batch b = l N + j, A = U(k_{j+1}) (closing on j = 0)
     bw::GemmArgs g;
     std::memset(&g, 0, sizeof(g));
@@ -688,7 +692,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
     g.sA = sU; g.sB = sU; g.sC = sP;
     g.a_next_N = N;
     g.batch = Kb;
-    BW_CUDA(bw::launch_zgemm(g, s), "overlap GEMM");
+    BW_CUDA(bw::launch_zgemm(g, s, mx), "overlap GEMM");
     prof_mark(ctx, s, "overlaps");
     // W = M_{N-1} ... M_0 for the nl loops at once
     const z64* Wcur = Mblk;  // M_0 of loop l at Mblk + l N pl^2
@@ -701,10 +705,15 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
       g.lda = pl; g.ldb = pl; g.ldc = pl;
       g.sA = (long long)N * sP; g.sB = sWcur; g.sC = sP;
       g.batch = nl;
-      BW_CUDA(bw::launch_zgemm(g, s), "loop-product GEMM");
+      BW_CUDA(bw::launch_zgemm(g, s, mx), "loop-product GEMM");
       Wcur = Wout;
       sWcur = sP;
     }
+    // the eigenphases in double-float as well when the cluster solver takes p; else W
+    // back to FP64 (nl consecutive p x p matrices: sWcur = sP, or N sP = sP at N = 1)
+    const bool df_eig = mx && bw::geig_df_eligible(pl);
+    if (mx && !df_eig)
+      BW_CUDA(bw::launch_convert_cdf(const_cast<z64*>(Wcur), nl * sP, false, s), "W conversion");
     if (N > 1) prof_mark(ctx, s, "loops");
     bw::BigEigArgs e;
     std::memset(&e, 0, sizeof(e));
@@ -724,6 +733,7 @@ bw_status run_big_loop(bw_ctx* ctx, const HostPlan& P, const Blob& blob, const P
     e.th = e_th;
     e.ord = e_ord;
     e.ctl = e_ctl;
+    e.df = df_eig ? 1 : 0;
     e.status = ctx->status;
     BW_CUDA(bw::launch_geig_big(e, s), "eigenphase kernel");
     prof_mark(ctx, s, "eigenphases");

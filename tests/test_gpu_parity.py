@@ -306,6 +306,10 @@ MANY = {
     "random254_p127": (lambda: I.random_hermitian_model(254, 43), P(4, 3), 127),
     "random256_p128": (lambda: I.random_hermitian_model(256, 44), P(4, 3), 128),
     "random300_p149": (lambda: I.random_hermitian_model(300, 45), P(3, 2), 149),
+    # coarse loops (8 k-points) of a disordered L = 12 supercell filled to p = 144 of
+    # n = 576: a Wilson matrix far from unitary, on which the double-float QR of the
+    # mixed request stalled short of deflation at a 2^-47 threshold
+    "disordered_L12_p144": (lambda: I.supercell(I.spin_hall(1.0), 12, W=2.0, seed=5), P(8, 8), 144),
 }
 
 
