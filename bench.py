@@ -755,6 +755,9 @@ def run_ours(args):
                 ach = fl[d] / (st[d] * 1e-3) / 1e12
                 fp32_stage = prec == "mixed" and d.startswith("lg_")
                 pk_ = peaks["fp32"] if fp32_stage else peaks["fp64"]
+                src = ("measured cuBLAS SGEMM (FP32 pipe)" if fp32_stage else
+                       "measured cuBLAS DGEMM: FP64-grade arithmetic, computed in double-float on "
+                       "the FP32 pipe" if prec == "mixed" else "measured cuBLAS DGEMM (FP64 pipe)")
                 sub[prec] = {"value": Kc * calls / (r["total_ms"] * 1e-3), "unit": UNIT,
                              "ms_per_call": r["total_ms"] / calls,
                              "per_call_ms": [round(x, 2) for x in r["per_call"]],
@@ -763,8 +766,7 @@ def run_ours(args):
                              "roofline": {"kernel": d, "bound": "alu", "achieved": ach, "peak": pk_,
                                           "unit": "TFLOP/s", "frac": ach / pk_,
                                           "algorithmic_flops_per_call": fl[d],
-                                          "peak_source": ("measured cuBLAS SGEMM (FP32 pipe)" if fp32_stage
-                                                          else "measured cuBLAS DGEMM (FP64 pipe)")}}
+                                          "peak_source": src}}
             cpu = sc_res.get((Ls, "cpu"))
             if cpu:
                 sub["cpu_baseline"] = {"value": cpu["k_points"] / cpu["seconds"], "unit": UNIT,
