@@ -973,6 +973,36 @@ __device__ __forceinline__ const T* plan_ptr(const T* p, const unsigned char* in
   return inl ? reinterpret_cast<const T*>(inl + (reinterpret_cast<const char*>(p) - dbase)) : p;
 }
 
+// Nested loop of one Wannier band at base point b for the fused kernel (n = 4,
+// complex double-float states), by the whole CTA: thread (i, q) = (tid / 4, tid % 4)
+// forms conj(w(i+1)[q]) w(i)[q] (every load of the base point in flight at once), the
+// row's four lanes sum them, and the rows' overlaps multiply by shuffles in each warp
+// and across the warps through shared memory (red: 8 cdf).
+__device__ __forceinline__ void nested_base_m1_cta(const LoopArgs& a, int b, cdf* red) {
+  const int Nt = a.N_t / n_planes(a), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sp = b / a.N, j = b - sp * a.N;
+  const cdf* wj = reinterpret_cast<const cdf*>(a.w) + ((long long)j * a.N_t + (long long)sp * Nt) * 4;
+  const cdf one(df(1.f), df(0.f));
+  cdf prod = one;
+  for (int i0 = 0; i0 < Nt; i0 += FUSED_THREADS / 4) {
+    const int i = i0 + (tid >> 2), q = tid & 3;
+    cdf z = cdf_zero();
+    if (i < Nt) cfma_conj(z, wj[(size_t)(i + 1 == Nt ? 0 : i + 1) * 4 + q], wj[(size_t)i * 4 + q]);
+    z = z + Arith<cdf>::shfl_xor(z, 1);
+    z = z + Arith<cdf>::shfl_xor(z, 2);
+    if (!(i < Nt)) z = one;
+#pragma unroll 1
+    for (int o = 4; o < 32; o <<= 1) z = z * Arith<cdf>::shfl_xor(z, o);
+    if (lane == 0) red[warp] = z;
+    __syncthreads();
+    if (tid == 0)
+#pragma unroll 1
+      for (int w = 0; w < FUSED_THREADS / 32; ++w) prod = prod * red[w];
+    __syncthreads();
+  }
+  if (tid == 0) a.nested_out[b] = df_phase(prod);
+}
+
 template <bool kNested1>
 __device__ __forceinline__ void loops_fused_body(const StatesArgs& sa, const LoopArgs& a,
                                                  const unsigned char* inl, const char* dbase) {
@@ -1070,7 +1100,9 @@ __device__ __forceinline__ void loops_fused_body(const StatesArgs& sa, const Loo
     // has passed this barrier; then the nested loops of one Wannier band
     __threadfence();
     cooperative_groups::this_grid().sync();
-    for (int b = blockIdx.x; b < a.N * n_planes(a); b += gridDim.x) nested_base_m1<cdf>(a, b);
+    // the scan's scratch, free by now: S and T (2 N x 64 bytes, contiguous) hold 8 cdf
+    cdf* red8 = reinterpret_cast<cdf*>(smem + Z.S);
+    for (int b = blockIdx.x; b < a.N * n_planes(a); b += gridDim.x) nested_base_m1_cta(a, b, red8);
   }
 }
 
