@@ -53,6 +53,8 @@ struct bw_ctx {
   int prof_n = 0;
   const char* prof_names[kProfMax] = {};
   cudaEvent_t prof_ev[kProfMax + 1] = {};
+  // the last hopping list's plan (a PlanCache, see plan_and_blob), owned
+  void* plan_cache = nullptr;
 };
 
 namespace {
@@ -209,6 +211,63 @@ void plan_to_blob(HostPlan& P, Blob& b) {
   }
   P.o_tdf = b.add(tdf);
   P.o_rowptr = b.add(P.row_ptr);
+}
+
+// The plan of the last hopping list seen on a context, with a copy of that list:
+// building a plan sorts and groups the list, which for a many-band model (~10^6
+// hoppings) costs more host time than the GPU work of a call, and a caller usually
+// passes the same model call after call (planes, precisions, loop kinds).  A list is
+// reused only when it matches the copy entry by entry.
+struct PlanCache {
+  int32_t n = 0;
+  int64_t nnz = -1;
+  std::vector<int32_t> R, i, j;
+  std::vector<bw_c128> t;
+  HostPlan P;
+  Blob blob;
+};
+
+bool same_model(const PlanCache& c, const bw_model* m) {
+  if (c.n != m->n || c.nnz != m->nnz) return false;
+  const size_t nz = size_t(m->nnz);
+  if (nz == 0) return true;
+  return std::memcmp(c.R.data(), m->R, 3 * nz * sizeof(int32_t)) == 0 &&
+         std::memcmp(c.i.data(), m->i, nz * sizeof(int32_t)) == 0 &&
+         std::memcmp(c.j.data(), m->j, nz * sizeof(int32_t)) == 0 &&
+         std::memcmp(c.t.data(), m->t, nz * sizeof(bw_c128)) == 0;
+}
+
+// make_plan + plan_to_blob, through the context's cache.
+bw_status plan_and_blob(bw_ctx* ctx, const bw_model* m, HostPlan& P, Blob& blob) {
+  PlanCache* c = static_cast<PlanCache*>(ctx->plan_cache);
+  if (m && c && same_model(*c, m)) {
+    P = c->P;
+    blob = c->blob;
+    return BW_OK;
+  }
+  bw_status st = make_plan(ctx, m, P);
+  if (st) return st;
+  blob = Blob();
+  plan_to_blob(P, blob);
+  if (!c) {
+    c = new PlanCache();
+    ctx->plan_cache = c;
+  }
+  const size_t nz = size_t(m->nnz);
+  c->n = m->n;
+  c->nnz = m->nnz;
+  c->R.assign(m->R, m->R + (nz ? 3 * nz : 0));
+  c->i.assign(m->i, m->i + nz);
+  c->j.assign(m->j, m->j + nz);
+  c->t.assign(m->t, m->t + nz);
+  c->P = P;
+  c->blob = blob;
+  return BW_OK;
+}
+
+void plan_cache_free(bw_ctx* ctx) {
+  delete static_cast<PlanCache*>(ctx->plan_cache);
+  ctx->plan_cache = nullptr;
 }
 
 bw::DevModel dev_model(const HostPlan& P, const char* base) {
@@ -764,7 +823,8 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
   if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
   HostPlan P;
-  if ((st = make_plan(ctx, model, P))) return st;
+  Blob blob;
+  if ((st = plan_and_blob(ctx, model, P, blob))) return st;
   const int n = P.n;
   if (p < 1 || p > n) return fail(ctx, BW_EINVAL, "need 1 <= p <= n (p = %d, n = %d)", p, n);
   if (n > bw::LARGE_N_MAX)
@@ -797,8 +857,6 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     return fail(ctx, BW_EINVAL, "pso_split must be 0 (split at zero) or 1 (at the median), got %d",
                 o.pso_median);
   const long long K = (long long)plane->N * plane->N_t;
-  Blob blob;
-  plan_to_blob(P, blob);
   if (spin) {
     op.o_row = blob.add(op.row);
     op.o_col = blob.add(op.col);
@@ -1087,6 +1145,7 @@ void bw_destroy(bw_ctx* ctx) {
   if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
   for (auto& e : ctx->prof_ev)
     if (e) cudaEventDestroy(e);
+  plan_cache_free(ctx);
   delete ctx;
 }
 
@@ -1174,11 +1233,10 @@ bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64
   if (K < 0) return fail(ctx, BW_EINVAL, "K < 0");
   if (K > 0 && (!f || !H_out)) return fail(ctx, BW_EINVAL, "f or H_out is NULL");
   HostPlan P;
-  bw_status st = make_plan(ctx, model, P);
+  Blob blob;
+  bw_status st = plan_and_blob(ctx, model, P, blob);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Blob blob;
-  plan_to_blob(P, blob);
   begin_call(ctx, s);
   if ((st = reserve(ctx, al256(blob.data.size()) + 4096, s))) return st;
   char* dblob = carve(ctx, blob.data.size());

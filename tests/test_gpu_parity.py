@@ -930,3 +930,23 @@ def test_unit_circle_double_float_against_fp64(lib, ctx):
     assert e_ratio <= 1e-14, e_ratio
     assert e_cis <= 1.5e-14, e_cis
     assert e_phase <= 2e-14, e_phase
+
+
+def test_plan_cache_follows_in_place_edits(lib, ctx):
+    """A context reuses the plan of an unchanged hopping list, and plans again when the
+    caller edits the same arrays in place: halving every intra-cell amplitude of the
+    BBH model (still Hermitian) changes the loop, and the result follows the oracle
+    of the edited model."""
+    torch = _torch()
+    model = I.bbh(0.5, 0.5)
+    plane = P(12, 12)
+    a, _ = lib.wilson_loop(model, plane, 2, ctx=ctx)
+    b, _ = lib.wilson_loop(model, plane, 2, ctx=ctx)
+    assert torch.equal(a, b)
+    intra = np.all(np.asarray(model.R) == 0, axis=1)
+    assert intra.any()
+    model.t[intra] *= 0.5
+    c, _ = lib.wilson_loop(model, plane, 2, ctx=ctx)
+    ref, _ = oracle.wilson_loop(model, plane, 2)
+    assert circ_err_rows(c.cpu().numpy(), ref) <= TOL["fp64"]
+    assert not torch.equal(a, c)
