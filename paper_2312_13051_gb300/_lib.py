@@ -207,8 +207,12 @@ def context(device: int | None = None) -> Context:
 
 def _stream_ptr(stream=None):
     import torch
-    s = torch.cuda.current_stream() if stream is None else stream
-    return C.c_void_p(s.cuda_stream)
+    if stream is None:
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if raw is not None:  # the current stream's handle without building a Stream object
+            return C.c_void_p(raw(torch.cuda.current_device()))
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
 
 
 def _ptr(t):
@@ -262,27 +266,47 @@ def _plane(plane) -> bw_plane:
                     (C.c_double * 3)(*map(float, plane.trans_dir)), int(plane.N), int(plane.N_t))
 
 
+_plane_cache: dict = {}
+
+
 def _plane_arg(plane):
     """(ctypes struct, entry-point suffix, leading output shape, the single plane) for a
-    plane or a stack of planes (any object with ``plane, sweep_dir, N_s``)."""
-    if hasattr(plane, "sweep_dir"):
-        sw = [int(round(x)) for x in plane.sweep_dir]
-        if any(abs(float(x) - round(float(x))) > 0 for x in plane.sweep_dir):
-            raise BWError(1, "sweep_dir must be an integer vector")
-        st = bw_plane_stack(_plane(plane.plane), (C.c_int32 * 3)(*sw), int(plane.N_s))
-        return st, "_stack", (int(plane.N_s),), plane.plane
-    return _plane(plane), "", (), plane
+    plane or a stack of planes (any object with ``plane, sweep_dir, N_s``).  The struct of
+    a single plane is reused for equal field values (the library only reads it)."""
+    if not hasattr(plane, "sweep_dir"):
+        key = (tuple(plane.origin), tuple(plane.loop_dir), tuple(plane.trans_dir), plane.N, plane.N_t)
+        st = _plane_cache.get(key)
+        if st is None:
+            st = _plane(plane)
+            if len(_plane_cache) > 256:
+                _plane_cache.clear()
+            _plane_cache[key] = st
+        return st, "", (), plane
+    sw = [int(round(x)) for x in plane.sweep_dir]
+    if any(abs(float(x) - round(float(x))) > 0 for x in plane.sweep_dir):
+        raise BWError(1, "sweep_dir must be an integer vector")
+    st = bw_plane_stack(_plane(plane.plane), (C.c_int32 * 3)(*sw), int(plane.N_s))
+    return st, "_stack", (int(plane.N_s),), plane.plane
 
 
 PSO_SPLIT = {"zero": 0, "median": 1}
 
 
+_default_opts = None
+
+
 def _opts(gap_tol=-1.0, pso_gap_tol=-1.0, wannier_gap_tol=-1.0, unitarise=False, max_sweeps=0,
           pso_split="zero"):
+    global _default_opts
     if pso_split not in PSO_SPLIT:
         raise BWError(1, f"pso_split must be one of {sorted(PSO_SPLIT)}")
-    return bw_opts(float(gap_tol), float(pso_gap_tol), float(wannier_gap_tol), int(unitarise),
-                   int(max_sweeps), PSO_SPLIT[pso_split])
+    args = (float(gap_tol), float(pso_gap_tol), float(wannier_gap_tol), int(unitarise),
+            int(max_sweeps), PSO_SPLIT[pso_split])
+    if args == (-1.0, -1.0, -1.0, 0, 0, 0):  # the defaults: one shared, read-only struct
+        if _default_opts is None:
+            _default_opts = bw_opts(*args)
+        return _default_opts
+    return bw_opts(*args)
 
 
 def _empty(shape, dtype, device):
@@ -340,11 +364,11 @@ def wilson_loop(model, plane, p: int, precision: str = "fp64", ctx: Context | No
     leading plane axis, phases[N_s, N_t, p] and min_gap[N_s, N_t]."""
     import torch
     ctx = ctx or context()
-    dev = _cuda_device(ctx)
     hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
+        dev = _cuda_device(ctx)
         out = (_empty(lead + (plane.N_t, p), torch.float64, dev),
                _empty(lead + (plane.N_t,), torch.float64, dev))
     ph, gap = out
@@ -363,12 +387,12 @@ def nested_wilson_loop(model, plane, p: int, cut: float = -np.pi, first: int = 0
     for a stack of planes each output has a leading plane axis (nested[N_s, N, m])."""
     import torch
     ctx = ctx or context()
-    dev = _cuda_device(ctx)
     m = p // 2 if m is None else int(m)
     hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
     if out is None:
+        dev = _cuda_device(ctx)
         out = (_empty(lead + (plane.N_t, p), torch.float64, dev),
                _empty(lead + (plane.N, m), torch.float64, dev),
                _empty(lead + (plane.N_t,), torch.float64, dev),
@@ -390,7 +414,6 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     plane axis."""
     import torch
     ctx = ctx or context()
-    dev = _cuda_device(ctx)
     hm = _host_model(model)
     pl, sfx, lead, plane = _plane_arg(plane)
     o = _opts(**opts)
@@ -398,6 +421,7 @@ def spin_resolved_wilson_loop(model, plane, p: int, spin_op, sign: int = -1,
     if S.shape != (model.n, model.n):
         raise BWError(1, f"spin operator must be {model.n} x {model.n}")
     if out is None:
+        dev = _cuda_device(ctx)
         out = (_empty(lead + (plane.N_t, p // 2), torch.float64, dev),
                _empty(lead + (plane.N_t, plane.N, p), torch.float64, dev) if want_pso else None,
                _empty(lead + (plane.N_t,), torch.float64, dev),

@@ -1147,15 +1147,30 @@ cudaError_t launch_loops_fused_df(const StatesArgs& sa, const LoopArgs& a, cudaS
     if ((e = inl ? set_smem_once(k_loops_fused_df_inl<true>, F.total, cached_ci)
                  : set_smem_once(k_loops_fused_df<true>, F.total, cached_c)) != cudaSuccess)
       return e;
-    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    // the device's SM count, cooperative support and the kernel's occupancy at this
+    // shared-memory size, queried once per thread, device, variant and size
+    struct Occ {
+      int dev = -1, inl = -1, sms = 0, coop = 0, per_sm = 0;
+      size_t smem = 0;
+    };
+    thread_local Occ occ;
+    int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
-    if ((e = inl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df_inl<true>,
-                                                                  FUSED_THREADS, F.total)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loops_fused_df<true>,
-                                                                  FUSED_THREADS, F.total)) != cudaSuccess)
-      return e;
+    if (occ.dev != dev || occ.inl != int(inl) || occ.smem != F.total) {
+      Occ q;
+      q.dev = dev;
+      q.inl = int(inl);
+      q.smem = F.total;
+      if ((e = cudaDeviceGetAttribute(&q.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&q.coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+      if ((e = inl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q.per_sm, k_loops_fused_df_inl<true>,
+                                                                    FUSED_THREADS, F.total)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q.per_sm, k_loops_fused_df<true>,
+                                                                    FUSED_THREADS, F.total)) != cudaSuccess)
+        return e;
+      occ = q;
+    }
+    const int sms = occ.sms, coop = occ.coop, per_sm = occ.per_sm;
     if (coop && (long long)per_sm * sms >= a.N_t) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(a.N_t);

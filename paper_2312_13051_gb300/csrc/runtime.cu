@@ -237,31 +237,32 @@ bool same_model(const PlanCache& c, const bw_model* m) {
          std::memcmp(c.t.data(), m->t, nz * sizeof(bw_c128)) == 0;
 }
 
-// make_plan + plan_to_blob, through the context's cache.
-bw_status plan_and_blob(bw_ctx* ctx, const bw_model* m, HostPlan& P, Blob& blob) {
+// make_plan + plan_to_blob, through the context's cache; *P and *blob point into the
+// cache and stay valid until the next call on the context.
+bw_status plan_and_blob(bw_ctx* ctx, const bw_model* m, const HostPlan** P, const Blob** blob) {
   PlanCache* c = static_cast<PlanCache*>(ctx->plan_cache);
-  if (m && c && same_model(*c, m)) {
-    P = c->P;
-    blob = c->blob;
-    return BW_OK;
+  if (!(m && c && same_model(*c, m))) {
+    HostPlan fresh;
+    bw_status st = make_plan(ctx, m, fresh);
+    if (st) return st;
+    if (!c) {
+      c = new PlanCache();
+      ctx->plan_cache = c;
+    }
+    c->nnz = -1;  // invalid until the copy below is complete
+    c->blob = Blob();
+    plan_to_blob(fresh, c->blob);
+    c->P = std::move(fresh);
+    const size_t nz = size_t(m->nnz);
+    c->R.assign(m->R, m->R + (nz ? 3 * nz : 0));
+    c->i.assign(m->i, m->i + nz);
+    c->j.assign(m->j, m->j + nz);
+    c->t.assign(m->t, m->t + nz);
+    c->n = m->n;
+    c->nnz = m->nnz;
   }
-  bw_status st = make_plan(ctx, m, P);
-  if (st) return st;
-  blob = Blob();
-  plan_to_blob(P, blob);
-  if (!c) {
-    c = new PlanCache();
-    ctx->plan_cache = c;
-  }
-  const size_t nz = size_t(m->nnz);
-  c->n = m->n;
-  c->nnz = m->nnz;
-  c->R.assign(m->R, m->R + (nz ? 3 * nz : 0));
-  c->i.assign(m->i, m->i + nz);
-  c->j.assign(m->j, m->j + nz);
-  c->t.assign(m->t, m->t + nz);
-  c->P = P;
-  c->blob = blob;
+  *P = &c->P;
+  *blob = &c->blob;
   return BW_OK;
 }
 
@@ -822,9 +823,10 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
   const bw_plane* plane = &PX.flat;
   if (prec != BW_FP64 && prec != BW_MIXED) return fail(ctx, BW_EINVAL, "unknown precision %d", int(prec));
   if (!phases) return fail(ctx, BW_EINVAL, "phases output is NULL");
-  HostPlan P;
-  Blob blob;
-  if ((st = plan_and_blob(ctx, model, P, blob))) return st;
+  const HostPlan* Pc = nullptr;
+  const Blob* Bc = nullptr;
+  if ((st = plan_and_blob(ctx, model, &Pc, &Bc))) return st;
+  const HostPlan& P = *Pc;
   const int n = P.n;
   if (p < 1 || p > n) return fail(ctx, BW_EINVAL, "need 1 <= p <= n (p = %d, n = %d)", p, n);
   if (n > bw::LARGE_N_MAX)
@@ -857,12 +859,16 @@ bw_status run_loop(bw_ctx* ctx, LoopKind kind, const bw_model* model, const bw_p
     return fail(ctx, BW_EINVAL, "pso_split must be 0 (split at zero) or 1 (at the median), got %d",
                 o.pso_median);
   const long long K = (long long)plane->N * plane->N_t;
+  // the plan's blob, with the spin operator appended for the loops that split by it
+  Blob blob_op;
   if (spin) {
-    op.o_row = blob.add(op.row);
-    op.o_col = blob.add(op.col);
-    op.o_val = blob.add(op.val);
-    op.o_rowp = blob.add(op.rowp);
+    blob_op = *Bc;
+    op.o_row = blob_op.add(op.row);
+    op.o_col = blob_op.add(op.col);
+    op.o_val = blob_op.add(op.val);
+    op.o_rowp = blob_op.add(op.rowp);
   }
+  const Blob& blob = spin ? blob_op : *Bc;
   if (big) {
     begin_call(ctx, s);
     if (kind == LoopKind::Spin)
@@ -1232,10 +1238,12 @@ bw_status bw_build_hk(bw_ctx* ctx, const bw_model* model, const double* f, int64
   ctx->err.clear();
   if (K < 0) return fail(ctx, BW_EINVAL, "K < 0");
   if (K > 0 && (!f || !H_out)) return fail(ctx, BW_EINVAL, "f or H_out is NULL");
-  HostPlan P;
-  Blob blob;
-  bw_status st = plan_and_blob(ctx, model, P, blob);
+  const HostPlan* Pc = nullptr;
+  const Blob* Bc = nullptr;
+  bw_status st = plan_and_blob(ctx, model, &Pc, &Bc);
   if (st) return st;
+  const HostPlan& P = *Pc;
+  const Blob& blob = *Bc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   begin_call(ctx, s);
   if ((st = reserve(ctx, al256(blob.data.size()) + 4096, s))) return st;
