@@ -13,7 +13,9 @@
  *  - Matrices are row-major.  An eigenvector block U (n x p) stores U[r*p + c]
  *    (row r = orbital, column c = band), like numpy's V[:, :p].
  *  - The model (hopping list) and the spin operator are HOST arrays, read during
- *    the call and not retained: the library turns them into its own device plan.
+ *    the call: the library turns the list into its own device plan.  A context keeps
+ *    a copy of the last list with its plan and reuses the plan while a later call
+ *    passes an identical list (compared entry by entry, so edits in place are seen).
  *    Every other array argument is a DEVICE pointer owned by the caller.
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
  *    stream).  The return value reports argument errors and launch failures only.
