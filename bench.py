@@ -13,6 +13,11 @@ and the nested loop on the lower Wannier band at every base point.
 
 Prints one JSON line on rank 0.  Under torchrun every rank runs its own copy of the
 workload (independent problems, no data-path collective): weak scaling.
+
+The CPU oracle (``oracle/``, test infrastructure) runs only in the bench's CPU leg,
+never inside a timed GPU region: the ``cpu_baseline`` measurement, the reference arm,
+and the parity of the timed outputs against it (``phase_err_rad`` keys), each after
+the GPU timing of its block.
 """
 from __future__ import annotations
 
